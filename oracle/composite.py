@@ -1,0 +1,181 @@
+"""O2: brute-force dense solve of the composite collocation system.
+
+HPS eliminates a composite spectral collocation system exactly (up to
+rounding): the leaf equations of Section 3.2 together with the interface
+conditions used by the merges (Appendix A.2: the outward normal derivatives
+of neighbouring leaves sum to zero; Appendix B.2: the incoming impedance of
+one leaf is minus the outgoing impedance of its neighbour).  This module
+writes that system out for a whole uniform tree and solves it with one dense
+LU, with no merge recursion and no block formulas, so it is an independent
+check of O1 on small trees.
+
+DtN unknowns: every leaf's interior Chebyshev values and the Gauss values on
+every interior leaf side (face).  Equations per leaf:
+    L_ii u_i + L_ie P g_leaf = f_i,
+and per interior panel (leaves alpha, beta on either side):
+    (Q u^alpha)_panel + (Q u^beta)_panel = 0,  u = [P g_leaf on I_e; u_i on I_i].
+
+ItI unknowns: every leaf's full p^2 values.  Equations per leaf:
+    L(I_i, :) u = f_i,   G u = P g_in,
+with g_in = root data on boundary panels and g_in = -(Q H u^beta)_panel on a
+panel shared with leaf beta.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import geometry as geo
+from . import leaf as lf
+
+
+def _leaf_panels(dim, L):
+    """For each leaf (Morton order) and each side/face slot, either
+    ('root', position in the canonical root boundary) or
+    ('int', panel id, orientation) with a shared interior panel id."""
+    n1 = 2 ** L
+    nl = n1 ** dim
+    corners = []
+    for m in range(nl):
+        idx = [0] * dim
+        for lev in range(L):
+            c = (m >> (dim * (L - 1 - lev))) & ((1 << dim) - 1)
+            for k in range(dim):
+                idx[k] = idx[k] * 2 + ((c >> k) & 1)
+        corners.append(tuple(idx))
+    slots = geo.SIDES_2D if dim == 2 else geo.FACES_3D
+    # canonical root panel positions
+    root_pos = {}
+    if dim == 2:
+        for s, (axis, side) in enumerate(geo.SIDES_2D):
+            for i in range(n1):
+                root_pos[(axis, side, (i,))] = s * n1 + i
+    else:
+        order = geo._face_panel_order(L)
+        for s, (axis, side) in enumerate(geo.FACES_3D):
+            for k, (i1, i2) in enumerate(order):
+                root_pos[(axis, side, (i1, i2))] = s * len(order) + k
+    panel_ids = {}
+    out = []
+    for m, idx in enumerate(corners):
+        row = []
+        for axis, side in slots:
+            tang = tuple(idx[k] for k in range(dim) if k != axis)
+            on_root = (idx[axis] == 0 and side == 0) or (idx[axis] == n1 - 1 and side == 1)
+            if on_root:
+                row.append(("root", root_pos[(axis, side, tang)]))
+            else:
+                plane = idx[axis] + side        # index of the grid plane
+                key = (axis, plane, tang)
+                if key not in panel_ids:
+                    panel_ids[key] = len(panel_ids)
+                row.append(("int", panel_ids[key]))
+        out.append(row)
+    return out, len(panel_ids)
+
+
+def solve_dtn(dim, p, L, lo, hi, a, b, c, f, g):
+    q = p - 2
+    corners, hvec = geo.uniform_leaf_boxes(dim, lo, hi, L)
+    hlen = float(hvec[0])
+    ops = lf.reference_ops(dim, p, q)
+    Ie, Ii = ops["Ie"], ops["Ii"]
+    P, Q = lf.dtn_P_Q(dim, p, q, hlen)
+    npan = q ** (dim - 1)
+    nslot = 2 * dim
+    panels, nint = _leaf_panels(dim, L)
+    nl = len(panels)
+    ni = len(Ii)
+    N = nl * ni + nint * npan
+    dt = np.result_type(f, g, float)
+    A = np.zeros((N, N), dt)
+    rhs = np.zeros(N, dt)
+    off_g = nl * ni
+
+    def gcols(slot_entry):
+        kind, k = slot_entry
+        return kind, k
+
+    for m in range(nl):
+        Lm = lf.assemble_L(dim, p, hlen, a[m], [bk[m] for bk in b], c[m])
+        Lii = Lm[np.ix_(Ii, Ii)]
+        LieP = Lm[np.ix_(Ii, Ie)] @ P
+        r0 = m * ni
+        A[r0:r0 + ni, r0:r0 + ni] = Lii
+        rhs[r0:r0 + ni] = f[m][Ii]
+        for s, ent in enumerate(panels[m]):
+            blk = LieP[:, s * npan:(s + 1) * npan]
+            kind, k = gcols(ent)
+            if kind == "root":
+                rhs[r0:r0 + ni] -= blk @ g[k * npan:(k + 1) * npan]
+            else:
+                A[r0:r0 + ni, off_g + k * npan:off_g + (k + 1) * npan] += blk
+    # flux balance rows, one block per interior panel (sum over its 2 leaves)
+    QP = Q[:, Ie] @ P              # boundary-data part of Q u
+    QI = Q[:, Ii]                  # interior part of Q u
+    for m in range(nl):
+        for s, ent in enumerate(panels[m]):
+            kind, k = ent
+            if kind != "int":
+                continue
+            rows = slice(off_g + k * npan, off_g + (k + 1) * npan)
+            srows = slice(s * npan, (s + 1) * npan)
+            A[rows, m * ni:(m + 1) * ni] += QI[srows, :]
+            for s2, ent2 in enumerate(panels[m]):
+                blk = QP[srows, s2 * npan:(s2 + 1) * npan]
+                if ent2[0] == "root":
+                    rhs[rows] -= blk @ g[ent2[1] * npan:(ent2[1] + 1) * npan]
+                else:
+                    k2 = ent2[1]
+                    A[rows, off_g + k2 * npan:off_g + (k2 + 1) * npan] += blk
+    sol = np.linalg.solve(A, rhs)
+    u = np.zeros((nl, p ** dim), dt)
+    for m in range(nl):
+        gl = np.zeros(nslot * npan, dt)
+        for s, (kind, k) in enumerate(panels[m]):
+            src = g if kind == "root" else sol[off_g:]
+            gl[s * npan:(s + 1) * npan] = src[k * npan:(k + 1) * npan]
+        u[m, Ie] = P @ gl
+        u[m, Ii] = sol[m * ni:(m + 1) * ni]
+    return u
+
+
+def solve_iti(p, L, lo, hi, a, b, c, f, g, eta):
+    dim = 2
+    q = p - 2
+    corners, hvec = geo.uniform_leaf_boxes(dim, lo, hi, L)
+    hlen = float(hvec[0])
+    ops = lf.reference_ops(dim, p, q)
+    Ii = ops["Ii"]
+    P, G, H, Qb = lf.iti_ops(p, q, hlen, eta)
+    QH = Qb @ H
+    panels, _ = _leaf_panels(dim, L)
+    nl = len(panels)
+    npl = p * p
+    nown = G.shape[0]
+    N = nl * npl
+    A = np.zeros((N, N), complex)
+    rhs = np.zeros(N, complex)
+    # neighbour lookup for interior panels
+    owners = {}
+    for m in range(nl):
+        for s, (kind, k) in enumerate(panels[m]):
+            if kind == "int":
+                owners.setdefault(k, []).append((m, s))
+    for m in range(nl):
+        Lm = lf.assemble_L(dim, p, hlen, a[m], [bk[m] for bk in b], c[m])
+        r0 = m * npl
+        cols = slice(m * npl, (m + 1) * npl)
+        A[r0:r0 + nown, cols] = G
+        A[r0 + nown:r0 + npl, cols] = Lm[Ii, :]
+        rhs[r0 + nown:r0 + npl] = f[m][Ii]
+        for s, (kind, k) in enumerate(panels[m]):
+            Ps = P[:, s * q:(s + 1) * q]
+            if kind == "root":
+                rhs[r0:r0 + nown] += Ps @ g[k * q:(k + 1) * q]
+            else:
+                (mb, sb), = [o for o in owners[k] if o[0] != m]
+                # G u^m = P_s g_in,  g_in = -(QH u^mb) on the neighbour's slot sb
+                A[r0:r0 + nown, mb * npl:(mb + 1) * npl] += Ps @ QH[sb * q:(sb + 1) * q, :]
+    sol = np.linalg.solve(A, rhs)
+    return sol.reshape(nl, npl)
