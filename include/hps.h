@@ -1,0 +1,191 @@
+/*
+ * hps.h -- C ABI of the GB300 (sm_103a) HPS fast direct solver.
+ *
+ * Hierarchical Poincare--Steklov solver for L u = a(x) Lap u + b(x).grad u
+ * + c(x) u = f on a square or cube with Dirichlet data (DtN variant) or
+ * incoming impedance data u_n + i eta u (ItI variant), after arXiv 2503.17535:
+ *   leaf stage     Section 3.2, Algorithms "2D DtN local solve" (App. A.1),
+ *                  "2D ItI local solve" (App. B.1), 3D DtN (App. C.1);
+ *   merge stage    Section 3.3, Eqs. "merge linear system", "merge outputs
+ *                  1-2", block formulas of Apps. A.2, B.2 (with the W route of
+ *                  Eq. "ItI D inverse") and C.2;
+ *   downward pass  Section 3.4, Algorithm "down pass".
+ *
+ * Conventions shared by every entry point:
+ *   - Leaves of a uniform tree of depth L: 2^(dL), numbered depth first with
+ *     children in Morton order c = cx + 2 cy (+ 4 cz) (leaf numbers are Morton
+ *     codes, coarsest level in the most significant bits).
+ *   - Per-leaf arrays ("leaf-major"): [n_leaves][p^d], nodes of one leaf in
+ *     tensor order, x fastest: (ix, iy, iz) -> ix + p iy + p^2 iz, where the p
+ *     Chebyshev--Lobatto points of each axis are ascending.
+ *   - Root boundary data g: the root's Gauss--Legendre points (q = p - 2 per
+ *     leaf side) ordered by sides S, E, N, W (2D: y = lo, x = hi, y = hi,
+ *     x = lo; each side by increasing coordinate) or by faces -x, +x, -y, +y,
+ *     -z, +z (3D: each face is the quadtree of its leaf panels in Morton order
+ *     over its two tangential axes, lower axis first; q^2 points per panel in
+ *     tensor order, lower tangential axis fastest).  hps_nodes() returns the
+ *     coordinates in exactly these orders.
+ *   - DtN: g = Dirichlet values u.  ItI: g = u_n + i eta u with the outward
+ *     normal (Section 2).  Real data is double; complex data is interleaved
+ *     (re, im) double pairs (C99 double complex / std::complex<double>).
+ *
+ * Memory: every pointer argument may be device memory (cudaMalloc /
+ * cudaMallocManaged) or host memory.  Host buffers are staged through the
+ * handle's own device buffers on the given stream (the call then returns
+ * after the copy back has completed).  The caller owns every buffer it passes;
+ * the library copies what it keeps.  The handle owns all factor storage.
+ *
+ * Streams: work is enqueued on the stream passed in (NULL = legacy default
+ * stream).  hps_build and hps_solve are asynchronous with respect to the host
+ * for device buffers, except that hps_build synchronises the stream once at
+ * its end to read the pivot status.  A handle must not be used from two host
+ * threads at the same time.
+ *
+ * Errors: every call returns an hps_status; nothing is thrown across the ABI.
+ * On failure *out handles are set to NULL and no memory is leaked.
+ */
+#ifndef HPS_GB300_H
+#define HPS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st; /* cudaStream_t is `struct CUstream_st *` */
+
+typedef enum {
+  HPS_OK = 0,
+  HPS_ERR_INVALID = -1,   /* bad argument: sizes, NULL pointers, q != p-2 ... */
+  HPS_ERR_OOM = -2,       /* planned footprint exceeds free device memory   */
+  HPS_ERR_SINGULAR = -3,  /* an exactly zero pivot in a leaf or merge LU     */
+  HPS_ERR_CUDA = -4,      /* a CUDA runtime call failed                      */
+  HPS_ERR_TIMEOUT = -5    /* a bounded device-side wait gave up              */
+} hps_status;
+
+enum { HPS_DTN = 0, HPS_ITI = 1 };
+enum { HPS_F64 = 0, HPS_C128 = 1 };
+
+/* Tree over the box [lo, hi] (a square or cube: leaves must be cubes).
+ * uniform_depth >= 0 selects the uniform tree of that depth; the adaptive
+ * fields are reserved and must be 0 / NULL. */
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  double lo[3], hi[3];
+  int uniform_depth;       /* L >= 0 */
+  int64_t n_leaves;        /* must equal 2^(dim L) */
+  const uint64_t* morton;  /* reserved, NULL */
+  const int8_t* level;     /* reserved, NULL */
+} hps_tree;
+
+/* Coefficients of L u = a Lap u + sum_k b_k d_k u + c u, each sampled at the
+ * leaf nodes ([n_leaves][p^d] doubles).  NULL selects a = 1, b_k = 0, c = 0.
+ * kind: HPS_DTN (2D or 3D, real data) or HPS_ITI (2D, complex data).
+ * dtype must be HPS_F64 for HPS_DTN and HPS_C128 for HPS_ITI (coefficients
+ * stay real in both; f, g and u follow dtype).  eta > 0 for HPS_ITI. */
+typedef struct {
+  int kind;
+  int dtype;
+  double eta;
+  const double* a;
+  const double* b[3];
+  const double* c;
+} hps_coeffs;
+
+typedef struct {
+  int version;          /* 1 */
+  int want_root_map;    /* 1: also form the root's T and h (not needed to solve) */
+  int profile;          /* 1: time every kernel launch with CUDA events (slower) */
+  int reserved[5];
+} hps_options;
+
+/* Kernel classes reported by hps_kernel_stats. */
+enum {
+  HPS_KCLASS_GEMM = 0,        /* batched / gathered FP64 or complex GEMM            */
+  HPS_KCLASS_LU_PANEL = 1,    /* panel LU with partial pivoting                      */
+  HPS_KCLASS_LASWP_TRSM = 2,  /* row interchanges + U12 triangular update            */
+  HPS_KCLASS_TRSM_DIAG = 3,   /* diagonal-block triangular solves                    */
+  HPS_KCLASS_ASSEMBLE = 4,    /* leaf operator assembly                              */
+  HPS_KCLASS_GATHER = 5,      /* merge gathers, row permutations, scatters           */
+  HPS_KCLASS_DOWN = 6,        /* downward-pass and leaf-output products              */
+  HPS_KCLASS_OTHER = 7,       /* fills and copies                                    */
+  HPS_KCLASS_COUNT = 8
+};
+
+typedef struct {
+  int64_t launches;  /* launches of this class in the last build or solve          */
+  double flops;      /* algorithmic FP64 flops (complex multiply-add = 8)          */
+  double ms;         /* summed CUDA-event time, or -1 when profiling is off         */
+} hps_kernel_stat;
+
+typedef struct hps_handle hps_handle;
+
+/* Coordinates where the caller samples coefficients, f and g:
+ * leaf_xyz: [n_leaves * p^d][dim] doubles (may be NULL),
+ * bdry_xyz: [n_root_bdry][dim] doubles (may be NULL), both host memory.
+ * n_root_bdry = 4 q 2^L (2D) or 6 q^2 4^L (3D).  Pure host computation.
+ * Errors: HPS_ERR_INVALID for an unsupported tree, p < 4 or q != p - 2. */
+hps_status hps_nodes(const hps_tree* tree, int p, int q, double* leaf_xyz, double* bdry_xyz);
+
+/* Sizes that go with a tree: number of leaves, points per leaf and root
+ * boundary points.  Any output pointer may be NULL. */
+hps_status hps_sizes(const hps_tree* tree, int p, int q, int64_t* n_leaves,
+                     int64_t* points_per_leaf, int64_t* n_root_bdry);
+
+/* Build the solution operator (leaf stage + all merges).  f ([n_leaves][p^d],
+ * real or complex per dtype) may be NULL (f = 0); it is the source used by
+ * hps_solve(..., f = NULL, ...).  opts may be NULL (defaults).  On success
+ * *out receives a new handle.  Errors: HPS_ERR_INVALID, HPS_ERR_OOM (before
+ * any large allocation), HPS_ERR_SINGULAR (zero pivot; hps_last_error_detail
+ * names the node), HPS_ERR_TIMEOUT, HPS_ERR_CUDA. */
+hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeffs,
+                     const void* f, const hps_options* opts, struct CUstream_st* stream,
+                     hps_handle** out);
+
+/* Apply the solution operator: u = solution on all leaf nodes
+ * ([n_leaves][p^d], dtype of the handle) for root boundary data g
+ * ([n_root_bdry]).  f == NULL reuses the build-time source; otherwise the
+ * upward particular pass (leaf and merge triangular solves with the stored
+ * factors) runs for the new f first.  u must not alias g or f. */
+hps_status hps_solve(hps_handle* h, const void* g, const void* f, void* u,
+                     struct CUstream_st* stream);
+
+/* nrhs independent right-hand sides at once: g is [nrhs][n_root_bdry],
+ * f is NULL or [nrhs][n_leaves][p^d], u is [nrhs][n_leaves][p^d]. */
+hps_status hps_solve_batched(hps_handle* h, int nrhs, const void* g, const void* f, void* u,
+                             struct CUstream_st* stream);
+
+/* Release a handle (NULL is accepted).  Synchronises the handle's last stream. */
+void hps_free(hps_handle* h);
+
+/* Static, NUL-terminated description of a status code. */
+const char* hps_error_string(hps_status s);
+
+/* Detail of the last error: for HPS_ERR_SINGULAR the leaf or merge-node id
+ * (leaves: 0..n_leaves-1; then the merge nodes level by level from the
+ * leaves up, in Morton order), else -1.  hps_build returns no handle on
+ * failure, so pass h = NULL to read the detail of the calling thread's last
+ * failed hps_build. */
+hps_status hps_last_error_detail(hps_handle* h, int64_t* node);
+
+/* Device bytes held by the handle (factors, operators, workspace). */
+int64_t hps_device_bytes(const hps_handle* h);
+
+/* Number of CUDA kernel launches issued by the last hps_build / hps_solve on h. */
+int64_t hps_last_launch_count(const hps_handle* h);
+
+/* Per-class launch count, algorithmic flops and (with profiling on) summed
+ * kernel time of the last hps_build / hps_solve on h.  Synchronises the
+ * handle's last stream when profiling is on.  HPS_ERR_INVALID for a bad class. */
+hps_status hps_kernel_stats(hps_handle* h, int kclass, hps_kernel_stat* out);
+
+/* Switch per-launch event timing on (1) or off (0) for later calls on h. */
+hps_status hps_set_profiling(hps_handle* h, int on);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPS_GB300_H */

@@ -1,0 +1,220 @@
+"""Python binding of the GB300 HPS solver C ABI (include/hps.h).
+
+The functions carry the C names and only marshal arguments: sizes and dtypes
+are checked, tensors / arrays are turned into pointers and the current CUDA
+stream is passed along.  Every step of the solver runs in libhps_gb300.so; if
+the library is missing the first call raises ImportError (there is no
+fallback).
+
+Arrays may be torch tensors (CUDA or CPU) or NumPy arrays.  Host arrays are
+staged to the device by the library itself.
+"""
+
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_int64, c_void_p
+
+import numpy as np
+
+from . import _capi
+from ._capi import (HPS_C128, HPS_DTN, HPS_F64, HPS_ITI, HPS_OK, hps_coeffs,  # noqa: F401
+                    hps_options, hps_tree)
+
+__all__ = ["hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
+           "hps_error_string", "hps_last_error_detail", "hps_device_bytes",
+           "hps_last_launch_count", "hps_kernel_stats", "hps_set_profiling", "uniform_tree",
+           "make_coeffs", "HPSError", "Handle"]
+
+
+class HPSError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _capi.lib().hps_error_string(status).decode()
+        super().__init__(f"{where}: {msg}")
+
+
+def _check(status: int, where: str):
+    if status != HPS_OK:
+        raise HPSError(status, where)
+
+
+def uniform_tree(dim: int, depth: int, lo=None, hi=None) -> hps_tree:
+    lo = lo if lo is not None else (-1.0,) * dim
+    hi = hi if hi is not None else (1.0,) * dim
+    t = hps_tree()
+    t.dim = dim
+    for a in range(3):
+        t.lo[a] = float(lo[a]) if a < dim else 0.0
+        t.hi[a] = float(hi[a]) if a < dim else 0.0
+    t.uniform_depth = depth
+    t.n_leaves = 2 ** (dim * depth)
+    t.morton = None
+    t.level = None
+    return t
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, complex_: bool, n: int, name: str, keep: list):
+    """Pointer of a contiguous float64 / complex128 buffer with n elements."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        import torch
+        want = torch.complex128 if complex_ else torch.float64
+        if x.dtype != want:
+            raise TypeError(f"{name}: dtype {x.dtype}, expected {want}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name}: tensor must be contiguous")
+        if x.numel() != n:
+            raise ValueError(f"{name}: {x.numel()} elements, expected {n}")
+        keep.append(x)
+        return x.data_ptr()
+    a = np.asarray(x)
+    want = np.complex128 if complex_ else np.float64
+    if a.dtype != want:
+        raise TypeError(f"{name}: dtype {a.dtype}, expected {np.dtype(want)}")
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name}: array must be C-contiguous")
+    if a.size != n:
+        raise ValueError(f"{name}: {a.size} elements, expected {n}")
+    keep.append(a)
+    return a.ctypes.data
+
+
+def _stream(stream):
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def hps_sizes(tree: hps_tree, p: int, q: int):
+    nl, ppl, nr = c_int64(), c_int64(), c_int64()
+    _check(_capi.lib().hps_sizes(byref(tree), p, q, byref(nl), byref(ppl), byref(nr)), "hps_sizes")
+    return nl.value, ppl.value, nr.value
+
+
+def hps_nodes(tree: hps_tree, p: int, q: int):
+    """(leaf_xyz, bdry_xyz) as NumPy arrays of shape (n, dim)."""
+    nl, ppl, nr = hps_sizes(tree, p, q)
+    leaf = np.zeros((nl * ppl, tree.dim))
+    bdry = np.zeros((nr, tree.dim))
+    _check(_capi.lib().hps_nodes(byref(tree), p, q, leaf.ctypes.data, bdry.ctypes.data), "hps_nodes")
+    return leaf, bdry
+
+
+class Handle:
+    """Owns an hps_handle*; released by hps_free (or garbage collection)."""
+
+    def __init__(self, ptr, tree, p, q, complex_):
+        self.ptr = ptr
+        self.dim = tree.dim
+        self.p, self.q = p, q
+        self.complex = complex_
+        self.n_leaves, self.ppl, self.n_root = hps_sizes(tree, p, q)
+
+    def __del__(self):
+        try:
+            hps_free(self)
+        except Exception:
+            pass
+
+
+def make_coeffs(kind: int, a=None, b=None, c=None, eta: float = 0.0, keep=None, n=None):
+    cf = hps_coeffs()
+    cf.kind = kind
+    cf.dtype = HPS_C128 if kind == HPS_ITI else HPS_F64
+    cf.eta = float(eta)
+    keep = keep if keep is not None else []
+    cf.a = _ptr(a, False, n, "a", keep) if a is not None else None
+    for k in range(3):
+        bk = b[k] if (b is not None and k < len(b)) else None
+        cf.b[k] = _ptr(bk, False, n, f"b[{k}]", keep) if bk is not None else None
+    cf.c = _ptr(c, False, n, "c", keep) if c is not None else None
+    return cf, keep
+
+
+def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None, f=None,
+              eta: float = 0.0, want_root_map: bool = False, profile: bool = False,
+              stream=None) -> Handle:
+    """Build the solution operator; coefficient and source arrays hold
+    n_leaves * p^dim values (leaf-major, tensor node order)."""
+    nl, ppl, _ = hps_sizes(tree, p, q)
+    n = nl * ppl
+    keep: list = []
+    cf, keep = make_coeffs(kind, a, b, c, eta, keep, n)
+    fp = _ptr(f, kind == HPS_ITI, n, "f", keep)
+    opts = hps_options()
+    opts.version = 1
+    opts.want_root_map = 1 if want_root_map else 0
+    opts.profile = 1 if profile else 0
+    out = c_void_p()
+    st = _stream(stream)
+    _check(_capi.lib().hps_build(byref(tree), p, q, byref(cf), fp, byref(opts), st, byref(out)),
+           "hps_build")
+    return Handle(out.value, tree, p, q, kind == HPS_ITI)
+
+
+def hps_solve_batched(h: Handle, nrhs: int, g, u, f=None, stream=None):
+    keep: list = []
+    gp = _ptr(g, h.complex, nrhs * h.n_root, "g", keep)
+    up = _ptr(u, h.complex, nrhs * h.n_leaves * h.ppl, "u", keep)
+    fp = _ptr(f, h.complex, nrhs * h.n_leaves * h.ppl, "f", keep)
+    _check(_capi.lib().hps_solve_batched(h.ptr, nrhs, gp, fp, up, _stream(stream)), "hps_solve")
+    return u
+
+
+def hps_solve(h: Handle, g, u, f=None, stream=None):
+    """u <- solution for root boundary data g (and source f, or the build-time
+    source when f is None)."""
+    return hps_solve_batched(h, 1, g, u, f=f, stream=stream)
+
+
+def hps_free(h: Handle):
+    if h is not None and h.ptr:
+        _capi.lib().hps_free(h.ptr)
+        h.ptr = None
+
+
+def hps_error_string(status: int) -> str:
+    return _capi.lib().hps_error_string(status).decode()
+
+
+def hps_last_error_detail(h: Handle | None = None) -> int:
+    node = c_int64()
+    _check(_capi.lib().hps_last_error_detail(h.ptr if h else None, byref(node)), "hps_last_error_detail")
+    return node.value
+
+
+def hps_device_bytes(h: Handle) -> int:
+    return int(_capi.lib().hps_device_bytes(h.ptr))
+
+
+def hps_last_launch_count(h: Handle) -> int:
+    return int(_capi.lib().hps_last_launch_count(h.ptr))
+
+
+def hps_kernel_stats(h: Handle) -> dict:
+    """{class name: {"launches", "flops", "ms"}} for the last build / solve."""
+    out = {}
+    for k, name in enumerate(_capi.KCLASSES):
+        st = _capi.hps_kernel_stat()
+        _check(_capi.lib().hps_kernel_stats(h.ptr, k, byref(st)), "hps_kernel_stats")
+        out[name] = {"launches": st.launches, "flops": st.flops, "ms": st.ms}
+    return out
+
+
+def hps_set_profiling(h: Handle, on: bool):
+    _check(_capi.lib().hps_set_profiling(h.ptr, 1 if on else 0), "hps_set_profiling")
+
+
+del ctypes

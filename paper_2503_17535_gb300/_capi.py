@@ -1,0 +1,89 @@
+"""ctypes declarations of the C ABI in include/hps.h.
+
+Argument marshalling only: every step of the solver runs in libhps_gb300.so.
+Importing this module fails loudly when the library has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int64, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhps_gb300.so")
+
+HPS_OK, HPS_ERR_INVALID, HPS_ERR_OOM, HPS_ERR_SINGULAR, HPS_ERR_CUDA, HPS_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+HPS_DTN, HPS_ITI = 0, 1
+HPS_F64, HPS_C128 = 0, 1
+
+EXPORTED = [
+    "hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
+    "hps_error_string", "hps_last_error_detail", "hps_device_bytes", "hps_last_launch_count",
+    "hps_kernel_stats", "hps_set_profiling",
+]
+
+KCLASSES = ["gemm", "lu_panel", "laswp_trsm", "trsm_diag", "assemble", "gather", "down", "other"]
+
+
+class hps_tree(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("lo", c_double * 3), ("hi", c_double * 3),
+                ("uniform_depth", c_int), ("n_leaves", c_int64),
+                ("morton", c_void_p), ("level", c_void_p)]
+
+
+class hps_coeffs(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("dtype", c_int), ("eta", c_double), ("a", c_void_p),
+                ("b", c_void_p * 3), ("c", c_void_p)]
+
+
+class hps_options(ctypes.Structure):
+    _fields_ = [("version", c_int), ("want_root_map", c_int), ("profile", c_int),
+                ("reserved", c_int * 5)]
+
+
+class hps_kernel_stat(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("flops", c_double), ("ms", c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build the CUDA extension first "
+            "(python -m paper_2503_17535_gb300.build or __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    L.hps_nodes.argtypes = [POINTER(hps_tree), c_int, c_int, c_void_p, c_void_p]
+    L.hps_nodes.restype = c_int
+    L.hps_sizes.argtypes = [POINTER(hps_tree), c_int, c_int, POINTER(c_int64), POINTER(c_int64),
+                            POINTER(c_int64)]
+    L.hps_sizes.restype = c_int
+    L.hps_build.argtypes = [POINTER(hps_tree), c_int, c_int, POINTER(hps_coeffs), c_void_p,
+                            POINTER(hps_options), c_void_p, POINTER(c_void_p)]
+    L.hps_build.restype = c_int
+    L.hps_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.hps_solve.restype = c_int
+    L.hps_solve_batched.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.hps_solve_batched.restype = c_int
+    L.hps_free.argtypes = [c_void_p]
+    L.hps_free.restype = None
+    L.hps_error_string.argtypes = [c_int]
+    L.hps_error_string.restype = c_char_p
+    L.hps_last_error_detail.argtypes = [c_void_p, POINTER(c_int64)]
+    L.hps_last_error_detail.restype = c_int
+    L.hps_device_bytes.argtypes = [c_void_p]
+    L.hps_device_bytes.restype = c_int64
+    L.hps_last_launch_count.argtypes = [c_void_p]
+    L.hps_last_launch_count.restype = c_int64
+    L.hps_kernel_stats.argtypes = [c_void_p, c_int, POINTER(hps_kernel_stat)]
+    L.hps_kernel_stats.restype = c_int
+    L.hps_set_profiling.argtypes = [c_void_p, c_int]
+    L.hps_set_profiling.restype = c_int
+    _lib = L
+    return L

@@ -1,0 +1,103 @@
+// Shared device-side helpers: a complex<double> value type, scalar traits and
+// a bounded inter-CTA barrier for cooperative launches.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hps {
+
+struct cplx {
+  double re, im;
+  __host__ __device__ cplx() : re(0.0), im(0.0) {}
+  __host__ __device__ cplx(double r) : re(r), im(0.0) {}
+  __host__ __device__ cplx(double r, double i) : re(r), im(i) {}
+};
+
+__host__ __device__ inline cplx operator+(cplx a, cplx b) { return cplx(a.re + b.re, a.im + b.im); }
+__host__ __device__ inline cplx operator-(cplx a, cplx b) { return cplx(a.re - b.re, a.im - b.im); }
+__host__ __device__ inline cplx operator-(cplx a) { return cplx(-a.re, -a.im); }
+__host__ __device__ inline cplx operator*(cplx a, cplx b) {
+  return cplx(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
+
+// Scalar traits: fused multiply-add acc + a*b, magnitude used for pivoting
+// (|re| + |im| for complex, no square root), reciprocal and zero test.
+__host__ __device__ inline double fmac(double acc, double a, double b) { return fma(a, b, acc); }
+__host__ __device__ inline cplx fmac(cplx acc, cplx a, cplx b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc - a*b
+__host__ __device__ inline double fmsc(double acc, double a, double b) { return fma(-a, b, acc); }
+__host__ __device__ inline cplx fmsc(cplx acc, cplx a, cplx b) {
+  acc.re = fma(-a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(-a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+__host__ __device__ inline double mag1(double a) { return fabs(a); }
+__host__ __device__ inline double mag1(cplx a) { return fabs(a.re) + fabs(a.im); }
+__host__ __device__ inline double recip(double a) { return 1.0 / a; }
+__host__ __device__ inline cplx recip(cplx a) {
+  // 1/(x+iy) = (x - iy)/(x^2+y^2), with scaling by the larger component
+  double s = fmax(fabs(a.re), fabs(a.im));
+  double xr = a.re / s, xi = a.im / s;
+  double d = s * (xr * xr + xi * xi);
+  return cplx(xr / d, -xi / d);
+}
+__host__ __device__ inline bool is_zero(double a) { return a == 0.0; }
+__host__ __device__ inline bool is_zero(cplx a) { return a.re == 0.0 && a.im == 0.0; }
+__host__ __device__ inline double scale(double a, double s) { return a * s; }
+__host__ __device__ inline cplx scale(cplx a, double s) { return cplx(a.re * s, a.im * s); }
+
+template <typename T> struct zero_of { __host__ __device__ static T get() { return T(0.0); } };
+
+// Error flag bits written by kernels into a device status word.
+enum : unsigned {
+  DEV_ERR_SINGULAR = 1u,
+  DEV_ERR_TIMEOUT = 2u,
+};
+
+// Bounded barrier for the G co-resident CTAs of one group (cooperative
+// launch).  bar[0] = arrival count, bar[1] = generation.  Gives up after
+// `limit` polls, sets DEV_ERR_TIMEOUT in *err and returns false; callers then
+// leave the kernel.  Every CTA of the group must call it the same number of
+// times.
+__device__ inline bool group_barrier(unsigned* bar, unsigned G, unsigned* err,
+                                     unsigned long long limit = 20000000ull) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = bar + 1;
+    unsigned gen = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == G - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned long long it = 0;
+      while (*vgen == gen) {
+        if (++it > limit) {
+          atomicOr(err, DEV_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        if (*((volatile unsigned*)err) & DEV_ERR_TIMEOUT) { ok = 0; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+}  // namespace hps

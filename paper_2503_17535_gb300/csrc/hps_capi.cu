@@ -1,0 +1,755 @@
+// C ABI of the HPS solver: planning, storage, build (leaf stage + merges)
+// and solve (upward particular pass, downward pass, leaf output).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hps.h"
+#include "hps_kernels.cuh"
+#include "linalg.h"
+#include "plan.h"
+
+using namespace hps;
+
+namespace {
+
+struct LevelDev {
+  int nmerge = 0, nch = 0, n = 0, nbc = 0, n_ext = 0, n_int = 0;
+  int *ext = nullptr, *var = nullptr, *eq = nullptr;
+  int *barow = nullptr, *bacol = nullptr, *bbrow = nullptr, *bcrow = nullptr;
+  void* TP = nullptr;   // [nmerge][n_ext x (n_ext+1)]  parent [T | h]
+  void* D = nullptr;    // [nmerge][n_int x n_int]
+  void* W = nullptr;    // ItI: [nmerge][(n_int/2)^2] (LU of W)
+  int* ipiv = nullptr;  // [nmerge][nlu]
+  int* perm = nullptr;
+  int* info = nullptr;  // [nmerge]
+  void* X = nullptr;    // [nmerge][n_int x (n_ext+1)]  D^{-1} [C | h_int]
+  int G = 1;
+  LuWork luw;
+  // solve workspace (nrhs columns)
+  void *r = nullptr, *hp = nullptr, *x = nullptr, *gint = nullptr, *gchild = nullptr;
+  bool top() const { return nmerge == 1; }
+};
+
+}  // namespace
+
+struct hps_handle {
+  int dim = 0, kind = 0, p = 0, q = 0, L = 0;
+  bool iti = false;
+  int64_t nl = 0, npts = 0, nroot = 0;
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, eta = 0.0, hlen = 0.0, s = 0.0;
+  hps_options opts{};
+  Spectral1D spec;
+  DtnLeafRef dref;
+  ItiLeafRef iref;
+  LeafConsts lc{};
+  int nlu_leaf = 0, xrows_leaf = 0, nb = 0;
+  // device constants
+  double *dD = nullptr, *dDD = nullptr, *dP = nullptr, *dQi = nullptr, *dQP = nullptr, *dsgn = nullptr;
+  int *dIi = nullptr, *dprow = nullptr, *diidx = nullptr, *downn = nullptr, *downa = nullptr;
+  cplx* dQH = nullptr;
+  // leaf storage
+  void* leafA = nullptr;  // LU of L_ii (DtN) or B (ItI)
+  int *leaf_ipiv = nullptr, *leaf_perm = nullptr, *leaf_info = nullptr;
+  void* leafX = nullptr;  // DtN: X = L_ii^{-1}[L_ie P | -f_i]; ItI: [Y | v]
+  void* leafTH = nullptr; // [T | h]
+  LuWork leaf_luw;
+  int leaf_G = 1;
+  std::vector<LevelDev> lev;
+  unsigned* dev_err = nullptr;
+  void* scratch = nullptr;  // build-time R / RHS buffer
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  Prof prof;
+  int64_t err_node = -1;
+  int num_sms = 0;
+  cudaStream_t last = nullptr;
+  // solve workspace
+  int ws_nrhs = 0;
+  int64_t ws_bytes = 0;
+  std::vector<void*> ws_allocs;
+  void *ws_xf = nullptr, *ws_hleaf = nullptr, *ws_gleaf = nullptr, *ws_g = nullptr, *ws_f = nullptr,
+       *ws_u = nullptr, *ws_rhs = nullptr;
+};
+
+namespace {
+
+#define HPS_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      return HPS_ERR_CUDA;                              \
+    }                                                   \
+  } while (0)
+
+void* dalloc(hps_handle* h, size_t bytes, std::vector<void*>* list = nullptr) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  (list ? *list : h->allocs).push_back(p);
+  h->bytes += (int64_t)bytes;
+  return p;
+}
+
+template <typename V>
+V* upload(hps_handle* h, const std::vector<V>& v, cudaStream_t st) {
+  V* d = (V*)dalloc(h, v.size() * sizeof(V));
+  if (!d) return nullptr;
+  if (cudaMemcpyAsync(d, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return nullptr;
+  return d;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+hps_status check_tree(const hps_tree* t, int p, int q) {
+  if (!t) return HPS_ERR_INVALID;
+  if (t->dim != 2 && t->dim != 3) return HPS_ERR_INVALID;
+  if (t->uniform_depth < 0 || t->morton || t->level) return HPS_ERR_INVALID;
+  if (t->uniform_depth > (t->dim == 2 ? 12 : 7)) return HPS_ERR_INVALID;
+  if (p < 4 || p > 24 || q != p - 2) return HPS_ERR_INVALID;
+  const int64_t nl = (int64_t)1 << (t->dim * t->uniform_depth);
+  if (t->n_leaves != nl) return HPS_ERR_INVALID;
+  double side = t->hi[0] - t->lo[0];
+  if (!(side > 0)) return HPS_ERR_INVALID;
+  for (int a = 1; a < t->dim; ++a)
+    if (!(std::fabs((t->hi[a] - t->lo[a]) - side) <= 1e-12 * side)) return HPS_ERR_INVALID;
+  return HPS_OK;
+}
+
+int64_t nroot_of(int dim, int q, int L) {
+  return dim == 2 ? 4LL * q * ((int64_t)1 << L) : 6LL * q * q * ((int64_t)1 << (2 * L));
+}
+
+template <typename T> struct Kind;
+template <> struct Kind<double> { static constexpr bool iti = false; };
+template <> struct Kind<cplx> { static constexpr bool iti = true; };
+
+// ------------------------------------------------------------- planning ----
+
+template <typename T>
+size_t plan_bytes(const hps_handle* h, bool with_solve_ws) {
+  size_t b = 0;
+  const size_t es = sizeof(T);
+  const int64_t nl = h->nl;
+  b += (size_t)nl * h->nlu_leaf * h->nlu_leaf * es;          // leaf LU
+  b += (size_t)nl * h->xrows_leaf * (h->nb + 1) * es;        // leaf X
+  b += (size_t)nl * h->nb * (h->nb + 1) * es;                // leaf T|h
+  b += (size_t)nl * h->nlu_leaf * 3 * sizeof(int);
+  size_t scratch = (size_t)nl * h->xrows_leaf * (h->nb + 1) * es;
+  int n = h->dim == 2 ? h->q : h->q * h->q;
+  int64_t nm = nl;
+  for (int m = 0; m < h->L; ++m) {
+    nm /= (h->dim == 2 ? 4 : 8);
+    const int nf = 2 * h->dim;
+    const int n_ext = nf * n * (h->dim == 2 ? 2 : 4);
+    const int nif = h->dim == 2 ? 4 : 12;
+    const int n_int = (h->iti ? 2 : 1) * nif * n;
+    b += (size_t)nm * n_ext * (n_ext + 1) * es;   // TP
+    b += (size_t)nm * n_int * n_int * es;         // D
+    if (h->iti) b += (size_t)nm * (n_int / 2) * (n_int / 2) * es;
+    b += (size_t)nm * n_int * (n_ext + 1) * es;   // X
+    scratch = std::max(scratch, (size_t)nm * n_int * (n_ext + 1) * es);
+    if (with_solve_ws) b += (size_t)nm * (3 * n_int + 2 * n_ext) * es * 2;
+    n *= (h->dim == 2 ? 2 : 4);
+  }
+  b += scratch;
+  return b;
+}
+
+// --------------------------------------------------------------- build -----
+
+template <typename T>
+hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cudaStream_t st) {
+  constexpr bool ITI = Kind<T>::iti;
+  const int dim = h->dim, p = h->p, q = h->q;
+  Prof* pf = &h->prof;
+  pf->reset();
+  pf->on = h->opts.profile != 0;
+  h->spec = make_spectral(p, q);
+  h->s = 2.0 / h->hlen;
+  if (!ITI) {
+    h->dref = make_dtn_leaf(h->spec, dim);
+    h->nb = h->dref.nb;
+    h->nlu_leaf = h->dref.ni;
+    h->xrows_leaf = h->dref.ni;
+  } else {
+    h->iref = make_iti_leaf(h->spec);
+    h->nb = h->iref.nb;
+    h->nlu_leaf = h->iref.npts;
+    h->xrows_leaf = h->iref.npts;
+  }
+  // footprint check before any large allocation
+  {
+    size_t need = plan_bytes<T>(h, false) + ((size_t)64 << 20);
+    size_t fr = 0, tot = 0;
+    HPS_CUDA(cudaMemGetInfo(&fr, &tot));
+    if (need > fr) return HPS_ERR_OOM;
+  }
+  // ---- constants
+  h->dD = upload(h, h->spec.D, st);
+  h->dDD = upload(h, h->spec.DD, st);
+  std::vector<int> iidx(h->npts, -1);
+  LeafConsts& k = h->lc;
+  k.dim = dim; k.p = p; k.npts = (int)h->npts; k.nb = h->nb; k.s = h->s; k.eta = h->eta;
+  k.D = h->dD; k.DD = h->dDD;
+  if (!ITI) {
+    const DtnLeafRef& r = h->dref;
+    for (int i = 0; i < r.ni; ++i) iidx[r.Ii[i]] = i;
+    h->dIi = upload(h, r.Ii, st);
+    h->dprow = upload(h, r.prow, st);
+    h->dP = upload(h, r.P, st);
+    h->dQi = upload(h, r.Qi, st);
+    h->dQP = upload(h, r.QP, st);
+    k.ni = r.ni; k.ne = r.ne; k.nown = 0;
+    k.Ii = h->dIi; k.prow = h->dprow; k.P = h->dP;
+  } else {
+    const ItiLeafRef& r = h->iref;
+    for (size_t i = 0; i < r.Ii.size(); ++i) iidx[r.Ii[i]] = (int)i;
+    h->dIi = upload(h, r.Ii, st);
+    h->dP = upload(h, r.P, st);
+    h->downn = upload(h, r.own_node, st);
+    h->downa = upload(h, r.own_axis, st);
+    h->dsgn = upload(h, r.own_sgn, st);
+    std::vector<std::complex<double>> QH = make_iti_QH(h->spec, h->hlen, h->eta);
+    std::vector<cplx> QHc(QH.size());
+    for (size_t i = 0; i < QH.size(); ++i) QHc[i] = cplx(QH[i].real(), QH[i].imag());
+    h->dQH = upload(h, QHc, st);
+    std::vector<int> prow(h->npts, -1);
+    h->dprow = upload(h, prow, st);
+    k.ni = (int)r.Ii.size(); k.ne = 0; k.nown = r.nown;
+    k.Ii = h->dIi; k.prow = h->dprow; k.P = h->dP;
+    k.own_node = h->downn; k.own_axis = h->downa; k.own_sgn = h->dsgn;
+  }
+  h->diidx = upload(h, iidx, st);
+  k.iidx = h->diidx;
+  if (!h->dD || !h->dDD || !h->dIi || !h->dP || !h->diidx || !h->dprow) return HPS_ERR_OOM;
+  h->dev_err = (unsigned*)dalloc(h, sizeof(unsigned) * 4);
+  if (!h->dev_err) return HPS_ERR_OOM;
+  HPS_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(unsigned) * 4, st));
+
+  // ---- input staging (coefficients and f may live in host memory)
+  std::vector<void*> tmp;
+  auto stage = [&](const void* src, size_t bytes) -> const void* {
+    if (!src || is_device_ptr(src)) return src;
+    void* d = dalloc(h, bytes, &tmp);
+    if (!d) return nullptr;
+    if (cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return nullptr;
+    return d;
+  };
+  const size_t cbytes = (size_t)h->nl * h->npts * sizeof(double);
+  Coeffs co{};
+  co.a = (const double*)stage(cf->a, cbytes);
+  for (int a = 0; a < 3; ++a) co.b[a] = (a < dim) ? (const double*)stage(cf->b[a], cbytes) : nullptr;
+  co.c = (const double*)stage(cf->c, cbytes);
+  const T* f = (const T*)stage(f_in, (size_t)h->nl * h->npts * sizeof(T));
+  if ((cf->a && !co.a) || (cf->c && !co.c) || (f_in && !f)) return HPS_ERR_OOM;
+
+  // ---- leaf stage (Algorithm "local solve")
+  const int64_t nl = h->nl;
+  const int nlu = h->nlu_leaf, nb = h->nb, xr = h->xrows_leaf;
+  h->leafA = dalloc(h, (size_t)nl * nlu * nlu * sizeof(T));
+  h->leafX = dalloc(h, (size_t)nl * xr * (nb + 1) * sizeof(T));
+  h->leafTH = dalloc(h, (size_t)nl * nb * (nb + 1) * sizeof(T));
+  h->leaf_ipiv = (int*)dalloc(h, (size_t)nl * nlu * sizeof(int));
+  h->leaf_perm = (int*)dalloc(h, (size_t)nl * nlu * sizeof(int));
+  h->leaf_info = (int*)dalloc(h, (size_t)nl * sizeof(int));
+  // scratch: largest R / RHS buffer of any stage
+  size_t scratch = (size_t)nl * xr * (nb + 1);
+  {
+    int n = dim == 2 ? q : q * q;
+    int64_t nm = nl;
+    for (int m = 0; m < h->L; ++m) {
+      nm /= (dim == 2 ? 4 : 8);
+      MergeMaps mm = make_merge_maps(dim, n, ITI);
+      scratch = std::max(scratch, (size_t)nm * mm.n_int * (mm.n_ext + 1));
+      n *= (dim == 2 ? 2 : 4);
+    }
+  }
+  h->scratch = dalloc(h, scratch * sizeof(T));
+  if (!h->leafA || !h->leafX || !h->leafTH || !h->leaf_ipiv || !h->leaf_perm || !h->leaf_info || !h->scratch)
+    return HPS_ERR_OOM;
+  HPS_CUDA(cudaMemsetAsync(h->leaf_info, 0, (size_t)nl * sizeof(int), st));
+  T* RHS = (T*)h->scratch;
+  if (!ITI) {
+    HPS_CUDA(leaf_dtn_assemble(k, nl, co, (const double*)f, (double*)h->leafA, (double*)RHS, st, pf));
+  } else {
+    HPS_CUDA(leaf_iti_assemble(k, nl, co, (const cplx*)f, (cplx*)h->leafA, (cplx*)RHS, st, pf));
+  }
+  h->leaf_G = lu_group_size<T>(nlu, (int)std::min<int64_t>(nl, 1 << 30), h->num_sms);
+  if (h->leaf_G > 1) {
+    h->leaf_luw.bars = (unsigned*)dalloc(h, sizeof(unsigned) * 2 * nl);
+    h->leaf_luw.pub_bytes = lu_pub_bytes<T>(nlu, (int)nl, h->leaf_G);
+    h->leaf_luw.pub = dalloc(h, h->leaf_luw.pub_bytes);
+    if (!h->leaf_luw.bars || !h->leaf_luw.pub) return HPS_ERR_OOM;
+    HPS_CUDA(cudaMemsetAsync(h->leaf_luw.bars, 0, sizeof(unsigned) * 2 * nl, st));
+  }
+  BOp<T> LA = bop<T>((T*)h->leafA, (int64_t)nlu * nlu, nlu);
+  HPS_CUDA(getrf<T>(LA, nlu, (int)nl, h->leaf_ipiv, h->leaf_perm, h->leaf_info, h->dev_err, h->leaf_G,
+                    h->leaf_luw, st, pf));
+  BOp<T> LX = bop<T>((T*)h->leafX, (int64_t)xr * (nb + 1), xr);
+  HPS_CUDA(permute_rows<T>(bop<T>(RHS, (int64_t)xr * (nb + 1), xr), LX, h->leaf_perm, nlu, nb + 1, (int)nl, st, pf));
+  HPS_CUDA(getrs_inplace<T>(LA, nlu, LX, nb + 1, (int)nl, st, pf));
+  {
+    GemmArgs<T> g;
+    g.M = nb; g.N = nb + 1; g.batch = (int)nl;
+    g.B = LX;
+    g.C = bop<T>((T*)h->leafTH, (int64_t)nb * (nb + 1), nb);
+    if (!ITI) {
+      HPS_CUDA(leaf_dtn_init_T(h->dQP, nb, h->s, nl, (double*)h->leafTH, st, pf));
+      g.K = xr;
+      g.A = bop<T>((T*)h->dQi, 0, nb);
+      g.alpha = T(-h->s);
+      g.beta = T(1.0);
+    } else {
+      g.K = (int)h->npts;
+      g.A = bop<T>((T*)h->dQH, 0, nb);
+      g.alpha = T(1.0);
+      g.beta = T(0.0);
+    }
+    HPS_CUDA(gemm<T>(g, st, pf));
+  }
+
+  // ---- merge stage (Algorithm "merge"), level by level
+  int n = dim == 2 ? q : q * q;
+  int64_t nm = nl;
+  const T* Tc = (const T*)h->leafTH;
+  int64_t cstride = (int64_t)nb * (nb + 1);
+  h->lev.resize(h->L);
+  for (int m = 0; m < h->L; ++m) {
+    LevelDev& Lv = h->lev[m];
+    const int nch = dim == 2 ? 4 : 8;
+    nm /= nch;
+    MergeMaps mm = make_merge_maps(dim, n, ITI);
+    Lv.nmerge = (int)nm; Lv.nch = nch; Lv.n = n; Lv.nbc = mm.nbc; Lv.n_ext = mm.n_ext; Lv.n_int = mm.n_int;
+    Lv.ext = upload(h, mm.ext, st);
+    Lv.var = upload(h, mm.var, st);
+    Lv.eq = upload(h, mm.eq, st);
+    Lv.barow = upload(h, mm.b_arow, st);
+    Lv.bacol = upload(h, mm.b_acol, st);
+    Lv.bbrow = upload(h, mm.b_brow, st);
+    Lv.bcrow = upload(h, mm.b_crow, st);
+    const int ne = mm.n_ext, ni = mm.n_int;
+    const int nlu_m = ITI ? ni / 2 : ni;
+    Lv.TP = dalloc(h, (size_t)nm * ne * (ne + 1) * sizeof(T));
+    Lv.D = dalloc(h, (size_t)nm * ni * ni * sizeof(T));
+    if (ITI) Lv.W = dalloc(h, (size_t)nm * nlu_m * nlu_m * sizeof(T));
+    Lv.X = dalloc(h, (size_t)nm * ni * (ne + 1) * sizeof(T));
+    Lv.ipiv = (int*)dalloc(h, (size_t)nm * nlu_m * sizeof(int));
+    Lv.perm = (int*)dalloc(h, (size_t)nm * nlu_m * sizeof(int));
+    Lv.info = (int*)dalloc(h, (size_t)nm * sizeof(int));
+    if (!Lv.ext || !Lv.var || !Lv.eq || !Lv.barow || !Lv.bacol || !Lv.bbrow || !Lv.bcrow || !Lv.TP ||
+        !Lv.D || (ITI && !Lv.W) || !Lv.X || !Lv.ipiv || !Lv.perm || !Lv.info)
+      return HPS_ERR_OOM;
+    HPS_CUDA(cudaMemsetAsync(Lv.info, 0, (size_t)nm * sizeof(int), st));
+    T* R = (T*)h->scratch;
+    // D, R = [C | h_int], TP = [A | h_ext]
+    HPS_CUDA(fill<T>(bop<T>((T*)Lv.D, (int64_t)ni * ni, ni), ni, ni, (int)nm, T(0.0), ITI ? T(1.0) : T(0.0), st, pf));
+    HPS_CUDA(fill<T>(bop<T>(R, (int64_t)ni * (ne + 1), ni), ni, ne + 1, (int)nm, T(0.0), T(0.0), st, pf));
+    HPS_CUDA(fill<T>(bop<T>((T*)Lv.TP, (int64_t)ne * (ne + 1), ne), ne, ne + 1, (int)nm, T(0.0), T(0.0), st, pf));
+    HPS_CUDA(merge_gather<T>(Tc, cstride, (int)nm, nch, mm.nbc, ne, ni, Lv.ext, Lv.var, Lv.eq, ITI,
+                             (T*)Lv.D, R, (T*)Lv.TP, st, pf));
+    Lv.G = lu_group_size<T>(nlu_m, (int)nm, h->num_sms);
+    if (Lv.G > 1) {
+      Lv.luw.bars = (unsigned*)dalloc(h, sizeof(unsigned) * 2 * nm);
+      Lv.luw.pub_bytes = lu_pub_bytes<T>(nlu_m, (int)nm, Lv.G);
+      Lv.luw.pub = dalloc(h, Lv.luw.pub_bytes);
+      if (!Lv.luw.bars || !Lv.luw.pub) return HPS_ERR_OOM;
+      HPS_CUDA(cudaMemsetAsync(Lv.luw.bars, 0, sizeof(unsigned) * 2 * nm, st));
+    }
+    BOp<T> XX = bop<T>((T*)Lv.X, (int64_t)ni * (ne + 1), ni);
+    if (!ITI) {
+      BOp<T> DD = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni);
+      HPS_CUDA(getrf<T>(DD, ni, (int)nm, Lv.ipiv, Lv.perm, Lv.info, h->dev_err, Lv.G, Lv.luw, st, pf));
+      HPS_CUDA(permute_rows<T>(bop<T>(R, (int64_t)ni * (ne + 1), ni), XX, Lv.perm, ni, ne + 1, (int)nm, st, pf));
+      HPS_CUDA(getrs_inplace<T>(DD, ni, XX, ne + 1, (int)nm, st, pf));
+    } else {
+      const int hn = ni / 2;
+      BOp<T> D12 = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni, (int64_t)hn * ni);
+      BOp<T> D21 = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni, (int64_t)hn);
+      BOp<T> WW = bop<T>((T*)Lv.W, (int64_t)hn * hn, hn);
+      BOp<T> R1 = bop<T>(R, (int64_t)ni * (ne + 1), ni);
+      BOp<T> R2 = bop<T>(R, (int64_t)ni * (ne + 1), ni, hn);
+      // W = I - D12 D21 (Eq. "ItI D inverse")
+      HPS_CUDA(fill<T>(WW, hn, hn, (int)nm, T(0.0), T(1.0), st, pf));
+      GemmArgs<T> g;
+      g.M = hn; g.N = hn; g.K = hn; g.batch = (int)nm;
+      g.A = D12; g.B = D21; g.C = WW; g.alpha = T(-1.0); g.beta = T(1.0);
+      HPS_CUDA(gemm<T>(g, st, pf));
+      // R1 <- R1 - D12 R2
+      GemmArgs<T> g2;
+      g2.M = hn; g2.N = ne + 1; g2.K = hn; g2.batch = (int)nm;
+      g2.A = D12; g2.B = R2; g2.C = R1; g2.alpha = T(-1.0); g2.beta = T(1.0);
+      HPS_CUDA(gemm<T>(g2, st, pf));
+      HPS_CUDA(getrf<T>(WW, hn, (int)nm, Lv.ipiv, Lv.perm, Lv.info, h->dev_err, Lv.G, Lv.luw, st, pf));
+      // X1 = W^{-1} R1
+      HPS_CUDA(permute_rows<T>(R1, XX, Lv.perm, hn, ne + 1, (int)nm, st, pf));
+      HPS_CUDA(getrs_inplace<T>(WW, hn, XX, ne + 1, (int)nm, st, pf));
+      // X2 = R2 - D21 X1
+      HPS_CUDA(copy_block<T>(R + hn, (int64_t)ni * (ne + 1), ni, (T*)Lv.X + hn, (int64_t)ni * (ne + 1), ni, hn,
+                             ne + 1, (int)nm, st, pf));
+      GemmArgs<T> g3;
+      g3.M = hn; g3.N = ne + 1; g3.K = hn; g3.batch = (int)nm;
+      g3.A = D21; g3.B = XX; g3.C = shifted(XX, hn); g3.alpha = T(-1.0); g3.beta = T(1.0);
+      HPS_CUDA(gemm<T>(g3, st, pf));
+    }
+    // [T | h] = [A | h_ext] - B X  (block-sparse: one product per child)
+    if (!Lv.top() || h->opts.want_root_map) {
+      GemmArgs<T> g;
+      g.M = mm.nbc / 2; g.N = ne + 1; g.K = mm.nbc / 2; g.batch = (int)(nm * nch);
+      g.A = bop<T>(const_cast<T*>(Tc), cstride, mm.nbc);
+      g.arow.idx = Lv.barow; g.arow.len = mm.nbc / 2; g.arow.period = nch;
+      g.acol.idx = Lv.bacol; g.acol.len = mm.nbc / 2; g.acol.period = nch;
+      g.B = grouped(bop<T>((T*)Lv.X, (int64_t)ni * (ne + 1), ni), nch);
+      g.brow.idx = Lv.bbrow; g.brow.len = mm.nbc / 2; g.brow.period = nch;
+      g.C = grouped(bop<T>((T*)Lv.TP, (int64_t)ne * (ne + 1), ne), nch);
+      g.crow.idx = Lv.bcrow; g.crow.len = mm.nbc / 2; g.crow.period = nch;
+      g.alpha = T(-1.0); g.beta = T(1.0);
+      HPS_CUDA(gemm<T>(g, st, pf));
+    }
+    Tc = (const T*)Lv.TP;
+    cstride = (int64_t)ne * (ne + 1);
+    n *= (dim == 2 ? 2 : 4);
+  }
+
+  // ---- status: singular pivots / timeouts
+  HPS_CUDA(cudaStreamSynchronize(st));
+  for (void* t : tmp) { cudaFree(t); }
+  unsigned derr = 0;
+  HPS_CUDA(cudaMemcpy(&derr, h->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (derr & DEV_ERR_TIMEOUT) return HPS_ERR_TIMEOUT;
+  {
+    std::vector<int> info(nl);
+    HPS_CUDA(cudaMemcpy(info.data(), h->leaf_info, nl * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < nl; ++i)
+      if (info[i]) { h->err_node = i; return HPS_ERR_SINGULAR; }
+    int64_t off = nl;
+    for (int m = 0; m < h->L; ++m) {
+      std::vector<int> li(h->lev[m].nmerge);
+      HPS_CUDA(cudaMemcpy(li.data(), h->lev[m].info, li.size() * sizeof(int), cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < li.size(); ++i)
+        if (li[i]) { h->err_node = off + (int64_t)i; return HPS_ERR_SINGULAR; }
+      off += h->lev[m].nmerge;
+    }
+  }
+  return HPS_OK;
+}
+
+// --------------------------------------------------------------- solve -----
+
+template <typename T>
+hps_status ensure_ws(hps_handle* h, int nrhs) {
+  if (h->ws_nrhs >= nrhs) return HPS_OK;
+  for (void* pp : h->ws_allocs) { cudaFree(pp); }
+  h->ws_allocs.clear();
+  h->bytes -= h->ws_bytes;
+  const int64_t before = h->bytes;
+  h->ws_nrhs = 0;
+  const size_t es = sizeof(T);
+  auto A = [&](size_t bytes) { return dalloc(h, bytes, &h->ws_allocs); };
+  h->ws_xf = A((size_t)h->nl * h->xrows_leaf * nrhs * es);
+  h->ws_hleaf = A((size_t)h->nl * h->nb * nrhs * es);
+  h->ws_gleaf = A((size_t)h->nl * h->nb * nrhs * es);
+  h->ws_g = A((size_t)h->nroot * nrhs * es);
+  h->ws_f = A((size_t)h->nl * h->npts * nrhs * es);
+  h->ws_u = A((size_t)h->nl * h->npts * nrhs * es);
+  h->ws_rhs = A((size_t)h->nl * h->xrows_leaf * nrhs * es);
+  if (!h->ws_xf || !h->ws_hleaf || !h->ws_gleaf || !h->ws_g || !h->ws_f || !h->ws_u || !h->ws_rhs)
+    return HPS_ERR_OOM;
+  for (int m = 0; m < h->L; ++m) {
+    LevelDev& Lv = h->lev[m];
+    const int64_t nm = Lv.nmerge;
+    Lv.r = A((size_t)nm * Lv.n_int * nrhs * es);
+    Lv.x = A((size_t)nm * Lv.n_int * nrhs * es);
+    Lv.hp = A((size_t)nm * Lv.n_ext * nrhs * es);
+    Lv.gint = A((size_t)nm * Lv.n_int * nrhs * es);
+    Lv.gchild = A((size_t)nm * Lv.nch * Lv.nbc * nrhs * es);
+    if (!Lv.r || !Lv.x || !Lv.hp || !Lv.gint || !Lv.gchild) return HPS_ERR_OOM;
+  }
+  h->ws_bytes = h->bytes - before;
+  h->ws_nrhs = nrhs;
+  return HPS_OK;
+}
+
+template <typename T>
+hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_in, void* u_out,
+                      cudaStream_t st) {
+  constexpr bool ITI = Kind<T>::iti;
+  hps_status rs = ensure_ws<T>(h, nrhs);
+  if (rs != HPS_OK) return rs;
+  Prof* pf = &h->prof;
+  pf->reset();
+  pf->on = h->opts.profile != 0;
+  const int64_t nl = h->nl;
+  const int nb = h->nb, xr = h->xrows_leaf, nlu = h->nlu_leaf;
+  // stage host inputs
+  const T* g = (const T*)g_in;
+  if (!is_device_ptr(g_in)) {
+    HPS_CUDA(cudaMemcpyAsync(h->ws_g, g_in, (size_t)h->nroot * nrhs * sizeof(T), cudaMemcpyHostToDevice, st));
+    g = (const T*)h->ws_g;
+  }
+  const T* f = (const T*)f_in;
+  if (f_in && !is_device_ptr(f_in)) {
+    HPS_CUDA(cudaMemcpyAsync(h->ws_f, f_in, (size_t)nl * h->npts * nrhs * sizeof(T), cudaMemcpyHostToDevice, st));
+    f = (const T*)h->ws_f;
+  }
+  const bool host_u = !is_device_ptr(u_out);
+  T* u = host_u ? (T*)h->ws_u : (T*)u_out;
+  const bool newf = (f != nullptr);
+
+  // ---- upward particular pass (new f): leaf and merge triangular solves
+  if (newf) {
+    T* xf = (T*)h->ws_xf;
+    T* tmp = (T*)h->ws_rhs;
+    HPS_CUDA(leaf_particular_rhs<T>(h->lc, nl, nrhs, f, tmp, ITI, st, pf));
+    BOp<T> LA = bop<T>((T*)h->leafA, (int64_t)nlu * nlu, nlu);
+    BOp<T> XF = bop<T>(xf, (int64_t)xr * nrhs, xr);
+    HPS_CUDA(permute_rows<T>(bop<T>(tmp, (int64_t)xr * nrhs, xr), XF, h->leaf_perm, nlu, nrhs, (int)nl, st, pf));
+    HPS_CUDA(getrs_inplace<T>(LA, nlu, XF, nrhs, (int)nl, st, pf));
+    GemmArgs<T> gl;
+    gl.M = nb; gl.N = nrhs; gl.K = ITI ? (int)h->npts : xr; gl.batch = (int)nl;
+    gl.A = ITI ? bop<T>((T*)h->dQH, 0, nb) : bop<T>((T*)h->dQi, 0, nb);
+    gl.B = XF;
+    gl.C = bop<T>((T*)h->ws_hleaf, (int64_t)nb * nrhs, nb);
+    gl.alpha = ITI ? T(1.0) : T(-h->s);
+    gl.beta = T(0.0);
+    HPS_CUDA(gemm<T>(gl, st, pf));
+    const T* hc = (const T*)h->ws_hleaf;
+    for (int m = 0; m < h->L; ++m) {
+      LevelDev& Lv = h->lev[m];
+      const int ne = Lv.n_ext, ni = Lv.n_int, nm = Lv.nmerge;
+      T* r = (T*)Lv.r;
+      T* x = (T*)Lv.x;
+      HPS_CUDA(fill<T>(bop<T>(r, (int64_t)ni * nrhs, ni), ni, nrhs, nm, T(0.0), T(0.0), st, pf));
+      HPS_CUDA(merge_gather_h<T>(hc, nm, Lv.nch, Lv.nbc, ne, ni, nrhs, Lv.ext, Lv.var, Lv.eq, ITI, r,
+                                 (T*)Lv.hp, st, pf));
+      BOp<T> XB = bop<T>(x, (int64_t)ni * nrhs, ni);
+      if (!ITI) {
+        BOp<T> DD = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni);
+        HPS_CUDA(permute_rows<T>(bop<T>(r, (int64_t)ni * nrhs, ni), XB, Lv.perm, ni, nrhs, nm, st, pf));
+        HPS_CUDA(getrs_inplace<T>(DD, ni, XB, nrhs, nm, st, pf));
+      } else {
+        const int hn = ni / 2;
+        BOp<T> D12 = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni, (int64_t)hn * ni);
+        BOp<T> D21 = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni, (int64_t)hn);
+        BOp<T> WW = bop<T>((T*)Lv.W, (int64_t)hn * hn, hn);
+        BOp<T> R1 = bop<T>(r, (int64_t)ni * nrhs, ni);
+        BOp<T> R2 = bop<T>(r, (int64_t)ni * nrhs, ni, hn);
+        GemmArgs<T> g2;
+        g2.M = hn; g2.N = nrhs; g2.K = hn; g2.batch = nm;
+        g2.A = D12; g2.B = R2; g2.C = R1; g2.alpha = T(-1.0); g2.beta = T(1.0);
+        HPS_CUDA(gemm<T>(g2, st, pf));
+        HPS_CUDA(permute_rows<T>(R1, XB, Lv.perm, hn, nrhs, nm, st, pf));
+        HPS_CUDA(getrs_inplace<T>(WW, hn, XB, nrhs, nm, st, pf));
+        HPS_CUDA(copy_block<T>(r + hn, (int64_t)ni * nrhs, ni, x + hn, (int64_t)ni * nrhs, ni, hn, nrhs, nm, st, pf));
+        GemmArgs<T> g3;
+        g3.M = hn; g3.N = nrhs; g3.K = hn; g3.batch = nm;
+        g3.A = D21; g3.B = XB; g3.C = shifted(XB, hn); g3.alpha = T(-1.0); g3.beta = T(1.0);
+        HPS_CUDA(gemm<T>(g3, st, pf));
+      }
+      if (!Lv.top()) {
+        GemmArgs<T> g;
+        g.M = Lv.nbc / 2; g.N = nrhs; g.K = Lv.nbc / 2; g.batch = nm * Lv.nch;
+        const T* Tc = m == 0 ? (const T*)h->leafTH : (const T*)h->lev[m - 1].TP;
+        const int64_t cstride = m == 0 ? (int64_t)nb * (nb + 1)
+                                       : (int64_t)h->lev[m - 1].n_ext * (h->lev[m - 1].n_ext + 1);
+        g.A = bop<T>(const_cast<T*>(Tc), cstride, Lv.nbc);
+        g.arow.idx = Lv.barow; g.arow.len = Lv.nbc / 2; g.arow.period = Lv.nch;
+        g.acol.idx = Lv.bacol; g.acol.len = Lv.nbc / 2; g.acol.period = Lv.nch;
+        g.B = grouped(bop<T>(x, (int64_t)ni * nrhs, ni), Lv.nch);
+        g.brow.idx = Lv.bbrow; g.brow.len = Lv.nbc / 2; g.brow.period = Lv.nch;
+        g.C = grouped(bop<T>((T*)Lv.hp, (int64_t)ne * nrhs, ne), Lv.nch);
+        g.crow.idx = Lv.bcrow; g.crow.len = Lv.nbc / 2; g.crow.period = Lv.nch;
+        g.alpha = T(-1.0); g.beta = T(1.0);
+        HPS_CUDA(gemm<T>(g, st, pf));
+      }
+      hc = (const T*)Lv.hp;
+    }
+  }
+
+  // ---- downward pass (Algorithm "down pass")
+  const T* gpar = g;
+  for (int m = h->L - 1; m >= 0; --m) {
+    LevelDev& Lv = h->lev[m];
+    T* gchild = (m == 0) ? (T*)h->ws_gleaf : (T*)Lv.gchild;
+    HPS_CUDA(down_level<T>((const T*)Lv.X, newf ? (const T*)Lv.x : nullptr, gpar, Lv.nmerge, Lv.nch, Lv.nbc,
+                           Lv.n_ext, Lv.n_int, nrhs, Lv.ext, Lv.var, (T*)Lv.gint, gchild, st, pf));
+    gpar = gchild;
+  }
+  // leaf output u = Y g + v
+  HPS_CUDA(leaf_output<T>(h->lc, nl, nrhs, (const T*)h->leafX, newf ? (const T*)h->ws_xf : nullptr, gpar, u,
+                          ITI, st, pf));
+  if (host_u) {
+    HPS_CUDA(cudaMemcpyAsync(u_out, u, (size_t)nl * h->npts * nrhs * sizeof(T), cudaMemcpyDeviceToHost, st));
+    HPS_CUDA(cudaStreamSynchronize(st));
+  }
+  return HPS_OK;
+}
+
+thread_local int64_t g_last_err_node = -1;
+
+void free_handle(hps_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (void* p : h->ws_allocs) cudaFree(p);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hps_error_string(hps_status s) {
+  switch (s) {
+    case HPS_OK: return "HPS_OK: success";
+    case HPS_ERR_INVALID: return "HPS_ERR_INVALID: invalid argument";
+    case HPS_ERR_OOM: return "HPS_ERR_OOM: not enough device memory";
+    case HPS_ERR_SINGULAR: return "HPS_ERR_SINGULAR: zero pivot in a leaf or merge factorisation";
+    case HPS_ERR_CUDA: return "HPS_ERR_CUDA: a CUDA runtime call failed";
+    case HPS_ERR_TIMEOUT: return "HPS_ERR_TIMEOUT: a bounded device-side wait gave up";
+  }
+  return "unknown hps_status";
+}
+
+hps_status hps_sizes(const hps_tree* tree, int p, int q, int64_t* n_leaves, int64_t* ppl, int64_t* nroot) {
+  hps_status s = check_tree(tree, p, q);
+  if (s != HPS_OK) return s;
+  const int L = tree->uniform_depth, d = tree->dim;
+  if (n_leaves) *n_leaves = (int64_t)1 << (d * L);
+  if (ppl) *ppl = d == 2 ? (int64_t)p * p : (int64_t)p * p * p;
+  if (nroot) *nroot = nroot_of(d, q, L);
+  return HPS_OK;
+}
+
+hps_status hps_nodes(const hps_tree* tree, int p, int q, double* leaf_xyz, double* bdry_xyz) {
+  hps_status s = check_tree(tree, p, q);
+  if (s != HPS_OK) return s;
+  try {
+    Spectral1D sp = make_spectral(p, q);
+    if (leaf_xyz) leaf_node_coords(tree->dim, tree->lo, tree->hi, tree->uniform_depth, sp, leaf_xyz);
+    if (bdry_xyz) root_boundary_coords(tree->dim, tree->lo, tree->hi, tree->uniform_depth, sp, bdry_xyz);
+  } catch (...) {
+    return HPS_ERR_INVALID;
+  }
+  return HPS_OK;
+}
+
+hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeffs, const void* f,
+                     const hps_options* opts, struct CUstream_st* stream, hps_handle** out) {
+  if (!out) return HPS_ERR_INVALID;
+  *out = nullptr;
+  hps_status s = check_tree(tree, p, q);
+  if (s != HPS_OK) return s;
+  if (!coeffs) return HPS_ERR_INVALID;
+  if (coeffs->kind != HPS_DTN && coeffs->kind != HPS_ITI) return HPS_ERR_INVALID;
+  if (coeffs->kind == HPS_DTN && coeffs->dtype != HPS_F64) return HPS_ERR_INVALID;
+  if (coeffs->kind == HPS_ITI && (coeffs->dtype != HPS_C128 || tree->dim != 2 || !(coeffs->eta > 0)))
+    return HPS_ERR_INVALID;
+  if (opts && opts->version != 1) return HPS_ERR_INVALID;
+  hps_handle* h = new (std::nothrow) hps_handle();
+  if (!h) return HPS_ERR_OOM;
+  h->dim = tree->dim; h->kind = coeffs->kind; h->p = p; h->q = q; h->L = tree->uniform_depth;
+  h->iti = coeffs->kind == HPS_ITI;
+  h->nl = (int64_t)1 << (h->dim * h->L);
+  h->npts = h->dim == 2 ? (int64_t)p * p : (int64_t)p * p * p;
+  h->nroot = nroot_of(h->dim, q, h->L);
+  for (int a = 0; a < 3; ++a) { h->lo[a] = tree->lo[a]; h->hi[a] = tree->hi[a]; }
+  h->hlen = (tree->hi[0] - tree->lo[0]) / (double)((int64_t)1 << h->L);
+  h->eta = coeffs->eta;
+  if (opts) h->opts = *opts;
+  else { h->opts.version = 1; h->opts.want_root_map = 0; h->opts.profile = 0; }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return HPS_ERR_CUDA;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last = st;
+  try {
+    s = h->iti ? build_impl<cplx>(h, coeffs, f, st) : build_impl<double>(h, coeffs, f, st);
+  } catch (...) {
+    s = HPS_ERR_INVALID;
+  }
+  if (s != HPS_OK && s != HPS_ERR_SINGULAR) {
+    free_handle(h);
+    return s;
+  }
+  if (s == HPS_ERR_SINGULAR) {
+    // no half-built handle is returned; the node id stays readable through
+    // hps_last_error_detail(NULL, &node) on this thread
+    g_last_err_node = h->err_node;
+    free_handle(h);
+    return s;
+  }
+  g_last_err_node = -1;
+  *out = h;
+  return HPS_OK;
+}
+
+hps_status hps_solve_batched(hps_handle* h, int nrhs, const void* g, const void* f, void* u,
+                             struct CUstream_st* stream) {
+  if (!h || !g || !u || nrhs < 1) return HPS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last = st;
+  hps_status s;
+  try {
+    s = h->iti ? solve_impl<cplx>(h, nrhs, g, f, u, st) : solve_impl<double>(h, nrhs, g, f, u, st);
+  } catch (...) {
+    s = HPS_ERR_INVALID;
+  }
+  return s;
+}
+
+hps_status hps_solve(hps_handle* h, const void* g, const void* f, void* u, struct CUstream_st* stream) {
+  return hps_solve_batched(h, 1, g, f, u, stream);
+}
+
+void hps_free(hps_handle* h) { free_handle(h); }
+
+hps_status hps_last_error_detail(hps_handle* h, int64_t* node) {
+  if (!node) return HPS_ERR_INVALID;
+  *node = h ? h->err_node : g_last_err_node;
+  return HPS_OK;
+}
+
+int64_t hps_device_bytes(const hps_handle* h) { return h ? h->bytes : 0; }
+
+int64_t hps_last_launch_count(const hps_handle* h) { return h ? h->prof.launches : 0; }
+
+hps_status hps_kernel_stats(hps_handle* h, int cls, hps_kernel_stat* out) {
+  if (!h || !out || cls < 0 || cls >= HPS_KCLASS_COUNT) return HPS_ERR_INVALID;
+  if (h->prof.on && cudaStreamSynchronize(h->last) != cudaSuccess) return HPS_ERR_CUDA;
+  out->launches = h->prof.n[cls];
+  out->flops = h->prof.flops[cls];
+  out->ms = h->prof.on ? h->prof.ms(cls) : -1.0;
+  return HPS_OK;
+}
+
+hps_status hps_set_profiling(hps_handle* h, int on) {
+  if (!h) return HPS_ERR_INVALID;
+  h->opts.profile = on ? 1 : 0;
+  return HPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,479 @@
+// HPS-specific device kernels (leaf assembly, merge gathers, downward pass,
+// leaf output).  These are gather/scatter and small dot-product kernels; the
+// dense FP64 work (LU, triangular solves, GEMM) lives in linalg.cu.
+#include "hps_kernels.cuh"
+
+#include <algorithm>
+
+namespace hps {
+
+namespace {
+
+inline int grid_for(int64_t total, int threads = 256, int cap = 65535 * 8) {
+  int64_t b = (total + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+__device__ inline void coords(int dim, int p, int idx, int* c) {
+  c[0] = idx % p;
+  c[1] = (idx / p) % p;
+  c[2] = dim == 3 ? idx / (p * p) : 0;
+}
+
+// Entry (i, j) of the leaf operator a Lap + sum_k b_k d_k + c (Section 3.2)
+// on the tensor Chebyshev grid: nonzero only when i and j differ along at
+// most one axis.
+__device__ inline double L_entry(const LeafConsts& k, double a, const double* bk, double c, int i,
+                                 int j) {
+  int ci[3], cj[3];
+  coords(k.dim, k.p, i, ci);
+  coords(k.dim, k.p, j, cj);
+  int ndiff = 0, dax = -1;
+  for (int ax = 0; ax < k.dim; ++ax)
+    if (ci[ax] != cj[ax]) { ++ndiff; dax = ax; }
+  if (ndiff > 1) return 0.0;
+  double v = 0.0;
+  const double s = k.s, s2 = k.s * k.s;
+  for (int ax = 0; ax < k.dim; ++ax) {
+    if (ndiff == 1 && ax != dax) continue;
+    const int e = ci[ax] * k.p + cj[ax];
+    v = fma(a * s2, k.DD[e], v);
+    v = fma(bk[ax] * s, k.D[e], v);
+  }
+  if (ndiff == 0) v += c;
+  return v;
+}
+
+__device__ inline void load_coeffs(const Coeffs& cf, int64_t at, int dim, double* a, double* b,
+                                   double* c) {
+  *a = cf.a ? cf.a[at] : 1.0;
+  for (int ax = 0; ax < 3; ++ax) b[ax] = (ax < dim && cf.b[ax]) ? cf.b[ax][at] : 0.0;
+  *c = cf.c ? cf.c[at] : 0.0;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- leaves ----
+
+__global__ void k_leaf_dtn_Lii(LeafConsts k, int64_t nl, Coeffs cf, double* Lii) {
+  const int64_t per = (int64_t)k.ni * k.ni;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nl * per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t leaf = e / per;
+    const int rc = (int)(e % per);
+    const int r = rc % k.ni, c = rc / k.ni;
+    const int i = k.Ii[r], j = k.Ii[c];
+    double a, b[3], cc;
+    load_coeffs(cf, leaf * k.npts + i, k.dim, &a, b, &cc);
+    Lii[e] = L_entry(k, a, b, cc, i, j);
+  }
+}
+
+__global__ void k_leaf_dtn_rhs(LeafConsts k, int64_t nl, Coeffs cf, const double* f, double* rhs) {
+  const int ncol = k.nb + 1;
+  const int64_t per = (int64_t)k.ni * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nl * per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t leaf = e / per;
+    const int rc = (int)(e % per);
+    const int r = rc % k.ni, col = rc / k.ni;
+    const int i = k.Ii[r];
+    if (col == k.nb) {
+      rhs[e] = f ? -f[leaf * k.npts + i] : 0.0;
+      continue;
+    }
+    double a, b[3], cc;
+    load_coeffs(cf, leaf * k.npts + i, k.dim, &a, b, &cc);
+    int ci[3];
+    coords(k.dim, k.p, i, ci);
+    double acc = 0.0;
+    for (int ax = 0; ax < k.dim; ++ax) {
+      for (int end = 0; end < 2; ++end) {
+        int cj[3] = {ci[0], ci[1], ci[2]};
+        cj[ax] = end ? k.p - 1 : 0;
+        const int j = cj[0] + k.p * (cj[1] + k.p * cj[2]);
+        const int pr = k.prow[j];
+        const int el = ci[ax] * k.p + cj[ax];
+        const double lij = fma(a * k.s * k.s, k.DD[el], b[ax] * k.s * k.D[el]);
+        acc = fma(lij, k.P[pr + (int64_t)col * k.ne], acc);
+      }
+    }
+    rhs[e] = acc;
+  }
+}
+
+cudaError_t leaf_dtn_assemble(const LeafConsts& k, int64_t nl, Coeffs cf, const double* f,
+                              double* Lii, double* rhs, cudaStream_t st, Prof* pf) {
+  if (pf) pf->begin(st);
+  k_leaf_dtn_Lii<<<grid_for(nl * k.ni * k.ni), 256, 0, st>>>(k, nl, cf, Lii);
+  if (pf) pf->end(K_ASSEMBLE, 0.0, st);
+  if (pf) pf->begin(st);
+  k_leaf_dtn_rhs<<<grid_for(nl * k.ni * (k.nb + 1)), 256, 0, st>>>(k, nl, cf, f, rhs);
+  if (pf) pf->end(K_ASSEMBLE, 2.0 * 2 * k.dim * (double)nl * k.ni * k.nb, st);
+  return cudaGetLastError();
+}
+
+__global__ void k_leaf_iti_B(LeafConsts k, int64_t nl, Coeffs cf, cplx* B) {
+  const int n = k.npts;
+  const int64_t per = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nl * per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t leaf = e / per;
+    const int rc = (int)(e % per);
+    const int r = rc % n, j = rc / n;
+    cplx v(0.0, 0.0);
+    if (r < k.nown) {
+      // incoming impedance row: sgn * s * d/dx_axis + i eta at the owned node
+      const int node = k.own_node[r], ax = k.own_axis[r];
+      int ci[3], cj[3];
+      coords(k.dim, k.p, node, ci);
+      coords(k.dim, k.p, j, cj);
+      bool same = true;
+      for (int a2 = 0; a2 < k.dim; ++a2)
+        if (a2 != ax && ci[a2] != cj[a2]) same = false;
+      if (same) v.re = k.own_sgn[r] * k.s * k.D[ci[ax] * k.p + cj[ax]];
+      if (j == node) v.im = k.eta;
+    } else {
+      const int i = k.Ii[r - k.nown];
+      double a, b[3], cc;
+      load_coeffs(cf, leaf * k.npts + i, k.dim, &a, b, &cc);
+      v.re = L_entry(k, a, b, cc, i, j);
+    }
+    B[e] = v;
+  }
+}
+
+__global__ void k_leaf_iti_rhs(LeafConsts k, int64_t nl, const cplx* f, cplx* rhs) {
+  const int n = k.npts, ncol = k.nb + 1;
+  const int64_t per = (int64_t)n * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nl * per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t leaf = e / per;
+    const int rc = (int)(e % per);
+    const int r = rc % n, col = rc / n;
+    cplx v(0.0, 0.0);
+    if (col < k.nb) {
+      if (r < k.nown) v = cplx(k.P[r + (int64_t)col * k.nown], 0.0);
+    } else if (r >= k.nown && f) {
+      v = f[leaf * k.npts + k.Ii[r - k.nown]];
+    }
+    rhs[e] = v;
+  }
+}
+
+cudaError_t leaf_iti_assemble(const LeafConsts& k, int64_t nl, Coeffs cf, const cplx* f, cplx* B,
+                              cplx* rhs, cudaStream_t st, Prof* pf) {
+  if (pf) pf->begin(st);
+  k_leaf_iti_B<<<grid_for(nl * k.npts * k.npts), 256, 0, st>>>(k, nl, cf, B);
+  if (pf) pf->end(K_ASSEMBLE, 0.0, st);
+  if (pf) pf->begin(st);
+  k_leaf_iti_rhs<<<grid_for(nl * k.npts * (k.nb + 1)), 256, 0, st>>>(k, nl, f, rhs);
+  if (pf) pf->end(K_ASSEMBLE, 0.0, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_leaf_particular_rhs(LeafConsts k, int64_t nl, int nrhs, const T* f, T* out, bool iti) {
+  const int rows = iti ? k.npts : k.ni;
+  const int64_t per = (int64_t)rows * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nl * per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t leaf = e / per;
+    const int rc = (int)(e % per);
+    const int r = rc % rows, c = rc / rows;
+    const int64_t fo = ((int64_t)c * nl + leaf) * k.npts;
+    T v = T(0.0);
+    if (!iti) v = -f[fo + k.Ii[r]];
+    else if (r >= k.nown) v = f[fo + k.Ii[r - k.nown]];
+    out[e] = v;
+  }
+}
+
+template <typename T>
+cudaError_t leaf_particular_rhs(const LeafConsts& k, int64_t nl, int nrhs, const T* f, T* out,
+                                bool iti, cudaStream_t st, Prof* pf) {
+  const int rows = iti ? k.npts : k.ni;
+  if (pf) pf->begin(st);
+  k_leaf_particular_rhs<T><<<grid_for(nl * rows * nrhs), 256, 0, st>>>(k, nl, nrhs, f, out, iti);
+  if (pf) pf->end(K_GATHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+__global__ void k_leaf_dtn_init_T(const double* QP, int nb, double s, int64_t nl, double* TH) {
+  const int64_t per = (int64_t)nb * (nb + 1);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nl * per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int rc = (int)(e % per);
+    TH[e] = (rc < nb * nb) ? s * QP[rc] : 0.0;
+  }
+}
+
+cudaError_t leaf_dtn_init_T(const double* QP, int nb, double s, int64_t nl, double* TH,
+                            cudaStream_t st, Prof* pf) {
+  if (pf) pf->begin(st);
+  k_leaf_dtn_init_T<<<grid_for(nl * nb * (nb + 1)), 256, 0, st>>>(QP, nb, s, nl, TH);
+  if (pf) pf->end(K_OTHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- merges ----
+
+__device__ inline void add_pair(double* p, double v) { atomicAdd(p, v); }
+__device__ inline void add_pair(cplx* p, cplx v) {
+  atomicAdd(&p->re, v.re);
+  atomicAdd(&p->im, v.im);
+}
+
+// One thread per (merge, child, child row i, child column j <= nbc).
+// DtN: D(var_i, var_j) += T (interface diagonal blocks get exactly two
+// addends, so the result does not depend on their order); C and A entries
+// and the h columns have a single owner except h_int, which also gets two.
+// ItI: D(eq_i, var_j) = T on top of the identity, R(eq_i, .) = T, single owner.
+template <typename T>
+__global__ void k_merge_gather(const T* Tc, int64_t cstride, int nmerge, int nch, int nbc, int n_ext,
+                               int n_int, const int* ext, const int* var, const int* eq, bool iti,
+                               T* D, T* R, T* TP) {
+  const int ncol = nbc + 1;
+  const int64_t per_child = (int64_t)nbc * ncol;
+  const int64_t total = (int64_t)nmerge * nch * per_child;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cidx = e / per_child;  // global child index = nch * merge + k
+    const int rc = (int)(e % per_child);
+    const int i = rc % nbc, j = rc / nbc;
+    const int k = (int)(cidx % nch);
+    const int64_t b = cidx / nch;
+    const T v = Tc[cidx * cstride + rc];
+    const int ei = ext[k * nbc + i];
+    const int ri = iti ? eq[k * nbc + i] : var[k * nbc + i];
+    T* Db = D + b * (int64_t)n_int * n_int;
+    T* Rb = R + b * (int64_t)n_int * (n_ext + 1);
+    T* Pb = TP + b * (int64_t)n_ext * (n_ext + 1);
+    if (j == nbc) {  // h column
+      if (ei >= 0) Pb[ei + (int64_t)n_ext * n_ext] = v;
+      else if (iti) Rb[ri + (int64_t)n_int * n_ext] = v;
+      else add_pair(&Rb[ri + (int64_t)n_int * n_ext], v);
+      continue;
+    }
+    const int ej = ext[k * nbc + j];
+    const int vj = var[k * nbc + j];
+    if (ei >= 0) {
+      if (ej >= 0) Pb[ei + (int64_t)ej * n_ext] = v;        // A
+      // (exterior row, interior column) = B: used in place, not stored
+    } else {
+      if (ej >= 0) Rb[ri + (int64_t)ej * n_int] = v;         // C
+      else if (iti) Db[ri + (int64_t)vj * n_int] = v;        // D12 / D21
+      else add_pair(&Db[ri + (int64_t)vj * n_int], v);       // D
+    }
+  }
+}
+
+template <typename T>
+cudaError_t merge_gather(const T* Tc, int64_t cstride, int nmerge, int nch, int nbc, int n_ext,
+                         int n_int, const int* ext, const int* var, const int* eq, bool iti, T* D,
+                         T* R, T* TP, cudaStream_t st, Prof* pf) {
+  const int64_t total = (int64_t)nmerge * nch * nbc * (nbc + 1);
+  if (pf) pf->begin(st);
+  k_merge_gather<T><<<grid_for(total), 256, 0, st>>>(Tc, cstride, nmerge, nch, nbc, n_ext, n_int, ext,
+                                                     var, eq, iti, D, R, TP);
+  if (pf) pf->end(K_GATHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_merge_gather_h(const T* hc, int nmerge, int nch, int nbc, int n_ext, int n_int,
+                                 int nrhs, const int* ext, const int* var, const int* eq, bool iti,
+                                 T* r, T* hp) {
+  const int64_t per_child = (int64_t)nbc * nrhs;
+  const int64_t total = (int64_t)nmerge * nch * per_child;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cidx = e / per_child;
+    const int rc = (int)(e % per_child);
+    const int i = rc % nbc, c = rc / nbc;
+    const int k = (int)(cidx % nch);
+    const int64_t b = cidx / nch;
+    const T v = hc[cidx * per_child + rc];
+    const int ei = ext[k * nbc + i];
+    if (ei >= 0) {
+      hp[b * (int64_t)n_ext * nrhs + ei + (int64_t)c * n_ext] = v;
+    } else {
+      const int ri = iti ? eq[k * nbc + i] : var[k * nbc + i];
+      T* p = &r[b * (int64_t)n_int * nrhs + ri + (int64_t)c * n_int];
+      if (iti) *p = v;
+      else add_pair(p, v);
+    }
+  }
+}
+
+template <typename T>
+cudaError_t merge_gather_h(const T* hc, int nmerge, int nch, int nbc, int n_ext, int n_int, int nrhs,
+                           const int* ext, const int* var, const int* eq, bool iti, T* r, T* hp,
+                           cudaStream_t st, Prof* pf) {
+  const int64_t total = (int64_t)nmerge * nch * nbc * nrhs;
+  if (pf) pf->begin(st);
+  k_merge_gather_h<T><<<grid_for(total), 256, 0, st>>>(hc, nmerge, nch, nbc, n_ext, n_int, nrhs, ext,
+                                                       var, eq, iti, r, hp);
+  if (pf) pf->end(K_GATHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- downward ----
+
+// gint(:, c) = -(X_C gpar(:, c) + xpart(:, c)); a warp per (merge, row, rhs)
+// block of rows: each thread owns one row and walks the columns.
+template <typename T>
+__global__ void k_down_gint(const T* X, const T* xp, const T* gpar, int nmerge, int n_ext, int n_int,
+                            int nrhs, T* gint) {
+  const int64_t total = (int64_t)nmerge * n_int * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % n_int);
+    const int64_t bc = e / n_int;
+    const int c = (int)(bc % nrhs);
+    const int64_t b = bc / nrhs;
+    const T* Xb = X + b * (int64_t)n_int * (n_ext + 1);
+    const T* g = gpar + b * (int64_t)n_ext * nrhs + (int64_t)c * n_ext;
+    T acc = xp ? xp[b * (int64_t)n_int * nrhs + r + (int64_t)c * n_int] : Xb[r + (int64_t)n_ext * n_int];
+    for (int j = 0; j < n_ext; ++j) acc = fmac(acc, Xb[r + (int64_t)j * n_int], g[j]);
+    gint[b * (int64_t)n_int * nrhs + r + (int64_t)c * n_int] = -acc;
+  }
+}
+
+template <typename T>
+__global__ void k_down_children(const T* gpar, const T* gint, int nmerge, int nch, int nbc, int n_ext,
+                                int n_int, int nrhs, const int* ext, const int* var, T* gchild) {
+  const int64_t per_child = (int64_t)nbc * nrhs;
+  const int64_t total = (int64_t)nmerge * nch * per_child;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cidx = e / per_child;
+    const int rc = (int)(e % per_child);
+    const int i = rc % nbc, c = rc / nbc;
+    const int k = (int)(cidx % nch);
+    const int64_t b = cidx / nch;
+    const int ei = ext[k * nbc + i];
+    T v;
+    if (ei >= 0) v = gpar[b * (int64_t)n_ext * nrhs + ei + (int64_t)c * n_ext];
+    else v = gint[b * (int64_t)n_int * nrhs + var[k * nbc + i] + (int64_t)c * n_int];
+    gchild[e] = v;
+  }
+}
+
+template <typename T>
+cudaError_t down_level(const T* X, const T* xp, const T* gpar, int nmerge, int nch, int nbc, int n_ext,
+                       int n_int, int nrhs, const int* ext, const int* var, T* gint, T* gchild,
+                       cudaStream_t st, Prof* pf) {
+  const double F = sizeof(T) == sizeof(cplx) ? 8.0 : 2.0;
+  if (pf) pf->begin(st);
+  k_down_gint<T><<<grid_for((int64_t)nmerge * n_int * nrhs, 128), 128, 0, st>>>(X, xp, gpar, nmerge, n_ext,
+                                                                           n_int, nrhs, gint);
+  if (pf) pf->end(K_DOWN, F * (double)nmerge * n_int * n_ext * nrhs, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (pf) pf->begin(st);
+  k_down_children<T><<<grid_for((int64_t)nmerge * nch * nbc * nrhs), 256, 0, st>>>(
+      gpar, gint, nmerge, nch, nbc, n_ext, n_int, nrhs, ext, var, gchild);
+  if (pf) pf->end(K_GATHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_leaf_output(LeafConsts k, int64_t nl, int nrhs, const T* X, const T* xp, const T* g,
+                              T* u, bool iti) {
+  const int64_t total = (int64_t)nrhs * nl * k.npts;
+  const int xrows = iti ? k.npts : k.ni;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int node = (int)(e % k.npts);
+    const int64_t lc = e / k.npts;
+    const int64_t leaf = lc % nl;
+    const int c = (int)(lc / nl);
+    const T* gl = g + (leaf * nrhs + c) * (int64_t)k.nb;
+    const T* Xl = X + leaf * (int64_t)xrows * (k.nb + 1);
+    T acc = T(0.0);
+    if (iti) {
+      acc = xp ? xp[(leaf * nrhs + c) * (int64_t)xrows + node] : Xl[node + (int64_t)k.nb * xrows];
+      for (int j = 0; j < k.nb; ++j) acc = fmac(acc, Xl[node + (int64_t)j * xrows], gl[j]);
+    } else {
+      const int pr = k.prow[node];
+      if (pr >= 0) {
+        for (int j = 0; j < k.nb; ++j) acc = fmac(acc, T(k.P[pr + (int64_t)j * k.ne]), gl[j]);
+      } else {
+        const int r = k.iidx[node];
+        acc = xp ? xp[(leaf * nrhs + c) * (int64_t)xrows + r] : Xl[r + (int64_t)k.nb * xrows];
+        for (int j = 0; j < k.nb; ++j) acc = fmac(acc, Xl[r + (int64_t)j * xrows], gl[j]);
+        acc = -acc;
+      }
+    }
+    u[e] = acc;
+  }
+}
+
+template <typename T>
+cudaError_t leaf_output(const LeafConsts& k, int64_t nl, int nrhs, const T* X, const T* xp, const T* g,
+                        T* u, bool iti, cudaStream_t st, Prof* pf) {
+  const double F = sizeof(T) == sizeof(cplx) ? 8.0 : 2.0;
+  if (pf) pf->begin(st);
+  k_leaf_output<T><<<grid_for((int64_t)nrhs * nl * k.npts), 256, 0, st>>>(k, nl, nrhs, X, xp, g, u, iti);
+  if (pf) pf->end(K_DOWN, F * (double)nrhs * nl * k.npts * k.nb, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_copy_block(const T* src, int64_t sstride, int sld, T* dst, int64_t dstride, int dld,
+                             int m, int ncols, int batch) {
+  const int64_t per = (int64_t)m * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e / per;
+    const int rc = (int)(e % per);
+    const int i = rc % m, j = rc / m;
+    dst[b * dstride + i + (int64_t)j * dld] = src[b * sstride + i + (int64_t)j * sld];
+  }
+}
+
+template <typename T>
+cudaError_t copy_block(const T* src, int64_t sstride, int sld, T* dst, int64_t dstride, int dld, int m,
+                       int ncols, int batch, cudaStream_t st, Prof* pf) {
+  if (pf) pf->begin(st);
+  k_copy_block<T><<<grid_for((int64_t)m * ncols * batch), 256, 0, st>>>(src, sstride, sld, dst, dstride,
+                                                                          dld, m, ncols, batch);
+  if (pf) pf->end(K_OTHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_scale_copy(const T* src, T* dst, int64_t n, double alpha) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = scale(src[e], alpha);
+}
+
+template <typename T>
+cudaError_t scale_copy(const T* src, T* dst, int64_t n, double alpha, cudaStream_t st, Prof* pf) {
+  if (pf) pf->begin(st);
+  k_scale_copy<T><<<grid_for(n), 256, 0, st>>>(src, dst, n, alpha);
+  if (pf) pf->end(K_OTHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+#define HPS_KINST(T)                                                                                  \
+  template cudaError_t leaf_particular_rhs<T>(const LeafConsts&, int64_t, int, const T*, T*, bool,    \
+                                              cudaStream_t, Prof*);                                   \
+  template cudaError_t merge_gather<T>(const T*, int64_t, int, int, int, int, int, const int*,        \
+                                       const int*, const int*, bool, T*, T*, T*, cudaStream_t, Prof*); \
+  template cudaError_t merge_gather_h<T>(const T*, int, int, int, int, int, int, const int*,          \
+                                         const int*, const int*, bool, T*, T*, cudaStream_t, Prof*);  \
+  template cudaError_t down_level<T>(const T*, const T*, const T*, int, int, int, int, int, int,      \
+                                     const int*, const int*, T*, T*, cudaStream_t, Prof*);            \
+  template cudaError_t leaf_output<T>(const LeafConsts&, int64_t, int, const T*, const T*, const T*,  \
+                                      T*, bool, cudaStream_t, Prof*);                                 \
+  template cudaError_t copy_block<T>(const T*, int64_t, int, T*, int64_t, int, int, int, int,         \
+                                     cudaStream_t, Prof*);                                            \
+  template cudaError_t scale_copy<T>(const T*, T*, int64_t, double, cudaStream_t, Prof*);
+
+HPS_KINST(double)
+HPS_KINST(cplx)
+
+}  // namespace hps

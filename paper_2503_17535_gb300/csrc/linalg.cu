@@ -1,0 +1,586 @@
+// Batched FP64 / complex128 dense kernels: gathered GEMM, panel LU with
+// partial pivoting (one CTA or a cooperative group of CTAs per matrix), row
+// interchanges + triangular update, and blocked triangular solves.
+//
+// GB300 has about 1 TFLOP/s of FP64 (2 DFMA per clock per SM), so every
+// kernel here is bound by the FP64 pipe long before HBM or shared memory:
+// the designs aim at keeping all 152 SMs issuing FMAs (enough CTAs per level,
+// cooperative groups for single large matrices) and at spending no FP64
+// instruction that is not part of the algorithm.
+#include "linalg.h"
+
+#include <algorithm>
+#include <cstdio>
+
+namespace hps {
+
+void Prof::begin(cudaStream_t st) {
+  if (!on) return;
+  cudaEventCreate(&pending);
+  cudaEventRecord(pending, st);
+}
+
+void Prof::end(int cls, double fl, cudaStream_t st) {
+  ++launches;
+  ++n[cls];
+  flops[cls] += fl;
+  if (!on || !pending) return;
+  cudaEvent_t e1;
+  cudaEventCreate(&e1);
+  cudaEventRecord(e1, st);
+  ev[cls].push_back(pending);
+  ev[cls].push_back(e1);
+  pending = nullptr;
+}
+
+void Prof::reset() {
+  for (int c = 0; c < K_COUNT; ++c) {
+    for (cudaEvent_t e : ev[c]) cudaEventDestroy(e);
+    ev[c].clear();
+    n[c] = 0;
+    flops[c] = 0.0;
+  }
+  if (pending) cudaEventDestroy(pending);
+  pending = nullptr;
+  launches = 0;
+}
+
+double Prof::ms(int cls) const {
+  double t = 0.0;
+  for (size_t i = 0; i + 1 < ev[cls].size(); i += 2) {
+    float m = 0.f;
+    if (cudaEventElapsedTime(&m, ev[cls][i], ev[cls][i + 1]) == cudaSuccess) t += m;
+  }
+  return t;
+}
+
+template <typename T> constexpr double fma_flops() { return 2.0; }
+template <> constexpr double fma_flops<cplx>() { return 8.0; }
+
+// ---------------------------------------------------------------- GEMM ----
+
+template <typename T> struct GemmTile;
+template <> struct GemmTile<double> { enum { BM = 64, BN = 64, BK = 16, TM = 4, TN = 4 }; };
+template <> struct GemmTile<cplx> { enum { BM = 32, BN = 32, BK = 16, TM = 2, TN = 2 }; };
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
+  constexpr int BM = GemmTile<T>::BM, BN = GemmTile<T>::BN, BK = GemmTile<T>::BK;
+  constexpr int TM = GemmTile<T>::TM, TN = GemmTile<T>::TN;
+  constexpr int RX = BM / TM;  // threads along M (16)
+  __shared__ T As[BK][BM];
+  __shared__ T Bs[BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % RX, ty = tid / RX;
+  for (int b = blockIdx.z; b < g.batch; b += gridDim.z) {
+    const T* A = g.A.item(b);
+    const T* B = g.B.item(b);
+    T* C = g.C.item(b);
+    const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+    T acc[TM][TN];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+      for (int c = 0; c < TN; ++c) acc[r][c] = T(0.0);
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+      for (int e = tid; e < BM * BK; e += 256) {
+        int i = e % BM, l = e / BM;
+        int gi = i0 + i, gl = k0 + l;
+        T v = T(0.0);
+        if (gi < g.M && gl < g.K)
+          v = A[(int64_t)g.arow.at(b, gi) + (int64_t)g.acol.at(b, gl) * g.A.ld];
+        As[l][i] = v;
+      }
+      for (int e = tid; e < BK * BN; e += 256) {
+        int l = e % BK, j = e / BK;
+        int gl = k0 + l, gj = j0 + j;
+        T v = T(0.0);
+        if (gl < g.K && gj < g.N) v = B[(int64_t)g.brow.at(b, gl) + (int64_t)gj * g.B.ld];
+        Bs[l][j] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T av[TM], bv[TN];
+#pragma unroll
+        for (int r = 0; r < TM; ++r) av[r] = As[kk][tx + RX * r];
+#pragma unroll
+        for (int c = 0; c < TN; ++c) bv[c] = Bs[kk][ty + (256 / RX) * c];
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+          for (int c = 0; c < TN; ++c) acc[r][c] = fmac(acc[r][c], av[r], bv[c]);
+      }
+      __syncthreads();
+    }
+    const bool use_beta = !is_zero(g.beta);
+#pragma unroll
+    for (int r = 0; r < TM; ++r) {
+      int gi = i0 + tx + RX * r;
+      if (gi >= g.M) continue;
+      int64_t ci = g.crow.at(b, gi);
+#pragma unroll
+      for (int c = 0; c < TN; ++c) {
+        int gj = j0 + ty + (256 / RX) * c;
+        if (gj >= g.N) continue;
+        T* p = C + ci + (int64_t)gj * g.C.ld;
+        T v = g.alpha * acc[r][c];
+        if (use_beta) v = fmac(v, g.beta, *p);
+        *p = v;
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  constexpr int BM = GemmTile<T>::BM, BN = GemmTile<T>::BN;
+  dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, std::min(g.batch, 65535));
+  if (pf) pf->begin(st);
+  k_gemm<T><<<grid, 256, 0, st>>>(g);
+  if (pf) pf->end(K_GEMM, fma_flops<T>() * g.M * (double)g.N * g.K * g.batch, st);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- fill -----
+
+template <typename T>
+__global__ void k_fill(BOp<T> C, int M, int N, int batch, T value, T diag) {
+  int64_t total = (int64_t)M * N;
+  for (int b = blockIdx.y; b < batch; b += gridDim.y) {
+    T* c = C.item(b);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      int i = (int)(e % M), j = (int)(e / M);
+      c[i + (int64_t)j * C.ld] = (i == j) ? diag : value;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t fill(BOp<T> C, int M, int N, int batch, T value, T diag, cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  int64_t total = (int64_t)M * N;
+  int bx = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  dim3 grid(bx, std::min(batch, 65535));
+  if (pf) pf->begin(st);
+  k_fill<T><<<grid, 256, 0, st>>>(C, M, N, batch, value, diag);
+  if (pf) pf->end(K_OTHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ panel LU ----
+
+// Factor the panel A[k0:n, k0:k0+nb) of each matrix with partial pivoting.
+// The rows [k0, n) are split into G contiguous chunks, one per CTA of the
+// matrix's group; each CTA holds its chunk of the panel in shared memory
+// (column-major, `ch` rows).  Per column: local argmax, publish candidate,
+// group barrier, global pick (largest |.|, lowest row on ties), swap, update.
+template <typename T, bool COOP>
+__global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int nb, int G, int* ipiv,
+                                                  int* info, unsigned* bars, T* pubv, double* pubm,
+                                                  int* pubr, unsigned* dev_err) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Ps = reinterpret_cast<T*>(smem_raw);
+  const int b = blockIdx.x / G, g = blockIdx.x % G;
+  const int rows = n - k0;
+  const int ch = (rows + G - 1) / G;
+  const int r0 = k0 + g * ch;                 // first global row of this chunk
+  const int rc = max(0, min(ch, n - r0));     // rows in this chunk
+  T* Ab = A.item(b);
+  const int lda = A.ld;
+  T* Wv = Ps + (size_t)ch * nb;               // winner row (nb)
+  T* Rv = Wv + nb;                            // old row j (nb)
+  __shared__ double red_m[32];
+  __shared__ int red_r[32];
+  __shared__ int s_piv;
+  __shared__ double s_pmag;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5;
+
+  for (int e = tid; e < rc * nb; e += nth) {
+    int r = e % rc, c = e / rc;
+    Ps[r + (size_t)c * ch] = Ab[(int64_t)(r0 + r) + (int64_t)(k0 + c) * lda];
+  }
+  __syncthreads();
+  T* pv = COOP ? pubv + (size_t)b * 2 * (G + 1) * nb : nullptr;
+  double* pm = COOP ? pubm + (size_t)b * 2 * G : nullptr;
+  int* pr = COOP ? pubr + (size_t)b * 2 * G : nullptr;
+  unsigned* bar = COOP ? bars + 2 * b : nullptr;
+
+  for (int jj = 0; jj < nb; ++jj) {
+    const int j = k0 + jj;
+    // local argmax over rows >= j in this chunk
+    double best = -1.0;
+    int brow = 0x7fffffff;
+    for (int r = max(0, j - r0) + tid; r < rc; r += nth) {
+      double m = mag1(Ps[r + (size_t)jj * ch]);
+      if (m > best || (m == best && r0 + r < brow)) { best = m; brow = r0 + r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double m2 = __shfl_down_sync(0xffffffffu, best, o);
+      int r2 = __shfl_down_sync(0xffffffffu, brow, o);
+      if (m2 > best || (m2 == best && r2 < brow)) { best = m2; brow = r2; }
+    }
+    if (lane == 0) { red_m[wid] = best; red_r[wid] = brow; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < (nth + 31) / 32; ++w)
+        if (red_m[w] > red_m[0] || (red_m[w] == red_m[0] && red_r[w] < red_r[0])) {
+          red_m[0] = red_m[w]; red_r[0] = red_r[w];
+        }
+    }
+    __syncthreads();
+    const bool own_j = (j >= r0 && j < r0 + rc);
+    if (COOP) {
+      const int slot = jj & 1;
+      if (tid == 0) { pm[slot * G + g] = red_m[0]; pr[slot * G + g] = red_r[0]; }
+      const int lr = red_r[0] - r0;
+      for (int c = tid; c < nb; c += nth) {
+        if (red_m[0] >= 0.0 && lr >= 0 && lr < rc)
+          pv[((size_t)slot * (G + 1) + g) * nb + c] = Ps[lr + (size_t)c * ch];
+        if (own_j) pv[((size_t)slot * (G + 1) + G) * nb + c] = Ps[(j - r0) + (size_t)c * ch];
+      }
+      if (!group_barrier(bar, G, dev_err)) return;
+      if (tid == 0) {
+        double bm = -1.0; int bg = 0, brr = 0x7fffffff;
+        for (int q = 0; q < G; ++q) {
+          double m = pm[slot * G + q]; int rr = pr[slot * G + q];
+          if (m > bm || (m == bm && rr < brr)) { bm = m; brr = rr; bg = q; }
+        }
+        s_piv = brr; s_pmag = bm; red_r[1] = bg;
+      }
+      __syncthreads();
+      const int bg = red_r[1];
+      for (int c = tid; c < nb; c += nth) {
+        Wv[c] = pv[((size_t)slot * (G + 1) + bg) * nb + c];
+        Rv[c] = pv[((size_t)slot * (G + 1) + G) * nb + c];
+      }
+    } else {
+      if (tid == 0) { s_piv = red_r[0]; s_pmag = red_m[0]; }
+      __syncthreads();
+      for (int c = tid; c < nb; c += nth) {
+        Wv[c] = Ps[(s_piv - r0) + (size_t)c * ch];
+        Rv[c] = Ps[(j - r0) + (size_t)c * ch];
+      }
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (g == 0 && tid == 0) {
+      ipiv[(int64_t)b * n + j] = p;
+      if (s_pmag == 0.0 && info[b] == 0) info[b] = j + 1;
+    }
+    // swap rows j and p inside the chunk(s)
+    for (int c = tid; c < nb; c += nth) {
+      if (own_j) Ps[(j - r0) + (size_t)c * ch] = Wv[c];
+      if (p != j && p >= r0 && p < r0 + rc) Ps[(p - r0) + (size_t)c * ch] = Rv[c];
+    }
+    __syncthreads();
+    // rank-1 update of the columns right of jj, rows below j
+    const bool zero_piv = (s_pmag == 0.0);
+    const T inv = zero_piv ? T(0.0) : recip(Wv[jj]);
+    const int rlo = max(0, j + 1 - r0);
+    const int nr = rc - rlo;
+    const int ncol = nb - jj - 1;
+    if (nr > 0 && ncol > 0) {
+      for (int e = tid; e < nr * ncol; e += nth) {
+        int r = rlo + e % nr, c = jj + 1 + e / nr;
+        T l = Ps[r + (size_t)jj * ch] * inv;
+        Ps[r + (size_t)c * ch] = fmsc(Ps[r + (size_t)c * ch], l, Wv[c]);
+      }
+    }
+    __syncthreads();
+    for (int r = rlo + tid; r < rc; r += nth) Ps[r + (size_t)jj * ch] = Ps[r + (size_t)jj * ch] * inv;
+    __syncthreads();
+  }
+  for (int e = tid; e < rc * nb; e += nth) {
+    int r = e % rc, c = e / rc;
+    Ab[(int64_t)(r0 + r) + (int64_t)(k0 + c) * lda] = Ps[r + (size_t)c * ch];
+  }
+}
+
+// Apply the panel's interchanges to every column outside the panel and
+// solve U12 = L11^{-1} A12 for the columns right of it.
+template <typename T>
+__global__ void __launch_bounds__(128) k_laswp_trsm(BOp<T> A, int n, int k0, int nb, const int* ipiv) {
+  extern __shared__ unsigned char smem_raw[];
+  T* L11 = reinterpret_cast<T*>(smem_raw);  // nb x nb, column-major
+  __shared__ int piv[64];
+  const int b = blockIdx.y;
+  T* Ab = A.item(b);
+  const int lda = A.ld;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    int r = e % nb, c = e / nb;
+    L11[e] = Ab[(int64_t)(k0 + r) + (int64_t)(k0 + c) * lda];
+  }
+  for (int e = threadIdx.x; e < nb; e += blockDim.x) piv[e] = ipiv[(int64_t)b * n + k0 + e];
+  __syncthreads();
+  const int ncols_out = n - nb;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncols_out; t += gridDim.x * blockDim.x) {
+    const int c = (t < k0) ? t : t + nb;
+    T* col = Ab + (int64_t)c * lda;
+    for (int jj = 0; jj < nb; ++jj) {
+      int p = piv[jj];
+      int j = k0 + jj;
+      if (p != j) { T tmp = col[j]; col[j] = col[p]; col[p] = tmp; }
+    }
+    if (c >= k0 + nb) {
+      T x[64];
+#pragma unroll 8
+      for (int jj = 0; jj < nb; ++jj) x[jj] = col[k0 + jj];
+      for (int jj = 1; jj < nb; ++jj) {
+        T s = x[jj];
+        for (int ii = 0; ii < jj; ++ii) s = fmsc(s, L11[jj + ii * nb], x[ii]);
+        x[jj] = s;
+      }
+#pragma unroll 8
+      for (int jj = 0; jj < nb; ++jj) col[k0 + jj] = x[jj];
+    }
+  }
+}
+
+__global__ void k_ipiv_to_perm(const int* ipiv, int* perm, int n, int batch) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const int* ip = ipiv + (int64_t)b * n;
+  int* pm = perm + (int64_t)b * n;
+  for (int i = 0; i < n; ++i) pm[i] = i;
+  for (int j = 0; j < n; ++j) {
+    int p = ip[j];
+    if (p != j) { int t = pm[j]; pm[j] = pm[p]; pm[p] = t; }
+  }
+}
+
+template <typename T> struct LuNB;
+template <> struct LuNB<double> { enum { NB = 32 }; };
+template <> struct LuNB<cplx> { enum { NB = 16 }; };
+
+template <typename T>
+int lu_group_size(int n, int batch, int num_sms) {
+  const int nb = LuNB<T>::NB;
+  // shared memory per CTA limited to ~96 KB for the panel chunk
+  const size_t cap = 96 * 1024;
+  int gmin = (int)((n * (size_t)nb * sizeof(T) + cap - 1) / cap);
+  int G = std::max(1, gmin);
+  // spread small batches over more CTAs so that all SMs get work
+  int want = (2 * num_sms) / std::max(batch, 1);
+  if (want > G) G = want;
+  int gmax = std::max(1, n / 32);
+  G = std::min(G, gmax);
+  // cooperative residency: keep batch * G within one wave
+  while (G > 1 && (int64_t)G * batch > 2 * num_sms) --G;
+  return std::max(G, 1);
+}
+
+template <typename T>
+size_t lu_pub_bytes(int n, int batch, int G) {
+  if (G <= 1) return 0;
+  const int nb = LuNB<T>::NB;
+  size_t v = (size_t)batch * 2 * (G + 1) * nb * sizeof(T);
+  size_t m = (size_t)batch * 2 * G * sizeof(double);
+  size_t r = (size_t)batch * 2 * G * sizeof(int);
+  return v + m + r + 256;
+}
+
+template <typename T>
+cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, unsigned* dev_err,
+                  int G, const LuWork& w, cudaStream_t st, Prof* pf) {
+  if (n <= 0 || batch <= 0) return cudaSuccess;
+  constexpr double F = fma_flops<T>();
+  const int nb0 = LuNB<T>::NB;
+  cudaError_t e;
+  for (int k0 = 0; k0 < n; k0 += nb0) {
+    const int nb = std::min(nb0, n - k0);
+    const int rows = n - k0;
+    int Gk = std::min(G, std::max(1, rows / 8));
+    const int ch = (rows + Gk - 1) / Gk;
+    size_t sm = ((size_t)ch * nb + 2 * nb) * sizeof(T);
+    double pfl = 0.0;  // panel: rank-1 updates and multipliers (FMA-equivalents)
+    for (int jj = 0; jj < nb; ++jj) {
+      const double below = (double)(n - (k0 + jj) - 1);
+      pfl += below * (nb - jj - 1) + below;
+    }
+    pfl *= F * batch;
+    if (pf) pf->begin(st);
+    if (Gk > 1) {
+      T* pubv = reinterpret_cast<T*>(w.pub);
+      double* pubm = reinterpret_cast<double*>(pubv + (size_t)batch * 2 * (G + 1) * nb0);
+      int* pubr = reinterpret_cast<int*>(pubm + (size_t)batch * 2 * G);
+      e = cudaFuncSetAttribute(k_lu_panel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)std::max<size_t>(sm, 1024));
+      if (e != cudaSuccess) return e;
+      BOp<T> Aa = A;
+      int nn = n, kk = k0, nbb = nb, GG = Gk;
+      unsigned* bars = w.bars;
+      void* args[] = {&Aa, &nn, &kk, &nbb, &GG, &ipiv, &info, &bars, &pubv, &pubm, &pubr, &dev_err};
+      e = cudaLaunchCooperativeKernel((void*)k_lu_panel<T, true>, dim3(batch * Gk), dim3(256), args,
+                                      sm, st);
+      if (e != cudaSuccess) return e;
+    } else {
+      e = cudaFuncSetAttribute(k_lu_panel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)std::max<size_t>(sm, 1024));
+      if (e != cudaSuccess) return e;
+      k_lu_panel<T, false><<<batch, 256, sm, st>>>(A, n, k0, nb, 1, ipiv, info, nullptr, nullptr,
+                                                   nullptr, nullptr, dev_err);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (pf) pf->end(K_LU_PANEL, pfl, st);
+    if (n > nb) {
+      const int ncols = n - nb;
+      int bx = std::min((ncols + 127) / 128, 1024);
+      size_t sm2 = (size_t)nb * nb * sizeof(T);
+      if (pf) pf->begin(st);
+      k_laswp_trsm<T><<<dim3(bx, batch), 128, sm2, st>>>(A, n, k0, nb, ipiv);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (pf) pf->end(K_LASWP_TRSM, F * 0.5 * nb * (nb - 1) * (double)(n - k0 - nb) * batch, st);
+    }
+    const int m2 = n - k0 - nb;
+    if (m2 > 0) {
+      GemmArgs<T> g;
+      g.M = m2; g.N = m2; g.K = nb; g.batch = batch;
+      g.A = shifted(A, (int64_t)(k0 + nb) + (int64_t)k0 * A.ld);
+      g.B = shifted(A, (int64_t)k0 + (int64_t)(k0 + nb) * A.ld);
+      g.C = shifted(A, (int64_t)(k0 + nb) + (int64_t)(k0 + nb) * A.ld);
+      g.alpha = T(-1.0); g.beta = T(1.0);
+      if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
+    }
+  }
+  if (pf) pf->begin(st);
+  k_ipiv_to_perm<<<(batch + 127) / 128, 128, 0, st>>>(ipiv, perm, n, batch);
+  if (pf) pf->end(K_OTHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ triangular solve ----
+
+template <typename T>
+__global__ void k_permute_rows(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrhs, int batch) {
+  int64_t total = (int64_t)n * nrhs;
+  for (int b = blockIdx.y; b < batch; b += gridDim.y) {
+    const T* s = src.item(b);
+    T* d = dst.item(b);
+    const int* pm = perm + (int64_t)b * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      int i = (int)(e % n), j = (int)(e / n);
+      d[i + (int64_t)j * dst.ld] = s[pm[i] + (int64_t)j * src.ld];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t permute_rows(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrhs, int batch,
+                         cudaStream_t st, Prof* pf) {
+  if (n <= 0 || nrhs <= 0 || batch <= 0) return cudaSuccess;
+  int64_t total = (int64_t)n * nrhs;
+  int bx = (int)std::min<int64_t>((total + 255) / 256, 2048);
+  if (pf) pf->begin(st);
+  k_permute_rows<T><<<dim3(bx, std::min(batch, 65535)), 256, 0, st>>>(src, dst, perm, n, nrhs, batch);
+  if (pf) pf->end(K_GATHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+// Diagonal-block solve: X[p0:p0+pb, :] <- L[p0:p0+pb, p0:p0+pb]^{-1} X (unit
+// lower, UPPER = false) or U^{-1} X (non-unit upper, UPPER = true).  One
+// thread per right-hand side column.
+template <typename T, bool UPPER>
+__global__ void __launch_bounds__(128) k_trsm_diag(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Ls = reinterpret_cast<T*>(smem_raw);  // pb x pb
+  const int b = blockIdx.y;
+  const T* Lb = LU.item(b);
+  T* Xb = X.item(b);
+  for (int e = threadIdx.x; e < pb * pb; e += blockDim.x) {
+    int r = e % pb, c = e / pb;
+    Ls[e] = Lb[(int64_t)(p0 + r) + (int64_t)(p0 + c) * LU.ld];
+  }
+  __syncthreads();
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrhs; j += gridDim.x * blockDim.x) {
+    T* col = Xb + (int64_t)j * X.ld + p0;
+    T x[32];
+    for (int r = 0; r < pb; ++r) x[r] = col[r];
+    if (!UPPER) {
+      for (int r = 1; r < pb; ++r) {
+        T s = x[r];
+        for (int c = 0; c < r; ++c) s = fmsc(s, Ls[r + c * pb], x[c]);
+        x[r] = s;
+      }
+    } else {
+      for (int r = pb - 1; r >= 0; --r) {
+        T s = x[r];
+        for (int c = r + 1; c < pb; ++c) s = fmsc(s, Ls[r + c * pb], x[c]);
+        T d = Ls[r + r * pb];
+        x[r] = is_zero(d) ? T(0.0) : s * recip(d);
+      }
+    }
+    for (int r = 0; r < pb; ++r) col[r] = x[r];
+  }
+}
+
+template <typename T>
+cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaStream_t st,
+                          Prof* pf) {
+  if (n <= 0 || nrhs <= 0 || batch <= 0) return cudaSuccess;
+  constexpr double F = fma_flops<T>();
+  const int pb0 = 32;
+  cudaError_t e;
+  const int bx = std::min((nrhs + 127) / 128, 1024);
+  // forward: unit lower
+  for (int p0 = 0; p0 < n; p0 += pb0) {
+    const int pb = std::min(pb0, n - p0);
+    if (pf) pf->begin(st);
+    k_trsm_diag<T, false><<<dim3(bx, batch), 128, (size_t)pb * pb * sizeof(T), st>>>(LU, X, p0, pb, nrhs, batch);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (pf) pf->end(K_TRSM_DIAG, F * 0.5 * pb * (pb - 1) * (double)nrhs * batch, st);
+    const int rest = n - p0 - pb;
+    if (rest > 0) {
+      GemmArgs<T> g;
+      g.M = rest; g.N = nrhs; g.K = pb; g.batch = batch;
+      g.A = shifted(LU, (int64_t)(p0 + pb) + (int64_t)p0 * LU.ld);
+      g.B = shifted(X, (int64_t)p0);
+      g.C = shifted(X, (int64_t)(p0 + pb));
+      g.alpha = T(-1.0); g.beta = T(1.0);
+      if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
+    }
+  }
+  // backward: non-unit upper
+  const int npan = (n + pb0 - 1) / pb0;
+  for (int pi = npan - 1; pi >= 0; --pi) {
+    const int p0 = pi * pb0;
+    const int pb = std::min(pb0, n - p0);
+    if (pf) pf->begin(st);
+    k_trsm_diag<T, true><<<dim3(bx, batch), 128, (size_t)pb * pb * sizeof(T), st>>>(LU, X, p0, pb, nrhs, batch);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (pf) pf->end(K_TRSM_DIAG, F * (0.5 * pb * (pb - 1) + pb) * (double)nrhs * batch, st);
+    if (p0 > 0) {
+      GemmArgs<T> g;
+      g.M = p0; g.N = nrhs; g.K = pb; g.batch = batch;
+      g.A = shifted(LU, (int64_t)p0 * LU.ld);
+      g.B = shifted(X, (int64_t)p0);
+      g.C = X;
+      g.alpha = T(-1.0); g.beta = T(1.0);
+      if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------- instantiation ----
+
+#define HPS_INST(T)                                                                              \
+  template cudaError_t gemm<T>(const GemmArgs<T>&, cudaStream_t, Prof*);                         \
+  template cudaError_t fill<T>(BOp<T>, int, int, int, T, T, cudaStream_t, Prof*);                \
+  template int lu_group_size<T>(int, int, int);                                                  \
+  template size_t lu_pub_bytes<T>(int, int, int);                                                \
+  template cudaError_t getrf<T>(BOp<T>, int, int, int*, int*, int*, unsigned*, int,              \
+                                const LuWork&, cudaStream_t, Prof*);                             \
+  template cudaError_t permute_rows<T>(BOp<T>, BOp<T>, const int*, int, int, int, cudaStream_t,  \
+                                       Prof*);                                                   \
+  template cudaError_t getrs_inplace<T>(BOp<T>, int, BOp<T>, int, int, cudaStream_t, Prof*);
+
+HPS_INST(double)
+HPS_INST(cplx)
+
+}  // namespace hps

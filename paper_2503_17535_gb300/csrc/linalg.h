@@ -1,0 +1,124 @@
+// Batched dense linear algebra on the device, FP64 and complex128.
+//
+// Column-major storage throughout.  A "batched operand" is either a device
+// array of per-item base pointers (ptrs != nullptr) or a base pointer plus a
+// fixed element stride between items; an element offset is then added to the
+// item's base.  All launchers enqueue on `st` and return a cudaError_t from
+// the launch check (nothing is synchronised here).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace hps {
+
+// Kernel classes for launch / flop accounting and optional event timing.
+enum KClass { K_GEMM = 0, K_LU_PANEL, K_LASWP_TRSM, K_TRSM_DIAG, K_ASSEMBLE, K_GATHER, K_DOWN,
+              K_OTHER, K_COUNT };
+
+// Launch accounting.  Every launch adds its class's algorithmic FP64 flops
+// (a complex multiply-add counts 8); with `on` set each launch is also
+// bracketed by CUDA events on its stream, summed by ms() after a sync.
+struct Prof {
+  bool on = false;
+  int64_t launches = 0;
+  int64_t n[K_COUNT] = {};
+  double flops[K_COUNT] = {};
+  std::vector<cudaEvent_t> ev[K_COUNT];
+  cudaEvent_t pending = nullptr;
+  void begin(cudaStream_t st);
+  void end(int cls, double fl, cudaStream_t st);
+  void reset();
+  double ms(int cls) const;
+  ~Prof() { reset(); }
+};
+
+template <typename T>
+struct BOp {
+  T* const* ptrs = nullptr;  // per-item bases (device array) or nullptr
+  T* base = nullptr;         // used when ptrs == nullptr
+  int64_t stride = 0;        // elements between items when ptrs == nullptr
+  int64_t off = 0;           // element offset added to every item's base
+  int ld = 0;                // leading dimension (column-major)
+  int div = 1;               // items b and b' share a base when b / div == b' / div
+  __host__ __device__ T* item(int b) const {
+    return (ptrs ? ptrs[b] : base + (int64_t)(b / div) * stride) + off;
+  }
+};
+
+template <typename T>
+BOp<T> bop(T* base, int64_t stride, int ld, int64_t off = 0) {
+  BOp<T> o; o.base = base; o.stride = stride; o.ld = ld; o.off = off; return o;
+}
+template <typename T>
+BOp<T> bopp(T* const* ptrs, int ld, int64_t off = 0) {
+  BOp<T> o; o.ptrs = ptrs; o.ld = ld; o.off = off; return o;
+}
+template <typename T>
+BOp<T> shifted(BOp<T> o, int64_t extra) { o.off += extra; return o; }
+template <typename T>
+BOp<T> grouped(BOp<T> o, int div) { o.div = div; return o; }
+
+// Optional row/column index maps for gathered GEMM operands.  A map is an
+// array [period][len]; batch item b uses row b % period.  nullptr = identity.
+struct IMap {
+  const int* idx = nullptr;
+  int len = 0;      // entries per period row
+  int period = 1;
+  __device__ int at(int b, int i) const { return idx ? idx[(b % period) * len + i] : i; }
+};
+
+// C(crow(i), j) = alpha * sum_l A(arow(i), acol(l)) * B(brow(l), j) + beta * C(crow(i), j)
+template <typename T>
+struct GemmArgs {
+  int M = 0, N = 0, K = 0, batch = 0;
+  BOp<T> A, B, C;
+  IMap arow, acol, brow, crow;
+  T alpha = T(1.0), beta = T(0.0);
+};
+
+template <typename T>
+cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf);
+
+// LU with partial pivoting of `batch` n x n matrices (in place), LAPACK
+// semantics: ipiv[j] = row swapped with row j (0-based), perm = the row
+// permutation P with P A = L U (perm[i] = original row of row i).
+// G > 1 spreads each matrix over G co-resident CTAs (cooperative launch).
+// ipiv/perm are int arrays of `batch * n` (item stride n).  info[b] = first
+// zero-pivot column + 1 (0 if none).  dev_err receives DEV_ERR_* bits.
+struct LuWork {
+  unsigned* bars = nullptr;   // 2 * batch barrier words (zeroed)
+  void* pub = nullptr;        // publish buffer for G > 1
+  size_t pub_bytes = 0;
+};
+
+template <typename T>
+int lu_group_size(int n, int batch, int num_sms);
+
+template <typename T>
+size_t lu_pub_bytes(int n, int batch, int G);
+
+template <typename T>
+cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, unsigned* dev_err,
+                  int G, const LuWork& w, cudaStream_t st, Prof* pf);
+
+// Solve (P^T L U) X = R in place for X given perm-gathered rows:
+//   permute_rows: X(i, j) = R(perm[i], j)
+//   getrs_inplace: X <- U^{-1} L^{-1} X
+template <typename T>
+cudaError_t permute_rows(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrhs, int batch,
+                         cudaStream_t st, Prof* pf);
+
+template <typename T>
+cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaStream_t st,
+                          Prof* pf);
+
+// C = alpha * C + beta (identity added on the diagonal when diag != 0) helpers
+template <typename T>
+cudaError_t fill(BOp<T> C, int M, int N, int batch, T value, T diag, cudaStream_t st, Prof* pf);
+
+}  // namespace hps

@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function declared in include/hps.h, computes node coordinates in the
+documented orders, and rejects invalid arguments."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2503_17535_gb300 as P
+    from paper_2503_17535_gb300 import _capi
+    if not os.path.exists(_capi.LIB_PATH):
+        from paper_2503_17535_gb300 import build
+        build.build()
+    return P
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "hps.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"\b(hps_[a-z_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(pkg):
+    from paper_2503_17535_gb300 import _capi
+    lib = ctypes.CDLL(_capi.LIB_PATH)
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(_capi.EXPORTED) == names
+
+
+def test_error_strings(pkg):
+    for s in (0, -1, -2, -3, -4, -5):
+        assert pkg.hps_error_string(s).startswith("HPS_")
+
+
+@pytest.mark.parametrize("dim,L,p", [(2, 0, 8), (2, 2, 8), (2, 1, 16), (3, 0, 6), (3, 1, 8), (3, 2, 6)])
+def test_nodes_match_oracle_geometry(pkg, dim, L, p):
+    from oracle import geometry as geo
+    lo = (-1.0, -0.5, 0.25)[:dim]
+    hi = tuple(x + 1.5 for x in lo)
+    t = pkg.uniform_tree(dim, L, lo, hi)
+    leaf, bdry = pkg.hps_nodes(t, p, p - 2)
+    assert np.allclose(leaf, geo.leaf_nodes(dim, lo, hi, L, p), atol=1e-14)
+    assert np.allclose(bdry, geo.root_boundary_points(dim, lo, hi, L, p - 2), atol=1e-14)
+
+
+def test_invalid_arguments_are_rejected(pkg):
+    t = pkg.uniform_tree(2, 2)
+    with pytest.raises(pkg.HPSError) as e:
+        pkg.hps_sizes(t, 8, 5)          # q != p - 2
+    assert e.value.status == -1
+    t.n_leaves = 7
+    with pytest.raises(pkg.HPSError):
+        pkg.hps_sizes(t, 8, 6)
+    t = pkg.uniform_tree(2, 1, (0, 0), (1, 2))   # leaves must be squares
+    with pytest.raises(pkg.HPSError):
+        pkg.hps_nodes(t, 8, 6)
+    t = pkg.uniform_tree(3, 1)
+    # ItI is 2D only: rejected before any device work
+    with pytest.raises(pkg.HPSError) as e:
+        pkg.hps_build(t, 8, 6, pkg.HPS_ITI, eta=1.0)
+    assert e.value.status == -1
+
+
+def test_sizes(pkg):
+    assert pkg.hps_sizes(pkg.uniform_tree(2, 6), 16, 14) == (4096, 256, 4 * 14 * 64)
+    assert pkg.hps_sizes(pkg.uniform_tree(3, 3), 8, 6) == (512, 512, 6 * 36 * 64)
