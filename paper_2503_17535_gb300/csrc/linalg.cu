@@ -132,13 +132,151 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
   }
 }
 
+// Complex GEMM by the 3M method: with A = Ar + i Ai and B = Br + i Bi, the
+// real products P1 = Ar Br, P2 = Ai Bi and P3 = (Ar + Ai)(Br + Bi) give
+// C = (P1 - P2) + i (P3 - P1 - P2).  Each complex multiply-add costs three
+// real FMAs instead of four on the FP64 pipe; the sums Ar + Ai and Br + Bi
+// are formed once per element when the tile is staged in shared memory.
+__global__ void __launch_bounds__(256) k_gemm_c3m(GemmArgs<cplx> g) {
+  constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2, RX = 16;
+  __shared__ double Ar[BK][BM], Ai[BK][BM], As[BK][BM];
+  __shared__ double Br[BK][BN], Bi[BK][BN], Bs[BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % RX, ty = tid / RX;
+  for (int b = blockIdx.z; b < g.batch; b += gridDim.z) {
+    const cplx* A = g.A.item(b);
+    const cplx* B = g.B.item(b);
+    cplx* C = g.C.item(b);
+    const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+    double p1[TM][TN], p2[TM][TN], p3[TM][TN];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+      for (int c = 0; c < TN; ++c) p1[r][c] = p2[r][c] = p3[r][c] = 0.0;
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+      for (int e = tid; e < BM * BK; e += 256) {
+        const int i = e % BM, l = e / BM;
+        const int gi = i0 + i, gl = k0 + l;
+        cplx v(0.0, 0.0);
+        if (gi < g.M && gl < g.K) v = A[(int64_t)g.arow.at(b, gi) + (int64_t)g.acol.at(b, gl) * g.A.ld];
+        Ar[l][i] = v.re; Ai[l][i] = v.im; As[l][i] = v.re + v.im;
+      }
+      for (int e = tid; e < BK * BN; e += 256) {
+        const int l = e % BK, j = e / BK;
+        const int gl = k0 + l, gj = j0 + j;
+        cplx v(0.0, 0.0);
+        if (gl < g.K && gj < g.N) v = B[(int64_t)g.brow.at(b, gl) + (int64_t)gj * g.B.ld];
+        Br[l][j] = v.re; Bi[l][j] = v.im; Bs[l][j] = v.re + v.im;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        double ar[TM], ai[TM], as[TM], br[TN], bi[TN], bs[TN];
+#pragma unroll
+        for (int r = 0; r < TM; ++r) { ar[r] = Ar[kk][tx + RX * r]; ai[r] = Ai[kk][tx + RX * r]; as[r] = As[kk][tx + RX * r]; }
+#pragma unroll
+        for (int c = 0; c < TN; ++c) { br[c] = Br[kk][ty + 16 * c]; bi[c] = Bi[kk][ty + 16 * c]; bs[c] = Bs[kk][ty + 16 * c]; }
+#pragma unroll
+        for (int r = 0; r < TM; ++r)
+#pragma unroll
+          for (int c = 0; c < TN; ++c) {
+            p1[r][c] = fma(ar[r], br[c], p1[r][c]);
+            p2[r][c] = fma(ai[r], bi[c], p2[r][c]);
+            p3[r][c] = fma(as[r], bs[c], p3[r][c]);
+          }
+      }
+      __syncthreads();
+    }
+    const bool use_beta = !is_zero(g.beta);
+#pragma unroll
+    for (int r = 0; r < TM; ++r) {
+      const int gi = i0 + tx + RX * r;
+      if (gi >= g.M) continue;
+      const int64_t ci = g.crow.at(b, gi);
+#pragma unroll
+      for (int c = 0; c < TN; ++c) {
+        const int gj = j0 + ty + 16 * c;
+        if (gj >= g.N) continue;
+        cplx* p = C + ci + (int64_t)gj * g.C.ld;
+        const cplx acc(p1[r][c] - p2[r][c], p3[r][c] - p1[r][c] - p2[r][c]);
+        cplx v = g.alpha * acc;
+        if (use_beta) v = fmac(v, g.beta, *p);
+        *p = v;
+      }
+    }
+  }
+}
+
+template <typename T> struct UseC3M { static constexpr bool value = false; };
+template <> struct UseC3M<cplx> { static constexpr bool value = true; };
+
+// Skinny variant for N <= 8 right-hand sides (the solve path): one thread
+// per output row, B chunks staged in shared memory, A read column by column
+// (coalesced along the rows).
+template <typename T>
+__global__ void __launch_bounds__(128) k_gemm_skinny(GemmArgs<T> g) {
+  constexpr int KC = 32;
+  __shared__ T Bs[KC][8];
+  const int tid = threadIdx.x;
+  for (int b = blockIdx.z; b < g.batch; b += gridDim.z) {
+    const T* A = g.A.item(b);
+    const T* B = g.B.item(b);
+    T* C = g.C.item(b);
+    const int i = blockIdx.x * 128 + tid;
+    const bool act = i < g.M;
+    const int64_t ar = act ? g.arow.at(b, i) : 0;
+    T acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = T(0.0);
+    for (int k0 = 0; k0 < g.K; k0 += KC) {
+      const int kc = min(KC, g.K - k0);
+      __syncthreads();
+      for (int e = tid; e < KC * 8; e += 128) {
+        const int l = e % KC, c = e / KC;
+        Bs[l][c] = (l < kc && c < g.N) ? B[(int64_t)g.brow.at(b, k0 + l) + (int64_t)c * g.B.ld] : T(0.0);
+      }
+      __syncthreads();
+      if (act) {
+        for (int l = 0; l < kc; ++l) {
+          const T a = A[ar + (int64_t)g.acol.at(b, k0 + l) * g.A.ld];
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c < g.N) acc[c] = fmac(acc[c], a, Bs[l][c]);
+        }
+      }
+    }
+    if (act) {
+      const int64_t ci = g.crow.at(b, i);
+      const bool use_beta = !is_zero(g.beta);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (c >= g.N) break;
+        T* p = C + ci + (int64_t)c * g.C.ld;
+        T v = g.alpha * acc[c];
+        if (use_beta) v = fmac(v, g.beta, *p);
+        *p = v;
+      }
+    }
+  }
+}
+
 template <typename T>
 cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   constexpr int BM = GemmTile<T>::BM, BN = GemmTile<T>::BN;
-  dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, std::min(g.batch, 65535));
   if (pf) pf->begin(st);
-  k_gemm<T><<<grid, 256, 0, st>>>(g);
+  if (g.N <= 8) {
+    dim3 grid((g.M + 127) / 128, 1, std::min(g.batch, 65535));
+    k_gemm_skinny<T><<<grid, 128, 0, st>>>(g);
+  } else if (UseC3M<T>::value) {
+    dim3 grid((g.M + 31) / 32, (g.N + 31) / 32, std::min(g.batch, 65535));
+    k_gemm_c3m<<<grid, 256, 0, st>>>(*reinterpret_cast<const GemmArgs<cplx>*>(&g));
+    if (pf) pf->end(K_GEMM, 6.0 * g.M * (double)g.N * g.K * g.batch, st);
+    return cudaGetLastError();
+  } else {
+    dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, std::min(g.batch, 65535));
+    k_gemm<T><<<grid, 256, 0, st>>>(g);
+  }
   if (pf) pf->end(K_GEMM, fma_flops<T>() * g.M * (double)g.N * g.K * g.batch, st);
   return cudaGetLastError();
 }
@@ -244,19 +382,35 @@ __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int n
         if (own_j) pv[((size_t)slot * (G + 1) + G) * nb + c] = Ps[(j - r0) + (size_t)c * ch];
       }
       if (!group_barrier(bar, G, dev_err)) return;
-      if (tid == 0) {
-        double bm = -1.0; int bg = 0, brr = 0x7fffffff;
-        for (int q = 0; q < G; ++q) {
-          double m = pm[slot * G + q]; int rr = pr[slot * G + q];
-          if (m > bm || (m == bm && rr < brr)) { bm = m; brr = rr; bg = q; }
+      // pick the global pivot: warp 0 reduces the G published candidates
+      // (loads bypass L1: the values were written by other CTAs)
+      if (wid == 0) {
+        double bm = -1.0;
+        int brr = 0x7fffffff, bg = 0;
+        for (int q2 = lane; q2 < G; q2 += 32) {
+          const double m = __ldcg(&pm[slot * G + q2]);
+          const int rr = __ldcg(&pr[slot * G + q2]);
+          if (m > bm || (m == bm && rr < brr)) { bm = m; brr = rr; bg = q2; }
         }
-        s_piv = brr; s_pmag = bm; red_r[1] = bg;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double m2 = __shfl_down_sync(0xffffffffu, bm, o);
+          const int r2 = __shfl_down_sync(0xffffffffu, brr, o);
+          const int g2 = __shfl_down_sync(0xffffffffu, bg, o);
+          if (m2 > bm || (m2 == bm && r2 < brr)) { bm = m2; brr = r2; bg = g2; }
+        }
+        if (lane == 0) { s_piv = brr; s_pmag = bm; red_r[1] = bg; }
       }
       __syncthreads();
       const int bg = red_r[1];
-      for (int c = tid; c < nb; c += nth) {
-        Wv[c] = pv[((size_t)slot * (G + 1) + bg) * nb + c];
-        Rv[c] = pv[((size_t)slot * (G + 1) + G) * nb + c];
+      const double* wsrc = reinterpret_cast<const double*>(pv + ((size_t)slot * (G + 1) + bg) * nb);
+      const double* rsrc = reinterpret_cast<const double*>(pv + ((size_t)slot * (G + 1) + G) * nb);
+      double* wdst = reinterpret_cast<double*>(Wv);
+      double* rdst = reinterpret_cast<double*>(Rv);
+      constexpr int DW = sizeof(T) / sizeof(double);
+      for (int c = tid; c < nb * DW; c += nth) {
+        wdst[c] = __ldcg(&wsrc[c]);
+        rdst[c] = __ldcg(&rsrc[c]);
       }
     } else {
       if (tid == 0) { s_piv = red_r[0]; s_pmag = red_m[0]; }
@@ -367,7 +521,7 @@ int lu_group_size(int n, int batch, int num_sms) {
   // spread small batches over more CTAs so that all SMs get work
   int want = (2 * num_sms) / std::max(batch, 1);
   if (want > G) G = want;
-  int gmax = std::max(1, n / 32);
+  int gmax = std::max(1, n / 64);
   G = std::min(G, gmax);
   // cooperative residency: keep batch * G within one wave
   while (G > 1 && (int64_t)G * batch > 2 * num_sms) --G;
@@ -483,39 +637,49 @@ cudaError_t permute_rows(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrh
 }
 
 // Diagonal-block solve: X[p0:p0+pb, :] <- L[p0:p0+pb, p0:p0+pb]^{-1} X (unit
-// lower, UPPER = false) or U^{-1} X (non-unit upper, UPPER = true).  One
-// thread per right-hand side column.
+// lower, UPPER = false) or U^{-1} X (non-unit upper, UPPER = true).  One warp
+// per right-hand side column, lane r owning row r (pb <= 32): each step
+// broadcasts the solved entry with a shuffle and the lanes below (above)
+// update their row, so a single column is solved in pb dependent steps.
+__device__ inline double shfl_val(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ inline cplx shfl_val(cplx v, int src) {
+  return cplx(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+}
+
 template <typename T, bool UPPER>
 __global__ void __launch_bounds__(128) k_trsm_diag(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch) {
   extern __shared__ unsigned char smem_raw[];
   T* Ls = reinterpret_cast<T*>(smem_raw);  // pb x pb
-  const int b = blockIdx.y;
-  const T* Lb = LU.item(b);
-  T* Xb = X.item(b);
-  for (int e = threadIdx.x; e < pb * pb; e += blockDim.x) {
-    int r = e % pb, c = e / pb;
-    Ls[e] = Lb[(int64_t)(p0 + r) + (int64_t)(p0 + c) * LU.ld];
-  }
-  __syncthreads();
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrhs; j += gridDim.x * blockDim.x) {
-    T* col = Xb + (int64_t)j * X.ld + p0;
-    T x[32];
-    for (int r = 0; r < pb; ++r) x[r] = col[r];
-    if (!UPPER) {
-      for (int r = 1; r < pb; ++r) {
-        T s = x[r];
-        for (int c = 0; c < r; ++c) s = fmsc(s, Ls[r + c * pb], x[c]);
-        x[r] = s;
-      }
-    } else {
-      for (int r = pb - 1; r >= 0; --r) {
-        T s = x[r];
-        for (int c = r + 1; c < pb; ++c) s = fmsc(s, Ls[r + c * pb], x[c]);
-        T d = Ls[r + r * pb];
-        x[r] = is_zero(d) ? T(0.0) : s * recip(d);
-      }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int b = blockIdx.y; b < batch; b += gridDim.y) {
+    const T* Lb = LU.item(b);
+    T* Xb = X.item(b);
+    __syncthreads();
+    for (int e = threadIdx.x; e < pb * pb; e += blockDim.x) {
+      int r = e % pb, c = e / pb;
+      Ls[e] = Lb[(int64_t)(p0 + r) + (int64_t)(p0 + c) * LU.ld];
     }
-    for (int r = 0; r < pb; ++r) col[r] = x[r];
+    __syncthreads();
+    for (int j = blockIdx.x * nw + wid; j < nrhs; j += gridDim.x * nw) {
+      T* col = Xb + (int64_t)j * X.ld + p0;
+      T x = lane < pb ? col[lane] : T(0.0);
+      if (!UPPER) {
+        for (int c = 0; c < pb - 1; ++c) {
+          const T xc = shfl_val(x, c);
+          if (lane > c && lane < pb) x = fmsc(x, Ls[lane + c * pb], xc);
+        }
+      } else {
+        for (int c = pb - 1; c >= 0; --c) {
+          if (lane == c) {
+            const T d = Ls[c + c * pb];
+            x = is_zero(d) ? T(0.0) : x * recip(d);
+          }
+          const T xc = shfl_val(x, c);
+          if (lane < c) x = fmsc(x, Ls[lane + c * pb], xc);
+        }
+      }
+      if (lane < pb) col[lane] = x;
+    }
   }
 }
 
@@ -526,12 +690,13 @@ cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaS
   constexpr double F = fma_flops<T>();
   const int pb0 = 32;
   cudaError_t e;
-  const int bx = std::min((nrhs + 127) / 128, 1024);
+  const int bx = std::min((nrhs + 3) / 4, 1024);
+  const int by = std::min(batch, 65535);
   // forward: unit lower
   for (int p0 = 0; p0 < n; p0 += pb0) {
     const int pb = std::min(pb0, n - p0);
     if (pf) pf->begin(st);
-    k_trsm_diag<T, false><<<dim3(bx, batch), 128, (size_t)pb * pb * sizeof(T), st>>>(LU, X, p0, pb, nrhs, batch);
+    k_trsm_diag<T, false><<<dim3(bx, by), 128, (size_t)pb * pb * sizeof(T), st>>>(LU, X, p0, pb, nrhs, batch);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (pf) pf->end(K_TRSM_DIAG, F * 0.5 * pb * (pb - 1) * (double)nrhs * batch, st);
     const int rest = n - p0 - pb;
@@ -551,7 +716,7 @@ cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaS
     const int p0 = pi * pb0;
     const int pb = std::min(pb0, n - p0);
     if (pf) pf->begin(st);
-    k_trsm_diag<T, true><<<dim3(bx, batch), 128, (size_t)pb * pb * sizeof(T), st>>>(LU, X, p0, pb, nrhs, batch);
+    k_trsm_diag<T, true><<<dim3(bx, by), 128, (size_t)pb * pb * sizeof(T), st>>>(LU, X, p0, pb, nrhs, batch);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (pf) pf->end(K_TRSM_DIAG, F * (0.5 * pb * (pb - 1) + pb) * (double)nrhs * batch, st);
     if (p0 > 0) {
