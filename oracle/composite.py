@@ -179,3 +179,120 @@ def solve_iti(p, L, lo, hi, a, b, c, f, g, eta):
                 A[r0:r0 + nown, mb * npl:(mb + 1) * npl] += Ps @ QH[sb * q:(sb + 1) * q, :]
     sol = np.linalg.solve(A, rhs)
     return sol.reshape(nl, npl)
+
+
+def solve_dtn_adaptive(leaves, p, lo, hi, a, b, c, f, g):
+    """O2 on an adaptive 2:1 octree (Section 4.2 discretisation): the
+    composite system with interface unknowns on the coarser panel of every
+    leaf-leaf interface.  A fine leaf takes its face data from the coarse
+    panel by interpolation; the flux balance on a coarse panel adds the
+    coarse side's normal derivative and the L2 projection of the four fine
+    sides' normal derivatives."""
+    from . import adaptive as ad
+    q = p - 2
+    q2 = q * q
+    leaves = ad.sort_leaves(leaves)
+    C2F, F2C = ad.panel_projections(q)
+    side_len = float(hi[0] - lo[0])
+    ops = lf.reference_ops(3, p, q)
+    Ie, Ii = ops["Ie"], ops["Ii"]
+    ni = len(Ii)
+    leafset = {(lv, tuple(ix)): n for n, (lv, ix) in enumerate(leaves)}
+    internal = set()
+    for lv, ix in leaves:
+        internal.update(ad._ancestors(lv, ix))
+    root, _ = ad.build_tree(leaves)
+    root_off, o = {}, 0
+    for fi in range(6):
+        for pn in root.faces[fi]:
+            root_off[(fi, pn)] = o
+            o += q2
+    # classify every leaf face: ('root', off) | ('panel', key) | ('coarse', key, quadrant)
+    faces_of = []
+    panel_ids = {}
+    for lv, ix in leaves:
+        row = []
+        n1 = 2 ** lv
+        for fi, (axis, sd) in enumerate(ad.FACES):
+            t1, t2 = ad.tangential(axis)
+            pos = (ix[t1], ix[t2])
+            nb = list(ix)
+            nb[axis] += 1 if sd else -1
+            if nb[axis] < 0 or nb[axis] >= n1:
+                row.append(("root", root_off[(fi, (lv, pos))]))
+                continue
+            nb = tuple(nb)
+            plane = ix[axis] + sd
+            if (lv, nb) in leafset or (lv, nb) in internal:
+                key = (lv, axis, plane, pos)
+                panel_ids.setdefault(key, len(panel_ids))
+                row.append(("panel", key))
+            else:
+                # the neighbour is a coarser leaf: use its face panel
+                key = (lv - 1, axis, plane // 2, (pos[0] // 2, pos[1] // 2))
+                panel_ids.setdefault(key, len(panel_ids))
+                quad = (pos[0] & 1) + 2 * (pos[1] & 1)
+                row.append(("coarse", key, quad))
+        faces_of.append(row)
+    nl = len(leaves)
+    npan = len(panel_ids)
+    N = nl * ni + npan * q2
+    dt = np.result_type(f, g, float)
+    A = np.zeros((N, N), dt)
+    rhs = np.zeros(N, dt)
+    og = nl * ni
+
+    def gmap(ent):
+        """(columns into the unknown vector, matrix) so that g_face = M x[cols],
+        or the root data."""
+        if ent[0] == "root":
+            return None, g[ent[1]:ent[1] + q2]
+        pid = panel_ids[ent[1]]
+        cols = np.arange(og + pid * q2, og + (pid + 1) * q2)
+        if ent[0] == "panel":
+            return cols, np.eye(q2)
+        return cols, C2F[ent[2] * q2:(ent[2] + 1) * q2]
+
+    for n, (lv, ix) in enumerate(leaves):
+        hlen = side_len / 2 ** lv
+        P_, Q = lf.dtn_P_Q(3, p, q, hlen)
+        Lm = lf.assemble_L(3, p, hlen, a[n], [bk[n] for bk in b], c[n])
+        LieP = Lm[np.ix_(Ii, Ie)] @ P_
+        r0 = n * ni
+        A[r0:r0 + ni, r0:r0 + ni] = Lm[np.ix_(Ii, Ii)]
+        rhs[r0:r0 + ni] = f[n][Ii]
+        QP = Q[:, Ie] @ P_
+        QI = Q[:, Ii]
+        for fi, ent in enumerate(faces_of[n]):
+            cols, M = gmap(ent)
+            blk = LieP[:, fi * q2:(fi + 1) * q2]
+            if cols is None:
+                rhs[r0:r0 + ni] -= blk @ M
+            else:
+                A[r0:r0 + ni, cols] += blk @ M
+        # flux rows: this leaf's normal derivative on every non-root face
+        for fi, ent in enumerate(faces_of[n]):
+            if ent[0] == "root":
+                continue
+            pid = panel_ids[ent[1]]
+            rows = slice(og + pid * q2, og + (pid + 1) * q2)
+            Wr = np.eye(q2) if ent[0] == "panel" else F2C[:, ent[2] * q2:(ent[2] + 1) * q2]
+            A[rows, r0:r0 + ni] += Wr @ QI[fi * q2:(fi + 1) * q2]
+            for fj, ent2 in enumerate(faces_of[n]):
+                cols, M = gmap(ent2)
+                blk = Wr @ QP[fi * q2:(fi + 1) * q2, fj * q2:(fj + 1) * q2]
+                if cols is None:
+                    rhs[rows] -= blk @ M
+                else:
+                    A[rows, cols] += blk @ M
+    sol = np.linalg.solve(A, rhs)
+    u = np.zeros((nl, p ** 3), dt)
+    for n in range(nl):
+        P_, _ = lf.dtn_P_Q(3, p, q, side_len / 2 ** leaves[n][0])
+        gl = np.zeros(6 * q2, dt)
+        for fi, ent in enumerate(faces_of[n]):
+            cols, M = gmap(ent)
+            gl[fi * q2:(fi + 1) * q2] = M if cols is None else M @ sol[cols]
+        u[n, Ie] = P_ @ gl
+        u[n, Ii] = sol[n * ni:(n + 1) * ni]
+    return u
