@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int n
   __shared__ int red_r[32];
   __shared__ int s_piv;
   __shared__ double s_pmag;
+  __shared__ double s_inv_raw[2];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5;
 
@@ -432,21 +433,25 @@ __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int n
       if (p != j && p >= r0 && p < r0 + rc) Ps[(p - r0) + (size_t)c * ch] = Rv[c];
     }
     __syncthreads();
-    // rank-1 update of the columns right of jj, rows below j
-    const bool zero_piv = (s_pmag == 0.0);
-    const T inv = zero_piv ? T(0.0) : recip(Wv[jj]);
+    // multipliers (one reciprocal of the pivot per column, computed once),
+    // then the rank-1 update of the columns right of jj, rows below j
+    if (tid == 0) {
+      const T inv0 = (s_pmag == 0.0) ? T(0.0) : recip(Wv[jj]);
+      *reinterpret_cast<T*>(s_inv_raw) = inv0;
+    }
+    __syncthreads();
+    const T inv = *reinterpret_cast<const T*>(s_inv_raw);
     const int rlo = max(0, j + 1 - r0);
     const int nr = rc - rlo;
     const int ncol = nb - jj - 1;
+    for (int r = rlo + tid; r < rc; r += nth) Ps[r + (size_t)jj * ch] = Ps[r + (size_t)jj * ch] * inv;
+    __syncthreads();
     if (nr > 0 && ncol > 0) {
       for (int e = tid; e < nr * ncol; e += nth) {
         int r = rlo + e % nr, c = jj + 1 + e / nr;
-        T l = Ps[r + (size_t)jj * ch] * inv;
-        Ps[r + (size_t)c * ch] = fmsc(Ps[r + (size_t)c * ch], l, Wv[c]);
+        Ps[r + (size_t)c * ch] = fmsc(Ps[r + (size_t)c * ch], Ps[r + (size_t)jj * ch], Wv[c]);
       }
     }
-    __syncthreads();
-    for (int r = rlo + tid; r < rc; r += nth) Ps[r + (size_t)jj * ch] = Ps[r + (size_t)jj * ch] * inv;
     __syncthreads();
   }
   for (int e = tid; e < rc * nb; e += nth) {
@@ -649,7 +654,8 @@ __device__ inline cplx shfl_val(cplx v, int src) {
 template <typename T, bool UPPER>
 __global__ void __launch_bounds__(128) k_trsm_diag(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch) {
   extern __shared__ unsigned char smem_raw[];
-  T* Ls = reinterpret_cast<T*>(smem_raw);  // pb x pb
+  T* Ls = reinterpret_cast<T*>(smem_raw);  // pb x pb, then pb reciprocals of the diagonal
+  T* Dinv = Ls + pb * pb;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int b = blockIdx.y; b < batch; b += gridDim.y) {
     const T* Lb = LU.item(b);
@@ -659,6 +665,12 @@ __global__ void __launch_bounds__(128) k_trsm_diag(BOp<T> LU, BOp<T> X, int p0, 
       int r = e % pb, c = e / pb;
       Ls[e] = Lb[(int64_t)(p0 + r) + (int64_t)(p0 + c) * LU.ld];
     }
+    __syncthreads();
+    if (UPPER)
+      for (int r = threadIdx.x; r < pb; r += blockDim.x) {
+        const T d = Ls[r + r * pb];
+        Dinv[r] = is_zero(d) ? T(0.0) : recip(d);
+      }
     __syncthreads();
     for (int j = blockIdx.x * nw + wid; j < nrhs; j += gridDim.x * nw) {
       T* col = Xb + (int64_t)j * X.ld + p0;
@@ -670,10 +682,7 @@ __global__ void __launch_bounds__(128) k_trsm_diag(BOp<T> LU, BOp<T> X, int p0, 
         }
       } else {
         for (int c = pb - 1; c >= 0; --c) {
-          if (lane == c) {
-            const T d = Ls[c + c * pb];
-            x = is_zero(d) ? T(0.0) : x * recip(d);
-          }
+          if (lane == c) x = x * Dinv[c];
           const T xc = shfl_val(x, c);
           if (lane < c) x = fmsc(x, Ls[lane + c * pb], xc);
         }
@@ -683,6 +692,64 @@ __global__ void __launch_bounds__(128) k_trsm_diag(BOp<T> LU, BOp<T> X, int p0, 
   }
 }
 
+// Many right-hand sides: one thread per column, the block's pb x pb diagonal
+// block staged once in shared memory for up to 128 columns.
+template <typename T, bool UPPER>
+__global__ void __launch_bounds__(128) k_trsm_diag_cols(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Ls = reinterpret_cast<T*>(smem_raw);
+  T* Dinv = Ls + pb * pb;
+  for (int b = blockIdx.y; b < batch; b += gridDim.y) {
+    const T* Lb = LU.item(b);
+    T* Xb = X.item(b);
+    __syncthreads();
+    for (int e = threadIdx.x; e < pb * pb; e += blockDim.x) {
+      int r = e % pb, c = e / pb;
+      Ls[e] = Lb[(int64_t)(p0 + r) + (int64_t)(p0 + c) * LU.ld];
+    }
+    __syncthreads();
+    if (UPPER)
+      for (int r = threadIdx.x; r < pb; r += blockDim.x) {
+        const T d = Ls[r + r * pb];
+        Dinv[r] = is_zero(d) ? T(0.0) : recip(d);
+      }
+    __syncthreads();
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrhs; j += gridDim.x * blockDim.x) {
+      T* col = Xb + (int64_t)j * X.ld + p0;
+      T x[32];
+      for (int r = 0; r < pb; ++r) x[r] = col[r];
+      if (!UPPER) {
+        for (int r = 1; r < pb; ++r) {
+          T s = x[r];
+          for (int c = 0; c < r; ++c) s = fmsc(s, Ls[r + c * pb], x[c]);
+          x[r] = s;
+        }
+      } else {
+        for (int r = pb - 1; r >= 0; --r) {
+          T s = x[r];
+          for (int c = r + 1; c < pb; ++c) s = fmsc(s, Ls[r + c * pb], x[c]);
+          x[r] = s * Dinv[r];
+        }
+      }
+      for (int r = 0; r < pb; ++r) col[r] = x[r];
+    }
+  }
+}
+
+template <typename T, bool UPPER>
+cudaError_t trsm_diag(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch, cudaStream_t st) {
+  const size_t sm = ((size_t)pb * pb + pb) * sizeof(T);
+  const int by = std::min(batch, 65535);
+  if (nrhs >= 16) {
+    const int bx = std::min((nrhs + 127) / 128, 1024);
+    k_trsm_diag_cols<T, UPPER><<<dim3(bx, by), 128, sm, st>>>(LU, X, p0, pb, nrhs, batch);
+  } else {
+    const int bx = std::min((nrhs + 3) / 4, 1024);
+    k_trsm_diag<T, UPPER><<<dim3(bx, by), 128, sm, st>>>(LU, X, p0, pb, nrhs, batch);
+  }
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaStream_t st,
                           Prof* pf) {
@@ -690,14 +757,12 @@ cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaS
   constexpr double F = fma_flops<T>();
   const int pb0 = 32;
   cudaError_t e;
-  const int bx = std::min((nrhs + 3) / 4, 1024);
-  const int by = std::min(batch, 65535);
+
   // forward: unit lower
   for (int p0 = 0; p0 < n; p0 += pb0) {
     const int pb = std::min(pb0, n - p0);
     if (pf) pf->begin(st);
-    k_trsm_diag<T, false><<<dim3(bx, by), 128, (size_t)pb * pb * sizeof(T), st>>>(LU, X, p0, pb, nrhs, batch);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = trsm_diag<T, false>(LU, X, p0, pb, nrhs, batch, st)) != cudaSuccess) return e;
     if (pf) pf->end(K_TRSM_DIAG, F * 0.5 * pb * (pb - 1) * (double)nrhs * batch, st);
     const int rest = n - p0 - pb;
     if (rest > 0) {
@@ -716,8 +781,7 @@ cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaS
     const int p0 = pi * pb0;
     const int pb = std::min(pb0, n - p0);
     if (pf) pf->begin(st);
-    k_trsm_diag<T, true><<<dim3(bx, by), 128, (size_t)pb * pb * sizeof(T), st>>>(LU, X, p0, pb, nrhs, batch);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = trsm_diag<T, true>(LU, X, p0, pb, nrhs, batch, st)) != cudaSuccess) return e;
     if (pf) pf->end(K_TRSM_DIAG, F * (0.5 * pb * (pb - 1) + pb) * (double)nrhs * batch, st);
     if (p0 > 0) {
       GemmArgs<T> g;
