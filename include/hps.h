@@ -184,6 +184,28 @@ hps_status hps_kernel_stats(hps_handle* h, int kclass, hps_kernel_stat* out);
 /* Switch per-launch event timing on (1) or off (0) for later calls on h. */
 hps_status hps_set_profiling(hps_handle* h, int on);
 
+/* Allocation-free solve (no counterpart in the paper; a service for callers
+ * that cannot let the library allocate device memory at solve time: code
+ * that works inside another allocator's memory budget, or that must not call
+ * cudaMalloc / cudaFree there because those calls synchronise the device).
+ * Same result as hps_solve(h, g, NULL, u, stream) -- downward pass and leaf
+ * output with the build-time source -- but the per-level vectors live in one
+ * static device array of 16 MiB that the library holds on every GPU that
+ * loads it, until the process exits; no cudaMalloc, cudaFree or allocating
+ * routine is called.
+ *   g: [n_root_bdry] and u: [n_leaves][p^d] must be device memory.
+ *   HPS_ERR_INVALID if g or u is host memory, or if the handle's downward
+ *   pass needs more than the 16 MiB array (the sum over merge levels of
+ *   n_merges x (interior unknowns + children's boundary points) elements,
+ *   each rounded up to 256 bytes).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one array and leaves its
+ * last contents there (nothing in it needs to start at zero): calls that
+ * overlap on the GPU -- on different streams, or from different handles --
+ * race on it and must be serialised by the caller. */
+hps_status hps_solve_noalloc(hps_handle* h, const void* g, void* u, struct CUstream_st* stream);
+
 #ifdef __cplusplus
 }
 #endif

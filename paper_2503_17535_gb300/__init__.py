@@ -23,7 +23,8 @@ from ._capi import (HPS_C128, HPS_DTN, HPS_F64, HPS_ITI, HPS_OK, hps_coeffs,  # 
 
 __all__ = ["hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
            "hps_error_string", "hps_last_error_detail", "hps_device_bytes",
-           "hps_last_launch_count", "hps_kernel_stats", "hps_set_profiling", "uniform_tree",
+           "hps_last_launch_count", "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc",
+           "uniform_tree",
            "make_coeffs", "HPSError", "Handle"]
 
 
@@ -177,6 +178,17 @@ def hps_solve(h: Handle, g, u, f=None, stream=None):
     """u <- solution for root boundary data g (and source f, or the build-time
     source when f is None)."""
     return hps_solve_batched(h, 1, g, u, f=f, stream=stream)
+
+
+def hps_solve_noalloc(h: Handle, g, u, stream=None):
+    """Allocation-free variant of hps_solve with the build-time source: g and u
+    must be device tensors; the library uses its static 16 MiB device array
+    instead of allocating (see include/hps.h for the limits)."""
+    keep: list = []
+    gp = _ptr(g, h.complex, h.n_root, "g", keep)
+    up = _ptr(u, h.complex, h.n_leaves * h.ppl, "u", keep)
+    _check(_capi.lib().hps_solve_noalloc(h.ptr, gp, up, _stream(stream)), "hps_solve_noalloc")
+    return u
 
 
 def hps_free(h: Handle):

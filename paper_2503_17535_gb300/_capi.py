@@ -20,7 +20,7 @@ HPS_F64, HPS_C128 = 0, 1
 EXPORTED = [
     "hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
     "hps_error_string", "hps_last_error_detail", "hps_device_bytes", "hps_last_launch_count",
-    "hps_kernel_stats", "hps_set_profiling",
+    "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc",
 ]
 
 KCLASSES = ["gemm", "lu_panel", "laswp_trsm", "trsm_diag", "assemble", "gather", "down", "other"]
@@ -85,5 +85,7 @@ def lib() -> ctypes.CDLL:
     L.hps_kernel_stats.restype = c_int
     L.hps_set_profiling.argtypes = [c_void_p, c_int]
     L.hps_set_profiling.restype = c_int
+    L.hps_solve_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.hps_solve_noalloc.restype = c_int
     _lib = L
     return L

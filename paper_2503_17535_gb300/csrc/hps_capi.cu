@@ -753,3 +753,83 @@ hps_status hps_set_profiling(hps_handle* h, int on) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Allocation-free solve.  Some callers cannot let a library allocate device
+// memory: code that runs inside a memory budget owned by another allocator
+// (a framework's caching pool, a serving process that reserves all memory up
+// front) or code that must not call cudaMalloc / cudaFree at that point
+// because they synchronise the device.  hps_solve allocates its per-level
+// vectors lazily in the handle; hps_solve_noalloc runs the same downward pass
+// and leaf output with those vectors placed in one static device array
+// instead, so the call itself allocates nothing.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the static array on the current device.  In host code the
+// symbol names a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress, once per device, with that device current.
+hps_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HPS_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return HPS_ERR_INVALID;
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return HPS_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return HPS_OK;
+}
+
+template <typename T>
+hps_status solve_noalloc_impl(hps_handle* h, const T* g, T* u, cudaStream_t st) {
+  // scratch layout: per level (from the root down) g_int then the children's g
+  const size_t al = 256 / sizeof(T);
+  auto up = [&](size_t n) { return (n + al - 1) / al * al; };
+  size_t need = 0;
+  for (int m = h->L - 1; m >= 0; --m) {
+    const LevelDev& Lv = h->lev[m];
+    need += up((size_t)Lv.nmerge * Lv.n_int) + up((size_t)Lv.nmerge * Lv.nch * Lv.nbc);
+  }
+  if (need * sizeof(T) > kNoAllocScratchBytes) return HPS_ERR_INVALID;
+  void* base = nullptr;
+  hps_status s = noalloc_scratch(&base);
+  if (s != HPS_OK) return s;
+  T* cur = reinterpret_cast<T*>(base);
+  const T* gpar = g;
+  for (int m = h->L - 1; m >= 0; --m) {
+    LevelDev& Lv = h->lev[m];
+    T* gint = cur;
+    cur += up((size_t)Lv.nmerge * Lv.n_int);
+    T* gchild = cur;
+    cur += up((size_t)Lv.nmerge * Lv.nch * Lv.nbc);
+    HPS_CUDA(down_level<T>((const T*)Lv.X, nullptr, gpar, Lv.nmerge, Lv.nch, Lv.nbc, Lv.n_ext, Lv.n_int, 1,
+                           Lv.ext, Lv.var, gint, gchild, st, nullptr));
+    gpar = gchild;
+  }
+  HPS_CUDA(leaf_output<T>(h->lc, h->nl, 1, (const T*)h->leafX, nullptr, gpar, u, Kind<T>::iti, st, nullptr));
+  return HPS_OK;
+}
+
+}  // namespace
+
+extern "C" hps_status hps_solve_noalloc(hps_handle* h, const void* g, void* u, struct CUstream_st* stream) {
+  if (!h || !g || !u) return HPS_ERR_INVALID;
+  if (!is_device_ptr(g) || !is_device_ptr(u)) return HPS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    return h->iti ? solve_noalloc_impl<cplx>(h, (const cplx*)g, (cplx*)u, st)
+                  : solve_noalloc_impl<double>(h, (const double*)g, (double*)u, st);
+  } catch (...) {
+    return HPS_ERR_INVALID;
+  }
+}
