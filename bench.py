@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Throughput benchmark of the GB300 HPS solver.
 
-Workload (one "step" = one pass of the whole hot path): build the ItI
+Default workload (one "step" = one pass of the whole hot path): build the ItI
 solution operator of the 2D variable-coefficient Helmholtz problem
 Lap u + k^2 (1 - n(x)) u = f on [-1, 1]^2 (k = 20, eta = 20, n = four seeded
 Gaussian bumps, complex128, uniform quadtree of depth 6 = 4096 leaves,
@@ -9,13 +9,19 @@ p = 16, q = 14: leaf stage + all merges), then solve for incoming impedance
 data g with a second seeded source f2 (upward particular pass with the stored
 factors, downward pass, leaf output), then release the handle.
 
+Other workloads (--workload): poisson2d (16 leaves, p = 8, Dirichlet),
+elliptic3d (512 leaves, p = 8, divergence-form 3D DtN) and adaptive3d (the
+3D operator with a sharp seeded source on an octree refined by hps_refine,
+eps = 1e-4, leaf depths 2..5).
+
 Device-timed numbers use CUDA events on the launching stream with every input
 already in HBM; the e2e number goes through the same public calls with host
 (NumPy) buffers, so host-to-device and device-to-host copies are inside the
-timed region.  The working set (about 11 GB of factors per step) is far larger
-than the 129 MB L2, so no flush is needed between steps.
+timed region.  The factor working set of a step (gigabytes for the large
+workloads) is far above the 129 MB L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload helmholtz2d|poisson2d|elliptic3d|adaptive3d]
 
 Under torchrun (N > 1) every rank runs an independent replica (the problems
 are independent: no collective on the data path) and rank 0 prints the
@@ -41,15 +47,25 @@ if ROOT not in sys.path:
 
 METRIC = "served solves/s & p50/p99 vs plain GPU HPS; FP64 roofline frac; rel err≤1e-10"
 UNIT = "solves/s"
-WORKLOAD = {"workload": "helmholtz2d_iti_c128_depth6_p16", "equation": "Lap u + k^2 (1 - n(x)) u = f",
-            "n_leaves": 4096, "depth": 6, "p": 16, "q": 14, "k": 20.0, "eta": 20.0,
-            "seed_problem": 1, "seed_solve_source": 11, "root_map": False,
-            "step": "hps_build + hps_solve(new f) + hps_free",
-            "l2": "no flush: about 11 GB of factors per step, far above the 129 MB L2"}
-CPU_SAMPLE_DEPTH = 3
-# FP64 FMA throughput per SM per clock (flops), measured on this GPU type by a
-# dependency-free DFMA stream with the SM clock sampled alongside
-FP64_FLOP_PER_CLK_SM = None
+FP64_FLOP_PER_CLK_SM = 4.0   # 2 DFMA per clock per SM: 152 x 4 x 2.07 GHz = 1.26 TFLOP/s
+
+WORKLOADS = {
+    "helmholtz2d": {"workload": "helmholtz2d_iti_c128_depth6_p16", "equation": "Lap u + k^2 (1 - n(x)) u = f",
+                    "dim": 2, "kind": "iti", "n_leaves": 4096, "depth": 6, "p": 16, "q": 14, "k": 20.0,
+                    "eta": 20.0, "seed_problem": 1, "cpu_depth": 3},
+    "poisson2d": {"workload": "poisson2d_dtn_f64_depth2_p8", "equation": "Lap u = f, Dirichlet",
+                  "dim": 2, "kind": "dtn", "n_leaves": 16, "depth": 2, "p": 8, "q": 6, "seed_problem": 0,
+                  "cpu_depth": 2},
+    "elliptic3d": {"workload": "elliptic3d_dtn_f64_depth3_p8", "equation": "div(a grad u) + c u = f",
+                   "dim": 3, "kind": "dtn", "n_leaves": 512, "depth": 3, "p": 8, "q": 6, "seed_problem": 2,
+                   "cpu_depth": 2},
+    "adaptive3d": {"workload": "adaptive3d_dtn_f64_p8_eps1e-4_depths2-5",
+                   "equation": "div(a grad u) + c u = f, sharp source", "dim": 3, "kind": "dtn",
+                   "depth": -1, "p": 8, "q": 6, "seed_problem": 3, "eps": 1e-4, "min_depth": 2,
+                   "max_depth": 5, "cpu_depth": None},
+}
+COMMON = {"seed_solve_source": 11, "root_map": False, "step": "hps_build + hps_solve(new f) + hps_free",
+          "l2": "no flush: the step's factor working set is far above the 129 MB L2"}
 
 
 def parse():
@@ -58,36 +74,75 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="helmholtz2d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--depth", type=int, default=6,
-                    help="quadtree depth (6 = the benchmark workload; smaller for profiler captures)")
+    ap.add_argument("--root", default="lazy", choices=["lazy", "explicit"],
+                    help="lazy: the top merge keeps D's factors and [C | h_int] and each solve applies "
+                         "D^-1 (hps_options.lazy_root); explicit: the top merge forms S and w as well")
+    ap.add_argument("--depth", type=int, default=None,
+                    help="uniform tree depth override (smaller cases for profiler captures)")
     args = ap.parse_args()
-    if args.depth != WORKLOAD["depth"]:
-        WORKLOAD["depth"] = args.depth
-        WORKLOAD["n_leaves"] = 4 ** args.depth
-        WORKLOAD["workload"] = f"helmholtz2d_iti_c128_depth{args.depth}_p16"
+    spec = dict(WORKLOADS[args.workload])
+    if args.depth is not None and spec["depth"] >= 0 and args.depth != spec["depth"]:
+        spec["depth"] = args.depth
+        spec["n_leaves"] = (4 if spec["dim"] == 2 else 8) ** args.depth
+        spec["workload"] = spec["workload"].replace(f"depth{WORKLOADS[args.workload]['depth']}",
+                                                    f"depth{args.depth}")
+        spec["cpu_depth"] = min(spec["cpu_depth"], args.depth)
+    spec["root"] = args.root if spec["depth"] >= 0 else "explicit"
+    args.spec = spec
     return args
 
 
-def problem(seed_offset=0):
+def problem(spec, seed_offset=0):
     import workloads as W
-    return W.helmholtz_bumps_2d(seed=WORKLOAD["seed_problem"] + seed_offset, k=WORKLOAD["k"],
-                                eta=WORKLOAD["eta"])
+    s = spec["seed_problem"] + seed_offset
+    if spec["workload"].startswith("helmholtz"):
+        return W.helmholtz_bumps_2d(seed=s, k=spec["k"], eta=spec["eta"])
+    if spec["workload"].startswith("poisson"):
+        return W.poisson_poly_2d(seed=s)
+    if spec["workload"].startswith("elliptic"):
+        return W.elliptic_3d(seed=s)
+    return W.adaptive_3d(seed_coeffs=2 + seed_offset, seed_source=s)
 
 
-def host_inputs(P, depth, seed_offset=0):
-    pr = problem(seed_offset)
-    p, q = WORKLOAD["p"], WORKLOAD["q"]
-    t = P.uniform_tree(2, depth, pr.lo, pr.hi)
+def make_tree(P, spec, pr, depth=None):
+    depth = spec["depth"] if depth is None else depth
+    if depth >= 0:
+        return P.uniform_tree(spec["dim"], depth, pr.lo, pr.hi), None
+    fa = lambda x: pr.coeffs(x)["a"]  # noqa: E731
+    fc = lambda x: pr.coeffs(x)["c"]  # noqa: E731
+    leaves = P.hps_refine(pr.lo, pr.hi, spec["p"], spec["eps"], spec["min_depth"], spec["max_depth"],
+                          [pr.source, fa, fc])
+    return P.adaptive_tree(leaves, pr.lo, pr.hi), leaves
+
+
+def host_inputs(P, spec, seed_offset=0, depth=None):
+    """Coefficients (only the non-default ones), sources and boundary data
+    sampled at the library's nodes."""
+    pr = problem(spec, seed_offset)
+    p, q = spec["p"], spec["q"]
+    t, leaves = make_tree(P, spec, pr, depth)
     x, xb = P.hps_nodes(t, p, q)
     nl, ppl, nr = P.hps_sizes(t, p, q)
-    c = pr.coeffs(x)["c"].reshape(nl, ppl).copy()
-    f = pr.source(x).reshape(nl, ppl).astype(np.complex128)
-    g = pr.boundary(xb).astype(np.complex128)
-    rng = np.random.default_rng(WORKLOAD["seed_solve_source"] + seed_offset)
-    f2 = (rng.standard_normal((nl, ppl)) + 1j * rng.standard_normal((nl, ppl))) * np.abs(f).max()
-    return pr, t, c, f, g, np.ascontiguousarray(f2)
+    cf = pr.coeffs(x)
+    cdt = np.complex128 if spec["kind"] == "iti" else np.float64
+    arrs = {}
+    if not np.all(cf["a"] == 1.0):
+        arrs["a"] = np.ascontiguousarray(cf["a"].reshape(nl, ppl))
+    if any(np.any(bk != 0.0) for bk in cf["b"]):
+        arrs["b"] = [np.ascontiguousarray(bk.reshape(nl, ppl)) for bk in cf["b"]]
+    if np.any(cf["c"] != 0.0):
+        arrs["c"] = np.ascontiguousarray(cf["c"].reshape(nl, ppl))
+    f = np.ascontiguousarray(pr.source(x).reshape(nl, ppl).astype(cdt))
+    g = np.ascontiguousarray(pr.boundary(xb).astype(cdt))
+    rng = np.random.default_rng(COMMON["seed_solve_source"] + seed_offset)
+    f2 = rng.standard_normal((nl, ppl)) * max(np.abs(f).max(), 1.0)
+    if spec["kind"] == "iti":
+        f2 = f2 + 1j * rng.standard_normal((nl, ppl)) * max(np.abs(f).max(), 1.0)
+    return {"pr": pr, "t": t, "leaves": leaves, "coef": arrs, "f": f, "g": g,
+            "f2": np.ascontiguousarray(f2.astype(cdt)), "nl": nl, "ppl": ppl}
 
 
 # ------------------------------------------------------------------ clocks --
@@ -98,8 +153,8 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
         self.proc = None
         self.lines = []
 
@@ -147,26 +202,53 @@ class ClockSampler:
                 "power_w_max": max(pw), "reasons": sorted(reasons)}
 
 
+# ----------------------------------------------------------- replicas ----
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over all ranks (the step time of the slowest
+    replica); identity for a single process."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(steps: int, total_ms: float, world: int, device=None) -> float:
+    """Whole-job solves/s of `world` independent replicas that each ran
+    `steps` steps: all steps over the slowest replica's time."""
+    return world * steps / (max_over_ranks(total_ms, world, device) / 1e3)
+
+
 # ----------------------------------------------------------------- our arm --
+
+def _build(P, spec, inp, arrs, f, profile=False):
+    kind = P.HPS_ITI if spec["kind"] == "iti" else P.HPS_DTN
+    return P.hps_build(inp["t"], spec["p"], spec["q"], kind, a=arrs.get("a"), b=arrs.get("b"), c=arrs.get("c"),
+                       f=f, eta=spec.get("eta", 0.0), profile=profile, lazy_root=spec["root"] == "lazy")
+
 
 def run_ours(args, rank, world):
     import torch
     import paper_2503_17535_gb300 as P
 
+    spec = args.spec
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    pr, t, c, f, g, f2 = host_inputs(P, WORKLOAD["depth"], seed_offset=rank)
-    p, q = WORKLOAD["p"], WORKLOAD["q"]
-    nl, ppl, nr = P.hps_sizes(t, p, q)
-    cd, fd, gd, f2d = (torch.from_numpy(v).to(dev) for v in (c, f, g, f2))
-    ud = torch.zeros((nl, ppl), dtype=torch.complex128, device=dev)
+    inp = host_inputs(P, spec, seed_offset=rank)
+    nl, ppl = inp["nl"], inp["ppl"]
+    to_dev = lambda v: torch.from_numpy(v).to(dev)  # noqa: E731
+    darr = {k: ([to_dev(x) for x in v] if isinstance(v, list) else to_dev(v)) for k, v in inp["coef"].items()}
+    fd, gd, f2d = to_dev(inp["f"]), to_dev(inp["g"]), to_dev(inp["f2"])
+    udt = torch.complex128 if spec["kind"] == "iti" else torch.float64
+    ud = torch.zeros((nl, ppl), dtype=udt, device=dev)
     stream = torch.cuda.current_stream(dev)
-
     launches = [0]
 
     def step():
-        h = P.hps_build(t, p, q, P.HPS_ITI, c=cd, f=fd, eta=WORKLOAD["eta"])
+        h = _build(P, spec, inp, darr, fd)
         launches[0] += P.hps_last_launch_count(h)
         P.hps_solve(h, gd, ud, f=f2d)
         launches[0] += P.hps_last_launch_count(h)
@@ -200,14 +282,11 @@ def run_ours(args, rank, world):
     clocks = sampler.stop()
     total_ms = t0.elapsed_time(t1)
     per = sorted(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value = replica_throughput(args.steps, total_ms, world, dev)
+    total_ms = max_over_ranks(total_ms, world, dev)
 
     # ---- one profiled step (untimed): per-class kernel times with CUDA events
-    h = P.hps_build(t, p, q, P.HPS_ITI, c=cd, f=fd, eta=WORKLOAD["eta"], profile=True)
+    h = _build(P, spec, inp, darr, fd, profile=True)
     sb = P.hps_kernel_stats(h)
     P.hps_solve(h, gd, ud, f=f2d)
     ss = P.hps_kernel_stats(h)
@@ -217,31 +296,32 @@ def run_ours(args, rank, world):
                    "ms": sb[k]["ms"] + ss[k]["ms"]} for k in sb}
     flops_step = sum(v["flops"] for v in classes.values())
     # algorithmic flops of the CPU-baseline sample (same problem, smaller depth)
-    _, ts_, cs_, fs_, gs_, f2s_ = host_inputs(P, CPU_SAMPLE_DEPTH, seed_offset=rank)
-    nls, ppls, _ = P.hps_sizes(ts_, p, q)
-    hs_ = P.hps_build(ts_, p, q, P.HPS_ITI, c=cs_, f=fs_, eta=WORKLOAD["eta"])
-    fl_s = sum(v["flops"] for v in P.hps_kernel_stats(hs_).values())
-    P.hps_solve(hs_, gs_, np.zeros((nls, ppls), np.complex128), f=f2s_)
-    fl_s += sum(v["flops"] for v in P.hps_kernel_stats(hs_).values())
-    P.hps_free(hs_)
-    sample_ratio = flops_step / fl_s
+    sample_ratio = 1.0
+    if spec["cpu_depth"] is not None and spec["cpu_depth"] != spec["depth"]:
+        inp_s = host_inputs(P, spec, seed_offset=rank, depth=spec["cpu_depth"])
+        hs_ = _build(P, spec, inp_s, inp_s["coef"], inp_s["f"])
+        fl_s = sum(v["flops"] for v in P.hps_kernel_stats(hs_).values())
+        P.hps_solve(hs_, inp_s["g"], np.zeros((inp_s["nl"], inp_s["ppl"]), inp_s["f"].dtype), f=inp_s["f2"])
+        fl_s += sum(v["flops"] for v in P.hps_kernel_stats(hs_).values())
+        P.hps_free(hs_)
+        sample_ratio = flops_step / fl_s
     dom = max(classes, key=lambda k: classes[k]["ms"])
-    sm_mhz = clocks.get("sm_mhz") or 1485.0
-    peak_tf = (FP64_FLOP_PER_CLK_SM or 4.0) * 152 * sm_mhz * 1e6 / 1e12
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak_tf = FP64_FLOP_PER_CLK_SM * 152 * sm_mhz * 1e6 / 1e12
     ach = classes[dom]["flops"] / (classes[dom]["ms"] / 1e3) / 1e12 if classes[dom]["ms"] > 0 else 0.0
     roofline = {"bound": "alu", "kernel_class": dom, "achieved": round(ach, 4), "peak": round(peak_tf, 4),
                 "unit": "TFLOP/s", "frac": round(ach / peak_tf, 4), "traffic": None,
-                "peak_source": "FP64 FMA pipe: flop/clk/SM x 152 SMs x median SM clock of this run",
+                "peak_source": "FP64 FMA pipe: 4 flop/clk/SM x 152 SMs x median SM clock of this run",
                 "launches_per_step": classes[dom]["launches"], "ms_per_step": round(classes[dom]["ms"], 3)}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        uh = np.zeros((nl, ppl), np.complex128)
+        uh = np.zeros((nl, ppl), inp["f"].dtype)
 
         def step_host():
-            h = P.hps_build(t, p, q, P.HPS_ITI, c=c, f=f, eta=WORKLOAD["eta"])
-            P.hps_solve(h, g, uh, f=f2)
+            h = _build(P, spec, inp, inp["coef"], inp["f"])
+            P.hps_solve(h, inp["g"], uh, f=inp["f2"])
             P.hps_free(h)
 
         step_host()
@@ -250,51 +330,67 @@ def run_ours(args, rank, world):
         for _ in range(args.steps):
             step_host()
         torch.cuda.synchronize()
-        te = time.perf_counter() - ts
-        if world > 1:
-            tt = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
+        te = max_over_ranks(time.perf_counter() - ts, world, dev)
+        coef_bytes = sum((sum(x.nbytes for x in v) if isinstance(v, list) else v.nbytes)
+                         for v in inp["coef"].values())
         e2e = {"value": round(world * args.steps / te, 4), "unit": UNIT,
-               "h2d_bytes_per_step": int(c.nbytes + f.nbytes + g.nbytes + f2.nbytes),
+               "h2d_bytes_per_step": int(coef_bytes + inp["f"].nbytes + inp["g"].nbytes + inp["f2"].nbytes),
                "d2h_bytes_per_step": int(uh.nbytes)}
     return {"value": value, "total_ms": total_ms, "per": per, "clocks": clocks, "roofline": roofline,
             "classes": classes, "flops_step": flops_step, "launches": launches[0] // max(args.steps, 1),
-            "e2e": e2e, "sample_ratio": sample_ratio}
+            "e2e": e2e, "sample_ratio": sample_ratio, "n_leaves": nl}
 
 
 # ------------------------------------------------------------- CPU oracle --
 
-def oracle_sample_step(depth=CPU_SAMPLE_DEPTH):
-    """One oracle build + new-source solve on the same problem at a smaller
-    depth; returns its wall time in seconds."""
-    import workloads as W  # noqa: F401
-    from oracle import geometry as geo
+def oracle_sample_step(spec, depth=None):
+    """One oracle build + new-source solve of the same problem (at a smaller
+    depth when the spec names one); returns its wall time in seconds."""
+    from oracle import adaptive as ad
     from oracle import hps as O
-    pr = problem()
-    p, q = WORKLOAD["p"], WORKLOAD["q"]
+    pr = problem(spec)
+    p, q = spec["p"], spec["q"]
+    rng = np.random.default_rng(COMMON["seed_solve_source"])
+    if spec["depth"] < 0:
+        fa = lambda x: pr.coeffs(x)["a"]  # noqa: E731
+        fc = lambda x: pr.coeffs(x)["c"]  # noqa: E731
+        leaves = ad.refine([pr.source, fa, fc], pr.lo, pr.hi, p, spec["eps"], spec["min_depth"],
+                           spec["max_depth"])
+        x, a, b, c, f, g = ad.sample_adaptive(pr, leaves, p)
+        f2 = rng.standard_normal(f.shape) * max(np.abs(f).max(), 1.0)
+        t0 = time.perf_counter()
+        ad.build_adaptive(leaves, p, pr.lo, pr.hi, a, b, c, f)
+        ad.solve_adaptive(ad.build_adaptive(leaves, p, pr.lo, pr.hi, a, b, c, f2), g)
+        return time.perf_counter() - t0
+    depth = spec["depth"] if depth is None else depth
     x, a, b, c, f, g = O.sample_problem(pr, p, q, depth)
-    rng = np.random.default_rng(WORKLOAD["seed_solve_source"])
-    f2 = (rng.standard_normal(f.shape) + 1j * rng.standard_normal(f.shape)) * np.abs(f).max()
+    f2 = rng.standard_normal(f.shape) * max(np.abs(f).max(), 1.0)
+    if spec["kind"] == "iti":
+        f2 = f2 + 1j * rng.standard_normal(f.shape) * max(np.abs(f).max(), 1.0)
     t0 = time.perf_counter()
-    O.build(2, "iti", p, q, depth, pr.lo, pr.hi, a, b, c, f, eta=pr.eta)
-    s2 = O.build(2, "iti", p, q, depth, pr.lo, pr.hi, a, b, c, f2, eta=pr.eta)
+    O.build(spec["dim"], spec["kind"], p, q, depth, pr.lo, pr.hi, a, b, c, f, eta=pr.eta)
+    s2 = O.build(spec["dim"], spec["kind"], p, q, depth, pr.lo, pr.hi, a, b, c, f2, eta=pr.eta)
     O.solve(s2, g)
-    del geo
     return time.perf_counter() - t0
 
 
-def flop_ratio():
-    """Algorithmic flops of the full workload over those of the CPU sample,
-    from a closed-form count of the leaf stage (LU of B, solves, T = QH Y)
-    and of the ItI merges (W, its LU, the W^{-1} and D21 solves, B X); it
-    agrees with the library's own launch counts to a few percent and is used
-    by the reference arm, which runs no GPU code."""
+def flop_ratio(spec):
+    """Algorithmic flops of the workload over those of its CPU sample, used
+    by the reference arm (which runs no GPU code).  Helmholtz: a closed-form
+    count of the leaf stage (LU of B, solves, T = QH Y) and of the ItI merges
+    (W, its LU, the W^{-1} and D21 solves, B X), within a few percent of the
+    library's own counts.  Other workloads: their samples are the full
+    problem, or for the uniform 3D problem the leaf-count ratio."""
+    if not spec["workload"].startswith("helmholtz"):
+        if spec["cpu_depth"] is None or spec["cpu_depth"] == spec["depth"]:
+            return 1.0
+        b = 4 if spec["dim"] == 2 else 8
+        return float(b ** (spec["depth"] - spec["cpu_depth"]))
+
     def flops(depth):
-        p, q = WORKLOAD["p"], WORKLOAD["q"]
+        p, q = spec["p"], spec["q"]
         npts, nb = p * p, 4 * q
         nl = 4 ** depth
-        # leaf: LU of B (npts), solve with nb + 1 columns, T = QH Y
         leaf = nl * 8 * (npts ** 3 / 3 + npts ** 2 * (nb + 1) + nb * npts * (nb + 1))
         merge = 0.0
         n = q
@@ -306,16 +402,21 @@ def flop_ratio():
             merge += nm * 8 * per
             n *= 2
         return leaf + merge
-    return flops(WORKLOAD["depth"]) / flops(CPU_SAMPLE_DEPTH)
+    return flops(spec["depth"]) / flops(spec["cpu_depth"])
 
 
-def cpu_baseline(ratio, reps=1):
-    ts = [oracle_sample_step() for _ in range(reps)]
+def cpu_baseline(spec, ratio, reps=1):
+    ts = [oracle_sample_step(spec, spec["cpu_depth"]) for _ in range(reps)]
     t = min(ts)
+    if spec["depth"] < 0:
+        what = "the full adaptive problem (same refined tree)"
+    elif spec["cpu_depth"] == spec["depth"]:
+        what = f"the full problem (depth {spec['depth']})"
+    else:
+        what = (f"the same problem at depth {spec['cpu_depth']}, scaled to depth {spec['depth']} by the "
+                f"algorithmic flop ratio {ratio:.1f} (library counts)")
     return {"value": round(1.0 / (t * ratio), 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"oracle (NumPy/SciPy LAPACK) build + new-source solve of the same problem at "
-                       f"depth {CPU_SAMPLE_DEPTH} (64 leaves, p=16), {t:.2f} s, scaled to depth "
-                       f"{WORKLOAD['depth']} by the algorithmic flop ratio {ratio:.1f} (library counts)"),
+            "sample": f"oracle (NumPy/SciPy LAPACK) build + new-source solve of {what}: {t:.2f} s",
             "blas_threads_env": os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
             or "default (all cores)"}
 
@@ -323,21 +424,25 @@ def cpu_baseline(ratio, reps=1):
 def run_reference(args, rank):
     if rank != 0:
         return None
+    spec = args.spec
     for _ in range(args.warmup):
-        oracle_sample_step()
-    ratio = flop_ratio()
-    ts = [oracle_sample_step() for _ in range(args.steps)]
+        oracle_sample_step(spec, spec["cpu_depth"])
+    ratio = flop_ratio(spec)
+    ts = [oracle_sample_step(spec, spec["cpu_depth"]) for _ in range(args.steps)]
     scaled = [t * ratio for t in ts]
     value = args.steps / sum(scaled)
+    cfg = {k: v for k, v in spec.items() if k not in ("cpu_depth",)}
+    cfg.update(COMMON)
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * sum(scaled) / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": WORKLOAD,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128" if spec["kind"] == "iti" else "f64",
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": (f"each step: oracle build + new-source solve at depth {CPU_SAMPLE_DEPTH} "
-                                        f"(mean {statistics.mean(ts):.2f} s), scaled to depth 6 by the flop "
-                                        f"ratio {ratio:.1f}")},
+                             "sample": (f"each step: oracle build + new-source solve at depth "
+                                        f"{spec['cpu_depth'] if spec['cpu_depth'] is not None else 'adaptive'}"
+                                        f" (mean {statistics.mean(ts):.2f} s), scaled by the flop ratio "
+                                        f"{ratio:.1f}")},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return line
 
@@ -346,6 +451,7 @@ def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    spec = args.spec
     if args.impl == "reference":
         line = run_reference(args, rank)
         if line is not None:
@@ -360,20 +466,23 @@ def main():
         p50 = per[len(per) // 2]
         p99 = per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]
         step_tf = r["flops_step"] / (statistics.median(per) / 1e3) / 1e12
+        cfg = {k: v for k, v in spec.items() if k not in ("cpu_depth",)}
+        cfg.update(COMMON)
+        cfg["n_leaves"] = r["n_leaves"]
+        cfg["parallelism"] = f"replicas x{world}"
         line = {"metric": METRIC, "value": round(r["value"], 4), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(r["total_ms"] / args.steps, 3), "p50_ms": round(p50, 3),
                 "p99_ms": round(p99, 3), "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-                "config": dict(WORKLOAD, parallelism=f"replicas x{world}"),
-                "clocks": r["clocks"], "e2e": r["e2e"], "gpu_launches": r["launches"] * args.steps,
+                "vs_baseline": None, "dtype": "c128" if spec["kind"] == "iti" else "f64", "data": "synthetic",
+                "config": cfg, "clocks": r["clocks"], "e2e": r["e2e"], "gpu_launches": r["launches"] * args.steps,
                 "roofline": r["roofline"],
                 "step_fp64": {"algorithmic_flops": r["flops_step"], "achieved_tflops": round(step_tf, 4),
                               "frac_of_peak": round(step_tf / r["roofline"]["peak"], 4)},
                 "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                                        "gflops": round(v["flops"] / 1e9, 3)} for k, v in r["classes"].items()}}
         if world == 1 and not args.no_cpu:
-            line["cpu_baseline"] = cpu_baseline(r["sample_ratio"])
+            line["cpu_baseline"] = cpu_baseline(spec, r["sample_ratio"])
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -69,16 +69,27 @@ enum { HPS_DTN = 0, HPS_ITI = 1 };
 enum { HPS_F64 = 0, HPS_C128 = 1 };
 
 /* Tree over the box [lo, hi] (a square or cube: leaves must be cubes).
- * uniform_depth >= 0 selects the uniform tree of that depth; the adaptive
- * fields are reserved and must be 0 / NULL. */
+ * uniform_depth >= 0 selects the uniform tree of that depth (morton and level
+ * must be NULL).  uniform_depth == -1 selects an adaptive octree (dim = 3,
+ * DtN only, Section 4.2): n_leaves leaves, leaf n at level[n] (0..16) with
+ * integer coordinates at that level encoded in morton[n] (bit 3b + a holds bit
+ * b of the coordinate along axis a), listed depth first in Morton order
+ * (the order hps_refine returns).  The leaves must tile the cube and be 2:1
+ * balanced across faces; else HPS_ERR_INVALID.  For an adaptive tree a node's
+ * boundary lists each face as the quadtree of its children's faces (Morton
+ * order over the two tangential axes), each leaf panel q^2 points. */
 typedef struct {
   int dim;                 /* 2 or 3 */
   double lo[3], hi[3];
-  int uniform_depth;       /* L >= 0 */
-  int64_t n_leaves;        /* must equal 2^(dim L) */
-  const uint64_t* morton;  /* reserved, NULL */
-  const int8_t* level;     /* reserved, NULL */
+  int uniform_depth;       /* L >= 0, or -1 for an adaptive octree */
+  int64_t n_leaves;        /* 2^(dim L) for uniform trees */
+  const uint64_t* morton;  /* adaptive: host array [n_leaves] */
+  const int8_t* level;     /* adaptive: host array [n_leaves] */
 } hps_tree;
+
+/* Callback evaluating a function at n points (xyz: [n][3], host memory) into
+ * out[n]; returns 0 on success.  ctx is the caller's pointer. */
+typedef int (*hps_eval_fn)(void* ctx, int64_t n, const double* xyz, double* out);
 
 /* Coefficients of L u = a Lap u + sum_k b_k d_k u + c u, each sampled at the
  * leaf nodes ([n_leaves][p^d] doubles).  NULL selects a = 1, b_k = 0, c = 0.
@@ -98,7 +109,12 @@ typedef struct {
   int version;          /* 1 */
   int want_root_map;    /* 1: also form the root's T and h (not needed to solve) */
   int profile;          /* 1: time every kernel launch with CUDA events (slower) */
-  int reserved[5];
+  int lazy_root;        /* 1: keep the root's [C | h_int] and D's factors instead of
+                           forming S = -D^{-1} C (Eq. "merge outputs 2"); each
+                           solve then applies D^{-1} to C g + h_int.  Saves the
+                           root's multi-RHS solve in hps_build; uniform trees,
+                           ignored with want_root_map. */
+  int reserved[4];
 } hps_options;
 
 /* Kernel classes reported by hps_kernel_stats. */
@@ -128,6 +144,23 @@ typedef struct hps_handle hps_handle;
  * n_root_bdry = 4 q 2^L (2D) or 6 q^2 4^L (3D).  Pure host computation.
  * Errors: HPS_ERR_INVALID for an unsupported tree, p < 4 or q != p - 2. */
 hps_status hps_nodes(const hps_tree* tree, int p, int q, double* leaf_xyz, double* bdry_xyz);
+
+/* Adaptive refinement (Section 4.2, Eq. "refinement check"): starting from
+ * the uniform octree of depth min_depth over the cube [lo, hi], a leaf is
+ * split while, for any of the n_fn functions, max |f(x1) - L_8f1 f(x0)| /
+ * ||f||_inf >= eps, where x0 are its p^3 Chebyshev nodes, x1 the nodes of its
+ * 8 children and L_8f1 the tensor interpolation between them (evaluated on
+ * the device); ||f||_inf is the largest |f| over all points sampled up to
+ * and including the current level.  Depth is capped at max_depth (<= 10).
+ * The union of the functions' trees is then 2:1 balanced across faces.  The
+ * functions are called on the host.  On return *n_leaves is the leaf count;
+ * morton / level (host arrays) are filled when capacity >= *n_leaves, in the
+ * order hps_tree expects.  HPS_ERR_INVALID for bad arguments or a failing
+ * callback. */
+hps_status hps_refine(const double lo[3], const double hi[3], int p, double eps, int min_depth,
+                      int max_depth, int n_fn, const hps_eval_fn* fns, void* const* ctxs,
+                      int64_t capacity, int64_t* n_leaves, uint64_t* morton, int8_t* level,
+                      struct CUstream_st* stream);
 
 /* Sizes that go with a tree: number of leaves, points per leaf and root
  * boundary points.  Any output pointer may be NULL. */
@@ -184,7 +217,7 @@ hps_status hps_kernel_stats(hps_handle* h, int kclass, hps_kernel_stat* out);
 /* Switch per-launch event timing on (1) or off (0) for later calls on h. */
 hps_status hps_set_profiling(hps_handle* h, int on);
 
-/* Allocation-free solve (no counterpart in the paper; a service for callers
+/* Allocation-free solve (uniform trees only; no counterpart in the paper; a service for callers
  * that cannot let the library allocate device memory at solve time: code
  * that works inside another allocator's memory budget, or that must not call
  * cudaMalloc / cudaFree there because those calls synchronise the device).
@@ -194,7 +227,8 @@ hps_status hps_set_profiling(hps_handle* h, int on);
  * loads it, until the process exits; no cudaMalloc, cudaFree or allocating
  * routine is called.
  *   g: [n_root_bdry] and u: [n_leaves][p^d] must be device memory.
- *   HPS_ERR_INVALID if g or u is host memory, or if the handle's downward
+ *   HPS_ERR_INVALID if g or u is host memory, if the handle keeps a lazy
+ *   root (hps_options.lazy_root), or if the handle's downward
  *   pass needs more than the 16 MiB array (the sum over merge levels of
  *   n_merges x (interior unknowns + children's boundary points) elements,
  *   each rounded up to 256 bytes).

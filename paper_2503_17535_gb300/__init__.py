@@ -24,7 +24,7 @@ from ._capi import (HPS_C128, HPS_DTN, HPS_F64, HPS_ITI, HPS_OK, hps_coeffs,  # 
 __all__ = ["hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
            "hps_error_string", "hps_last_error_detail", "hps_device_bytes",
            "hps_last_launch_count", "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc",
-           "uniform_tree",
+           "uniform_tree", "adaptive_tree", "hps_refine",
            "make_coeffs", "HPSError", "Handle"]
 
 
@@ -52,6 +52,34 @@ def uniform_tree(dim: int, depth: int, lo=None, hi=None) -> hps_tree:
     t.n_leaves = 2 ** (dim * depth)
     t.morton = None
     t.level = None
+    return t
+
+
+def morton_code(ix) -> int:
+    """Morton code of integer coordinates (x in the lowest bit)."""
+    c = 0
+    for b in range(21):
+        for a in range(3):
+            c |= ((int(ix[a]) >> b) & 1) << (3 * b + a)
+    return c
+
+
+def adaptive_tree(leaves, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0)) -> hps_tree:
+    """hps_tree of an adaptive octree from leaves [(level, (ix, iy, iz))] in
+    depth-first Morton order (the arrays are kept alive by the returned
+    structure)."""
+    t = hps_tree()
+    t.dim = 3
+    for a in range(3):
+        t.lo[a] = float(lo[a])
+        t.hi[a] = float(hi[a])
+    t.uniform_depth = -1
+    t.n_leaves = len(leaves)
+    mort = np.array([morton_code(ix) for _, ix in leaves], dtype=np.uint64)
+    lev = np.array([lv for lv, _ in leaves], dtype=np.int8)
+    t.morton = mort.ctypes.data
+    t.level = lev.ctypes.data
+    t._keep = (mort, lev)
     return t
 
 
@@ -119,6 +147,7 @@ class Handle:
     def __init__(self, ptr, tree, p, q, complex_):
         self.ptr = ptr
         self.dim = tree.dim
+        self.tree = tree
         self.p, self.q = p, q
         self.complex = complex_
         self.n_leaves, self.ppl, self.n_root = hps_sizes(tree, p, q)
@@ -146,7 +175,7 @@ def make_coeffs(kind: int, a=None, b=None, c=None, eta: float = 0.0, keep=None, 
 
 def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None, f=None,
               eta: float = 0.0, want_root_map: bool = False, profile: bool = False,
-              stream=None) -> Handle:
+              lazy_root: bool = False, stream=None) -> Handle:
     """Build the solution operator; coefficient and source arrays hold
     n_leaves * p^dim values (leaf-major, tensor node order)."""
     nl, ppl, _ = hps_sizes(tree, p, q)
@@ -158,6 +187,7 @@ def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None,
     opts.version = 1
     opts.want_root_map = 1 if want_root_map else 0
     opts.profile = 1 if profile else 0
+    opts.lazy_root = 1 if lazy_root else 0
     out = c_void_p()
     st = _stream(stream)
     _check(_capi.lib().hps_build(byref(tree), p, q, byref(cf), fp, byref(opts), st, byref(out)),
@@ -189,6 +219,50 @@ def hps_solve_noalloc(h: Handle, g, u, stream=None):
     up = _ptr(u, h.complex, h.n_leaves * h.ppl, "u", keep)
     _check(_capi.lib().hps_solve_noalloc(h.ptr, gp, up, _stream(stream)), "hps_solve_noalloc")
     return u
+
+
+def hps_refine(lo, hi, p: int, eps: float, min_depth: int, max_depth: int, funcs, stream=None):
+    """Adaptive refinement in the library (device interpolation check, 2:1
+    balance); funcs are Python callables f(xyz (n, 3)) -> values (n,),
+    evaluated when the library asks for samples.  Returns the leaves as
+    [(level, (ix, iy, iz))] in the order adaptive_tree() expects."""
+    errors = []
+
+    def wrap(fn):
+        def cb(ctx, n, xyz, out):
+            try:
+                x = np.ctypeslib.as_array(xyz, shape=(n, 3))
+                o = np.ctypeslib.as_array(out, shape=(n,))
+                o[:] = np.asarray(fn(x), dtype=np.float64)
+                return 0
+            except Exception as e:  # noqa: BLE001
+                errors.append(e)
+                return 1
+        return _capi.EVAL_FN(cb)
+
+    cbs = [wrap(fn) for fn in funcs]
+    arr = (_capi.EVAL_FN * len(cbs))(*cbs)
+    lo3 = (ctypes.c_double * 3)(*[float(v) for v in lo])
+    hi3 = (ctypes.c_double * 3)(*[float(v) for v in hi])
+    L = _capi.lib()
+    st = _stream(stream)
+    cap = min(8 ** max_depth, 1 << 22)
+    mort = np.zeros(cap, np.uint64)
+    lev = np.zeros(cap, np.int8)
+    n = c_int64(0)
+    _check(L.hps_refine(lo3, hi3, p, eps, min_depth, max_depth, len(cbs), arr, None, cap, byref(n),
+                        mort.ctypes.data, lev.ctypes.data, st), "hps_refine")
+    mort, lev = mort[:n.value], lev[:n.value]
+    if errors:
+        raise errors[0]
+    out = []
+    for code, lv in zip(mort.tolist(), lev.tolist()):
+        ix = [0, 0, 0]
+        for b in range(lv):
+            for a in range(3):
+                ix[a] |= ((code >> (3 * b + a)) & 1) << b
+        out.append((lv, tuple(ix)))
+    return out
 
 
 def hps_free(h: Handle):
@@ -229,4 +303,3 @@ def hps_set_profiling(h: Handle, on: bool):
     _check(_capi.lib().hps_set_profiling(h.ptr, 1 if on else 0), "hps_set_profiling")
 
 
-del ctypes

@@ -20,8 +20,10 @@ HPS_F64, HPS_C128 = 0, 1
 EXPORTED = [
     "hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
     "hps_error_string", "hps_last_error_detail", "hps_device_bytes", "hps_last_launch_count",
-    "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc",
+    "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc", "hps_refine",
 ]
+
+EVAL_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int64, POINTER(c_double), POINTER(c_double))
 
 KCLASSES = ["gemm", "lu_panel", "laswp_trsm", "trsm_diag", "assemble", "gather", "down", "other"]
 
@@ -39,7 +41,7 @@ class hps_coeffs(ctypes.Structure):
 
 class hps_options(ctypes.Structure):
     _fields_ = [("version", c_int), ("want_root_map", c_int), ("profile", c_int),
-                ("reserved", c_int * 5)]
+                ("lazy_root", c_int), ("reserved", c_int * 4)]
 
 
 class hps_kernel_stat(ctypes.Structure):
@@ -87,5 +89,9 @@ def lib() -> ctypes.CDLL:
     L.hps_set_profiling.restype = c_int
     L.hps_solve_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.hps_solve_noalloc.restype = c_int
+    L.hps_refine.argtypes = [POINTER(c_double), POINTER(c_double), c_int, c_double, c_int, c_int, c_int,
+                             POINTER(EVAL_FN), POINTER(c_void_p), c_int64, POINTER(c_int64), c_void_p,
+                             c_void_p, c_void_p]
+    L.hps_refine.restype = c_int
     _lib = L
     return L

@@ -1,0 +1,173 @@
+// Internal definition of the solver handle and small host helpers shared by
+// the C ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "adaptive.h"
+#include "adaptive_kernels.cuh"
+#include "hps.h"
+#include "hps_kernels.cuh"
+#include "linalg.h"
+#include "plan.h"
+
+namespace hps {
+
+struct LevelDev {
+  int nmerge = 0, nch = 0, n = 0, nbc = 0, n_ext = 0, n_int = 0;
+  int *ext = nullptr, *var = nullptr, *eq = nullptr;
+  int *barow = nullptr, *bacol = nullptr, *bbrow = nullptr, *bcrow = nullptr;
+  // ItI interior blocks by parity: [2][nbc/2] interior points, own vars, eq rows
+  int *odd_pts = nullptr, *odd_var = nullptr, *odd_eq = nullptr;
+  int *even_pts = nullptr, *even_var = nullptr, *even_eq = nullptr;
+  void* TP = nullptr;   // [nmerge][n_ext x (n_ext+1)]  parent [T | h]
+  void* D = nullptr;    // [nmerge][n_int x n_int]
+  void* W = nullptr;    // ItI: [nmerge][(n_int/2)^2] (LU of W)
+  int* ipiv = nullptr;  // [nmerge][nlu]
+  int* perm = nullptr;
+  int* info = nullptr;  // [nmerge]
+  void* X = nullptr;    // [nmerge][n_int x (n_ext+1)]  D^{-1} [C | h_int]
+  int G = 1;
+  LuWork luw;
+  bool lazy = false;    // root only: X holds [C | h_int]; D^{-1} is applied per solve
+  // solve workspace (nrhs columns)
+  void *r = nullptr, *hp = nullptr, *x = nullptr, *gint = nullptr, *gchild = nullptr;
+  bool top() const { return nmerge == 1; }
+};
+
+// Adaptive-tree storage: one merge of the nonuniform octree.
+struct AChildDev {
+  ProjDev pj;                 // projection descriptors (device arrays)
+  int* ext = nullptr;         // per projected point
+  int* var = nullptr;
+  int *barow = nullptr, *bacol = nullptr, *bbrow = nullptr, *bcrow = nullptr;
+  int ne_c = 0, ni_c = 0;     // exterior / interior projected points
+  void* Tp = nullptr;         // np x (np + 1) projected [T | h]
+};
+
+struct AMergeDev {
+  int node = -1, n_ext = 0, n_int = 0;
+  AChildDev ch[8];
+  void *D = nullptr, *X = nullptr, *TP = nullptr;
+  int *ipiv = nullptr, *perm = nullptr, *info = nullptr;
+  int G = 1;
+  LuWork luw;
+  // solve workspace (nrhs columns)
+  void *r = nullptr, *x = nullptr, *hp = nullptr, *gint = nullptr, *g = nullptr;
+};
+
+}  // namespace hps
+
+using hps::ATree;
+using hps::cplx;
+using hps::DtnLeafRef;
+using hps::ItiLeafRef;
+using hps::LeafConsts;
+using hps::LevelDev;
+using hps::LuWork;
+using hps::Prof;
+using hps::Spectral1D;
+
+struct hps_handle {
+  int dim = 0, kind = 0, p = 0, q = 0, L = 0;
+  bool iti = false;
+  int64_t nl = 0, npts = 0, nroot = 0;
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, eta = 0.0, hlen = 0.0, s = 0.0;
+  hps_options opts{};
+  Spectral1D spec;
+  DtnLeafRef dref;
+  ItiLeafRef iref;
+  LeafConsts lc{};
+  int nlu_leaf = 0, xrows_leaf = 0, nb = 0;
+  // device constants
+  double *dD = nullptr, *dDD = nullptr, *dP = nullptr, *dQi = nullptr, *dQP = nullptr, *dsgn = nullptr;
+  int *dIi = nullptr, *dprow = nullptr, *diidx = nullptr, *downn = nullptr, *downa = nullptr;
+  cplx* dQH = nullptr;
+  // leaf storage
+  void* leafA = nullptr;  // LU of L_ii (DtN) or B (ItI)
+  int *leaf_ipiv = nullptr, *leaf_perm = nullptr, *leaf_info = nullptr;
+  void* leafX = nullptr;  // DtN: X = L_ii^{-1}[L_ie P | -f_i]; ItI: [Y | v]
+  void* leafTH = nullptr; // [T | h]
+  LuWork leaf_luw;
+  int leaf_G = 1;
+  std::vector<LevelDev> lev;
+  unsigned* dev_err = nullptr;
+  void* scratch = nullptr;  // build-time R / RHS buffer
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  Prof prof;
+  int64_t err_node = -1;
+  int num_sms = 0;
+  cudaStream_t last = nullptr;
+  // solve workspace
+  int ws_nrhs = 0;
+  // adaptive trees
+  bool adaptive = false;
+  ATree at;
+  std::vector<hps::AMergeDev> am;
+  std::vector<int> node_merge;   // tree node -> index in am, or -1
+  double *dC2F = nullptr, *dF2C = nullptr, *dsleaf = nullptr;
+  void* aproj_tmp = nullptr;     // projection temporaries (build)
+  void* ws_vtmp = nullptr;       // projected-vector temporary (solve)
+  int max_np = 0;
+  int64_t ws_bytes = 0;
+  std::vector<void*> ws_allocs;
+  void *ws_xf = nullptr, *ws_hleaf = nullptr, *ws_gleaf = nullptr, *ws_g = nullptr, *ws_f = nullptr,
+       *ws_u = nullptr, *ws_rhs = nullptr;
+};
+
+namespace hps {
+
+#define HPS_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      return HPS_ERR_CUDA;                              \
+    }                                                   \
+  } while (0)
+
+#define HPS_TRY(call)                                   \
+  do {                                                  \
+    hps_status s_ = (call);                             \
+    if (s_ != HPS_OK) return s_;                        \
+  } while (0)
+
+inline void* dalloc(hps_handle* h, size_t bytes, std::vector<void*>* list = nullptr) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  (list ? *list : h->allocs).push_back(p);
+  h->bytes += (int64_t)bytes;
+  return p;
+}
+
+template <typename V>
+V* upload(hps_handle* h, const std::vector<V>& v, cudaStream_t st) {
+  V* d = (V*)dalloc(h, v.size() * sizeof(V));
+  if (!d) return nullptr;
+  if (cudaMemcpyAsync(d, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return nullptr;
+  return d;
+}
+
+inline bool is_device_ptr(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T> struct Kind;
+template <> struct Kind<double> { static constexpr bool iti = false; };
+template <> struct Kind<cplx> { static constexpr bool iti = true; };
+
+}  // namespace hps

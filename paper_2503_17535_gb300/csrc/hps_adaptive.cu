@@ -1,0 +1,579 @@
+// Adaptive 3D DtN build and solve (Section 4.2): the leaf stage with
+// per-leaf sizes, then the nonuniform merges one merge node at a time, deepest
+// level first: each child's [T | h] is projected onto the coarsened interfaces
+// (4-to-1 panel projections), gathered into D, [C | h_int] and [A | h_ext],
+// D is factored (a cooperative group of CTAs), X = D^{-1}[C | h_int] and
+// [T | h] = [A | h_ext] - B X with one gathered product per child.  The
+// downward pass interpolates interface data back onto fine panels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "handle.h"
+#include "hps_adaptive.h"
+
+namespace hps {
+
+namespace {
+
+template <typename V>
+V* up_vec(hps_handle* h, const std::vector<V>& v, cudaStream_t st) {
+  return upload(h, v, st);
+}
+
+const double* child_T(hps_handle* h, int child_node, int* n, int* ld) {
+  const ANode& K = h->at.nodes[child_node];
+  if (K.leaf >= 0) {
+    *n = h->nb;
+    *ld = h->nb;
+    return (const double*)h->leafTH + (int64_t)K.leaf * h->nb * (h->nb + 1);
+  }
+  const AMergeDev& M = h->am[h->node_merge[child_node]];
+  *n = M.n_ext;
+  *ld = M.n_ext;
+  return (const double*)M.TP;
+}
+
+}  // namespace
+
+hps_status adaptive_tree_from_abi(const hps_tree* t, int p, int q, ATree* out) {
+  if (!t || t->dim != 3 || t->uniform_depth != -1 || !t->morton || !t->level || t->n_leaves < 1)
+    return HPS_ERR_INVALID;
+  if (p < 4 || p > 24 || q != p - 2) return HPS_ERR_INVALID;
+  const double side = t->hi[0] - t->lo[0];
+  if (!(side > 0)) return HPS_ERR_INVALID;
+  for (int a = 1; a < 3; ++a)
+    if (!(std::fabs((t->hi[a] - t->lo[a]) - side) <= 1e-12 * side)) return HPS_ERR_INVALID;
+  const char* why = nullptr;
+  try {
+    if (!build_atree(p, q, t->lo, t->hi, t->n_leaves, t->morton, t->level, out, &why)) return HPS_ERR_INVALID;
+  } catch (...) {
+    return HPS_ERR_INVALID;
+  }
+  return HPS_OK;
+}
+
+hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs* cf, const void* f_in,
+                          cudaStream_t st) {
+  using T = double;
+  Prof* pf = &h->prof;
+  pf->reset();
+  pf->on = h->opts.profile != 0;
+  hps_status rs = adaptive_tree_from_abi(tree, h->p, h->q, &h->at);
+  if (rs != HPS_OK) return rs;
+  ATree& at = h->at;
+  const int p = h->p, q = h->q, q2 = q * q;
+  h->spec = make_spectral(p, q);
+  h->dref = make_dtn_leaf(h->spec, 3);
+  h->nb = h->dref.nb;
+  h->nlu_leaf = h->dref.ni;
+  h->xrows_leaf = h->dref.ni;
+  const int64_t nl = h->nl;
+  const int nb = h->nb, ni = h->dref.ni;
+  // ---- footprint check
+  size_t need = (size_t)nl * ((size_t)ni * ni + (size_t)ni * (nb + 1) + (size_t)nb * (nb + 1)) * sizeof(T);
+  size_t scratch_R = (size_t)nl * ni * (nb + 1), tmp = 0;
+  int max_np = 0;
+  for (const MergePlanA& pl : at.plans) {
+    need += ((size_t)pl.n_ext * (pl.n_ext + 1) + (size_t)pl.n_int * pl.n_int + (size_t)pl.n_int * (pl.n_ext + 1)) *
+            sizeof(T);
+    scratch_R = std::max(scratch_R, (size_t)pl.n_int * (pl.n_ext + 1));
+    for (int c = 0; c < 8; ++c) {
+      need += (size_t)pl.ch[c].np * (pl.ch[c].np + 1) * sizeof(T);
+      tmp = std::max(tmp, (size_t)pl.ch[c].n * (pl.ch[c].np + 1));
+      max_np = std::max(max_np, pl.ch[c].np);
+    }
+  }
+  need += (scratch_R + tmp) * sizeof(T) + ((size_t)64 << 20);
+  {
+    size_t fr = 0, tot = 0;
+    HPS_CUDA(cudaMemGetInfo(&fr, &tot));
+    if (need > fr) return HPS_ERR_OOM;
+  }
+  h->max_np = max_np;
+  // ---- constants
+  h->dD = upload(h, h->spec.D, st);
+  h->dDD = upload(h, h->spec.DD, st);
+  std::vector<int> iidx(h->npts, -1);
+  for (int i = 0; i < ni; ++i) iidx[h->dref.Ii[i]] = i;
+  h->dIi = upload(h, h->dref.Ii, st);
+  h->dprow = upload(h, h->dref.prow, st);
+  h->dP = upload(h, h->dref.P, st);
+  h->dQi = upload(h, h->dref.Qi, st);
+  h->dQP = upload(h, h->dref.QP, st);
+  h->diidx = upload(h, iidx, st);
+  std::vector<double> sl(nl), C2F, F2C;
+  for (int64_t n = 0; n < nl; ++n) sl[n] = 2.0 / (at.side / (double)((int64_t)1 << at.nodes[at.leaf_node[n]].level));
+  h->dsleaf = upload(h, sl, st);
+  panel_projections(h->spec, &C2F, &F2C);
+  h->dC2F = upload(h, C2F, st);
+  h->dF2C = upload(h, F2C, st);
+  h->dev_err = (unsigned*)dalloc(h, sizeof(unsigned) * 4);
+  if (!h->dD || !h->dDD || !h->dIi || !h->dprow || !h->dP || !h->dQi || !h->dQP || !h->diidx || !h->dsleaf ||
+      !h->dC2F || !h->dF2C || !h->dev_err)
+    return HPS_ERR_OOM;
+  HPS_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(unsigned) * 4, st));
+  LeafConsts& k = h->lc;
+  k = LeafConsts{};
+  k.dim = 3; k.p = p; k.npts = (int)h->npts; k.nb = nb; k.s = 1.0; k.eta = 0.0;
+  k.D = h->dD; k.DD = h->dDD; k.ni = ni; k.ne = h->dref.ne; k.nown = 0;
+  k.Ii = h->dIi; k.prow = h->dprow; k.P = h->dP; k.iidx = h->diidx; k.sleaf = h->dsleaf;
+
+  // ---- staged inputs
+  std::vector<void*> tmpbufs;
+  auto stage = [&](const void* src, size_t bytes) -> const void* {
+    if (!src || is_device_ptr(src)) return src;
+    void* d = dalloc(h, bytes, &tmpbufs);
+    if (!d) return nullptr;
+    if (cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return nullptr;
+    return d;
+  };
+  const size_t cbytes = (size_t)nl * h->npts * sizeof(double);
+  Coeffs co{};
+  co.a = (const double*)stage(cf->a, cbytes);
+  for (int a = 0; a < 3; ++a) co.b[a] = (const double*)stage(cf->b[a], cbytes);
+  co.c = (const double*)stage(cf->c, cbytes);
+  const T* f = (const T*)stage(f_in, cbytes);
+
+  // ---- leaf stage
+  h->leafA = dalloc(h, (size_t)nl * ni * ni * sizeof(T));
+  h->leafX = dalloc(h, (size_t)nl * ni * (nb + 1) * sizeof(T));
+  h->leafTH = dalloc(h, (size_t)nl * nb * (nb + 1) * sizeof(T));
+  h->leaf_ipiv = (int*)dalloc(h, (size_t)nl * ni * sizeof(int));
+  h->leaf_perm = (int*)dalloc(h, (size_t)nl * ni * sizeof(int));
+  h->leaf_info = (int*)dalloc(h, (size_t)nl * sizeof(int));
+  h->scratch = dalloc(h, scratch_R * sizeof(T));
+  h->aproj_tmp = dalloc(h, std::max<size_t>(tmp, 16) * sizeof(T));
+  if (!h->leafA || !h->leafX || !h->leafTH || !h->leaf_ipiv || !h->leaf_perm || !h->leaf_info || !h->scratch ||
+      !h->aproj_tmp)
+    return HPS_ERR_OOM;
+  HPS_CUDA(cudaMemsetAsync(h->leaf_info, 0, (size_t)nl * sizeof(int), st));
+  T* RHS = (T*)h->scratch;
+  HPS_CUDA(leaf_dtn_assemble(k, nl, co, f, (T*)h->leafA, RHS, st, pf));
+  h->leaf_G = lu_group_size<T>(ni, (int)nl, h->num_sms);
+  if (h->leaf_G > 1) {
+    h->leaf_luw.bars = (unsigned*)dalloc(h, sizeof(unsigned) * 2 * nl);
+    h->leaf_luw.pub_bytes = lu_pub_bytes<T>(ni, (int)nl, h->leaf_G);
+    h->leaf_luw.pub = dalloc(h, h->leaf_luw.pub_bytes);
+    if (!h->leaf_luw.bars || !h->leaf_luw.pub) return HPS_ERR_OOM;
+    HPS_CUDA(cudaMemsetAsync(h->leaf_luw.bars, 0, sizeof(unsigned) * 2 * nl, st));
+  }
+  BOp<T> LA = bop<T>((T*)h->leafA, (int64_t)ni * ni, ni);
+  HPS_CUDA(getrf<T>(LA, ni, (int)nl, h->leaf_ipiv, h->leaf_perm, h->leaf_info, h->dev_err, h->leaf_G, h->leaf_luw,
+                    st, pf));
+  BOp<T> LX = bop<T>((T*)h->leafX, (int64_t)ni * (nb + 1), ni);
+  HPS_CUDA(permute_rows<T>(bop<T>(RHS, (int64_t)ni * (nb + 1), ni), LX, h->leaf_perm, ni, nb + 1, (int)nl, st, pf));
+  HPS_CUDA(getrs_inplace<T>(LA, ni, LX, nb + 1, (int)nl, st, pf));
+  HPS_CUDA(leaf_dtn_init_T(h->dQP, nb, 1.0, nl, (T*)h->leafTH, st, pf));
+  {
+    GemmArgs<T> g;
+    g.M = nb; g.N = nb + 1; g.K = ni; g.batch = (int)nl;
+    g.A = bop<T>(h->dQi, 0, nb);
+    g.B = LX;
+    g.C = bop<T>((T*)h->leafTH, (int64_t)nb * (nb + 1), nb);
+    g.alpha = -1.0; g.beta = 1.0;
+    HPS_CUDA(gemm<T>(g, st, pf));
+  }
+  // T = s (QP - Q_i X) per leaf size
+  HPS_CUDA(scale_blocks<T>((T*)h->leafTH, (int64_t)nb * (nb + 1), h->dsleaf, nl, st, pf));
+
+  // ---- nonuniform merges, deepest first
+  h->node_merge.assign(at.nodes.size(), -1);
+  h->am.resize(at.plans.size());
+  for (size_t mi = 0; mi < at.plans.size(); ++mi) h->node_merge[at.plans[mi].node] = (int)mi;
+  for (size_t mi = 0; mi < at.plans.size(); ++mi) {
+    const MergePlanA& pl = at.plans[mi];
+    AMergeDev& M = h->am[mi];
+    M.node = pl.node;
+    M.n_ext = pl.n_ext;
+    M.n_int = pl.n_int;
+    const int ne = pl.n_ext, nI = pl.n_int;
+    const bool is_root = pl.node == 0;
+    M.TP = dalloc(h, (size_t)ne * (ne + 1) * sizeof(T));
+    M.D = dalloc(h, (size_t)nI * nI * sizeof(T));
+    M.X = dalloc(h, (size_t)nI * (ne + 1) * sizeof(T));
+    M.ipiv = (int*)dalloc(h, (size_t)nI * sizeof(int));
+    M.perm = (int*)dalloc(h, (size_t)nI * sizeof(int));
+    M.info = (int*)dalloc(h, sizeof(int));
+    if (!M.TP || !M.D || !M.X || !M.ipiv || !M.perm || !M.info) return HPS_ERR_OOM;
+    HPS_CUDA(cudaMemsetAsync(M.info, 0, sizeof(int), st));
+    const ANode& nd = at.nodes[pl.node];
+    // project every child onto the coarsened interfaces
+    for (int c = 0; c < 8; ++c) {
+      const ChildProj& cp = pl.ch[c];
+      AChildDev& CD = M.ch[c];
+      std::vector<int4> src4(cp.np);
+      for (int i = 0; i < cp.np; ++i) src4[i] = make_int4(cp.src[i][0], cp.src[i][1], cp.src[i][2], cp.src[i][3]);
+      CD.pj.n = cp.n;
+      CD.pj.np = cp.np;
+      CD.pj.q2 = q2;
+      CD.pj.kind = up_vec(h, cp.kind, st);
+      CD.pj.u = up_vec(h, cp.u, st);
+      CD.pj.src = up_vec(h, src4, st);
+      CD.pj.bcopy = up_vec(h, cp.back_copy, st);
+      CD.pj.bbase = up_vec(h, cp.back_base, st);
+      CD.pj.bquad = up_vec(h, cp.back_quad, st);
+      CD.pj.bt = up_vec(h, cp.back_t, st);
+      CD.ext = up_vec(h, cp.ext, st);
+      CD.var = up_vec(h, cp.var, st);
+      CD.barow = up_vec(h, cp.b_arow, st);
+      CD.bacol = up_vec(h, cp.b_acol, st);
+      CD.bbrow = up_vec(h, cp.b_brow, st);
+      CD.bcrow = up_vec(h, cp.b_crow, st);
+      CD.ne_c = (int)cp.b_arow.size();
+      CD.ni_c = (int)cp.b_acol.size();
+      CD.Tp = dalloc(h, (size_t)cp.np * (cp.np + 1) * sizeof(T));
+      if (!CD.pj.kind || !CD.pj.u || !CD.pj.src || !CD.pj.bcopy || !CD.pj.bbase || !CD.pj.bquad || !CD.pj.bt ||
+          !CD.ext || !CD.var || !CD.barow || !CD.bacol || !CD.bbrow || !CD.bcrow || !CD.Tp)
+        return HPS_ERR_OOM;
+      int n = 0, ld = 0;
+      const T* Tc = child_T(h, nd.child[c], &n, &ld);
+      T* tmpT = (T*)h->aproj_tmp;
+      HPS_CUDA(proj_cols<T>(Tc, ld, n, CD.pj, h->dC2F, tmpT, n, st, pf));
+      HPS_CUDA(proj_rows<T>(tmpT, n, cp.np + 1, CD.pj, h->dF2C, (T*)CD.Tp, cp.np, st, pf));
+    }
+    T* R = (T*)h->scratch;
+    HPS_CUDA(fill<T>(bop<T>((T*)M.D, 0, nI), nI, nI, 1, 0.0, 0.0, st, pf));
+    HPS_CUDA(fill<T>(bop<T>(R, 0, nI), nI, ne + 1, 1, 0.0, 0.0, st, pf));
+    HPS_CUDA(fill<T>(bop<T>((T*)M.TP, 0, ne), ne, ne + 1, 1, 0.0, 0.0, st, pf));
+    for (int c = 0; c < 8; ++c) {
+      const AChildDev& CD = M.ch[c];
+      HPS_CUDA(merge_gather<T>((const T*)CD.Tp, 0, 1, 1, CD.pj.np, ne, nI, CD.ext, CD.var, CD.var, false, (T*)M.D, R,
+                               (T*)M.TP, st, pf));
+    }
+    M.G = lu_group_size<T>(nI, 1, h->num_sms);
+    if (M.G > 1) {
+      M.luw.bars = (unsigned*)dalloc(h, sizeof(unsigned) * 2);
+      M.luw.pub_bytes = lu_pub_bytes<T>(nI, 1, M.G);
+      M.luw.pub = dalloc(h, M.luw.pub_bytes);
+      if (!M.luw.bars || !M.luw.pub) return HPS_ERR_OOM;
+      HPS_CUDA(cudaMemsetAsync(M.luw.bars, 0, sizeof(unsigned) * 2, st));
+    }
+    BOp<T> DD = bop<T>((T*)M.D, 0, nI);
+    BOp<T> XX = bop<T>((T*)M.X, 0, nI);
+    HPS_CUDA(getrf<T>(DD, nI, 1, M.ipiv, M.perm, M.info, h->dev_err, M.G, M.luw, st, pf));
+    HPS_CUDA(permute_rows<T>(bop<T>(R, 0, nI), XX, M.perm, nI, ne + 1, 1, st, pf));
+    HPS_CUDA(getrs_inplace<T>(DD, nI, XX, ne + 1, 1, st, pf));
+    if (!is_root || h->opts.want_root_map) {
+      for (int c = 0; c < 8; ++c) {
+        const AChildDev& CD = M.ch[c];
+        GemmArgs<T> g;
+        g.M = CD.ne_c; g.N = ne + 1; g.K = CD.ni_c; g.batch = 1;
+        g.A = bop<T>((T*)CD.Tp, 0, CD.pj.np);
+        g.arow.idx = CD.barow; g.arow.len = CD.ne_c;
+        g.acol.idx = CD.bacol; g.acol.len = CD.ni_c;
+        g.B = XX;
+        g.brow.idx = CD.bbrow; g.brow.len = CD.ni_c;
+        g.C = bop<T>((T*)M.TP, 0, ne);
+        g.crow.idx = CD.bcrow; g.crow.len = CD.ne_c;
+        g.alpha = -1.0; g.beta = 1.0;
+        HPS_CUDA(gemm<T>(g, st, pf));
+      }
+    }
+  }
+  HPS_CUDA(cudaStreamSynchronize(st));
+  for (void* tb : tmpbufs) cudaFree(tb);
+  unsigned derr = 0;
+  HPS_CUDA(cudaMemcpy(&derr, h->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (derr & DEV_ERR_TIMEOUT) return HPS_ERR_TIMEOUT;
+  std::vector<int> info(nl);
+  HPS_CUDA(cudaMemcpy(info.data(), h->leaf_info, nl * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < nl; ++i)
+    if (info[i]) { h->err_node = i; return HPS_ERR_SINGULAR; }
+  for (size_t mi = 0; mi < h->am.size(); ++mi) {
+    int v = 0;
+    HPS_CUDA(cudaMemcpy(&v, h->am[mi].info, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v) { h->err_node = nl + (int64_t)mi; return HPS_ERR_SINGULAR; }
+  }
+  return HPS_OK;
+}
+
+static hps_status adaptive_ws(hps_handle* h, int nrhs) {
+  using T = double;
+  if (h->ws_nrhs >= nrhs) return HPS_OK;
+  for (void* pp : h->ws_allocs) cudaFree(pp);
+  h->ws_allocs.clear();
+  h->bytes -= h->ws_bytes;
+  const int64_t before = h->bytes;
+  const size_t es = sizeof(T);
+  auto A = [&](size_t bytes) { return dalloc(h, bytes, &h->ws_allocs); };
+  h->ws_xf = A((size_t)h->nl * h->xrows_leaf * nrhs * es);
+  h->ws_hleaf = A((size_t)h->nl * h->nb * nrhs * es);
+  h->ws_gleaf = A((size_t)h->nl * h->nb * nrhs * es);
+  h->ws_g = A((size_t)h->nroot * nrhs * es);
+  h->ws_f = A((size_t)h->nl * h->npts * nrhs * es);
+  h->ws_u = A((size_t)h->nl * h->npts * nrhs * es);
+  h->ws_rhs = A((size_t)h->nl * h->xrows_leaf * nrhs * es);
+  void* vt = A((size_t)std::max(h->max_np, 1) * nrhs * es);
+  if (!h->ws_xf || !h->ws_hleaf || !h->ws_gleaf || !h->ws_g || !h->ws_f || !h->ws_u || !h->ws_rhs || !vt)
+    return HPS_ERR_OOM;
+  h->ws_vtmp = vt;
+  for (AMergeDev& M : h->am) {
+    M.r = A((size_t)M.n_int * nrhs * es);
+    M.x = A((size_t)M.n_int * nrhs * es);
+    M.hp = A((size_t)M.n_ext * nrhs * es);
+    M.gint = A((size_t)M.n_int * nrhs * es);
+    M.g = A((size_t)M.n_ext * nrhs * es);
+    if (!M.r || !M.x || !M.hp || !M.gint || !M.g) return HPS_ERR_OOM;
+  }
+  h->ws_bytes = h->bytes - before;
+  h->ws_nrhs = nrhs;
+  return HPS_OK;
+}
+
+hps_status adaptive_solve(hps_handle* h, int nrhs, const void* g_in, const void* f_in, void* u_out,
+                          cudaStream_t st) {
+  using T = double;
+  hps_status rs = adaptive_ws(h, nrhs);
+  if (rs != HPS_OK) return rs;
+  Prof* pf = &h->prof;
+  pf->reset();
+  pf->on = h->opts.profile != 0;
+  const ATree& at = h->at;
+  const int64_t nl = h->nl;
+  const int nb = h->nb, ni = h->dref.ni;
+  const T* g = (const T*)g_in;
+  if (!is_device_ptr(g_in)) {
+    HPS_CUDA(cudaMemcpyAsync(h->ws_g, g_in, (size_t)h->nroot * nrhs * sizeof(T), cudaMemcpyHostToDevice, st));
+    g = (const T*)h->ws_g;
+  }
+  const T* f = (const T*)f_in;
+  if (f_in && !is_device_ptr(f_in)) {
+    HPS_CUDA(cudaMemcpyAsync(h->ws_f, f_in, (size_t)nl * h->npts * nrhs * sizeof(T), cudaMemcpyHostToDevice, st));
+    f = (const T*)h->ws_f;
+  }
+  const bool host_u = !is_device_ptr(u_out);
+  T* u = host_u ? (T*)h->ws_u : (T*)u_out;
+  const bool newf = f != nullptr;
+  T* vt = (T*)h->ws_vtmp;
+
+  if (newf) {
+    T* xf = (T*)h->ws_xf;
+    T* tmp = (T*)h->ws_rhs;
+    HPS_CUDA(leaf_particular_rhs<T>(h->lc, nl, nrhs, f, tmp, false, st, pf));
+    BOp<T> LA = bop<T>((T*)h->leafA, (int64_t)ni * ni, ni);
+    BOp<T> XF = bop<T>(xf, (int64_t)ni * nrhs, ni);
+    HPS_CUDA(permute_rows<T>(bop<T>(tmp, (int64_t)ni * nrhs, ni), XF, h->leaf_perm, ni, nrhs, (int)nl, st, pf));
+    HPS_CUDA(getrs_inplace<T>(LA, ni, XF, nrhs, (int)nl, st, pf));
+    GemmArgs<T> gl;
+    gl.M = nb; gl.N = nrhs; gl.K = ni; gl.batch = (int)nl;
+    gl.A = bop<T>(h->dQi, 0, nb);
+    gl.B = XF;
+    gl.C = bop<T>((T*)h->ws_hleaf, (int64_t)nb * nrhs, nb);
+    gl.alpha = -1.0; gl.beta = 0.0;
+    HPS_CUDA(gemm<T>(gl, st, pf));
+    HPS_CUDA(scale_blocks<T>((T*)h->ws_hleaf, (int64_t)nb * nrhs, h->dsleaf, nl, st, pf));
+    for (size_t mi = 0; mi < h->am.size(); ++mi) {
+      AMergeDev& M = h->am[mi];
+      const ANode& nd = at.nodes[M.node];
+      const int ne = M.n_ext, nI = M.n_int;
+      HPS_CUDA(fill<T>(bop<T>((T*)M.r, 0, nI), nI, nrhs, 1, 0.0, 0.0, st, pf));
+      for (int c = 0; c < 8; ++c) {
+        const AChildDev& CD = M.ch[c];
+        const ANode& K = at.nodes[nd.child[c]];
+        const T* hc;
+        int ldh;
+        if (K.leaf >= 0) { hc = (const T*)h->ws_hleaf + (int64_t)K.leaf * nb * nrhs; ldh = nb; }
+        else { const AMergeDev& C2 = h->am[h->node_merge[nd.child[c]]]; hc = (const T*)C2.hp; ldh = C2.n_ext; }
+        HPS_CUDA(proj_rows<T>(hc, ldh, nrhs, CD.pj, h->dF2C, vt, CD.pj.np, st, pf));
+        HPS_CUDA(merge_gather_h<T>(vt, 1, 1, CD.pj.np, ne, nI, nrhs, CD.ext, CD.var, CD.var, false, (T*)M.r,
+                                   (T*)M.hp, st, pf));
+      }
+      BOp<T> DD = bop<T>((T*)M.D, 0, nI);
+      BOp<T> XB = bop<T>((T*)M.x, 0, nI);
+      HPS_CUDA(permute_rows<T>(bop<T>((T*)M.r, 0, nI), XB, M.perm, nI, nrhs, 1, st, pf));
+      HPS_CUDA(getrs_inplace<T>(DD, nI, XB, nrhs, 1, st, pf));
+      if (M.node != 0) {
+        for (int c = 0; c < 8; ++c) {
+          const AChildDev& CD = M.ch[c];
+          GemmArgs<T> gg;
+          gg.M = CD.ne_c; gg.N = nrhs; gg.K = CD.ni_c; gg.batch = 1;
+          gg.A = bop<T>((T*)CD.Tp, 0, CD.pj.np);
+          gg.arow.idx = CD.barow; gg.arow.len = CD.ne_c;
+          gg.acol.idx = CD.bacol; gg.acol.len = CD.ni_c;
+          gg.B = XB;
+          gg.brow.idx = CD.bbrow; gg.brow.len = CD.ni_c;
+          gg.C = bop<T>((T*)M.hp, 0, ne);
+          gg.crow.idx = CD.bcrow; gg.crow.len = CD.ne_c;
+          gg.alpha = -1.0; gg.beta = 1.0;
+          HPS_CUDA(gemm<T>(gg, st, pf));
+        }
+      }
+    }
+  }
+  // downward pass, root first
+  for (size_t k2 = h->am.size(); k2-- > 0;) {
+    AMergeDev& M = h->am[k2];
+    const ANode& nd = at.nodes[M.node];
+    const T* gpar = (M.node == 0) ? g : (const T*)M.g;
+    HPS_CUDA(down_gint<T>((const T*)M.X, newf ? (const T*)M.x : nullptr, gpar, 1, M.n_ext, M.n_int, nrhs,
+                          (T*)M.gint, st, pf));
+    for (int c = 0; c < 8; ++c) {
+      const AChildDev& CD = M.ch[c];
+      HPS_CUDA(down_children<T>(gpar, (const T*)M.gint, 1, 1, CD.pj.np, M.n_ext, M.n_int, nrhs, CD.ext, CD.var,
+                                vt, st, pf));
+      const ANode& K = at.nodes[nd.child[c]];
+      T* gc;
+      int ldg;
+      if (K.leaf >= 0) { gc = (T*)h->ws_gleaf + (int64_t)K.leaf * nb * nrhs; ldg = nb; }
+      else { AMergeDev& C2 = h->am[h->node_merge[nd.child[c]]]; gc = (T*)C2.g; ldg = C2.n_ext; }
+      HPS_CUDA(unproject<T>(vt, CD.pj.np, CD.pj, h->dC2F, gc, ldg, nrhs, st, pf));
+    }
+  }
+  const T* gleaf = h->am.empty() ? g : (const T*)h->ws_gleaf;
+  HPS_CUDA(leaf_output<T>(h->lc, nl, nrhs, (const T*)h->leafX, newf ? (const T*)h->ws_xf : nullptr, gleaf, u, false,
+                          st, pf));
+  if (host_u) {
+    HPS_CUDA(cudaMemcpyAsync(u_out, u, (size_t)nl * h->npts * nrhs * sizeof(T), cudaMemcpyDeviceToHost, st));
+    HPS_CUDA(cudaStreamSynchronize(st));
+  }
+  return HPS_OK;
+}
+
+// ---------------------------------------------------------------- refine ----
+
+namespace {
+
+// p Chebyshev values on [-1, 1] -> the two children's Chebyshev nodes
+// ([-1, 0] then [0, 1]): 2p x p, row-major.
+std::vector<double> child_interp(const Spectral1D& s) {
+  const int p = s.p;
+  std::vector<double> w(p), M((size_t)2 * p * p, 0.0);
+  for (int j = 0; j < p; ++j) {
+    w[j] = 1.0;
+    for (int k = 0; k < p; ++k)
+      if (k != j) w[j] *= (s.xc[j] - s.xc[k]);
+    w[j] = 1.0 / w[j];
+  }
+  for (int i = 0; i < 2 * p; ++i) {
+    const double t = (i < p) ? 0.5 * (s.xc[i] - 1.0) : 0.5 * (s.xc[i - p] + 1.0);
+    int hit = -1;
+    for (int j = 0; j < p; ++j)
+      if (t == s.xc[j]) hit = j;
+    if (hit >= 0) { M[(size_t)i * p + hit] = 1.0; continue; }
+    double den = 0.0;
+    for (int j = 0; j < p; ++j) den += w[j] / (t - s.xc[j]);
+    for (int j = 0; j < p; ++j) M[(size_t)i * p + j] = (w[j] / (t - s.xc[j])) / den;
+  }
+  return M;
+}
+
+void leaf_points(const double* lo, double side, int level, const int64_t* ix, const Spectral1D& s, double* out) {
+  const int p = s.p;
+  const double h = side / (double)((int64_t)1 << level);
+  for (int node = 0; node < p * p * p; ++node) {
+    const int c[3] = {node % p, (node / p) % p, node / (p * p)};
+    for (int a = 0; a < 3; ++a) out[(size_t)node * 3 + a] = lo[a] + (ix[a] + 0.5 * (s.xc[c[a]] + 1.0)) * h;
+  }
+}
+
+}  // namespace
+
+hps_status adaptive_refine(const double* lo, const double* hi, int p, double eps, int min_depth, int max_depth,
+                           int n_fn, const hps_eval_fn* fns, void* const* ctxs, int64_t capacity,
+                           int64_t* n_leaves, uint64_t* morton, int8_t* level, cudaStream_t st) {
+  if (!lo || !hi || p < 4 || p > 24 || !(eps > 0) || min_depth < 0 || max_depth < min_depth || max_depth > 10 ||
+      n_fn < 1 || !fns || !n_leaves)
+    return HPS_ERR_INVALID;
+  const double side = hi[0] - lo[0];
+  if (!(side > 0)) return HPS_ERR_INVALID;
+  for (int a = 1; a < 3; ++a)
+    if (!(std::fabs((hi[a] - lo[a]) - side) <= 1e-12 * side)) return HPS_ERR_INVALID;
+  const Spectral1D s = make_spectral(p, p - 2);
+  const std::vector<double> I1 = child_interp(s);
+  const int npts = p * p * p;
+  using Leaf = std::pair<int, std::array<int64_t, 3>>;
+  std::vector<Leaf> cand, fin;
+  const int64_t n1 = (int64_t)1 << min_depth;
+  for (int64_t z = 0; z < n1; ++z)
+    for (int64_t y = 0; y < n1; ++y)
+      for (int64_t x = 0; x < n1; ++x) cand.push_back({min_depth, {x, y, z}});
+  std::vector<double> norms(n_fn, 0.0);
+  double* dI1 = nullptr;
+  double *d0 = nullptr, *d1 = nullptr, *derr = nullptr;
+  size_t cap_leaves = 0;
+  auto release = [&]() {
+    cudaFree(dI1); cudaFree(d0); cudaFree(d1); cudaFree(derr);
+    dI1 = d0 = d1 = derr = nullptr;
+  };
+  if (cudaMalloc(&dI1, I1.size() * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return HPS_ERR_OOM; }
+  if (cudaMemcpy(dI1, I1.data(), I1.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    release();
+    return HPS_ERR_CUDA;
+  }
+  while (!cand.empty()) {
+    if (cand[0].first >= max_depth) {
+      fin.insert(fin.end(), cand.begin(), cand.end());
+      break;
+    }
+    const size_t nc = cand.size();
+    std::vector<double> x0(nc * npts * 3), x1(nc * 8 * npts * 3);
+    for (size_t n = 0; n < nc; ++n) {
+      leaf_points(lo, side, cand[n].first, cand[n].second.data(), s, &x0[n * npts * 3]);
+      for (int c = 0; c < 8; ++c) {
+        const int64_t ci[3] = {2 * cand[n].second[0] + (c & 1), 2 * cand[n].second[1] + ((c >> 1) & 1),
+                               2 * cand[n].second[2] + (c >> 2)};
+        leaf_points(lo, side, cand[n].first + 1, ci, s, &x1[(n * 8 + c) * npts * 3]);
+      }
+    }
+    if (nc > cap_leaves) {
+      cudaFree(d0); cudaFree(d1); cudaFree(derr);
+      d0 = d1 = derr = nullptr;
+      if (cudaMalloc(&d0, nc * npts * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&d1, nc * 8 * npts * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&derr, nc * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return HPS_ERR_OOM;
+      }
+      cap_leaves = nc;
+    }
+    std::vector<char> split(nc, 0);
+    std::vector<std::vector<double>> errs(n_fn);
+    std::vector<double> v0(nc * npts), v1(nc * 8 * npts);
+    for (int k = 0; k < n_fn; ++k) {
+      void* ctx = ctxs ? ctxs[k] : nullptr;
+      if (fns[k](ctx, (int64_t)(nc * npts), x0.data(), v0.data()) != 0 ||
+          fns[k](ctx, (int64_t)(nc * 8 * npts), x1.data(), v1.data()) != 0) {
+        release();
+        return HPS_ERR_INVALID;
+      }
+      for (double v : v0) norms[k] = std::max(norms[k], std::fabs(v));
+      for (double v : v1) norms[k] = std::max(norms[k], std::fabs(v));
+      errs[k].resize(nc);
+      if (cudaMemcpyAsync(d0, v0.data(), v0.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(d1, v1.data(), v1.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          refine_check(d0, d1, (int64_t)nc, p, dI1, derr, st) != cudaSuccess ||
+          cudaMemcpyAsync(errs[k].data(), derr, nc * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        release();
+        return HPS_ERR_CUDA;
+      }
+    }
+    // the norms include every sample of this level before any decision
+    for (int k = 0; k < n_fn; ++k)
+      for (size_t n = 0; n < nc; ++n)
+        if (norms[k] > 0.0 && errs[k][n] / norms[k] >= eps) split[n] = 1;
+    std::vector<Leaf> nxt;
+    for (size_t n = 0; n < nc; ++n) {
+      if (!split[n]) { fin.push_back(cand[n]); continue; }
+      for (int c = 0; c < 8; ++c)
+        nxt.push_back({cand[n].first + 1, {2 * cand[n].second[0] + (c & 1), 2 * cand[n].second[1] + ((c >> 1) & 1),
+                                           2 * cand[n].second[2] + (c >> 2)}});
+    }
+    cand.swap(nxt);
+  }
+  release();
+  balance_leaves(&fin);
+  *n_leaves = (int64_t)fin.size();
+  if ((int64_t)fin.size() > capacity || !morton || !level) return capacity < 0 ? HPS_ERR_INVALID : HPS_OK;
+  for (size_t n = 0; n < fin.size(); ++n) {
+    morton[n] = morton_encode(fin[n].second.data());
+    level[n] = (int8_t)fin[n].first;
+  }
+  return HPS_OK;
+}
+
+}  // namespace hps

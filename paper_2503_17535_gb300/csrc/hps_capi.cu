@@ -11,114 +11,12 @@
 #include <string>
 #include <vector>
 
-#include "hps.h"
-#include "hps_kernels.cuh"
-#include "linalg.h"
-#include "plan.h"
+#include "handle.h"
+#include "hps_adaptive.h"
 
 using namespace hps;
 
 namespace {
-
-struct LevelDev {
-  int nmerge = 0, nch = 0, n = 0, nbc = 0, n_ext = 0, n_int = 0;
-  int *ext = nullptr, *var = nullptr, *eq = nullptr;
-  int *barow = nullptr, *bacol = nullptr, *bbrow = nullptr, *bcrow = nullptr;
-  void* TP = nullptr;   // [nmerge][n_ext x (n_ext+1)]  parent [T | h]
-  void* D = nullptr;    // [nmerge][n_int x n_int]
-  void* W = nullptr;    // ItI: [nmerge][(n_int/2)^2] (LU of W)
-  int* ipiv = nullptr;  // [nmerge][nlu]
-  int* perm = nullptr;
-  int* info = nullptr;  // [nmerge]
-  void* X = nullptr;    // [nmerge][n_int x (n_ext+1)]  D^{-1} [C | h_int]
-  int G = 1;
-  LuWork luw;
-  // solve workspace (nrhs columns)
-  void *r = nullptr, *hp = nullptr, *x = nullptr, *gint = nullptr, *gchild = nullptr;
-  bool top() const { return nmerge == 1; }
-};
-
-}  // namespace
-
-struct hps_handle {
-  int dim = 0, kind = 0, p = 0, q = 0, L = 0;
-  bool iti = false;
-  int64_t nl = 0, npts = 0, nroot = 0;
-  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, eta = 0.0, hlen = 0.0, s = 0.0;
-  hps_options opts{};
-  Spectral1D spec;
-  DtnLeafRef dref;
-  ItiLeafRef iref;
-  LeafConsts lc{};
-  int nlu_leaf = 0, xrows_leaf = 0, nb = 0;
-  // device constants
-  double *dD = nullptr, *dDD = nullptr, *dP = nullptr, *dQi = nullptr, *dQP = nullptr, *dsgn = nullptr;
-  int *dIi = nullptr, *dprow = nullptr, *diidx = nullptr, *downn = nullptr, *downa = nullptr;
-  cplx* dQH = nullptr;
-  // leaf storage
-  void* leafA = nullptr;  // LU of L_ii (DtN) or B (ItI)
-  int *leaf_ipiv = nullptr, *leaf_perm = nullptr, *leaf_info = nullptr;
-  void* leafX = nullptr;  // DtN: X = L_ii^{-1}[L_ie P | -f_i]; ItI: [Y | v]
-  void* leafTH = nullptr; // [T | h]
-  LuWork leaf_luw;
-  int leaf_G = 1;
-  std::vector<LevelDev> lev;
-  unsigned* dev_err = nullptr;
-  void* scratch = nullptr;  // build-time R / RHS buffer
-  std::vector<void*> allocs;
-  int64_t bytes = 0;
-  Prof prof;
-  int64_t err_node = -1;
-  int num_sms = 0;
-  cudaStream_t last = nullptr;
-  // solve workspace
-  int ws_nrhs = 0;
-  int64_t ws_bytes = 0;
-  std::vector<void*> ws_allocs;
-  void *ws_xf = nullptr, *ws_hleaf = nullptr, *ws_gleaf = nullptr, *ws_g = nullptr, *ws_f = nullptr,
-       *ws_u = nullptr, *ws_rhs = nullptr;
-};
-
-namespace {
-
-#define HPS_CUDA(call)                                  \
-  do {                                                  \
-    cudaError_t e_ = (call);                            \
-    if (e_ != cudaSuccess) {                            \
-      return HPS_ERR_CUDA;                              \
-    }                                                   \
-  } while (0)
-
-void* dalloc(hps_handle* h, size_t bytes, std::vector<void*>* list = nullptr) {
-  if (bytes == 0) bytes = 16;
-  void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  (list ? *list : h->allocs).push_back(p);
-  h->bytes += (int64_t)bytes;
-  return p;
-}
-
-template <typename V>
-V* upload(hps_handle* h, const std::vector<V>& v, cudaStream_t st) {
-  V* d = (V*)dalloc(h, v.size() * sizeof(V));
-  if (!d) return nullptr;
-  if (cudaMemcpyAsync(d, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return nullptr;
-  return d;
-}
-
-bool is_device_ptr(const void* p) {
-  if (!p) return true;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 hps_status check_tree(const hps_tree* t, int p, int q) {
   if (!t) return HPS_ERR_INVALID;
@@ -138,10 +36,6 @@ hps_status check_tree(const hps_tree* t, int p, int q) {
 int64_t nroot_of(int dim, int q, int L) {
   return dim == 2 ? 4LL * q * ((int64_t)1 << L) : 6LL * q * q * ((int64_t)1 << (2 * L));
 }
-
-template <typename T> struct Kind;
-template <> struct Kind<double> { static constexpr bool iti = false; };
-template <> struct Kind<cplx> { static constexpr bool iti = true; };
 
 // ------------------------------------------------------------- planning ----
 
@@ -347,6 +241,22 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
     Lv.bacol = upload(h, mm.b_acol, st);
     Lv.bbrow = upload(h, mm.b_brow, st);
     Lv.bcrow = upload(h, mm.b_crow, st);
+    if (ITI) {
+      const int hb = mm.nbc / 2;
+      auto pick = [&](int c0, int c1, const std::vector<int>& src) {
+        std::vector<int> v(src.begin() + (size_t)c0 * hb, src.begin() + (size_t)(c0 + 1) * hb);
+        v.insert(v.end(), src.begin() + (size_t)c1 * hb, src.begin() + (size_t)(c1 + 1) * hb);
+        return v;
+      };
+      Lv.odd_pts = upload(h, pick(1, 2, mm.b_acol), st);
+      Lv.odd_var = upload(h, pick(1, 2, mm.b_brow), st);
+      Lv.odd_eq = upload(h, pick(1, 2, mm.i_eq), st);
+      Lv.even_pts = upload(h, pick(0, 3, mm.b_acol), st);
+      Lv.even_var = upload(h, pick(0, 3, mm.b_brow), st);
+      Lv.even_eq = upload(h, pick(0, 3, mm.i_eq), st);
+      if (!Lv.odd_pts || !Lv.odd_var || !Lv.odd_eq || !Lv.even_pts || !Lv.even_var || !Lv.even_eq)
+        return HPS_ERR_OOM;
+    }
     const int ne = mm.n_ext, ni = mm.n_int;
     const int nlu_m = ITI ? ni / 2 : ni;
     Lv.TP = dalloc(h, (size_t)nm * ne * (ne + 1) * sizeof(T));
@@ -360,7 +270,9 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
         !Lv.D || (ITI && !Lv.W) || !Lv.X || !Lv.ipiv || !Lv.perm || !Lv.info)
       return HPS_ERR_OOM;
     HPS_CUDA(cudaMemsetAsync(Lv.info, 0, (size_t)nm * sizeof(int), st));
-    T* R = (T*)h->scratch;
+    Lv.lazy = Lv.top() && h->opts.lazy_root && !h->opts.want_root_map;
+    // at a lazy root [C | h_int] is kept (in X's storage) instead of X
+    T* R = Lv.lazy ? (T*)Lv.X : (T*)h->scratch;
     // D, R = [C | h_int], TP = [A | h_ext]
     HPS_CUDA(fill<T>(bop<T>((T*)Lv.D, (int64_t)ni * ni, ni), ni, ni, (int)nm, T(0.0), ITI ? T(1.0) : T(0.0), st, pf));
     HPS_CUDA(fill<T>(bop<T>(R, (int64_t)ni * (ne + 1), ni), ni, ne + 1, (int)nm, T(0.0), T(0.0), st, pf));
@@ -379,8 +291,10 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
     if (!ITI) {
       BOp<T> DD = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni);
       HPS_CUDA(getrf<T>(DD, ni, (int)nm, Lv.ipiv, Lv.perm, Lv.info, h->dev_err, Lv.G, Lv.luw, st, pf));
-      HPS_CUDA(permute_rows<T>(bop<T>(R, (int64_t)ni * (ne + 1), ni), XX, Lv.perm, ni, ne + 1, (int)nm, st, pf));
-      HPS_CUDA(getrs_inplace<T>(DD, ni, XX, ne + 1, (int)nm, st, pf));
+      if (!Lv.lazy) {
+        HPS_CUDA(permute_rows<T>(bop<T>(R, (int64_t)ni * (ne + 1), ni), XX, Lv.perm, ni, ne + 1, (int)nm, st, pf));
+        HPS_CUDA(getrs_inplace<T>(DD, ni, XX, ne + 1, (int)nm, st, pf));
+      }
     } else {
       const int hn = ni / 2;
       BOp<T> D12 = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni, (int64_t)hn * ni);
@@ -388,17 +302,39 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
       BOp<T> WW = bop<T>((T*)Lv.W, (int64_t)hn * hn, hn);
       BOp<T> R1 = bop<T>(R, (int64_t)ni * (ne + 1), ni);
       BOp<T> R2 = bop<T>(R, (int64_t)ni * (ne + 1), ni, hn);
-      // W = I - D12 D21 (Eq. "ItI D inverse")
+      (void)D12;
+      (void)R2;
+      // D12 (D21) is nonzero only in the interior-interior blocks of the odd
+      // (even) children: its product with a matrix is one gathered product
+      // per child, rows = the child's equation rows, K = its interior points.
+      const int hb = mm.nbc / 2;
+      auto child_block = [&](bool odd, BOp<T> B, BOp<T> C, int N) {
+        GemmArgs<T> g;
+        g.M = hb; g.N = N; g.K = hb; g.batch = (int)nm * 2;
+        BOp<T> A = bop<T>(const_cast<T*>(Tc) + (odd ? cstride : 0), (int64_t)nch * cstride, mm.nbc);
+        A.div = 2;
+        A.sub = (odd ? 1 : 3) * cstride;
+        g.A = A;
+        g.arow.idx = odd ? Lv.odd_pts : Lv.even_pts; g.arow.len = hb; g.arow.period = 2;
+        g.acol = g.arow;
+        g.B = B;
+        g.brow.idx = odd ? Lv.odd_var : Lv.even_var; g.brow.len = hb; g.brow.period = 2;
+        g.C = C;
+        g.crow.idx = odd ? Lv.odd_eq : Lv.even_eq; g.crow.len = hb; g.crow.period = 2;
+        g.alpha = T(-1.0); g.beta = T(1.0);
+        return gemm<T>(g, st, pf);
+      };
+      // W = I - D12 D21 (Eq. "ItI D inverse"): rows of the odd children's
+      // equations, D21 read from D's lower-left block (rows = own vars)
       HPS_CUDA(fill<T>(WW, hn, hn, (int)nm, T(0.0), T(1.0), st, pf));
-      GemmArgs<T> g;
-      g.M = hn; g.N = hn; g.K = hn; g.batch = (int)nm;
-      g.A = D12; g.B = D21; g.C = WW; g.alpha = T(-1.0); g.beta = T(1.0);
-      HPS_CUDA(gemm<T>(g, st, pf));
+      HPS_CUDA(child_block(true, grouped(bop<T>((T*)Lv.D, (int64_t)ni * ni, ni), 2), grouped(WW, 2), hn));
+      if (Lv.lazy) {
+        HPS_CUDA(getrf<T>(WW, hn, (int)nm, Lv.ipiv, Lv.perm, Lv.info, h->dev_err, Lv.G, Lv.luw, st, pf));
+        goto merged;
+      }
       // R1 <- R1 - D12 R2
-      GemmArgs<T> g2;
-      g2.M = hn; g2.N = ne + 1; g2.K = hn; g2.batch = (int)nm;
-      g2.A = D12; g2.B = R2; g2.C = R1; g2.alpha = T(-1.0); g2.beta = T(1.0);
-      HPS_CUDA(gemm<T>(g2, st, pf));
+      HPS_CUDA(child_block(true, grouped(bop<T>(R, (int64_t)ni * (ne + 1), ni), 2),
+                           grouped(bop<T>(R, (int64_t)ni * (ne + 1), ni), 2), ne + 1));
       HPS_CUDA(getrf<T>(WW, hn, (int)nm, Lv.ipiv, Lv.perm, Lv.info, h->dev_err, Lv.G, Lv.luw, st, pf));
       // X1 = W^{-1} R1
       HPS_CUDA(permute_rows<T>(R1, XX, Lv.perm, hn, ne + 1, (int)nm, st, pf));
@@ -406,11 +342,10 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
       // X2 = R2 - D21 X1
       HPS_CUDA(copy_block<T>(R + hn, (int64_t)ni * (ne + 1), ni, (T*)Lv.X + hn, (int64_t)ni * (ne + 1), ni, hn,
                              ne + 1, (int)nm, st, pf));
-      GemmArgs<T> g3;
-      g3.M = hn; g3.N = ne + 1; g3.K = hn; g3.batch = (int)nm;
-      g3.A = D21; g3.B = XX; g3.C = shifted(XX, hn); g3.alpha = T(-1.0); g3.beta = T(1.0);
-      HPS_CUDA(gemm<T>(g3, st, pf));
+      (void)D21;
+      HPS_CUDA(child_block(false, grouped(XX, 2), grouped(XX, 2), ne + 1));
     }
+  merged:
     // [T | h] = [A | h_ext] - B X  (block-sparse: one product per child)
     if (!Lv.top() || h->opts.want_root_map) {
       GemmArgs<T> g;
@@ -489,6 +424,53 @@ hps_status ensure_ws(hps_handle* h, int nrhs) {
   return HPS_OK;
 }
 
+// y = D^{-1} b for every merge of level m and nrhs columns (b, y: n_int x
+// nrhs per merge, column-major, distinct buffers; b is overwritten).  DtN:
+// the LU factors of D.  ItI: D = [[I, D12], [D21, I]] with W = I - D12 D21
+// factored; D12 / D21 blocks are read from the children's T (block-sparse).
+template <typename T>
+hps_status apply_Dinv(hps_handle* h, int m, T* b, T* y, int nrhs, cudaStream_t st, Prof* pf) {
+  LevelDev& Lv = h->lev[m];
+  const int ni = Lv.n_int, nm = Lv.nmerge;
+  BOp<T> YB = bop<T>(y, (int64_t)ni * nrhs, ni);
+  if (!Kind<T>::iti) {
+    BOp<T> DD = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni);
+    HPS_CUDA(permute_rows<T>(bop<T>(b, (int64_t)ni * nrhs, ni), YB, Lv.perm, ni, nrhs, nm, st, pf));
+    HPS_CUDA(getrs_inplace<T>(DD, ni, YB, nrhs, nm, st, pf));
+    return HPS_OK;
+  }
+  const int hn = ni / 2, nb = h->nb;
+  BOp<T> WW = bop<T>((T*)Lv.W, (int64_t)hn * hn, hn);
+  BOp<T> B1 = bop<T>(b, (int64_t)ni * nrhs, ni);
+  const T* Tcs = m == 0 ? (const T*)h->leafTH : (const T*)h->lev[m - 1].TP;
+  const int64_t cst = m == 0 ? (int64_t)nb * (nb + 1) : (int64_t)h->lev[m - 1].n_ext * (h->lev[m - 1].n_ext + 1);
+  const int hb = Lv.nbc / 2;
+  auto child_block = [&](bool odd, BOp<T> B, BOp<T> C) {
+    GemmArgs<T> g;
+    g.M = hb; g.N = nrhs; g.K = hb; g.batch = nm * 2;
+    BOp<T> A = bop<T>(const_cast<T*>(Tcs) + (odd ? cst : 0), (int64_t)Lv.nch * cst, Lv.nbc);
+    A.div = 2;
+    A.sub = (odd ? 1 : 3) * cst;
+    g.A = A;
+    g.arow.idx = odd ? Lv.odd_pts : Lv.even_pts; g.arow.len = hb; g.arow.period = 2;
+    g.acol = g.arow;
+    g.B = B;
+    g.brow.idx = odd ? Lv.odd_var : Lv.even_var; g.brow.len = hb; g.brow.period = 2;
+    g.C = C;
+    g.crow.idx = odd ? Lv.odd_eq : Lv.even_eq; g.crow.len = hb; g.crow.period = 2;
+    g.alpha = T(-1.0); g.beta = T(1.0);
+    return gemm<T>(g, st, pf);
+  };
+  // b1 <- b1 - D12 b2 (odd children's interior blocks)
+  HPS_CUDA(child_block(true, grouped(B1, 2), grouped(B1, 2)));
+  HPS_CUDA(permute_rows<T>(B1, YB, Lv.perm, hn, nrhs, nm, st, pf));
+  HPS_CUDA(getrs_inplace<T>(WW, hn, YB, nrhs, nm, st, pf));
+  HPS_CUDA(copy_block<T>(b + hn, (int64_t)ni * nrhs, ni, y + hn, (int64_t)ni * nrhs, ni, hn, nrhs, nm, st, pf));
+  // y2 <- b2 - D21 y1 (even children's interior blocks)
+  HPS_CUDA(child_block(false, grouped(YB, 2), grouped(YB, 2)));
+  return HPS_OK;
+}
+
 template <typename T>
 hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_in, void* u_out,
                       cudaStream_t st) {
@@ -541,30 +523,8 @@ hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_i
       HPS_CUDA(fill<T>(bop<T>(r, (int64_t)ni * nrhs, ni), ni, nrhs, nm, T(0.0), T(0.0), st, pf));
       HPS_CUDA(merge_gather_h<T>(hc, nm, Lv.nch, Lv.nbc, ne, ni, nrhs, Lv.ext, Lv.var, Lv.eq, ITI, r,
                                  (T*)Lv.hp, st, pf));
-      BOp<T> XB = bop<T>(x, (int64_t)ni * nrhs, ni);
-      if (!ITI) {
-        BOp<T> DD = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni);
-        HPS_CUDA(permute_rows<T>(bop<T>(r, (int64_t)ni * nrhs, ni), XB, Lv.perm, ni, nrhs, nm, st, pf));
-        HPS_CUDA(getrs_inplace<T>(DD, ni, XB, nrhs, nm, st, pf));
-      } else {
-        const int hn = ni / 2;
-        BOp<T> D12 = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni, (int64_t)hn * ni);
-        BOp<T> D21 = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni, (int64_t)hn);
-        BOp<T> WW = bop<T>((T*)Lv.W, (int64_t)hn * hn, hn);
-        BOp<T> R1 = bop<T>(r, (int64_t)ni * nrhs, ni);
-        BOp<T> R2 = bop<T>(r, (int64_t)ni * nrhs, ni, hn);
-        GemmArgs<T> g2;
-        g2.M = hn; g2.N = nrhs; g2.K = hn; g2.batch = nm;
-        g2.A = D12; g2.B = R2; g2.C = R1; g2.alpha = T(-1.0); g2.beta = T(1.0);
-        HPS_CUDA(gemm<T>(g2, st, pf));
-        HPS_CUDA(permute_rows<T>(R1, XB, Lv.perm, hn, nrhs, nm, st, pf));
-        HPS_CUDA(getrs_inplace<T>(WW, hn, XB, nrhs, nm, st, pf));
-        HPS_CUDA(copy_block<T>(r + hn, (int64_t)ni * nrhs, ni, x + hn, (int64_t)ni * nrhs, ni, hn, nrhs, nm, st, pf));
-        GemmArgs<T> g3;
-        g3.M = hn; g3.N = nrhs; g3.K = hn; g3.batch = nm;
-        g3.A = D21; g3.B = XB; g3.C = shifted(XB, hn); g3.alpha = T(-1.0); g3.beta = T(1.0);
-        HPS_CUDA(gemm<T>(g3, st, pf));
-      }
+      if (Lv.lazy) break;  // the root's D^{-1} is applied in the downward pass
+      HPS_TRY(apply_Dinv<T>(h, m, r, x, nrhs, st, pf));
       if (!Lv.top()) {
         GemmArgs<T> g;
         g.M = Lv.nbc / 2; g.N = nrhs; g.K = Lv.nbc / 2; g.batch = nm * Lv.nch;
@@ -590,8 +550,18 @@ hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_i
   for (int m = h->L - 1; m >= 0; --m) {
     LevelDev& Lv = h->lev[m];
     T* gchild = (m == 0) ? (T*)h->ws_gleaf : (T*)Lv.gchild;
-    HPS_CUDA(down_level<T>((const T*)Lv.X, newf ? (const T*)Lv.x : nullptr, gpar, Lv.nmerge, Lv.nch, Lv.nbc,
-                           Lv.n_ext, Lv.n_int, nrhs, Lv.ext, Lv.var, (T*)Lv.gint, gchild, st, pf));
+    if (Lv.lazy) {
+      // Lv.X = [C | h_int]: t = -(C g + h), with the solve's own h when f is new,
+      // then g_int = D^{-1} t
+      HPS_CUDA(down_gint<T>((const T*)Lv.X, newf ? (const T*)Lv.r : nullptr, gpar, Lv.nmerge, Lv.n_ext,
+                            Lv.n_int, nrhs, (T*)Lv.x, st, pf));
+      HPS_TRY(apply_Dinv<T>(h, m, (T*)Lv.x, (T*)Lv.gint, nrhs, st, pf));
+      HPS_CUDA(down_children<T>(gpar, (const T*)Lv.gint, Lv.nmerge, Lv.nch, Lv.nbc, Lv.n_ext, Lv.n_int, nrhs,
+                                Lv.ext, Lv.var, gchild, st, pf));
+    } else {
+      HPS_CUDA(down_level<T>((const T*)Lv.X, newf ? (const T*)Lv.x : nullptr, gpar, Lv.nmerge, Lv.nch,
+                             Lv.nbc, Lv.n_ext, Lv.n_int, nrhs, Lv.ext, Lv.var, (T*)Lv.gint, gchild, st, pf));
+    }
     gpar = gchild;
   }
   // leaf output u = Y g + v
@@ -630,7 +600,27 @@ const char* hps_error_string(hps_status s) {
   return "unknown hps_status";
 }
 
+hps_status hps_refine(const double lo[3], const double hi[3], int p, double eps, int min_depth, int max_depth,
+                      int n_fn, const hps_eval_fn* fns, void* const* ctxs, int64_t capacity, int64_t* n_leaves,
+                      uint64_t* morton, int8_t* level, struct CUstream_st* stream) {
+  try {
+    return adaptive_refine(lo, hi, p, eps, min_depth, max_depth, n_fn, fns, ctxs, capacity, n_leaves, morton,
+                           level, (cudaStream_t)stream);
+  } catch (...) {
+    return HPS_ERR_INVALID;
+  }
+}
+
 hps_status hps_sizes(const hps_tree* tree, int p, int q, int64_t* n_leaves, int64_t* ppl, int64_t* nroot) {
+  if (tree && tree->uniform_depth == -1) {
+    ATree at;
+    hps_status s = adaptive_tree_from_abi(tree, p, q, &at);
+    if (s != HPS_OK) return s;
+    if (n_leaves) *n_leaves = tree->n_leaves;
+    if (ppl) *ppl = (int64_t)p * p * p;
+    if (nroot) *nroot = at.nodes[0].n_bdry;
+    return HPS_OK;
+  }
   hps_status s = check_tree(tree, p, q);
   if (s != HPS_OK) return s;
   const int L = tree->uniform_depth, d = tree->dim;
@@ -641,6 +631,15 @@ hps_status hps_sizes(const hps_tree* tree, int p, int q, int64_t* n_leaves, int6
 }
 
 hps_status hps_nodes(const hps_tree* tree, int p, int q, double* leaf_xyz, double* bdry_xyz) {
+  if (tree && tree->uniform_depth == -1) {
+    ATree at;
+    hps_status s = adaptive_tree_from_abi(tree, p, q, &at);
+    if (s != HPS_OK) return s;
+    Spectral1D sp = make_spectral(p, q);
+    if (leaf_xyz) atree_leaf_coords(at, sp, leaf_xyz);
+    if (bdry_xyz) atree_root_coords(at, sp, bdry_xyz);
+    return HPS_OK;
+  }
   hps_status s = check_tree(tree, p, q);
   if (s != HPS_OK) return s;
   try {
@@ -657,7 +656,17 @@ hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeff
                      const hps_options* opts, struct CUstream_st* stream, hps_handle** out) {
   if (!out) return HPS_ERR_INVALID;
   *out = nullptr;
-  hps_status s = check_tree(tree, p, q);
+  const bool adaptive = tree && tree->uniform_depth == -1;
+  hps_status s = HPS_OK;
+  int64_t a_nroot = 0;
+  if (adaptive) {
+    int64_t nl = 0, ppl = 0;
+    s = hps_sizes(tree, p, q, &nl, &ppl, &a_nroot);
+    if (s != HPS_OK) return s;
+    if (!coeffs || coeffs->kind != HPS_DTN) return HPS_ERR_INVALID;
+  } else {
+    s = check_tree(tree, p, q);
+  }
   if (s != HPS_OK) return s;
   if (!coeffs) return HPS_ERR_INVALID;
   if (coeffs->kind != HPS_DTN && coeffs->kind != HPS_ITI) return HPS_ERR_INVALID;
@@ -675,6 +684,14 @@ hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeff
   for (int a = 0; a < 3; ++a) { h->lo[a] = tree->lo[a]; h->hi[a] = tree->hi[a]; }
   h->hlen = (tree->hi[0] - tree->lo[0]) / (double)((int64_t)1 << h->L);
   h->eta = coeffs->eta;
+  if (adaptive) {
+    h->adaptive = true;
+    h->L = 0;
+    h->nl = tree->n_leaves;
+    h->npts = (int64_t)p * p * p;
+    h->nroot = a_nroot;
+    h->hlen = 0.0;
+  }
   if (opts) h->opts = *opts;
   else { h->opts.version = 1; h->opts.want_root_map = 0; h->opts.profile = 0; }
   int dev = 0;
@@ -687,7 +704,8 @@ hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeff
   cudaStream_t st = (cudaStream_t)stream;
   h->last = st;
   try {
-    s = h->iti ? build_impl<cplx>(h, coeffs, f, st) : build_impl<double>(h, coeffs, f, st);
+    if (h->adaptive) s = adaptive_build(h, tree, coeffs, f, st);
+    else s = h->iti ? build_impl<cplx>(h, coeffs, f, st) : build_impl<double>(h, coeffs, f, st);
   } catch (...) {
     s = HPS_ERR_INVALID;
   }
@@ -714,7 +732,8 @@ hps_status hps_solve_batched(hps_handle* h, int nrhs, const void* g, const void*
   h->last = st;
   hps_status s;
   try {
-    s = h->iti ? solve_impl<cplx>(h, nrhs, g, f, u, st) : solve_impl<double>(h, nrhs, g, f, u, st);
+    if (h->adaptive) s = adaptive_solve(h, nrhs, g, f, u, st);
+    else s = h->iti ? solve_impl<cplx>(h, nrhs, g, f, u, st) : solve_impl<double>(h, nrhs, g, f, u, st);
   } catch (...) {
     s = HPS_ERR_INVALID;
   }
@@ -823,7 +842,7 @@ hps_status solve_noalloc_impl(hps_handle* h, const T* g, T* u, cudaStream_t st) 
 }  // namespace
 
 extern "C" hps_status hps_solve_noalloc(hps_handle* h, const void* g, void* u, struct CUstream_st* stream) {
-  if (!h || !g || !u) return HPS_ERR_INVALID;
+  if (!h || !g || !u || h->adaptive || (h->L > 0 && h->lev[h->L - 1].lazy)) return HPS_ERR_INVALID;
   if (!is_device_ptr(g) || !is_device_ptr(u)) return HPS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   try {

@@ -23,8 +23,8 @@ __device__ inline void coords(int dim, int p, int idx, int* c) {
 // Entry (i, j) of the leaf operator a Lap + sum_k b_k d_k + c (Section 3.2)
 // on the tensor Chebyshev grid: nonzero only when i and j differ along at
 // most one axis.
-__device__ inline double L_entry(const LeafConsts& k, double a, const double* bk, double c, int i,
-                                 int j) {
+__device__ inline double L_entry(const LeafConsts& k, double s, double a, const double* bk, double c,
+                                 int i, int j) {
   int ci[3], cj[3];
   coords(k.dim, k.p, i, ci);
   coords(k.dim, k.p, j, cj);
@@ -33,7 +33,7 @@ __device__ inline double L_entry(const LeafConsts& k, double a, const double* bk
     if (ci[ax] != cj[ax]) { ++ndiff; dax = ax; }
   if (ndiff > 1) return 0.0;
   double v = 0.0;
-  const double s = k.s, s2 = k.s * k.s;
+  const double s2 = s * s;
   for (int ax = 0; ax < k.dim; ++ax) {
     if (ndiff == 1 && ax != dax) continue;
     const int e = ci[ax] * k.p + cj[ax];
@@ -65,7 +65,8 @@ __global__ void k_leaf_dtn_Lii(LeafConsts k, int64_t nl, Coeffs cf, double* Lii)
     const int i = k.Ii[r], j = k.Ii[c];
     double a, b[3], cc;
     load_coeffs(cf, leaf * k.npts + i, k.dim, &a, b, &cc);
-    Lii[e] = L_entry(k, a, b, cc, i, j);
+    const double s = k.sleaf ? k.sleaf[leaf] : k.s;
+    Lii[e] = L_entry(k, s, a, b, cc, i, j);
   }
 }
 
@@ -84,6 +85,7 @@ __global__ void k_leaf_dtn_rhs(LeafConsts k, int64_t nl, Coeffs cf, const double
     }
     double a, b[3], cc;
     load_coeffs(cf, leaf * k.npts + i, k.dim, &a, b, &cc);
+    const double s = k.sleaf ? k.sleaf[leaf] : k.s;
     int ci[3];
     coords(k.dim, k.p, i, ci);
     double acc = 0.0;
@@ -94,7 +96,7 @@ __global__ void k_leaf_dtn_rhs(LeafConsts k, int64_t nl, Coeffs cf, const double
         const int j = cj[0] + k.p * (cj[1] + k.p * cj[2]);
         const int pr = k.prow[j];
         const int el = ci[ax] * k.p + cj[ax];
-        const double lij = fma(a * k.s * k.s, k.DD[el], b[ax] * k.s * k.D[el]);
+        const double lij = fma(a * s * s, k.DD[el], b[ax] * s * k.D[el]);
         acc = fma(lij, k.P[pr + (int64_t)col * k.ne], acc);
       }
     }
@@ -137,7 +139,7 @@ __global__ void k_leaf_iti_B(LeafConsts k, int64_t nl, Coeffs cf, cplx* B) {
       const int i = k.Ii[r - k.nown];
       double a, b[3], cc;
       load_coeffs(cf, leaf * k.npts + i, k.dim, &a, b, &cc);
-      v.re = L_entry(k, a, b, cc, i, j);
+      v.re = L_entry(k, k.s, a, b, cc, i, j);
     }
     B[e] = v;
   }
@@ -379,6 +381,27 @@ cudaError_t down_level(const T* X, const T* xp, const T* gpar, int nmerge, int n
 }
 
 template <typename T>
+cudaError_t down_gint(const T* X, const T* xp, const T* gpar, int nmerge, int n_ext, int n_int, int nrhs,
+                      T* gint, cudaStream_t st, Prof* pf) {
+  const double F = sizeof(T) == sizeof(cplx) ? 8.0 : 2.0;
+  if (pf) pf->begin(st);
+  k_down_gint<T><<<grid_for((int64_t)nmerge * n_int * nrhs, 128), 128, 0, st>>>(X, xp, gpar, nmerge, n_ext,
+                                                                           n_int, nrhs, gint);
+  if (pf) pf->end(K_DOWN, F * (double)nmerge * n_int * n_ext * nrhs, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t down_children(const T* gpar, const T* gint, int nmerge, int nch, int nbc, int n_ext, int n_int,
+                          int nrhs, const int* ext, const int* var, T* gchild, cudaStream_t st, Prof* pf) {
+  if (pf) pf->begin(st);
+  k_down_children<T><<<grid_for((int64_t)nmerge * nch * nbc * nrhs), 256, 0, st>>>(
+      gpar, gint, nmerge, nch, nbc, n_ext, n_int, nrhs, ext, var, gchild);
+  if (pf) pf->end(K_GATHER, 0.0, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
 __global__ void k_leaf_output(LeafConsts k, int64_t nl, int nrhs, const T* X, const T* xp, const T* g,
                               T* u, bool iti) {
   const int64_t total = (int64_t)nrhs * nl * k.npts;
@@ -471,7 +494,11 @@ cudaError_t scale_copy(const T* src, T* dst, int64_t n, double alpha, cudaStream
                                       T*, bool, cudaStream_t, Prof*);                                 \
   template cudaError_t copy_block<T>(const T*, int64_t, int, T*, int64_t, int, int, int, int,         \
                                      cudaStream_t, Prof*);                                            \
-  template cudaError_t scale_copy<T>(const T*, T*, int64_t, double, cudaStream_t, Prof*);
+  template cudaError_t scale_copy<T>(const T*, T*, int64_t, double, cudaStream_t, Prof*);                 \
+  template cudaError_t down_gint<T>(const T*, const T*, const T*, int, int, int, int, T*, cudaStream_t,     \
+                                    Prof*);                                                                 \
+  template cudaError_t down_children<T>(const T*, const T*, int, int, int, int, int, int, const int*,       \
+                                        const int*, T*, cudaStream_t, Prof*);
 
 HPS_KINST(double)
 HPS_KINST(cplx)

@@ -15,6 +15,7 @@ namespace hps {
 struct LeafConsts {
   int dim, p, npts, ni, ne, nb, nown;
   double s;         // 2 / leaf side
+  const double* sleaf;  // per-leaf 2 / side (adaptive trees) or null
   double eta;       // ItI impedance parameter
   const double* D;  // p x p row-major reference differentiation matrix
   const double* DD; // D*D row-major
@@ -71,6 +72,14 @@ template <typename T>
 cudaError_t down_level(const T* X, const T* xp, const T* gpar, int nmerge, int nch, int nbc,
                        int n_ext, int n_int, int nrhs, const int* ext, const int* var, T* gint,
                        T* gchild, cudaStream_t st, Prof* pf);
+
+// The two halves of down_level, for merges whose children differ in size.
+template <typename T>
+cudaError_t down_gint(const T* X, const T* xp, const T* gpar, int nmerge, int n_ext, int n_int, int nrhs,
+                      T* gint, cudaStream_t st, Prof* pf);
+template <typename T>
+cudaError_t down_children(const T* gpar, const T* gint, int nmerge, int nch, int nbc, int n_ext, int n_int,
+                          int nrhs, const int* ext, const int* var, T* gchild, cudaStream_t st, Prof* pf);
 
 // Leaf output u = Y g + v for every leaf and right-hand side.
 //   DtN: u(I_e) = P g, u(I_i) = -(X_Y g + xpart)   (X = ni x (nb+1))

@@ -45,8 +45,9 @@ struct BOp {
   int64_t off = 0;           // element offset added to every item's base
   int ld = 0;                // leading dimension (column-major)
   int div = 1;               // items b and b' share a base when b / div == b' / div
+  int64_t sub = 0;           // extra stride for b % div (items inside one group)
   __host__ __device__ T* item(int b) const {
-    return (ptrs ? ptrs[b] : base + (int64_t)(b / div) * stride) + off;
+    return (ptrs ? ptrs[b] : base + (int64_t)(b / div) * stride + (int64_t)(b % div) * sub) + off;
   }
 };
 

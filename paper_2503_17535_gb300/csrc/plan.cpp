@@ -326,7 +326,7 @@ MergeMaps make_merge_maps(int dim, int n, bool iti) {
     for (int i = 0; i < m.nbc; ++i) {
       const size_t slot = (size_t)k * m.nbc + i;
       if (m.ext[slot] >= 0) { m.b_arow.push_back(i); m.b_crow.push_back(m.ext[slot]); }
-      else { m.b_acol.push_back(i); m.b_brow.push_back(m.var[slot]); }
+      else { m.b_acol.push_back(i); m.b_brow.push_back(m.var[slot]); m.i_eq.push_back(m.eq[slot]); }
     }
   }
   if ((int)m.b_arow.size() != m.nch * m.nbc / 2) throw std::runtime_error("merge map size");

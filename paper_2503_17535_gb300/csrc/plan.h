@@ -75,6 +75,10 @@ struct MergeMaps {
   std::vector<int> ext, var, eq;           // [nch][nbc]
   std::vector<int> b_arow, b_crow;         // [nch][nbc/2]  child exterior points -> parent rows
   std::vector<int> b_acol, b_brow;         // [nch][nbc/2]  child interior points -> X rows (var)
+  // ItI: per child its interior points' equation rows (eq), same order as
+  // b_acol; the D12 / D21 products run over children {1, 2} (odd parity,
+  // whose equations fill D12) and {0, 3} (even parity, D21).
+  std::vector<int> i_eq;                   // [nch][nbc/2]
 };
 
 MergeMaps make_merge_maps(int dim, int n, bool iti);

@@ -76,3 +76,45 @@ def test_invalid_arguments_are_rejected(pkg):
 def test_sizes(pkg):
     assert pkg.hps_sizes(pkg.uniform_tree(2, 6), 16, 14) == (4096, 256, 4 * 14 * 64)
     assert pkg.hps_sizes(pkg.uniform_tree(3, 3), 8, 6) == (512, 512, 6 * 36 * 64)
+
+
+def _two_one_tree():
+    from oracle import adaptive as ad
+    leaves = [(1, (i, j, k)) for i in range(2) for j in range(2) for k in range(2) if (i, j, k) != (0, 0, 0)]
+    leaves += ad.children_of(1, (0, 0, 0))
+    leaves.remove((2, (1, 1, 1)))
+    leaves += ad.children_of(2, (1, 1, 1))
+    return ad.sort_leaves(ad.balance(leaves))
+
+
+@pytest.mark.parametrize("p", [6, 8])
+def test_adaptive_nodes_match_oracle(pkg, p):
+    from oracle import adaptive as ad
+    leaves = _two_one_tree()
+    lo, hi = (-1.0, -0.5, 0.0), (1.0, 1.5, 2.0)
+    t = pkg.adaptive_tree(leaves, lo, hi)
+    nl, ppl, nr = pkg.hps_sizes(t, p, p - 2)
+    assert (nl, ppl) == (len(leaves), p ** 3)
+    leaf, bdry = pkg.hps_nodes(t, p, p - 2)
+    assert np.allclose(leaf, ad.all_leaf_nodes(leaves, lo, hi, p), atol=1e-14)
+    assert np.allclose(bdry, ad.root_boundary_points(leaves, lo, hi, p - 2), atol=1e-14)
+
+
+def test_adaptive_trees_are_validated(pkg):
+    from oracle import adaptive as ad
+    leaves = _two_one_tree()
+    # out of order
+    bad = list(reversed(leaves))
+    with pytest.raises(pkg.HPSError):
+        pkg.hps_sizes(pkg.adaptive_tree(bad), 6, 4)
+    # a gap in the tiling
+    with pytest.raises(pkg.HPSError):
+        pkg.hps_sizes(pkg.adaptive_tree(leaves[1:]), 6, 4)
+    # not 2:1 balanced: one level-1 cell refined twice next to a level-1 leaf
+    unb = [(1, (i, j, k)) for i in range(2) for j in range(2) for k in range(2) if (i, j, k) != (0, 0, 0)]
+    unb += [lf for lf in ad.children_of(1, (0, 0, 0)) if lf[1] != (1, 1, 1)]
+    unb += ad.children_of(2, (1, 1, 1))
+    unb = ad.sort_leaves(unb)
+    with pytest.raises(pkg.HPSError):
+        pkg.hps_sizes(pkg.adaptive_tree(unb), 6, 4)
+    assert pkg.hps_sizes(pkg.adaptive_tree(ad.sort_leaves(ad.balance(unb))), 6, 4)[0] > len(unb)

@@ -21,4 +21,5 @@ from .problems import (  # noqa: F401
     e7_wavefront_3d,
     polynomial_field,
     sharp_source_3d,
+    adaptive_3d,
 )

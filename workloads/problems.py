@@ -289,6 +289,19 @@ def sharp_source_3d(seed: int = 3, width: float = 0.05) -> Problem:
                    info={"centre": z.tolist(), "width": width})
 
 
+def adaptive_3d(seed_coeffs: int = 2, seed_source: int = 3, width: float = 0.05) -> Problem:
+    """Workload 3b: the variable-coefficient operator of elliptic_3d (seed 2)
+    driven by the sharp seeded Gaussian source of sharp_source_3d (seed 3,
+    width 0.05) with zero Dirichlet data.  The adaptive tree is refined on f,
+    a and c (eps = 1e-4, leaf depths 2..5)."""
+    pe = elliptic_3d(seed=seed_coeffs)
+    ps = sharp_source_3d(seed=seed_source, width=width)
+    return Problem(name=f"adaptive3d_seed{seed_coeffs}_{seed_source}", dim=3, lo=pe.lo, hi=pe.hi, kind="dtn",
+                   seed=seed_source, coeffs=pe.coeffs, source=ps.source, boundary=ps.boundary,
+                   info={"centre": ps.info["centre"], "width": width, "eps": 1e-4, "min_depth": 2,
+                         "max_depth": 5, "refine_on": ["f", "a", "c"]})
+
+
 # ---------------------------------------------------------------------------
 # the paper's closed-form test problems (Sections 5.1 and 6.1)
 # ---------------------------------------------------------------------------
