@@ -221,6 +221,11 @@ def replica_throughput(steps: int, total_ms: float, world: int, device=None) -> 
     return world * steps / (max_over_ranks(total_ms, world, device) / 1e3)
 
 
+def pct(sorted_ms, q):
+    """Nearest-rank percentile of an ascending list."""
+    return sorted_ms[min(len(sorted_ms) - 1, int(round(q / 100.0 * (len(sorted_ms) - 1))))]
+
+
 # ----------------------------------------------------------------- our arm --
 
 def _build(P, spec, inp, arrs, f, profile=False):
@@ -285,6 +290,34 @@ def run_ours(args, rank, world):
     value = replica_throughput(args.steps, total_ms, world, dev)
     total_ms = max_over_ranks(total_ms, world, dev)
 
+    # ---- build and solve timed separately (p50 / p99 over `steps` runs each):
+    # hps_build alone, a solve with a new source (upward + downward pass) and
+    # an apply-only solve (downward pass with the build-time source)
+    def timed(fn, n):
+        ts = []
+        for _ in range(n):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ts.sort()
+        return {"p50_ms": round(pct(ts, 50), 3), "p99_ms": round(pct(ts, 99), 3), "runs": n}
+
+    hold = []
+
+    def build_only():
+        if hold:
+            P.hps_free(hold.pop())
+        hold.append(_build(P, spec, inp, darr, fd))
+
+    phases = {"build": timed(build_only, args.steps)}
+    hk = hold.pop()
+    phases["solve_new_f"] = timed(lambda: P.hps_solve(hk, gd, ud, f=f2d), max(args.steps, 10))
+    phases["solve_apply"] = timed(lambda: P.hps_solve(hk, gd, ud), max(args.steps, 10))
+    P.hps_free(hk)
+
     # ---- one profiled step (untimed): per-class kernel times with CUDA events
     h = _build(P, spec, inp, darr, fd, profile=True)
     sb = P.hps_kernel_stats(h)
@@ -338,7 +371,7 @@ def run_ours(args, rank, world):
                "d2h_bytes_per_step": int(uh.nbytes)}
     return {"value": value, "total_ms": total_ms, "per": per, "clocks": clocks, "roofline": roofline,
             "classes": classes, "flops_step": flops_step, "launches": launches[0] // max(args.steps, 1),
-            "e2e": e2e, "sample_ratio": sample_ratio, "n_leaves": nl}
+            "e2e": e2e, "sample_ratio": sample_ratio, "n_leaves": nl, "phases": phases}
 
 
 # ------------------------------------------------------------- CPU oracle --
@@ -359,7 +392,6 @@ def oracle_sample_step(spec, depth=None):
         x, a, b, c, f, g = ad.sample_adaptive(pr, leaves, p)
         f2 = rng.standard_normal(f.shape) * max(np.abs(f).max(), 1.0)
         t0 = time.perf_counter()
-        ad.build_adaptive(leaves, p, pr.lo, pr.hi, a, b, c, f)
         ad.solve_adaptive(ad.build_adaptive(leaves, p, pr.lo, pr.hi, a, b, c, f2), g)
         return time.perf_counter() - t0
     depth = spec["depth"] if depth is None else depth
@@ -367,8 +399,9 @@ def oracle_sample_step(spec, depth=None):
     f2 = rng.standard_normal(f.shape) * max(np.abs(f).max(), 1.0)
     if spec["kind"] == "iti":
         f2 = f2 + 1j * rng.standard_normal(f.shape) * max(np.abs(f).max(), 1.0)
+    # the oracle has no separate particular pass: a build with the solve's
+    # source followed by the solve gives the same u as build(f) + solve(new f)
     t0 = time.perf_counter()
-    O.build(spec["dim"], spec["kind"], p, q, depth, pr.lo, pr.hi, a, b, c, f, eta=pr.eta)
     s2 = O.build(spec["dim"], spec["kind"], p, q, depth, pr.lo, pr.hi, a, b, c, f2, eta=pr.eta)
     O.solve(s2, g)
     return time.perf_counter() - t0
@@ -463,8 +496,7 @@ def main():
     r = run_ours(args, rank, world)
     if rank == 0:
         per = r["per"]
-        p50 = per[len(per) // 2]
-        p99 = per[min(len(per) - 1, int(round(0.99 * (len(per) - 1))))]
+        p50, p99 = pct(per, 50), pct(per, 99)
         step_tf = r["flops_step"] / (statistics.median(per) / 1e3) / 1e12
         cfg = {k: v for k, v in spec.items() if k not in ("cpu_depth",)}
         cfg.update(COMMON)
@@ -476,7 +508,7 @@ def main():
                 "p99_ms": round(p99, 3), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "c128" if spec["kind"] == "iti" else "f64", "data": "synthetic",
                 "config": cfg, "clocks": r["clocks"], "e2e": r["e2e"], "gpu_launches": r["launches"] * args.steps,
-                "roofline": r["roofline"],
+                "roofline": r["roofline"], "phases": r["phases"],
                 "step_fp64": {"algorithmic_flops": r["flops_step"], "achieved_tflops": round(step_tf, 4),
                               "frac_of_peak": round(step_tf / r["roofline"]["peak"], 4)},
                 "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
