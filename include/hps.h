@@ -113,7 +113,11 @@ typedef struct {
                            forming S = -D^{-1} C (Eq. "merge outputs 2"); each
                            solve then applies D^{-1} to C g + h_int.  Saves the
                            root's multi-RHS solve in hps_build; uniform trees,
-                           ignored with want_root_map. */
+                           ignored with want_root_map.  With up to 8 right-hand
+                           sides the root's triangular solves run as one
+                           flag-ordered launch per triangle; if one of its
+                           bounded waits gives up, that hps_solve (host u) or
+                           the next one on the handle returns HPS_ERR_TIMEOUT. */
   int reserved[4];
 } hps_options;
 
@@ -134,6 +138,9 @@ typedef struct {
   int64_t launches;  /* launches of this class in the last build or solve          */
   double flops;      /* algorithmic FP64 flops (complex multiply-add = 8)          */
   double ms;         /* summed CUDA-event time, or -1 when profiling is off         */
+  double exec_flops; /* flops the FP64 pipe executes: equal to flops except for the
+                        complex GEMM, which takes 3 real products per complex
+                        multiply-add (Gauss / 3M form: 6 flops instead of 8)   */
 } hps_kernel_stat;
 
 typedef struct hps_handle hps_handle;
@@ -216,6 +223,25 @@ hps_status hps_kernel_stats(hps_handle* h, int kclass, hps_kernel_stat* out);
 
 /* Switch per-launch event timing on (1) or off (0) for later calls on h. */
 hps_status hps_set_profiling(hps_handle* h, int on);
+
+/* Per-launch trace of the last hps_build / hps_solve on h, recorded while
+ * profiling is on (hps_options.profile or hps_set_profiling): one record per
+ * library kernel launch, in launch order.  Shapes: GEMM m x n result with
+ * inner dimension k; LU panel rows x panel width (k = CTAs per matrix);
+ * row-interchange/U12 update panel width x trailing columns; diagonal
+ * triangular solve block size x right-hand sides; 0 for other classes. */
+typedef struct {
+  int kclass;        /* HPS_KCLASS_*                                     */
+  int m, n, k;       /* launch shape (see above)                         */
+  int64_t batch;     /* matrices / merges / leaves in the launch         */
+  double flops;      /* algorithmic flops of the launch                  */
+  double ms;         /* CUDA-event time of the launch                    */
+} hps_trace_rec;
+/* Number of records (0 when profiling was off).  Synchronises the handle's
+ * last stream.  HPS_ERR_INVALID for a NULL handle or pointer. */
+hps_status hps_trace_count(hps_handle* h, int64_t* count);
+/* Record i (0 <= i < count); HPS_ERR_INVALID when i is out of range. */
+hps_status hps_trace_get(hps_handle* h, int64_t i, hps_trace_rec* out);
 
 /* Allocation-free solve (uniform trees only; no counterpart in the paper; a service for callers
  * that cannot let the library allocate device memory at solve time: code

@@ -290,12 +290,28 @@ def hps_last_launch_count(h: Handle) -> int:
 
 
 def hps_kernel_stats(h: Handle) -> dict:
-    """{class name: {"launches", "flops", "ms"}} for the last build / solve."""
+    """{class name: {"launches", "flops", "exec_flops", "ms"}} for the last
+    build / solve (flops: algorithmic, complex multiply-add = 8; exec_flops:
+    what the FP64 pipe executes)."""
     out = {}
     for k, name in enumerate(_capi.KCLASSES):
         st = _capi.hps_kernel_stat()
         _check(_capi.lib().hps_kernel_stats(h.ptr, k, byref(st)), "hps_kernel_stats")
-        out[name] = {"launches": st.launches, "flops": st.flops, "ms": st.ms}
+        out[name] = {"launches": st.launches, "flops": st.flops, "exec_flops": st.exec_flops, "ms": st.ms}
+    return out
+
+
+def hps_trace(h: Handle) -> list:
+    """Per-launch records of the last build / solve on h (profiling on):
+    [{"kclass", "m", "n", "k", "batch", "flops", "ms"}] in launch order."""
+    n = c_int64(0)
+    _check(_capi.lib().hps_trace_count(h.ptr, byref(n)), "hps_trace_count")
+    out = []
+    rec = _capi.hps_trace_rec()
+    for i in range(n.value):
+        _check(_capi.lib().hps_trace_get(h.ptr, i, byref(rec)), "hps_trace_get")
+        out.append({"kclass": _capi.KCLASSES[rec.kclass], "m": rec.m, "n": rec.n, "k": rec.k,
+                    "batch": rec.batch, "flops": rec.flops, "ms": rec.ms})
     return out
 
 

@@ -20,7 +20,8 @@ HPS_F64, HPS_C128 = 0, 1
 EXPORTED = [
     "hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
     "hps_error_string", "hps_last_error_detail", "hps_device_bytes", "hps_last_launch_count",
-    "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc", "hps_refine",
+    "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc", "hps_refine", "hps_trace_count",
+    "hps_trace_get",
 ]
 
 EVAL_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int64, POINTER(c_double), POINTER(c_double))
@@ -45,7 +46,12 @@ class hps_options(ctypes.Structure):
 
 
 class hps_kernel_stat(ctypes.Structure):
-    _fields_ = [("launches", c_int64), ("flops", c_double), ("ms", c_double)]
+    _fields_ = [("launches", c_int64), ("flops", c_double), ("ms", c_double), ("exec_flops", c_double)]
+
+
+class hps_trace_rec(ctypes.Structure):
+    _fields_ = [("kclass", c_int), ("m", c_int), ("n", c_int), ("k", c_int), ("batch", c_int64),
+                ("flops", c_double), ("ms", c_double)]
 
 
 _lib = None
@@ -87,6 +93,10 @@ def lib() -> ctypes.CDLL:
     L.hps_kernel_stats.restype = c_int
     L.hps_set_profiling.argtypes = [c_void_p, c_int]
     L.hps_set_profiling.restype = c_int
+    L.hps_trace_count.argtypes = [c_void_p, POINTER(c_int64)]
+    L.hps_trace_count.restype = c_int
+    L.hps_trace_get.argtypes = [c_void_p, c_int64, POINTER(hps_trace_rec)]
+    L.hps_trace_get.restype = c_int
     L.hps_solve_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.hps_solve_noalloc.restype = c_int
     L.hps_refine.argtypes = [POINTER(c_double), POINTER(c_double), c_int, c_double, c_int, c_int, c_int,

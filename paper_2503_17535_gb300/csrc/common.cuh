@@ -55,6 +55,14 @@ __host__ __device__ inline bool is_zero(cplx a) { return a.re == 0.0 && a.im == 
 __host__ __device__ inline double scale(double a, double s) { return a * s; }
 __host__ __device__ inline cplx scale(cplx a, double s) { return cplx(a.re * s, a.im * s); }
 
+// Load through L2 only (no L1): for values another CTA of the same launch
+// has written and published with a fence and a flag.
+__device__ inline double ld_cg(const double* p) { return __ldcg(p); }
+__device__ inline cplx ld_cg(const cplx* p) {
+  const double* q = reinterpret_cast<const double*>(p);
+  return cplx(__ldcg(q), __ldcg(q + 1));
+}
+
 template <typename T> struct zero_of { __host__ __device__ static T get() { return T(0.0); } };
 
 // Error flag bits written by kernels into a device status word.

@@ -101,6 +101,8 @@ struct hps_handle {
   Prof prof;
   int64_t err_node = -1;
   int num_sms = 0;
+  hps::TrsvWork trsv;            // flag-ordered solves with a lazy root's factors
+  int* trsv_err_host = nullptr;  // host-mapped error word of trsv (cudaHostAlloc)
   cudaStream_t last = nullptr;
   // solve workspace
   int ws_nrhs = 0;

@@ -271,6 +271,20 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
       return HPS_ERR_OOM;
     HPS_CUDA(cudaMemsetAsync(Lv.info, 0, (size_t)nm * sizeof(int), st));
     Lv.lazy = Lv.top() && h->opts.lazy_root && !h->opts.want_root_map;
+    if (Lv.lazy && nm == 1) {
+      // flags and a host-mapped error word for the flag-ordered solves
+      const int nf = (ni + 31) / 32;
+      h->trsv.flags = (unsigned*)dalloc(h, (size_t)nf * sizeof(unsigned));
+      if (!h->trsv.flags) return HPS_ERR_OOM;
+      HPS_CUDA(cudaMemsetAsync(h->trsv.flags, 0, (size_t)nf * sizeof(unsigned), st));
+      h->trsv.nflags = nf;
+      HPS_CUDA(cudaHostAlloc((void**)&h->trsv_err_host, sizeof(int), cudaHostAllocMapped));
+      *h->trsv_err_host = 0;
+      int* dp = nullptr;
+      HPS_CUDA(cudaHostGetDevicePointer((void**)&dp, h->trsv_err_host, 0));
+      h->trsv.host_err = h->trsv_err_host;
+      h->trsv.dev_err = dp;
+    }
     // at a lazy root [C | h_int] is kept (in X's storage) instead of X
     T* R = Lv.lazy ? (T*)Lv.X : (T*)h->scratch;
     // D, R = [C | h_int], TP = [A | h_ext]
@@ -436,7 +450,10 @@ hps_status apply_Dinv(hps_handle* h, int m, T* b, T* y, int nrhs, cudaStream_t s
   if (!Kind<T>::iti) {
     BOp<T> DD = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni);
     HPS_CUDA(permute_rows<T>(bop<T>(b, (int64_t)ni * nrhs, ni), YB, Lv.perm, ni, nrhs, nm, st, pf));
-    HPS_CUDA(getrs_inplace<T>(DD, ni, YB, nrhs, nm, st, pf));
+    if (trsv_flags_applicable<T>(ni, nrhs, nm, h->trsv))
+      HPS_CUDA(getrs_flags<T>((const T*)Lv.D, ni, ni, y, ni, nrhs, h->trsv, st, pf));
+    else
+      HPS_CUDA(getrs_inplace<T>(DD, ni, YB, nrhs, nm, st, pf));
     return HPS_OK;
   }
   const int hn = ni / 2, nb = h->nb;
@@ -464,7 +481,10 @@ hps_status apply_Dinv(hps_handle* h, int m, T* b, T* y, int nrhs, cudaStream_t s
   // b1 <- b1 - D12 b2 (odd children's interior blocks)
   HPS_CUDA(child_block(true, grouped(B1, 2), grouped(B1, 2)));
   HPS_CUDA(permute_rows<T>(B1, YB, Lv.perm, hn, nrhs, nm, st, pf));
-  HPS_CUDA(getrs_inplace<T>(WW, hn, YB, nrhs, nm, st, pf));
+  if (trsv_flags_applicable<T>(hn, nrhs, nm, h->trsv))
+    HPS_CUDA(getrs_flags<T>((const T*)Lv.W, hn, hn, y, ni, nrhs, h->trsv, st, pf));
+  else
+    HPS_CUDA(getrs_inplace<T>(WW, hn, YB, nrhs, nm, st, pf));
   HPS_CUDA(copy_block<T>(b + hn, (int64_t)ni * nrhs, ni, y + hn, (int64_t)ni * nrhs, ni, hn, nrhs, nm, st, pf));
   // y2 <- b2 - D21 y1 (even children's interior blocks)
   HPS_CUDA(child_block(false, grouped(YB, 2), grouped(YB, 2)));
@@ -475,6 +495,8 @@ template <typename T>
 hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_in, void* u_out,
                       cudaStream_t st) {
   constexpr bool ITI = Kind<T>::iti;
+  // a bounded wait of an earlier flag-ordered solve on this handle gave up
+  if (h->trsv_err_host && *(volatile int*)h->trsv_err_host) return HPS_ERR_TIMEOUT;
   hps_status rs = ensure_ws<T>(h, nrhs);
   if (rs != HPS_OK) return rs;
   Prof* pf = &h->prof;
@@ -570,6 +592,7 @@ hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_i
   if (host_u) {
     HPS_CUDA(cudaMemcpyAsync(u_out, u, (size_t)nl * h->npts * nrhs * sizeof(T), cudaMemcpyDeviceToHost, st));
     HPS_CUDA(cudaStreamSynchronize(st));
+    if (h->trsv_err_host && *(volatile int*)h->trsv_err_host) return HPS_ERR_TIMEOUT;
   }
   return HPS_OK;
 }
@@ -581,6 +604,7 @@ void free_handle(hps_handle* h) {
   cudaDeviceSynchronize();
   for (void* p : h->ws_allocs) cudaFree(p);
   for (void* p : h->allocs) cudaFree(p);
+  if (h->trsv_err_host) cudaFreeHost(h->trsv_err_host);
   delete h;
 }
 
@@ -762,12 +786,33 @@ hps_status hps_kernel_stats(hps_handle* h, int cls, hps_kernel_stat* out) {
   out->launches = h->prof.n[cls];
   out->flops = h->prof.flops[cls];
   out->ms = h->prof.on ? h->prof.ms(cls) : -1.0;
+  out->exec_flops = h->prof.exec[cls];
   return HPS_OK;
 }
 
 hps_status hps_set_profiling(hps_handle* h, int on) {
   if (!h) return HPS_ERR_INVALID;
   h->opts.profile = on ? 1 : 0;
+  return HPS_OK;
+}
+
+hps_status hps_trace_count(hps_handle* h, int64_t* count) {
+  if (!h || !count) return HPS_ERR_INVALID;
+  if (h->prof.on && cudaStreamSynchronize(h->last) != cudaSuccess) return HPS_ERR_CUDA;
+  *count = (int64_t)h->prof.trace.size();
+  return HPS_OK;
+}
+
+hps_status hps_trace_get(hps_handle* h, int64_t i, hps_trace_rec* out) {
+  if (!h || !out || i < 0 || i >= (int64_t)h->prof.trace.size()) return HPS_ERR_INVALID;
+  const Prof::Rec& r = h->prof.trace[(size_t)i];
+  out->kclass = r.cls;
+  out->m = r.m;
+  out->n = r.n;
+  out->k = r.k;
+  out->batch = r.batch;
+  out->flops = r.flops;
+  out->ms = h->prof.rec_ms(r);
   return HPS_OK;
 }
 

@@ -342,6 +342,52 @@ __global__ void k_down_gint(const T* X, const T* xp, const T* gpar, int nmerge, 
   }
 }
 
+// Same product for levels with few long rows (the top merges): a CTA holds
+// 32 rows x CG column groups; each warp reads 32 consecutive rows of one
+// column (coalesced), the CG partial sums are added in shared memory in a
+// fixed order, so the result does not depend on scheduling.
+template <typename T, int CG>
+__global__ void __launch_bounds__(32 * CG) k_down_gint_split(const T* X, const T* xp, const T* gpar, int nmerge,
+                                                         int n_ext, int n_int, int nrhs, T* gint) {
+  __shared__ T part[CG][33];
+  const int lane = threadIdx.x, cg = threadIdx.y;
+  const int r = blockIdx.x * 32 + lane;
+  const int64_t bc = blockIdx.y;  // merge * nrhs + rhs
+  const int c = (int)(bc % nrhs);
+  const int64_t b = bc / nrhs;
+  const T* Xb = X + b * (int64_t)n_int * (n_ext + 1);
+  const T* g = gpar + b * (int64_t)n_ext * nrhs + (int64_t)c * n_ext;
+  T acc = T(0.0);
+  if (r < n_int) {
+    int j = cg;
+#pragma unroll 4
+    for (; j < n_ext; j += CG) acc = fmac(acc, Xb[r + (int64_t)j * n_int], g[j]);
+  }
+  part[cg][lane] = acc;
+  __syncthreads();
+  if (cg == 0 && r < n_int) {
+    T s = xp ? xp[b * (int64_t)n_int * nrhs + r + (int64_t)c * n_int] : Xb[r + (int64_t)n_ext * n_int];
+    for (int k = 0; k < CG; ++k) s = s + part[k][lane];
+    gint[b * (int64_t)n_int * nrhs + r + (int64_t)c * n_int] = -s;
+  }
+}
+
+// Rows of work below which the split kernel is used (about two resident
+// threads per SM lane of the whole GPU would otherwise be idle).
+constexpr int64_t kDownSplitRows = 1 << 17;
+
+template <typename T>
+void launch_down_gint(const T* X, const T* xp, const T* gpar, int nmerge, int n_ext, int n_int, int nrhs,
+                      T* gint, cudaStream_t st) {
+  const int64_t rows = (int64_t)nmerge * n_int * nrhs;
+  if (rows < kDownSplitRows && n_ext >= 256 && (int64_t)nmerge * nrhs <= 65535) {
+    dim3 grid((n_int + 31) / 32, nmerge * nrhs);
+    k_down_gint_split<T, 16><<<grid, dim3(32, 16), 0, st>>>(X, xp, gpar, nmerge, n_ext, n_int, nrhs, gint);
+  } else {
+    k_down_gint<T><<<grid_for(rows, 128), 128, 0, st>>>(X, xp, gpar, nmerge, n_ext, n_int, nrhs, gint);
+  }
+}
+
 template <typename T>
 __global__ void k_down_children(const T* gpar, const T* gint, int nmerge, int nch, int nbc, int n_ext,
                                 int n_int, int nrhs, const int* ext, const int* var, T* gchild) {
@@ -368,8 +414,7 @@ cudaError_t down_level(const T* X, const T* xp, const T* gpar, int nmerge, int n
                        cudaStream_t st, Prof* pf) {
   const double F = sizeof(T) == sizeof(cplx) ? 8.0 : 2.0;
   if (pf) pf->begin(st);
-  k_down_gint<T><<<grid_for((int64_t)nmerge * n_int * nrhs, 128), 128, 0, st>>>(X, xp, gpar, nmerge, n_ext,
-                                                                           n_int, nrhs, gint);
+  launch_down_gint<T>(X, xp, gpar, nmerge, n_ext, n_int, nrhs, gint, st);
   if (pf) pf->end(K_DOWN, F * (double)nmerge * n_int * n_ext * nrhs, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -385,8 +430,7 @@ cudaError_t down_gint(const T* X, const T* xp, const T* gpar, int nmerge, int n_
                       T* gint, cudaStream_t st, Prof* pf) {
   const double F = sizeof(T) == sizeof(cplx) ? 8.0 : 2.0;
   if (pf) pf->begin(st);
-  k_down_gint<T><<<grid_for((int64_t)nmerge * n_int * nrhs, 128), 128, 0, st>>>(X, xp, gpar, nmerge, n_ext,
-                                                                           n_int, nrhs, gint);
+  launch_down_gint<T>(X, xp, gpar, nmerge, n_ext, n_int, nrhs, gint, st);
   if (pf) pf->end(K_DOWN, F * (double)nmerge * n_int * n_ext * nrhs, st);
   return cudaGetLastError();
 }

@@ -20,17 +20,31 @@ void Prof::begin(cudaStream_t st) {
   cudaEventRecord(pending, st);
 }
 
-void Prof::end(int cls, double fl, cudaStream_t st) {
+void Prof::end(int cls, double fl, cudaStream_t st, double executed) {
   ++launches;
   ++n[cls];
   flops[cls] += fl;
-  if (!on || !pending) return;
+  exec[cls] += executed < 0.0 ? fl : executed;
+  if (!on || !pending) {
+    dims[0] = dims[1] = dims[2] = dims[3] = 0;
+    return;
+  }
   cudaEvent_t e1;
   cudaEventCreate(&e1);
   cudaEventRecord(e1, st);
+  trace.push_back(Rec{cls, dims[0], dims[1], dims[2], dims[3], fl, (int64_t)ev[cls].size()});
+  dims[0] = dims[1] = dims[2] = dims[3] = 0;
   ev[cls].push_back(pending);
   ev[cls].push_back(e1);
   pending = nullptr;
+}
+
+double Prof::rec_ms(const Rec& r) const {
+  float m = 0.f;
+  if (r.ev + 1 < (int64_t)ev[r.cls].size() &&
+      cudaEventElapsedTime(&m, ev[r.cls][r.ev], ev[r.cls][r.ev + 1]) == cudaSuccess)
+    return m;
+  return -1.0;
 }
 
 void Prof::reset() {
@@ -39,10 +53,12 @@ void Prof::reset() {
     ev[c].clear();
     n[c] = 0;
     flops[c] = 0.0;
+    exec[c] = 0.0;
   }
   if (pending) cudaEventDestroy(pending);
   pending = nullptr;
   launches = 0;
+  trace.clear();
 }
 
 double Prof::ms(int cls) const {
@@ -212,11 +228,13 @@ template <> struct UseC3M<cplx> { static constexpr bool value = true; };
 
 // Skinny variant for N <= 8 right-hand sides (the solve path): one thread
 // per output row, B chunks staged in shared memory, A read column by column
-// (coalesced along the rows).
-template <typename T>
+// (coalesced along the rows).  NC is the column count rounded up to 1, 2, 4
+// or 8: the FP64 pipe spends its cycles on predicated-off FMAs too, so the
+// kernel never carries more columns than it needs.
+template <typename T, int NC>
 __global__ void __launch_bounds__(128) k_gemm_skinny(GemmArgs<T> g) {
   constexpr int KC = 32;
-  __shared__ T Bs[KC][8];
+  __shared__ T Bs[KC][NC];
   const int tid = threadIdx.x;
   for (int b = blockIdx.z; b < g.batch; b += gridDim.z) {
     const T* A = g.A.item(b);
@@ -225,23 +243,32 @@ __global__ void __launch_bounds__(128) k_gemm_skinny(GemmArgs<T> g) {
     const int i = blockIdx.x * 128 + tid;
     const bool act = i < g.M;
     const int64_t ar = act ? g.arow.at(b, i) : 0;
-    T acc[8];
+    T acc[NC];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = T(0.0);
+    for (int c = 0; c < NC; ++c) acc[c] = T(0.0);
     for (int k0 = 0; k0 < g.K; k0 += KC) {
       const int kc = min(KC, g.K - k0);
       __syncthreads();
-      for (int e = tid; e < KC * 8; e += 128) {
+      for (int e = tid; e < KC * NC; e += 128) {
         const int l = e % KC, c = e / KC;
         Bs[l][c] = (l < kc && c < g.N) ? B[(int64_t)g.brow.at(b, k0 + l) + (int64_t)c * g.B.ld] : T(0.0);
       }
       __syncthreads();
       if (act) {
-        for (int l = 0; l < kc; ++l) {
-          const T a = A[ar + (int64_t)g.acol.at(b, k0 + l) * g.A.ld];
+        if (kc == KC) {
+          // full chunk: unrolled so that several column loads are in flight
+#pragma unroll 8
+          for (int l = 0; l < KC; ++l) {
+            const T a = A[ar + (int64_t)g.acol.at(b, k0 + l) * g.A.ld];
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (c < g.N) acc[c] = fmac(acc[c], a, Bs[l][c]);
+            for (int c = 0; c < NC; ++c) acc[c] = fmac(acc[c], a, Bs[l][c]);
+          }
+        } else {
+          for (int l = 0; l < kc; ++l) {
+            const T a = A[ar + (int64_t)g.acol.at(b, k0 + l) * g.A.ld];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = fmac(acc[c], a, Bs[l][c]);
+          }
         }
       }
     }
@@ -249,7 +276,7 @@ __global__ void __launch_bounds__(128) k_gemm_skinny(GemmArgs<T> g) {
       const int64_t ci = g.crow.at(b, i);
       const bool use_beta = !is_zero(g.beta);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < NC; ++c) {
         if (c >= g.N) break;
         T* p = C + ci + (int64_t)c * g.C.ld;
         T v = g.alpha * acc[c];
@@ -260,18 +287,79 @@ __global__ void __launch_bounds__(128) k_gemm_skinny(GemmArgs<T> g) {
   }
 }
 
+// Skinny product with few rows in the whole launch (the top levels of the
+// solve): 32 rows x 8 groups of the inner dimension per CTA, the 8 partial
+// sums added in shared memory in a fixed order.
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_gemm_skinny_kg(GemmArgs<T> g) {
+  __shared__ T part[8][NC][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int b = blockIdx.z; b < g.batch; b += gridDim.z) {
+    const T* A = g.A.item(b);
+    const T* B = g.B.item(b);
+    T* C = g.C.item(b);
+    const int i = blockIdx.x * 32 + lane;
+    const bool act = i < g.M;
+    const int64_t ar = act ? g.arow.at(b, i) : 0;
+    T acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = T(0.0);
+    if (act) {
+#pragma unroll 4
+      for (int l = w; l < g.K; l += 8) {
+        const T a = A[ar + (int64_t)g.acol.at(b, l) * g.A.ld];
+        const int64_t br = g.brow.at(b, l);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (c < g.N) acc[c] = fmac(acc[c], a, B[br + (int64_t)c * g.B.ld]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) part[w][c][lane] = acc[c];
+    __syncthreads();
+    if (w == 0 && act) {
+      const int64_t ci = g.crow.at(b, i);
+      const bool use_beta = !is_zero(g.beta);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        if (c >= g.N) break;
+        T v = part[0][c][lane];
+        for (int k = 1; k < 8; ++k) v = v + part[k][c][lane];
+        T* p = C + ci + (int64_t)c * g.C.ld;
+        v = g.alpha * v;
+        if (use_beta) v = fmac(v, g.beta, *p);
+        *p = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T>
 cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   constexpr int BM = GemmTile<T>::BM, BN = GemmTile<T>::BN;
-  if (pf) pf->begin(st);
-  if (g.N <= 8) {
+  if (pf) {
+    pf->begin(st);
+    pf->note(g.M, g.N, g.K, g.batch);
+  }
+  if (g.N <= 8 && g.K >= 128 && (int64_t)((g.M + 127) / 128) * g.batch < 304) {
+    dim3 grid((g.M + 31) / 32, 1, std::min(g.batch, 65535));
+    if (g.N == 1) k_gemm_skinny_kg<T, 1><<<grid, 256, 0, st>>>(g);
+    else if (g.N == 2) k_gemm_skinny_kg<T, 2><<<grid, 256, 0, st>>>(g);
+    else if (g.N <= 4) k_gemm_skinny_kg<T, 4><<<grid, 256, 0, st>>>(g);
+    else k_gemm_skinny_kg<T, 8><<<grid, 256, 0, st>>>(g);
+  } else if (g.N <= 8) {
     dim3 grid((g.M + 127) / 128, 1, std::min(g.batch, 65535));
-    k_gemm_skinny<T><<<grid, 128, 0, st>>>(g);
+    if (g.N == 1) k_gemm_skinny<T, 1><<<grid, 128, 0, st>>>(g);
+    else if (g.N == 2) k_gemm_skinny<T, 2><<<grid, 128, 0, st>>>(g);
+    else if (g.N <= 4) k_gemm_skinny<T, 4><<<grid, 128, 0, st>>>(g);
+    else k_gemm_skinny<T, 8><<<grid, 128, 0, st>>>(g);
   } else if (UseC3M<T>::value) {
     dim3 grid((g.M + 31) / 32, (g.N + 31) / 32, std::min(g.batch, 65535));
     k_gemm_c3m<<<grid, 256, 0, st>>>(*reinterpret_cast<const GemmArgs<cplx>*>(&g));
-    if (pf) pf->end(K_GEMM, 6.0 * g.M * (double)g.N * g.K * g.batch, st);
+    const double mnk = g.M * (double)g.N * g.K * g.batch;
+    if (pf) pf->end(K_GEMM, 8.0 * mnk, st, 6.0 * mnk);
     return cudaGetLastError();
   } else {
     dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, std::min(g.batch, 65535));
@@ -562,7 +650,10 @@ cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, u
       pfl += below * (nb - jj - 1) + below;
     }
     pfl *= F * batch;
-    if (pf) pf->begin(st);
+    if (pf) {
+      pf->begin(st);
+      pf->note(rows, nb, Gk, batch);  // k: CTAs per matrix
+    }
     if (Gk > 1) {
       T* pubv = reinterpret_cast<T*>(w.pub);
       double* pubm = reinterpret_cast<double*>(pubv + (size_t)batch * 2 * (G + 1) * nb0);
@@ -590,7 +681,10 @@ cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, u
       const int ncols = n - nb;
       int bx = std::min((ncols + 127) / 128, 1024);
       size_t sm2 = (size_t)nb * nb * sizeof(T);
-      if (pf) pf->begin(st);
+      if (pf) {
+        pf->begin(st);
+        pf->note(nb, n - k0 - nb, nb, batch);
+      }
       k_laswp_trsm<T><<<dim3(bx, batch), 128, sm2, st>>>(A, n, k0, nb, ipiv);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       if (pf) pf->end(K_LASWP_TRSM, F * 0.5 * nb * (nb - 1) * (double)(n - k0 - nb) * batch, st);
@@ -761,7 +855,10 @@ cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaS
   // forward: unit lower
   for (int p0 = 0; p0 < n; p0 += pb0) {
     const int pb = std::min(pb0, n - p0);
-    if (pf) pf->begin(st);
+    if (pf) {
+      pf->begin(st);
+      pf->note(pb, nrhs, pb, batch);
+    }
     if ((e = trsm_diag<T, false>(LU, X, p0, pb, nrhs, batch, st)) != cudaSuccess) return e;
     if (pf) pf->end(K_TRSM_DIAG, F * 0.5 * pb * (pb - 1) * (double)nrhs * batch, st);
     const int rest = n - p0 - pb;
@@ -780,7 +877,10 @@ cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaS
   for (int pi = npan - 1; pi >= 0; --pi) {
     const int p0 = pi * pb0;
     const int pb = std::min(pb0, n - p0);
-    if (pf) pf->begin(st);
+    if (pf) {
+      pf->begin(st);
+      pf->note(pb, nrhs, pb, batch);
+    }
     if ((e = trsm_diag<T, true>(LU, X, p0, pb, nrhs, batch, st)) != cudaSuccess) return e;
     if (pf) pf->end(K_TRSM_DIAG, F * (0.5 * pb * (pb - 1) + pb) * (double)nrhs * batch, st);
     if (p0 > 0) {
@@ -796,6 +896,178 @@ cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaS
   return cudaSuccess;
 }
 
+// --------------------------------------------- flag-ordered solve ----
+//
+// Triangular solve of a single large factor with few right-hand sides.  The
+// blocked getrs issues two launches per 32 rows, each far too small to fill
+// the GPU; here one launch per triangle walks the 32-row blocks in dependency
+// order (forward: first to last; backward: last to first).  CTA c takes the
+// logical blocks c, c + G, c + 2G, ... in increasing order; for each it
+// subtracts the contributions of all earlier blocks as their solutions are
+// published (warp w handles earlier blocks w, w + 8, ...), solves its own
+// 32 x 32 diagonal block with warp shuffles, writes the result and raises
+// the block's flag.  The launch is cooperative, so every CTA is resident, and
+// the earliest unfinished block depends only on finished ones: the walk
+// always makes progress.  Waits are bounded: on timeout the flag error word
+// is set and the block proceeds (wrong values, but the launch ends).
+template <typename T, int NR, bool UPPER>
+__global__ void __launch_bounds__(256) k_trsv_flags(const T* __restrict__ LU, int ld, int n, T* X, int ldx,
+                                                   int nrhs, unsigned* flags, unsigned epoch,
+                                                   volatile int* err) {
+  // warp 0: the block's right-hand side and diagonal solve; warps 1..7: the
+  // contributions of earlier blocks.  Every warp loads its 32 matrix entries
+  // per row before it waits for the solution they multiply, so the critical
+  // path per block is a flag, 32 values of x and 32 FMAs, not 32 loads.
+  __shared__ T part[7][NR][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nblk = (n + 31) / 32;
+  for (int t = blockIdx.x; t < nblk; t += gridDim.x) {
+    const int j = UPPER ? nblk - 1 - t : t;
+    const int r = j * 32 + lane;
+    const bool rv = r < n;
+    if (w > 0) {
+      T acc[NR];
+#pragma unroll
+      for (int c = 0; c < NR; ++c) acc[c] = T(0.0);
+      for (int tp = w - 1; tp < t; tp += 7) {
+        const int i = UPPER ? nblk - 1 - tp : tp;
+        const int qn = min(32, n - i * 32);
+        const T* col = LU + (int64_t)(i * 32) * ld + r;
+        T a[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) a[q] = (rv && q < qn) ? col[(int64_t)q * ld] : T(0.0);
+        if (lane == 0) {
+          const volatile unsigned* f = flags + i;
+          unsigned long long it = 0;
+          while (*f != epoch) {
+            if (++it > (1ull << 24)) {
+              *err = 1;
+              break;
+            }
+            __nanosleep(32);
+          }
+          __threadfence();
+        }
+        __syncwarp();
+        const int ri = i * 32 + lane;
+        T xi[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) xi[c] = (ri < n && c < nrhs) ? ld_cg(X + ri + (int64_t)c * ldx) : T(0.0);
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+#pragma unroll
+          for (int c = 0; c < NR; ++c) acc[c] = fmsc(acc[c], a[q], shfl_val(xi[c], q));
+      }
+#pragma unroll
+      for (int c = 0; c < NR; ++c) part[w - 1][c][lane] = acc[c];
+    }
+    T dg[32], x[NR];
+    const int pb = min(32, n - j * 32);
+    if (w == 0) {
+      const T* dcol = LU + (int64_t)(j * 32) * ld + r;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) dg[q] = (rv && q < pb) ? dcol[(int64_t)q * ld] : T(0.0);
+#pragma unroll
+      for (int c = 0; c < NR; ++c) x[c] = (rv && c < nrhs) ? X[r + (int64_t)c * ldx] : T(0.0);
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+      for (int c = 0; c < NR; ++c)
+        for (int k = 0; k < 7; ++k) x[c] = x[c] + part[k][c][lane];
+      if (!UPPER) {
+#pragma unroll
+        for (int cc = 0; cc < 31; ++cc) {
+#pragma unroll
+          for (int c = 0; c < NR; ++c) {
+            const T xc = shfl_val(x[c], cc);
+            if (lane > cc && lane < pb) x[c] = fmsc(x[c], dg[cc], xc);
+          }
+        }
+      } else {
+        T d = T(1.0);
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (q == lane) d = dg[q];
+        const T dinv = (!rv || is_zero(d)) ? T(0.0) : recip(d);
+#pragma unroll
+        for (int cc = 31; cc >= 0; --cc) {
+#pragma unroll
+          for (int c = 0; c < NR; ++c) {
+            if (lane == cc) x[c] = x[c] * dinv;
+            const T xc = shfl_val(x[c], cc);
+            if (lane < cc) x[c] = fmsc(x[c], dg[cc], xc);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NR; ++c)
+        if (rv && c < nrhs) X[r + (int64_t)c * ldx] = x[c];
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) atomicExch(flags + j, epoch);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+bool trsv_flags_applicable(int n, int nrhs, int batch, const TrsvWork& w) {
+  return batch == 1 && nrhs >= 1 && nrhs <= 8 && n >= 128 && w.flags && w.dev_err &&
+         (n + 31) / 32 <= w.nflags;
+}
+
+template <typename T, int NR, bool UPPER>
+cudaError_t launch_trsv_flags(const T* LU, int n, int ld, T* X, int ldx, int nrhs, TrsvWork& w,
+                              cudaStream_t st) {
+  static int per_sm = -1, sms = 0;
+  cudaError_t e;
+  if (per_sm < 0) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_flags<T, NR, UPPER>, 256, 0)) !=
+        cudaSuccess)
+      return e;
+  }
+  const int nblk = (n + 31) / 32;
+  const int G = std::max(1, std::min(nblk, per_sm * sms));
+  const unsigned ep = ++w.epoch;
+  unsigned* fl = w.flags;
+  int* errp = const_cast<int*>(w.dev_err);
+  void* args[] = {(void*)&LU, &ld, &n, &X, &ldx, &nrhs, &fl, (void*)&ep, &errp};
+  return cudaLaunchCooperativeKernel((void*)k_trsv_flags<T, NR, UPPER>, dim3(G), dim3(256), args, 0, st);
+}
+
+template <typename T, bool UPPER>
+cudaError_t trsv_flags_dispatch(const T* LU, int n, int ld, T* X, int ldx, int nrhs, TrsvWork& w,
+                                cudaStream_t st) {
+  if (nrhs == 1) return launch_trsv_flags<T, 1, UPPER>(LU, n, ld, X, ldx, nrhs, w, st);
+  if (nrhs == 2) return launch_trsv_flags<T, 2, UPPER>(LU, n, ld, X, ldx, nrhs, w, st);
+  if (nrhs <= 4) return launch_trsv_flags<T, 4, UPPER>(LU, n, ld, X, ldx, nrhs, w, st);
+  return launch_trsv_flags<T, 8, UPPER>(LU, n, ld, X, ldx, nrhs, w, st);
+}
+
+template <typename T>
+cudaError_t getrs_flags(const T* LU, int n, int ld, T* X, int ldx, int nrhs, TrsvWork& w, cudaStream_t st,
+                        Prof* pf) {
+  constexpr double F = fma_flops<T>();
+  cudaError_t e;
+  if (pf) {
+    pf->begin(st);
+    pf->note(n, nrhs, 32, 1);
+  }
+  if ((e = trsv_flags_dispatch<T, false>(LU, n, ld, X, ldx, nrhs, w, st)) != cudaSuccess) return e;
+  if (pf) pf->end(K_TRSM_DIAG, F * 0.5 * n * (double)(n - 1) * nrhs, st);
+  if (pf) {
+    pf->begin(st);
+    pf->note(n, nrhs, 32, 1);
+  }
+  if ((e = trsv_flags_dispatch<T, true>(LU, n, ld, X, ldx, nrhs, w, st)) != cudaSuccess) return e;
+  if (pf) pf->end(K_TRSM_DIAG, F * (0.5 * n * (double)(n - 1) + n) * nrhs, st);
+  return cudaSuccess;
+}
+
 // ------------------------------------------------------- instantiation ----
 
 #define HPS_INST(T)                                                                              \
@@ -807,7 +1079,9 @@ cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaS
                                 const LuWork&, cudaStream_t, Prof*);                             \
   template cudaError_t permute_rows<T>(BOp<T>, BOp<T>, const int*, int, int, int, cudaStream_t,  \
                                        Prof*);                                                   \
-  template cudaError_t getrs_inplace<T>(BOp<T>, int, BOp<T>, int, int, cudaStream_t, Prof*);
+  template cudaError_t getrs_inplace<T>(BOp<T>, int, BOp<T>, int, int, cudaStream_t, Prof*);                   \
+  template bool trsv_flags_applicable<T>(int, int, int, const TrsvWork&);                        \
+  template cudaError_t getrs_flags<T>(const T*, int, int, T*, int, int, TrsvWork&, cudaStream_t, Prof*);
 
 HPS_INST(double)
 HPS_INST(cplx)

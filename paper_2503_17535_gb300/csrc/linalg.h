@@ -27,11 +27,20 @@ struct Prof {
   bool on = false;
   int64_t launches = 0;
   int64_t n[K_COUNT] = {};
-  double flops[K_COUNT] = {};
+  double flops[K_COUNT] = {};  // algorithmic (complex multiply-add = 8)
+  double exec[K_COUNT] = {};   // executed on the FP64 pipe (3M complex GEMM: 6 per multiply-add)
   std::vector<cudaEvent_t> ev[K_COUNT];
   cudaEvent_t pending = nullptr;
+  // per-launch trace (profiling on): class, problem shape, flops and the
+  // index of the launch's event pair in ev[cls]
+  struct Rec { int cls, m, n, k; int64_t batch; double flops; int64_t ev; };
+  std::vector<Rec> trace;
+  int dims[4] = {0, 0, 0, 0};
   void begin(cudaStream_t st);
-  void end(int cls, double fl, cudaStream_t st);
+  // shape of the next launch (m x n result, inner dimension k, batch)
+  void note(int m, int n, int k, int64_t batch) { dims[0] = m; dims[1] = n; dims[2] = k; dims[3] = (int)batch; }
+  void end(int cls, double fl, cudaStream_t st, double executed = -1.0);
+  double rec_ms(const Rec& r) const;
   void reset();
   double ms(int cls) const;
   ~Prof() { reset(); }
@@ -117,6 +126,28 @@ cudaError_t permute_rows(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrh
 template <typename T>
 cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaStream_t st,
                           Prof* pf);
+
+// One n x n LU factor against nrhs <= 8 columns (X <- U^{-1} L^{-1} X, X
+// already row-permuted), each triangle in a single cooperative launch:
+// 32-row blocks are solved in dependency order and published through
+// per-block flags (flags[i] == epoch once block i is final).  The caller
+// keeps one flag per 32 rows (device, initially 0) and a counter; each call
+// uses two fresh epochs.  A wait that exceeds its poll limit stores 1 in
+// *host_err (host-mapped memory) and the block goes on, so no launch hangs.
+struct TrsvWork {
+  unsigned* flags = nullptr;
+  int nflags = 0;
+  unsigned epoch = 0;
+  volatile int* host_err = nullptr;  // host-mapped
+  volatile int* dev_err = nullptr;   // its device alias
+};
+
+template <typename T>
+bool trsv_flags_applicable(int n, int nrhs, int batch, const TrsvWork& w);
+
+template <typename T>
+cudaError_t getrs_flags(const T* LU, int n, int ld, T* X, int ldx, int nrhs, TrsvWork& w, cudaStream_t st,
+                        Prof* pf);
 
 // C = alpha * C + beta (identity added on the diagonal when diag != 0) helpers
 template <typename T>
