@@ -64,6 +64,14 @@ WORKLOADS = {
                    "depth": -1, "p": 8, "q": 6, "seed_problem": 3, "eps": 1e-4, "min_depth": 2,
                    "max_depth": 5, "cpu_depth": None},
 }
+# Serving workload: seeded operators (kind, depth, p drawn as listed) resident
+# in a request server; a Poisson stream of requests, 80 % solves with a new
+# seeded source and boundary data on a resident operator, 20 % rebuilds of an
+# operator with a new seeded coefficient field.
+SERVE = {"workload": "serve2d_poisson_arrivals", "seed": 4, "n_ops": 6, "depths": [3, 7], "ps": [8, 12, 16],
+         "kinds": ["dtn", "iti"], "rebuild_frac": 0.2, "requests": 60, "rates": [0.5, 0.9, 1.5],
+         "pool": 3, "max_batch": 8, "n_streams": 4, "op_budget_gb": 150}
+
 COMMON = {"seed_solve_source": 11, "root_map": False, "step": "hps_build + hps_solve(new f) + hps_free",
           "l2": "no flush: the step's factor working set is far above the 129 MB L2"}
 
@@ -74,7 +82,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="helmholtz2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="helmholtz2d", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--requests", type=int, default=None, help="serve: requests per arrival rate")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--root", default="lazy", choices=["lazy", "explicit"],
@@ -85,6 +94,11 @@ def parse():
     ap.add_argument("--depth", type=int, default=None,
                     help="uniform tree depth override (smaller cases for profiler captures)")
     args = ap.parse_args()
+    if args.workload == "serve":
+        args.spec = dict(SERVE)
+        if args.requests:
+            args.spec["requests"] = args.requests
+        return args
     spec = dict(WORKLOADS[args.workload])
     if args.depth is not None and spec["depth"] >= 0 and args.depth != spec["depth"]:
         spec["depth"] = args.depth
@@ -491,10 +505,190 @@ def run_reference(args, rank):
     return line
 
 
+# ----------------------------------------------------------------- serving --
+
+def serve_operators(P, spec):
+    """The seeded operator set: (kind, depth, p) per slot, redrawn with the
+    next seed while the planned footprint exceeds op_budget_gb."""
+    seed = spec["seed"]
+    while True:
+        rng = np.random.default_rng(seed)
+        ops = []
+        for i in range(spec["n_ops"]):
+            kind = spec["kinds"][int(rng.integers(0, len(spec["kinds"])))]
+            depth = int(rng.integers(spec["depths"][0], spec["depths"][1] + 1))
+            p = int(spec["ps"][int(rng.integers(0, len(spec["ps"])))])
+            ops.append({"kind": kind, "depth": depth, "p": p, "q": p - 2})
+        tot = sum(P.hps_plan_bytes(P.uniform_tree(2, o["depth"]), o["p"], o["q"],
+                                   P.HPS_ITI if o["kind"] == "iti" else P.HPS_DTN) for o in ops)
+        if tot <= spec["op_budget_gb"] * 1e9:
+            return ops, seed, tot
+        seed += 1000
+
+
+def serve_inputs(P, op, field_seed, rng):
+    """Coefficient arrays of one operator (coefficient field seed), plus
+    solve inputs drawn from rng."""
+    import workloads as W
+    pr = (W.helmholtz_bumps_2d(seed=field_seed) if op["kind"] == "iti" else W.elliptic_2d(seed=field_seed))
+    t = P.uniform_tree(2, op["depth"], pr.lo, pr.hi)
+    x, xb = P.hps_nodes(t, op["p"], op["q"])
+    nl, ppl, nr = P.hps_sizes(t, op["p"], op["q"])
+    cf = pr.coeffs(x)
+    cdt = np.complex128 if op["kind"] == "iti" else np.float64
+    d = {"t": t, "kind": P.HPS_ITI if op["kind"] == "iti" else P.HPS_DTN, "eta": pr.eta or 0.0,
+         "a": np.ascontiguousarray(cf["a"].reshape(nl, ppl)),
+         "b": [np.ascontiguousarray(bk.reshape(nl, ppl)) for bk in cf["b"]],
+         "c": np.ascontiguousarray(cf["c"].reshape(nl, ppl)),
+         "f": np.ascontiguousarray(pr.source(x).reshape(nl, ppl).astype(cdt)), "shape": (nl, ppl), "cdt": cdt}
+    return d
+
+
+def run_serve(args, rank, world):
+    """Served solves/s and p50 / p99 latency of the request server against the
+    plain path (one request at a time, hps_build / hps_solve directly) on the
+    same seeded request stream and arrival times."""
+    import threading  # noqa: F401  (the server's threads are native)
+    import torch
+    import paper_2503_17535_gb300 as P
+
+    spec = args.spec
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ops, op_seed, op_bytes = serve_operators(P, spec)
+    rng = np.random.default_rng(op_seed + 1)
+    pools = []
+    for i, op in enumerate(ops):
+        fields = [serve_inputs(P, op, 100 + 10 * i + k, rng) for k in range(spec["pool"])]
+        sol = []
+        for k in range(spec["pool"]):
+            d = fields[0]
+            nl, ppl = d["shape"]
+            nr = P.hps_sizes(d["t"], op["p"], op["q"])[2]
+            g = rng.standard_normal(nr)
+            f = rng.standard_normal((nl, ppl))
+            if d["cdt"] == np.complex128:
+                g = g + 1j * rng.standard_normal(nr)
+                f = f + 1j * rng.standard_normal((nl, ppl))
+            sol.append((np.ascontiguousarray(g.astype(d["cdt"])), np.ascontiguousarray(f.astype(d["cdt"]))))
+        pools.append({"fields": fields, "solves": sol})
+    R = spec["requests"]
+    req = []
+    for r in range(R):
+        slot = int(rng.integers(0, len(ops)))
+        if rng.random() < spec["rebuild_frac"]:
+            req.append(("build", slot, int(rng.integers(1, spec["pool"]))))
+        else:
+            req.append(("solve", slot, int(rng.integers(0, spec["pool"]))))
+
+    def plain_initial():
+        hs = []
+        for i, op in enumerate(ops):
+            d = pools[i]["fields"][0]
+            hs.append(P.hps_build(d["t"], op["p"], op["q"], d["kind"], a=d["a"], b=d["b"], c=d["c"], f=d["f"],
+                                  eta=d["eta"], lazy_root=True))
+        torch.cuda.synchronize()
+        return hs
+
+    def plain_run(arrivals):
+        hs = plain_initial()
+        outs = [np.zeros(pools[i]["fields"][0]["shape"], pools[i]["fields"][0]["cdt"]) for i in range(len(ops))]
+        t0 = time.perf_counter()
+        lat, service = [], []
+        for r, (kind, slot, k) in enumerate(req):
+            if arrivals is not None:
+                wait = arrivals[r] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+            ts = time.perf_counter()
+            op = ops[slot]
+            if kind == "build":
+                d = pools[slot]["fields"][k]
+                P.hps_free(hs[slot])
+                hs[slot] = P.hps_build(d["t"], op["p"], op["q"], d["kind"], a=d["a"], b=d["b"], c=d["c"],
+                                       f=d["f"], eta=d["eta"], lazy_root=True)
+                torch.cuda.synchronize()
+            else:
+                g, f = pools[slot]["solves"][k]
+                P.hps_solve(hs[slot], g, outs[slot], f=f)
+            te = time.perf_counter()
+            service.append(te - ts)
+            lat.append(te - t0 - (arrivals[r] if arrivals is not None else (ts - t0)))
+        span = time.perf_counter() - t0
+        for h in hs:
+            P.hps_free(h)
+        return {"lat_ms": [1e3 * v for v in lat], "service_s": service, "span_s": span}
+
+    def served_run(arrivals):
+        S = P.Server(n_slots=len(ops), n_streams=spec["n_streams"], max_batch=spec["max_batch"], lazy_root=True)
+        # one output buffer per slot: the benchmark does not read the results
+        # (the GPU tests check them), so requests of a slot may share it
+        outs = [np.zeros(pools[i]["fields"][0]["shape"], pools[i]["fields"][0]["cdt"]) for i in range(len(ops))]
+        for i, op in enumerate(ops):
+            d = pools[i]["fields"][0]
+            S.wait(S.submit_build(i, d["t"], op["p"], op["q"], d["kind"], a=d["a"], b=d["b"], c=d["c"],
+                                  f=d["f"], eta=d["eta"]))
+        t0 = time.perf_counter()
+        tickets = []
+        for r, (kind, slot, k) in enumerate(req):
+            wait = arrivals[r] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            op = ops[slot]
+            if kind == "build":
+                d = pools[slot]["fields"][k]
+                tickets.append(S.submit_build(slot, d["t"], op["p"], op["q"], d["kind"], a=d["a"], b=d["b"],
+                                              c=d["c"], f=d["f"], eta=d["eta"]))
+            else:
+                g, f = pools[slot]["solves"][k]
+                tickets.append(S.submit_solve(slot, g, outs[slot], f=f))
+        infos = [S.wait(t) for t in tickets]
+        st = S.stats()
+        S.close()
+        lat = [i["t_done_ms"] - i["t_submit_ms"] for i in infos]
+        span = (max(i["t_done_ms"] for i in infos) - min(i["t_submit_ms"] for i in infos)) / 1e3
+        return {"lat_ms": lat, "span_s": span, "max_batch": st["max_batch_seen"], "batches": st["batches"]}
+
+    def pct_of(v, q):
+        return round(float(np.percentile(np.asarray(v), q)), 3)
+
+    base = plain_run(None)  # back to back: the one-at-a-time capacity
+    cap = R / sum(base["service_s"])
+    rates = []
+    for rho in spec["rates"]:
+        lam = rho * cap
+        arr = np.cumsum(np.random.default_rng(spec["seed"] + int(100 * rho)).exponential(1.0 / lam, size=R))
+        arr -= arr[0]
+        sv = served_run(arr)
+        pl = plain_run(arr)
+        rates.append({"load": rho, "offered_per_s": round(lam, 3),
+                      "served": {"solves_per_s": round(R / sv["span_s"], 3), "p50_ms": pct_of(sv["lat_ms"], 50),
+                                 "p99_ms": pct_of(sv["lat_ms"], 99), "max_batch": sv["max_batch"],
+                                 "batches": sv["batches"]},
+                      "plain": {"solves_per_s": round(R / pl["span_s"], 3), "p50_ms": pct_of(pl["lat_ms"], 50),
+                                "p99_ms": pct_of(pl["lat_ms"], 99)}})
+    top = rates[-1]
+    n_build = sum(1 for r in req if r[0] == "build")
+    cfg = {k: v for k, v in spec.items() if k not in ("op_budget_gb",)}
+    cfg.update({"operators": ops, "operator_seed": op_seed, "operator_bytes": int(op_bytes),
+                "requests_build": n_build, "requests_solve": R - n_build, "root": "lazy",
+                "plain_capacity_per_s": round(cap, 3),
+                "value_at": f"load {top['load']} x plain capacity (saturated): whole-run served requests/s"})
+    line = {"metric": METRIC, "value": top["served"]["solves_per_s"], "unit": "requests/s", "n_gpus": world,
+            "steps": R, "warmup": 0, "p50_ms": top["served"]["p50_ms"], "p99_ms": top["served"]["p99_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+c128",
+            "data": "synthetic", "config": cfg, "rates": rates,
+            "vs_plain": round(top["served"]["solves_per_s"] / max(top["plain"]["solves_per_s"], 1e-9), 3)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "serve":
+        return run_serve(args, rank, world)
     spec = args.spec
     if args.impl == "reference":
         line = run_reference(args, rank)

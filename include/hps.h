@@ -62,7 +62,8 @@ typedef enum {
   HPS_ERR_OOM = -2,       /* planned footprint exceeds free device memory   */
   HPS_ERR_SINGULAR = -3,  /* an exactly zero pivot in a leaf or merge LU     */
   HPS_ERR_CUDA = -4,      /* a CUDA runtime call failed                      */
-  HPS_ERR_TIMEOUT = -5    /* a bounded device-side wait gave up              */
+  HPS_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up              */
+  HPS_PENDING = 1         /* hps_server_poll: the request has not finished   */
 } hps_status;
 
 enum { HPS_DTN = 0, HPS_ITI = 1 };
@@ -212,6 +213,12 @@ hps_status hps_last_error_detail(hps_handle* h, int64_t* node);
 
 /* Device bytes held by the handle (factors, operators, workspace). */
 int64_t hps_device_bytes(const hps_handle* h);
+
+/* Planned device bytes of a handle that hps_build would create for a uniform
+ * tree (factors, operators and a one-right-hand-side solve workspace), before
+ * building it: the figure a caller admits work by.  Pure host computation.
+ * HPS_ERR_INVALID for adaptive trees and bad arguments. */
+hps_status hps_plan_bytes(const hps_tree* tree, int p, int q, int kind, int64_t* bytes);
 
 /* Number of CUDA kernel launches issued by the last hps_build / hps_solve on h. */
 int64_t hps_last_launch_count(const hps_handle* h);

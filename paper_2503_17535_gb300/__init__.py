@@ -319,3 +319,134 @@ def hps_set_profiling(h: Handle, on: bool):
     _check(_capi.lib().hps_set_profiling(h.ptr, 1 if on else 0), "hps_set_profiling")
 
 
+
+
+def hps_plan_bytes(tree: hps_tree, p: int, q: int, kind: int) -> int:
+    """Planned device bytes of the handle hps_build would create (uniform trees)."""
+    out = c_int64(0)
+    _check(_capi.lib().hps_plan_bytes(byref(tree), p, q, kind, byref(out)), "hps_plan_bytes")
+    return out.value
+
+
+class _Borrowed(Handle):
+    """A server-owned operator, for inspection only (never freed here)."""
+
+    def __del__(self):
+        self.ptr = None
+
+
+class Server:
+    """Request server of include/hps_serve.h: resident operators in slots,
+    solve requests merged into batched solves on a pool of streams, builds
+    on a separate thread, admitted by planned device footprint.  Buffers are
+    host numpy arrays; the server keeps references until a request is
+    waited for."""
+
+    def __init__(self, n_slots: int = 16, n_streams: int = 4, max_batch: int = 8, hbm_budget: int = 0,
+                 lazy_root: bool = False):
+        o = _capi.hps_server_options()
+        o.version = 1
+        o.n_slots, o.n_streams, o.max_batch = n_slots, n_streams, max_batch
+        o.hbm_budget = hbm_budget
+        o.lazy_root = 1 if lazy_root else 0
+        out = c_void_p()
+        _check(_capi.lib().hps_server_create(byref(o), byref(out)), "hps_server_create")
+        self.ptr = out.value
+        self._keep: dict = {}
+        self._meta: dict = {}   # slot -> (tree, p, q, complex) of the last submitted build
+
+    def submit_build(self, slot: int, tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None,
+                     f=None, eta: float = 0.0, lazy_root=None) -> int:
+        nl, ppl, _ = hps_sizes(tree, p, q)
+        n = nl * ppl
+        keep: list = [tree]
+        cf, keep = make_coeffs(kind, a, b, c, eta, keep, n)
+        fp = _ptr(f, kind == HPS_ITI, n, "f", keep)
+        optp = None
+        if lazy_root is not None:
+            opts = hps_options()
+            opts.version = 1
+            opts.lazy_root = 1 if lazy_root else 0
+            keep.append(opts)
+            optp = byref(opts)
+        keep.append(cf)
+        t = c_int64(0)
+        _check(_capi.lib().hps_server_submit_build(self.ptr, slot, byref(tree), p, q, byref(cf), fp, optp,
+                                                   byref(t)), "hps_server_submit_build")
+        self._keep[t.value] = keep
+        self._meta[slot] = (tree, p, q, kind == HPS_ITI)
+        return t.value
+
+    def submit_solve(self, slot: int, g, u, f=None) -> int:
+        if slot not in self._meta:
+            raise ValueError(f"slot {slot} has no build submitted")
+        tree, p, q, cplx_ = self._meta[slot]
+        nl, ppl, nr = hps_sizes(tree, p, q)
+        keep: list = []
+        gp = _ptr(g, cplx_, nr, "g", keep)
+        up = _ptr(u, cplx_, nl * ppl, "u", keep)
+        fp = _ptr(f, cplx_, nl * ppl, "f", keep)
+        for x in keep:
+            if _is_torch(x):
+                raise TypeError("server buffers are host numpy arrays")
+        t = c_int64(0)
+        _check(_capi.lib().hps_server_submit_solve(self.ptr, slot, gp, fp, up, byref(t)),
+               "hps_server_submit_solve")
+        self._keep[t.value] = keep
+        return t.value
+
+    @staticmethod
+    def _info(ti) -> dict:
+        return {"status": ti.status, "kind": "build" if ti.kind == 1 else "solve", "slot": ti.slot,
+                "batch": ti.batch, "t_submit_ms": ti.t_submit_ms, "t_start_ms": ti.t_start_ms,
+                "t_done_ms": ti.t_done_ms}
+
+    def wait(self, ticket: int, check: bool = True) -> dict:
+        ti = _capi.hps_ticket_info()
+        st = _capi.lib().hps_server_wait(self.ptr, ticket, byref(ti))
+        self._keep.pop(ticket, None)
+        if st == HPS_OK or not check:
+            return self._info(ti)
+        raise HPSError(st, "hps_server_wait")
+
+    def poll(self, ticket: int):
+        ti = _capi.hps_ticket_info()
+        st = _capi.lib().hps_server_poll(self.ptr, ticket, byref(ti))
+        if st == _capi.HPS_PENDING:
+            return None
+        self._keep.pop(ticket, None)
+        if st != HPS_OK:
+            raise HPSError(st, "hps_server_poll")
+        return self._info(ti)
+
+    def stats(self) -> dict:
+        s = _capi.hps_server_stats()
+        _check(_capi.lib().hps_server_get_stats(self.ptr, byref(s)), "hps_server_get_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def operator(self, slot: int):
+        """The slot's operator (a borrowed handle) once its requests are done."""
+        out = c_void_p()
+        _check(_capi.lib().hps_server_operator(self.ptr, slot, byref(out)), "hps_server_operator")
+        if not out.value:
+            return None
+        tree, p, q, cplx_ = self._meta[slot]
+        return _Borrowed(out.value, tree, p, q, cplx_)
+
+    def close(self):
+        if self.ptr:
+            _capi.lib().hps_server_destroy(self.ptr)
+            self.ptr = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhps_gb300.so")
 
 HPS_OK, HPS_ERR_INVALID, HPS_ERR_OOM, HPS_ERR_SINGULAR, HPS_ERR_CUDA, HPS_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+HPS_PENDING = 1
 HPS_DTN, HPS_ITI = 0, 1
 HPS_F64, HPS_C128 = 0, 1
 
@@ -21,7 +22,10 @@ EXPORTED = [
     "hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
     "hps_error_string", "hps_last_error_detail", "hps_device_bytes", "hps_last_launch_count",
     "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc", "hps_refine", "hps_trace_count",
-    "hps_trace_get",
+    "hps_trace_get", "hps_plan_bytes",
+    # request server (include/hps_serve.h)
+    "hps_server_create", "hps_server_destroy", "hps_server_submit_build", "hps_server_submit_solve",
+    "hps_server_wait", "hps_server_poll", "hps_server_get_stats", "hps_server_operator",
 ]
 
 EVAL_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int64, POINTER(c_double), POINTER(c_double))
@@ -52,6 +56,21 @@ class hps_kernel_stat(ctypes.Structure):
 class hps_trace_rec(ctypes.Structure):
     _fields_ = [("kclass", c_int), ("m", c_int), ("n", c_int), ("k", c_int), ("batch", c_int64),
                 ("flops", c_double), ("ms", c_double)]
+
+
+class hps_server_options(ctypes.Structure):
+    _fields_ = [("version", c_int), ("n_slots", c_int), ("n_streams", c_int), ("max_batch", c_int),
+                ("hbm_budget", c_int64), ("lazy_root", c_int), ("reserved", c_int * 7)]
+
+
+class hps_ticket_info(ctypes.Structure):
+    _fields_ = [("status", c_int), ("kind", c_int), ("slot", c_int), ("batch", c_int),
+                ("t_submit_ms", c_double), ("t_start_ms", c_double), ("t_done_ms", c_double)]
+
+
+class hps_server_stats(ctypes.Structure):
+    _fields_ = [("solves", c_int64), ("builds", c_int64), ("batches", c_int64), ("max_batch_seen", c_int64),
+                ("resident_bytes", c_int64), ("hbm_budget", c_int64)]
 
 
 _lib = None
@@ -97,6 +116,26 @@ def lib() -> ctypes.CDLL:
     L.hps_trace_count.restype = c_int
     L.hps_trace_get.argtypes = [c_void_p, c_int64, POINTER(hps_trace_rec)]
     L.hps_trace_get.restype = c_int
+    L.hps_plan_bytes.argtypes = [POINTER(hps_tree), c_int, c_int, c_int, POINTER(c_int64)]
+    L.hps_plan_bytes.restype = c_int
+    L.hps_server_create.argtypes = [POINTER(hps_server_options), POINTER(c_void_p)]
+    L.hps_server_create.restype = c_int
+    L.hps_server_destroy.argtypes = [c_void_p]
+    L.hps_server_destroy.restype = None
+    L.hps_server_submit_build.argtypes = [c_void_p, c_int, POINTER(hps_tree), c_int, c_int,
+                                          POINTER(hps_coeffs), c_void_p, POINTER(hps_options),
+                                          POINTER(c_int64)]
+    L.hps_server_submit_build.restype = c_int
+    L.hps_server_submit_solve.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, POINTER(c_int64)]
+    L.hps_server_submit_solve.restype = c_int
+    L.hps_server_wait.argtypes = [c_void_p, c_int64, POINTER(hps_ticket_info)]
+    L.hps_server_wait.restype = c_int
+    L.hps_server_poll.argtypes = [c_void_p, c_int64, POINTER(hps_ticket_info)]
+    L.hps_server_poll.restype = c_int
+    L.hps_server_get_stats.argtypes = [c_void_p, POINTER(hps_server_stats)]
+    L.hps_server_get_stats.restype = c_int
+    L.hps_server_operator.argtypes = [c_void_p, c_int, POINTER(c_void_p)]
+    L.hps_server_operator.restype = c_int
     L.hps_solve_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     L.hps_solve_noalloc.restype = c_int
     L.hps_refine.argtypes = [POINTER(c_double), POINTER(c_double), c_int, c_double, c_int, c_int, c_int,

@@ -620,6 +620,7 @@ const char* hps_error_string(hps_status s) {
     case HPS_ERR_SINGULAR: return "HPS_ERR_SINGULAR: zero pivot in a leaf or merge factorisation";
     case HPS_ERR_CUDA: return "HPS_ERR_CUDA: a CUDA runtime call failed";
     case HPS_ERR_TIMEOUT: return "HPS_ERR_TIMEOUT: a bounded device-side wait gave up";
+    case HPS_PENDING: return "HPS_PENDING: the request has not finished";
   }
   return "unknown hps_status";
 }
@@ -777,6 +778,26 @@ hps_status hps_last_error_detail(hps_handle* h, int64_t* node) {
 }
 
 int64_t hps_device_bytes(const hps_handle* h) { return h ? h->bytes : 0; }
+
+hps_status hps_plan_bytes(const hps_tree* tree, int p, int q, int kind, int64_t* bytes) {
+  if (!bytes) return HPS_ERR_INVALID;
+  *bytes = 0;
+  hps_status s = check_tree(tree, p, q);
+  if (s != HPS_OK) return s;
+  if (kind != HPS_DTN && kind != HPS_ITI) return HPS_ERR_INVALID;
+  if (kind == HPS_ITI && tree->dim != 2) return HPS_ERR_INVALID;
+  hps_handle h;
+  h.dim = tree->dim; h.p = p; h.q = q; h.L = tree->uniform_depth; h.iti = kind == HPS_ITI;
+  h.nl = (int64_t)1 << (h.dim * h.L);
+  h.npts = h.dim == 2 ? (int64_t)p * p : (int64_t)p * p * p;
+  const int64_t ni = h.dim == 2 ? (int64_t)(p - 2) * (p - 2) : (int64_t)(p - 2) * (p - 2) * (p - 2);
+  h.nb = h.dim == 2 ? 4 * q : 6 * q * q;
+  h.nlu_leaf = (int)(h.iti ? h.npts : ni);
+  h.xrows_leaf = h.nlu_leaf;
+  const size_t b = h.iti ? plan_bytes<cplx>(&h, true) : plan_bytes<double>(&h, true);
+  *bytes = (int64_t)b;
+  return HPS_OK;
+}
 
 int64_t hps_last_launch_count(const hps_handle* h) { return h ? h->prof.launches : 0; }
 

@@ -1020,18 +1020,22 @@ bool trsv_flags_applicable(int n, int nrhs, int batch, const TrsvWork& w) {
 template <typename T, int NR, bool UPPER>
 cudaError_t launch_trsv_flags(const T* LU, int n, int ld, T* X, int ldx, int nrhs, TrsvWork& w,
                               cudaStream_t st) {
-  static int per_sm = -1, sms = 0;
-  cudaError_t e;
-  if (per_sm < 0) {
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_flags<T, NR, UPPER>, 256, 0)) !=
-        cudaSuccess)
-      return e;
-  }
+  // resident CTAs of this kernel on the whole GPU (thread-safe one-time
+  // initialisation; 0 if the query failed)
+  static const int resident = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv_flags<T, NR, UPPER>, 256, 0) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return per_sm * sms;
+  }();
+  if (resident <= 0) return cudaErrorInvalidConfiguration;
   const int nblk = (n + 31) / 32;
-  const int G = std::max(1, std::min(nblk, per_sm * sms));
+  const int G = std::max(1, std::min(nblk, resident));
   const unsigned ep = ++w.epoch;
   unsigned* fl = w.flags;
   int* errp = const_cast<int*>(w.dev_err);

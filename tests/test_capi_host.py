@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI (no GPU needed): the library loads, exports
-every function declared in include/hps.h, computes node coordinates in the
+every function declared in include/*.h, computes node coordinates in the
 documented orders, and rejects invalid arguments."""
 
 import ctypes
@@ -23,10 +23,15 @@ def pkg():
 
 
 def declared_functions():
-    txt = open(os.path.join(ROOT, "include", "hps.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    names = re.findall(r"\b(hps_[a-z_]+)\s*\(", txt)
-    return sorted(set(names))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if not fn.endswith(".h"):
+            continue
+        txt = open(os.path.join(inc, fn)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names.update(re.findall(r"\b(hps_[a-z_]+)\s*\(", txt))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(pkg):
@@ -40,7 +45,7 @@ def test_every_declared_symbol_is_exported(pkg):
 
 
 def test_error_strings(pkg):
-    for s in (0, -1, -2, -3, -4, -5):
+    for s in (0, -1, -2, -3, -4, -5, 1):
         assert pkg.hps_error_string(s).startswith("HPS_")
 
 
@@ -118,3 +123,27 @@ def test_adaptive_trees_are_validated(pkg):
     with pytest.raises(pkg.HPSError):
         pkg.hps_sizes(pkg.adaptive_tree(unb), 6, 4)
     assert pkg.hps_sizes(pkg.adaptive_tree(ad.sort_leaves(ad.balance(unb))), 6, 4)[0] > len(unb)
+
+
+def test_server_options_are_validated(pkg):
+    for kw in ({"n_slots": 0 - 1}, {"n_streams": 65}, {"max_batch": 257}, {"hbm_budget": -1}):
+        with pytest.raises(pkg.HPSError) as e:
+            pkg.Server(**kw)
+        assert e.value.status == -1
+
+
+def test_server_without_a_device_fails_cleanly(pkg):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(pkg.HPSError) as e:
+        pkg.Server()
+    assert e.value.status == -4
+
+
+def test_plan_bytes_grows_with_the_tree(pkg):
+    b = [pkg.hps_plan_bytes(pkg.uniform_tree(2, L), 16, 14, pkg.HPS_ITI) for L in (2, 3, 4)]
+    assert b[0] < b[1] < b[2]
+    assert 3.5 < b[2] / b[1] < 4.5
+    with pytest.raises(pkg.HPSError):
+        pkg.hps_plan_bytes(pkg.uniform_tree(3, 1), 8, 6, pkg.HPS_ITI)

@@ -16,6 +16,7 @@ from .problems import (  # noqa: F401
     poisson_poly_2d,
     helmholtz_bumps_2d,
     elliptic_3d,
+    elliptic_2d,
     e1_dtn_2d,
     e2_iti_2d,
     e7_wavefront_3d,

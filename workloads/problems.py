@@ -215,24 +215,16 @@ def helmholtz_bumps_2d(seed: int = 1, k: float = 20.0, eta: Optional[float] = No
 # workload 3: 3D divergence-form elliptic problem
 # ---------------------------------------------------------------------------
 
-def elliptic_3d(seed: int = 2, n_modes: int = 8, lo=(-1.0, -1.0, -1.0),
-                hi=(1.0, 1.0, 1.0)) -> Problem:
-    """div(a grad u) + c u = f on [-1,1]^3, Dirichlet data.
-
-    Expanded as a Lap u + grad(a) . grad u + c u, so the first-order
-    coefficients are b = grad a.  a = 1 + 0.5 s(x)/S with s a sum of
-    ``n_modes`` seeded modes alpha_m sin(k_m . x + phi_m) and S = sum|alpha_m|,
-    so a lies in [0.5, 1.5].  c = 0.5 + 0.5 sin(kc . x + phic) lies in [0, 1].
-    The manufactured solution is u = sin(w1 . x + p1) + 0.5 cos(w2 . x + p2)."""
+def _elliptic(dim: int, seed: int, n_modes: int, lo, hi) -> Problem:
     rng = np.random.default_rng(seed)
-    km = rng.uniform(-3.0, 3.0, size=(n_modes, 3))
+    km = rng.uniform(-3.0, 3.0, size=(n_modes, dim))
     phim = rng.uniform(0, 2 * np.pi, size=n_modes)
     alpha = rng.uniform(-1.0, 1.0, size=n_modes)
     S = np.abs(alpha).sum()
-    kc = rng.uniform(-2.0, 2.0, size=3)
+    kc = rng.uniform(-2.0, 2.0, size=dim)
     phic = rng.uniform(0, 2 * np.pi)
-    w1 = rng.uniform(-2.0, 2.0, size=3)
-    w2 = rng.uniform(-2.0, 2.0, size=3)
+    w1 = rng.uniform(-2.0, 2.0, size=dim)
+    w2 = rng.uniform(-2.0, 2.0, size=dim)
     p1, p2 = rng.uniform(0, 2 * np.pi, size=2)
 
     def a_and_grad(x):
@@ -247,7 +239,7 @@ def elliptic_3d(seed: int = 2, n_modes: int = 8, lo=(-1.0, -1.0, -1.0),
     def coeffs(x):
         x = np.atleast_2d(x)
         a, ga = a_and_grad(x)
-        return {"a": a, "b": [ga[:, 0], ga[:, 1], ga[:, 2]], "c": cfun(x)}
+        return {"a": a, "b": [ga[:, k] for k in range(dim)], "c": cfun(x)}
 
     def u(x):
         x = np.atleast_2d(x)
@@ -265,9 +257,28 @@ def elliptic_3d(seed: int = 2, n_modes: int = 8, lo=(-1.0, -1.0, -1.0),
         a, ga = a_and_grad(x)
         return a * lap_u(x) + (ga * grad_u(x)).sum(axis=1) + cfun(x) * u(x)
 
-    return Problem(name=f"elliptic3d_seed{seed}", dim=3, lo=tuple(lo), hi=tuple(hi), kind="dtn",
+    return Problem(name=f"elliptic{dim}d_seed{seed}", dim=dim, lo=tuple(lo), hi=tuple(hi), kind="dtn",
                    seed=seed, coeffs=coeffs, source=f, boundary=u, u_exact=u,
                    info={"n_modes": n_modes})
+
+
+def elliptic_3d(seed: int = 2, n_modes: int = 8, lo=(-1.0, -1.0, -1.0),
+                hi=(1.0, 1.0, 1.0)) -> Problem:
+    """div(a grad u) + c u = f on [-1,1]^3, Dirichlet data.
+
+    Expanded as a Lap u + grad(a) . grad u + c u, so the first-order
+    coefficients are b = grad a.  a = 1 + 0.5 s(x)/S with s a sum of
+    ``n_modes`` seeded modes alpha_m sin(k_m . x + phi_m) and S = sum|alpha_m|,
+    so a lies in [0.5, 1.5].  c = 0.5 + 0.5 sin(kc . x + phic) lies in [0, 1].
+    The manufactured solution is u = sin(w1 . x + p1) + 0.5 cos(w2 . x + p2)."""
+    return _elliptic(3, seed, n_modes, lo, hi)
+
+
+def elliptic_2d(seed: int = 4, n_modes: int = 8, lo=(-1.0, -1.0), hi=(1.0, 1.0)) -> Problem:
+    """The 2D counterpart of elliptic_3d (same construction on [-1,1]^2): a
+    variable-coefficient DtN problem whose coefficient field is drawn from
+    ``seed``, used for the rebuild requests of the serving workload."""
+    return _elliptic(2, seed, n_modes, lo, hi)
 
 
 def sharp_source_3d(seed: int = 3, width: float = 0.05) -> Problem:
