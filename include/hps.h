@@ -119,7 +119,14 @@ typedef struct {
                            flag-ordered launch per triangle; if one of its
                            bounded waits gives up, that hps_solve (host u) or
                            the next one on the handle returns HPS_ERR_TIMEOUT. */
-  int reserved[4];
+  int graph_solve;      /* 1: hps_solve / hps_solve_batched with device buffers on a
+                           non-default stream replay a CUDA graph of the whole
+                           solve (upward and downward passes), captured on the
+                           second call with the same (nrhs, g, f, u) pointers;
+                           up to 8 graphs per handle.  Uniform trees; ignored
+                           while profiling.  The caller may change the data
+                           behind the pointers between calls, not the pointers. */
+  int reserved[3];
 } hps_options;
 
 /* Kernel classes reported by hps_kernel_stats. */

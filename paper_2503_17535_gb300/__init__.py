@@ -175,7 +175,7 @@ def make_coeffs(kind: int, a=None, b=None, c=None, eta: float = 0.0, keep=None, 
 
 def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None, f=None,
               eta: float = 0.0, want_root_map: bool = False, profile: bool = False,
-              lazy_root: bool = False, stream=None) -> Handle:
+              lazy_root: bool = False, graph_solve: bool = False, stream=None) -> Handle:
     """Build the solution operator; coefficient and source arrays hold
     n_leaves * p^dim values (leaf-major, tensor node order)."""
     nl, ppl, _ = hps_sizes(tree, p, q)
@@ -188,6 +188,7 @@ def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None,
     opts.want_root_map = 1 if want_root_map else 0
     opts.profile = 1 if profile else 0
     opts.lazy_root = 1 if lazy_root else 0
+    opts.graph_solve = 1 if graph_solve else 0
     out = c_void_p()
     st = _stream(stream)
     _check(_capi.lib().hps_build(byref(tree), p, q, byref(cf), fp, byref(opts), st, byref(out)),

@@ -46,7 +46,7 @@ class hps_coeffs(ctypes.Structure):
 
 class hps_options(ctypes.Structure):
     _fields_ = [("version", c_int), ("want_root_map", c_int), ("profile", c_int),
-                ("lazy_root", c_int), ("reserved", c_int * 4)]
+                ("lazy_root", c_int), ("graph_solve", c_int), ("reserved", c_int * 3)]
 
 
 class hps_kernel_stat(ctypes.Structure):

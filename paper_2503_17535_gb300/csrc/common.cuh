@@ -17,6 +17,7 @@ struct cplx {
 __host__ __device__ inline cplx operator+(cplx a, cplx b) { return cplx(a.re + b.re, a.im + b.im); }
 __host__ __device__ inline cplx operator-(cplx a, cplx b) { return cplx(a.re - b.re, a.im - b.im); }
 __host__ __device__ inline cplx operator-(cplx a) { return cplx(-a.re, -a.im); }
+__host__ __device__ inline bool operator==(cplx a, cplx b) { return a.re == b.re && a.im == b.im; }
 __host__ __device__ inline cplx operator*(cplx a, cplx b) {
   return cplx(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
 }

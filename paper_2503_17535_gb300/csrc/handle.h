@@ -48,6 +48,27 @@ struct AChildDev {
   void* Tp = nullptr;         // np x (np + 1) projected [T | h]
 };
 
+// Merges of one tree level with the same interface sizes: their dense
+// factorisations and solves run as one batched call (pointer arrays).
+struct AGroup {
+  int level = 0, n_int = 0, n_ext = 0, G = 1;
+  std::vector<int> members;      // indices into hps_handle::am
+  LuWork luw;
+  int *ipiv = nullptr, *perm = nullptr, *info = nullptr;  // [members][n_int], [members]
+  double **dD = nullptr, **dX = nullptr, **dR = nullptr;  // build operands
+  double **dTP = nullptr;                                 // parents' [T | h]
+  double **dr = nullptr, **dx = nullptr, **dhp = nullptr; // solve workspace
+  // per child position: when every member's child has the same projected
+  // sizes, one batched B X product over the group (maps concatenated,
+  // period = members), else one product per member
+  struct ChildBatch {
+    bool ok = false;
+    int ne_c = 0, ni_c = 0, np = 0;
+    int *barow = nullptr, *bacol = nullptr, *bbrow = nullptr, *bcrow = nullptr;
+    double** dTp = nullptr;
+  } cb[8];
+};
+
 struct AMergeDev {
   int node = -1, n_ext = 0, n_int = 0;
   AChildDev ch[8];
@@ -101,6 +122,16 @@ struct hps_handle {
   Prof prof;
   int64_t err_node = -1;
   int num_sms = 0;
+  // captured solves (hps_options.graph_solve): key -> executable graph
+  struct GraphEntry {
+    int nrhs = 0;
+    const void *g = nullptr, *f = nullptr;
+    void* u = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool warm = false;  // seen once (workspace allocated), not captured yet
+  };
+  std::vector<GraphEntry> graphs;
+  bool capturing = false;
   hps::TrsvWork trsv;            // flag-ordered solves with a lazy root's factors
   int* trsv_err_host = nullptr;  // host-mapped error word of trsv (cudaHostAlloc)
   cudaStream_t last = nullptr;
@@ -110,6 +141,7 @@ struct hps_handle {
   bool adaptive = false;
   ATree at;
   std::vector<hps::AMergeDev> am;
+  std::vector<hps::AGroup> ag;   // batched groups, deepest level first
   std::vector<int> node_merge;   // tree node -> index in am, or -1
   double *dC2F = nullptr, *dF2C = nullptr, *dsleaf = nullptr;
   void* aproj_tmp = nullptr;     // projection temporaries (build)

@@ -55,6 +55,51 @@ hps_status adaptive_tree_from_abi(const hps_tree* t, int p, int q, ATree* out) {
   return HPS_OK;
 }
 
+// C <- C - B X for every member of a group, per child position: X (n_int
+// rows, N columns) and C (n_ext rows) of each member through the pointer
+// arrays dXs / dCs; in the build, C = [T | h] (skipped for the root unless
+// the root map is wanted); in the solve, C = h_ext.
+static hps_status group_b_products(hps_handle* h, const AGroup& A, double** dXs, int N, double** dCs, bool build,
+                                   cudaStream_t st, Prof* pf) {
+  using T = double;
+  const int nbat = (int)A.members.size();
+  for (int c = 0; c < 8; ++c) {
+    const AGroup::ChildBatch& cb = A.cb[c];
+    if (cb.ok) {
+      GemmArgs<T> g;
+      g.M = cb.ne_c; g.N = N; g.K = cb.ni_c; g.batch = nbat;
+      g.A = bopp<T>(cb.dTp, cb.np);
+      g.arow.idx = cb.barow; g.arow.len = cb.ne_c; g.arow.period = nbat;
+      g.acol.idx = cb.bacol; g.acol.len = cb.ni_c; g.acol.period = nbat;
+      g.B = bopp<T>(dXs, A.n_int);
+      g.brow.idx = cb.bbrow; g.brow.len = cb.ni_c; g.brow.period = nbat;
+      g.C = bopp<T>(dCs, A.n_ext);
+      g.crow.idx = cb.bcrow; g.crow.len = cb.ne_c; g.crow.period = nbat;
+      g.alpha = -1.0; g.beta = 1.0;
+      HPS_CUDA(gemm<T>(g, st, pf));
+      continue;
+    }
+    for (int k2 = 0; k2 < nbat; ++k2) {
+      const AMergeDev& M = h->am[(size_t)A.members[k2]];
+      if (M.node == 0 && !(build && h->opts.want_root_map)) continue;
+      const AChildDev& CD = M.ch[c];
+      GemmArgs<T> g;
+      g.M = CD.ne_c; g.N = N; g.K = CD.ni_c; g.batch = 1;
+      g.A = bop<T>((T*)CD.Tp, 0, CD.pj.np);
+      g.arow.idx = CD.barow; g.arow.len = CD.ne_c;
+      g.acol.idx = CD.bacol; g.acol.len = CD.ni_c;
+      g.B = bopp<T>(dXs, M.n_int);
+      g.B.ptrs = dXs + k2;
+      g.brow.idx = CD.bbrow; g.brow.len = CD.ni_c;
+      g.C = bopp<T>(dCs + k2, M.n_ext);
+      g.crow.idx = CD.bcrow; g.crow.len = CD.ne_c;
+      g.alpha = -1.0; g.beta = 1.0;
+      HPS_CUDA(gemm<T>(g, st, pf));
+    }
+  }
+  return HPS_OK;
+}
+
 hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs* cf, const void* f_in,
                           cudaStream_t st) {
   using T = double;
@@ -76,10 +121,16 @@ hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs*
   size_t need = (size_t)nl * ((size_t)ni * ni + (size_t)ni * (nb + 1) + (size_t)nb * (nb + 1)) * sizeof(T);
   size_t scratch_R = (size_t)nl * ni * (nb + 1), tmp = 0;
   int max_np = 0;
+  {
+    // the merges of one level keep their [C | h_int] side by side
+    std::vector<size_t> per_level((size_t)at.max_level + 1, 0);
+    for (const MergePlanA& pl : at.plans)
+      per_level[(size_t)at.nodes[pl.node].level] += (size_t)pl.n_int * (pl.n_ext + 1);
+    for (size_t v : per_level) scratch_R = std::max(scratch_R, v);
+  }
   for (const MergePlanA& pl : at.plans) {
     need += ((size_t)pl.n_ext * (pl.n_ext + 1) + (size_t)pl.n_int * pl.n_int + (size_t)pl.n_int * (pl.n_ext + 1)) *
             sizeof(T);
-    scratch_R = std::max(scratch_R, (size_t)pl.n_int * (pl.n_ext + 1));
     for (int c = 0; c < 8; ++c) {
       need += (size_t)pl.ch[c].np * (pl.ch[c].np + 1) * sizeof(T);
       tmp = std::max(tmp, (size_t)pl.ch[c].n * (pl.ch[c].np + 1));
@@ -179,99 +230,171 @@ hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs*
   // T = s (QP - Q_i X) per leaf size
   HPS_CUDA(scale_blocks<T>((T*)h->leafTH, (int64_t)nb * (nb + 1), h->dsleaf, nl, st, pf));
 
-  // ---- nonuniform merges, deepest first
+  // ---- nonuniform merges, level by level from the deepest.  Per merge: the
+  // children's [T | h] projected onto the coarsened interfaces and gathered
+  // into D, [C | h_int] and [A | h_ext]; per group of equal-size merges of
+  // the level: LU(D) and X = D^{-1}[C | h_int] as batched calls; per merge:
+  // [T | h] = [A | h_ext] - B X.
   h->node_merge.assign(at.nodes.size(), -1);
   h->am.resize(at.plans.size());
+  h->ag.clear();
   for (size_t mi = 0; mi < at.plans.size(); ++mi) h->node_merge[at.plans[mi].node] = (int)mi;
-  for (size_t mi = 0; mi < at.plans.size(); ++mi) {
-    const MergePlanA& pl = at.plans[mi];
-    AMergeDev& M = h->am[mi];
-    M.node = pl.node;
-    M.n_ext = pl.n_ext;
-    M.n_int = pl.n_int;
-    const int ne = pl.n_ext, nI = pl.n_int;
-    const bool is_root = pl.node == 0;
-    M.TP = dalloc(h, (size_t)ne * (ne + 1) * sizeof(T));
-    M.D = dalloc(h, (size_t)nI * nI * sizeof(T));
-    M.X = dalloc(h, (size_t)nI * (ne + 1) * sizeof(T));
-    M.ipiv = (int*)dalloc(h, (size_t)nI * sizeof(int));
-    M.perm = (int*)dalloc(h, (size_t)nI * sizeof(int));
-    M.info = (int*)dalloc(h, sizeof(int));
-    if (!M.TP || !M.D || !M.X || !M.ipiv || !M.perm || !M.info) return HPS_ERR_OOM;
-    HPS_CUDA(cudaMemsetAsync(M.info, 0, sizeof(int), st));
-    const ANode& nd = at.nodes[pl.node];
-    // project every child onto the coarsened interfaces
-    for (int c = 0; c < 8; ++c) {
-      const ChildProj& cp = pl.ch[c];
-      AChildDev& CD = M.ch[c];
-      std::vector<int4> src4(cp.np);
-      for (int i = 0; i < cp.np; ++i) src4[i] = make_int4(cp.src[i][0], cp.src[i][1], cp.src[i][2], cp.src[i][3]);
-      CD.pj.n = cp.n;
-      CD.pj.np = cp.np;
-      CD.pj.q2 = q2;
-      CD.pj.kind = up_vec(h, cp.kind, st);
-      CD.pj.u = up_vec(h, cp.u, st);
-      CD.pj.src = up_vec(h, src4, st);
-      CD.pj.bcopy = up_vec(h, cp.back_copy, st);
-      CD.pj.bbase = up_vec(h, cp.back_base, st);
-      CD.pj.bquad = up_vec(h, cp.back_quad, st);
-      CD.pj.bt = up_vec(h, cp.back_t, st);
-      CD.ext = up_vec(h, cp.ext, st);
-      CD.var = up_vec(h, cp.var, st);
-      CD.barow = up_vec(h, cp.b_arow, st);
-      CD.bacol = up_vec(h, cp.b_acol, st);
-      CD.bbrow = up_vec(h, cp.b_brow, st);
-      CD.bcrow = up_vec(h, cp.b_crow, st);
-      CD.ne_c = (int)cp.b_arow.size();
-      CD.ni_c = (int)cp.b_acol.size();
-      CD.Tp = dalloc(h, (size_t)cp.np * (cp.np + 1) * sizeof(T));
-      if (!CD.pj.kind || !CD.pj.u || !CD.pj.src || !CD.pj.bcopy || !CD.pj.bbase || !CD.pj.bquad || !CD.pj.bt ||
-          !CD.ext || !CD.var || !CD.barow || !CD.bacol || !CD.bbrow || !CD.bcrow || !CD.Tp)
-        return HPS_ERR_OOM;
-      int n = 0, ld = 0;
-      const T* Tc = child_T(h, nd.child[c], &n, &ld);
-      T* tmpT = (T*)h->aproj_tmp;
-      HPS_CUDA(proj_cols<T>(Tc, ld, n, CD.pj, h->dC2F, tmpT, n, st, pf));
-      HPS_CUDA(proj_rows<T>(tmpT, n, cp.np + 1, CD.pj, h->dF2C, (T*)CD.Tp, cp.np, st, pf));
-    }
-    T* R = (T*)h->scratch;
-    HPS_CUDA(fill<T>(bop<T>((T*)M.D, 0, nI), nI, nI, 1, 0.0, 0.0, st, pf));
-    HPS_CUDA(fill<T>(bop<T>(R, 0, nI), nI, ne + 1, 1, 0.0, 0.0, st, pf));
-    HPS_CUDA(fill<T>(bop<T>((T*)M.TP, 0, ne), ne, ne + 1, 1, 0.0, 0.0, st, pf));
-    for (int c = 0; c < 8; ++c) {
-      const AChildDev& CD = M.ch[c];
-      HPS_CUDA(merge_gather<T>((const T*)CD.Tp, 0, 1, 1, CD.pj.np, ne, nI, CD.ext, CD.var, CD.var, false, (T*)M.D, R,
-                               (T*)M.TP, st, pf));
-    }
-    M.G = lu_group_size<T>(nI, 1, h->num_sms);
-    if (M.G > 1) {
-      M.luw.bars = (unsigned*)dalloc(h, sizeof(unsigned) * 2);
-      M.luw.pub_bytes = lu_pub_bytes<T>(nI, 1, M.G);
-      M.luw.pub = dalloc(h, M.luw.pub_bytes);
-      if (!M.luw.bars || !M.luw.pub) return HPS_ERR_OOM;
-      HPS_CUDA(cudaMemsetAsync(M.luw.bars, 0, sizeof(unsigned) * 2, st));
-    }
-    BOp<T> DD = bop<T>((T*)M.D, 0, nI);
-    BOp<T> XX = bop<T>((T*)M.X, 0, nI);
-    HPS_CUDA(getrf<T>(DD, nI, 1, M.ipiv, M.perm, M.info, h->dev_err, M.G, M.luw, st, pf));
-    HPS_CUDA(permute_rows<T>(bop<T>(R, 0, nI), XX, M.perm, nI, ne + 1, 1, st, pf));
-    HPS_CUDA(getrs_inplace<T>(DD, nI, XX, ne + 1, 1, st, pf));
-    if (!is_root || h->opts.want_root_map) {
+  std::vector<T*> Rof(at.plans.size(), nullptr);
+  for (size_t i0 = 0; i0 < at.plans.size();) {
+    const int lev = at.nodes[at.plans[i0].node].level;
+    size_t i1 = i0;
+    while (i1 < at.plans.size() && at.nodes[at.plans[i1].node].level == lev) ++i1;
+    size_t roff = 0;
+    for (size_t mi = i0; mi < i1; ++mi) {
+      const MergePlanA& pl = at.plans[mi];
+      AMergeDev& M = h->am[mi];
+      M.node = pl.node;
+      M.n_ext = pl.n_ext;
+      M.n_int = pl.n_int;
+      const int ne = pl.n_ext, nI = pl.n_int;
+      M.TP = dalloc(h, (size_t)ne * (ne + 1) * sizeof(T));
+      M.D = dalloc(h, (size_t)nI * nI * sizeof(T));
+      M.X = dalloc(h, (size_t)nI * (ne + 1) * sizeof(T));
+      if (!M.TP || !M.D || !M.X) return HPS_ERR_OOM;
+      const ANode& nd = at.nodes[pl.node];
+      // project every child onto the coarsened interfaces
+      for (int c = 0; c < 8; ++c) {
+        const ChildProj& cp = pl.ch[c];
+        AChildDev& CD = M.ch[c];
+        std::vector<int4> src4(cp.np);
+        for (int i = 0; i < cp.np; ++i) src4[i] = make_int4(cp.src[i][0], cp.src[i][1], cp.src[i][2], cp.src[i][3]);
+        CD.pj.n = cp.n;
+        CD.pj.np = cp.np;
+        CD.pj.q2 = q2;
+        CD.pj.kind = up_vec(h, cp.kind, st);
+        CD.pj.u = up_vec(h, cp.u, st);
+        CD.pj.src = up_vec(h, src4, st);
+        CD.pj.bcopy = up_vec(h, cp.back_copy, st);
+        CD.pj.bbase = up_vec(h, cp.back_base, st);
+        CD.pj.bquad = up_vec(h, cp.back_quad, st);
+        CD.pj.bt = up_vec(h, cp.back_t, st);
+        CD.ext = up_vec(h, cp.ext, st);
+        CD.var = up_vec(h, cp.var, st);
+        CD.barow = up_vec(h, cp.b_arow, st);
+        CD.bacol = up_vec(h, cp.b_acol, st);
+        CD.bbrow = up_vec(h, cp.b_brow, st);
+        CD.bcrow = up_vec(h, cp.b_crow, st);
+        CD.ne_c = (int)cp.b_arow.size();
+        CD.ni_c = (int)cp.b_acol.size();
+        CD.Tp = dalloc(h, (size_t)cp.np * (cp.np + 1) * sizeof(T));
+        if (!CD.pj.kind || !CD.pj.u || !CD.pj.src || !CD.pj.bcopy || !CD.pj.bbase || !CD.pj.bquad || !CD.pj.bt ||
+            !CD.ext || !CD.var || !CD.barow || !CD.bacol || !CD.bbrow || !CD.bcrow || !CD.Tp)
+          return HPS_ERR_OOM;
+        int n = 0, ld = 0;
+        const T* Tc = child_T(h, nd.child[c], &n, &ld);
+        T* tmpT = (T*)h->aproj_tmp;
+        HPS_CUDA(proj_cols<T>(Tc, ld, n, CD.pj, h->dC2F, tmpT, n, st, pf));
+        HPS_CUDA(proj_rows<T>(tmpT, n, cp.np + 1, CD.pj, h->dF2C, (T*)CD.Tp, cp.np, st, pf));
+      }
+      T* R = (T*)h->scratch + roff;
+      Rof[mi] = R;
+      roff += (size_t)nI * (ne + 1);
+      HPS_CUDA(fill<T>(bop<T>((T*)M.D, 0, nI), nI, nI, 1, 0.0, 0.0, st, pf));
+      HPS_CUDA(fill<T>(bop<T>(R, 0, nI), nI, ne + 1, 1, 0.0, 0.0, st, pf));
+      HPS_CUDA(fill<T>(bop<T>((T*)M.TP, 0, ne), ne, ne + 1, 1, 0.0, 0.0, st, pf));
       for (int c = 0; c < 8; ++c) {
         const AChildDev& CD = M.ch[c];
-        GemmArgs<T> g;
-        g.M = CD.ne_c; g.N = ne + 1; g.K = CD.ni_c; g.batch = 1;
-        g.A = bop<T>((T*)CD.Tp, 0, CD.pj.np);
-        g.arow.idx = CD.barow; g.arow.len = CD.ne_c;
-        g.acol.idx = CD.bacol; g.acol.len = CD.ni_c;
-        g.B = XX;
-        g.brow.idx = CD.bbrow; g.brow.len = CD.ni_c;
-        g.C = bop<T>((T*)M.TP, 0, ne);
-        g.crow.idx = CD.bcrow; g.crow.len = CD.ne_c;
-        g.alpha = -1.0; g.beta = 1.0;
-        HPS_CUDA(gemm<T>(g, st, pf));
+        HPS_CUDA(merge_gather<T>((const T*)CD.Tp, 0, 1, 1, CD.pj.np, ne, nI, CD.ext, CD.var, CD.var, false,
+                                 (T*)M.D, R, (T*)M.TP, st, pf));
       }
     }
+    // groups of equal sizes within the level, in first-appearance order
+    std::vector<std::pair<std::pair<int, int>, std::vector<int>>> groups;
+    for (size_t mi = i0; mi < i1; ++mi) {
+      const std::pair<int, int> key(at.plans[mi].n_int, at.plans[mi].n_ext);
+      size_t gi = 0;
+      while (gi < groups.size() && groups[gi].first != key) ++gi;
+      if (gi == groups.size()) groups.push_back({key, {}});
+      groups[gi].second.push_back((int)mi);
+    }
+    for (auto& gr : groups) {
+      AGroup A;
+      A.level = lev;
+      A.n_int = gr.first.first;
+      A.n_ext = gr.first.second;
+      A.members = gr.second;
+      const int nI = A.n_int, ne = A.n_ext, nbat = (int)A.members.size();
+      A.ipiv = (int*)dalloc(h, (size_t)nbat * nI * sizeof(int));
+      A.perm = (int*)dalloc(h, (size_t)nbat * nI * sizeof(int));
+      A.info = (int*)dalloc(h, (size_t)nbat * sizeof(int));
+      std::vector<T*> vD, vX, vR;
+      for (int k2 = 0; k2 < nbat; ++k2) {
+        AMergeDev& M = h->am[(size_t)A.members[k2]];
+        vD.push_back((T*)M.D);
+        vX.push_back((T*)M.X);
+        vR.push_back(Rof[(size_t)A.members[k2]]);
+      }
+      A.dD = upload(h, vD, st);
+      A.dX = upload(h, vX, st);
+      A.dR = upload(h, vR, st);
+      if (!A.ipiv || !A.perm || !A.info || !A.dD || !A.dX || !A.dR) return HPS_ERR_OOM;
+      HPS_CUDA(cudaMemsetAsync(A.info, 0, (size_t)nbat * sizeof(int), st));
+      for (int k2 = 0; k2 < nbat; ++k2) {
+        AMergeDev& M = h->am[(size_t)A.members[k2]];
+        M.ipiv = A.ipiv + (size_t)k2 * nI;
+        M.perm = A.perm + (size_t)k2 * nI;
+        M.info = A.info + k2;
+      }
+      A.G = lu_group_size<T>(nI, nbat, h->num_sms);
+      if (A.G > 1) {
+        A.luw.bars = (unsigned*)dalloc(h, sizeof(unsigned) * 2 * nbat);
+        A.luw.pub_bytes = lu_pub_bytes<T>(nI, nbat, A.G);
+        A.luw.pub = dalloc(h, A.luw.pub_bytes);
+        if (!A.luw.bars || !A.luw.pub) return HPS_ERR_OOM;
+        HPS_CUDA(cudaMemsetAsync(A.luw.bars, 0, sizeof(unsigned) * 2 * nbat, st));
+      }
+      BOp<T> DD = bopp<T>(A.dD, nI);
+      BOp<T> XX = bopp<T>(A.dX, nI);
+      HPS_CUDA(getrf<T>(DD, nI, nbat, A.ipiv, A.perm, A.info, h->dev_err, A.G, A.luw, st, pf));
+      HPS_CUDA(permute_rows<T>(bopp<T>(A.dR, nI), XX, A.perm, nI, ne + 1, nbat, st, pf));
+      HPS_CUDA(getrs_inplace<T>(DD, nI, XX, ne + 1, nbat, st, pf));
+      std::vector<T*> vTP;
+      for (int mi : A.members) vTP.push_back((T*)h->am[(size_t)mi].TP);
+      A.dTP = upload(h, vTP, st);
+      if (!A.dTP) return HPS_ERR_OOM;
+      for (int c = 0; c < 8; ++c) {
+        AGroup::ChildBatch& cb = A.cb[c];
+        const ChildProj& c0 = at.plans[(size_t)A.members[0]].ch[c];
+        cb.ok = nbat > 1;
+        for (int mi : A.members) {
+          const ChildProj& cp = at.plans[(size_t)mi].ch[c];
+          if (cp.b_arow.size() != c0.b_arow.size() || cp.b_acol.size() != c0.b_acol.size() || cp.np != c0.np)
+            cb.ok = false;
+        }
+        if (!cb.ok) continue;
+        cb.ne_c = (int)c0.b_arow.size();
+        cb.ni_c = (int)c0.b_acol.size();
+        cb.np = c0.np;
+        std::vector<int> ar, ac, br, cr;
+        std::vector<T*> tp;
+        for (int mi : A.members) {
+          const ChildProj& cp = at.plans[(size_t)mi].ch[c];
+          ar.insert(ar.end(), cp.b_arow.begin(), cp.b_arow.end());
+          ac.insert(ac.end(), cp.b_acol.begin(), cp.b_acol.end());
+          br.insert(br.end(), cp.b_brow.begin(), cp.b_brow.end());
+          cr.insert(cr.end(), cp.b_crow.begin(), cp.b_crow.end());
+          tp.push_back((T*)h->am[(size_t)mi].ch[c].Tp);
+        }
+        cb.barow = upload(h, ar, st);
+        cb.bacol = upload(h, ac, st);
+        cb.bbrow = upload(h, br, st);
+        cb.bcrow = upload(h, cr, st);
+        cb.dTp = upload(h, tp, st);
+        if (!cb.barow || !cb.bacol || !cb.bbrow || !cb.bcrow || !cb.dTp) return HPS_ERR_OOM;
+      }
+      h->ag.push_back(std::move(A));
+    }
+    // [T | h] = [A | h_ext] - B X, one product per child position of a group
+    for (size_t gi = h->ag.size() - groups.size(); gi < h->ag.size(); ++gi) {
+      const AGroup& A = h->ag[gi];
+      HPS_TRY(group_b_products(h, A, A.dX, A.n_ext + 1, A.dTP, true, st, pf));
+    }
+    i0 = i1;
   }
   HPS_CUDA(cudaStreamSynchronize(st));
   for (void* tb : tmpbufs) cudaFree(tb);
@@ -317,6 +440,24 @@ static hps_status adaptive_ws(hps_handle* h, int nrhs) {
     M.gint = A((size_t)M.n_int * nrhs * es);
     M.g = A((size_t)M.n_ext * nrhs * es);
     if (!M.r || !M.x || !M.hp || !M.gint || !M.g) return HPS_ERR_OOM;
+  }
+  // pointer arrays of the batched group solves
+  for (AGroup& G : h->ag) {
+    std::vector<T*> vr, vx, vh;
+    for (int mi : G.members) {
+      vr.push_back((T*)h->am[(size_t)mi].r);
+      vx.push_back((T*)h->am[(size_t)mi].x);
+      vh.push_back((T*)h->am[(size_t)mi].hp);
+    }
+    const size_t pb = vr.size() * sizeof(T*);
+    G.dr = (T**)A(pb);
+    G.dx = (T**)A(pb);
+    G.dhp = (T**)A(pb);
+    if (!G.dr || !G.dx || !G.dhp) return HPS_ERR_OOM;
+    if (cudaMemcpy(G.dr, vr.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(G.dx, vx.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(G.dhp, vh.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess)
+      return HPS_ERR_CUDA;
   }
   h->ws_bytes = h->bytes - before;
   h->ws_nrhs = nrhs;
@@ -365,42 +506,41 @@ hps_status adaptive_solve(hps_handle* h, int nrhs, const void* g_in, const void*
     gl.alpha = -1.0; gl.beta = 0.0;
     HPS_CUDA(gemm<T>(gl, st, pf));
     HPS_CUDA(scale_blocks<T>((T*)h->ws_hleaf, (int64_t)nb * nrhs, h->dsleaf, nl, st, pf));
-    for (size_t mi = 0; mi < h->am.size(); ++mi) {
-      AMergeDev& M = h->am[mi];
-      const ANode& nd = at.nodes[M.node];
-      const int ne = M.n_ext, nI = M.n_int;
-      HPS_CUDA(fill<T>(bop<T>((T*)M.r, 0, nI), nI, nrhs, 1, 0.0, 0.0, st, pf));
-      for (int c = 0; c < 8; ++c) {
-        const AChildDev& CD = M.ch[c];
-        const ANode& K = at.nodes[nd.child[c]];
-        const T* hc;
-        int ldh;
-        if (K.leaf >= 0) { hc = (const T*)h->ws_hleaf + (int64_t)K.leaf * nb * nrhs; ldh = nb; }
-        else { const AMergeDev& C2 = h->am[h->node_merge[nd.child[c]]]; hc = (const T*)C2.hp; ldh = C2.n_ext; }
-        HPS_CUDA(proj_rows<T>(hc, ldh, nrhs, CD.pj, h->dF2C, vt, CD.pj.np, st, pf));
-        HPS_CUDA(merge_gather_h<T>(vt, 1, 1, CD.pj.np, ne, nI, nrhs, CD.ext, CD.var, CD.var, false, (T*)M.r,
-                                   (T*)M.hp, st, pf));
-      }
-      BOp<T> DD = bop<T>((T*)M.D, 0, nI);
-      BOp<T> XB = bop<T>((T*)M.x, 0, nI);
-      HPS_CUDA(permute_rows<T>(bop<T>((T*)M.r, 0, nI), XB, M.perm, nI, nrhs, 1, st, pf));
-      HPS_CUDA(getrs_inplace<T>(DD, nI, XB, nrhs, 1, st, pf));
-      if (M.node != 0) {
-        for (int c = 0; c < 8; ++c) {
-          const AChildDev& CD = M.ch[c];
-          GemmArgs<T> gg;
-          gg.M = CD.ne_c; gg.N = nrhs; gg.K = CD.ni_c; gg.batch = 1;
-          gg.A = bop<T>((T*)CD.Tp, 0, CD.pj.np);
-          gg.arow.idx = CD.barow; gg.arow.len = CD.ne_c;
-          gg.acol.idx = CD.bacol; gg.acol.len = CD.ni_c;
-          gg.B = XB;
-          gg.brow.idx = CD.bbrow; gg.brow.len = CD.ni_c;
-          gg.C = bop<T>((T*)M.hp, 0, ne);
-          gg.crow.idx = CD.bcrow; gg.crow.len = CD.ne_c;
-          gg.alpha = -1.0; gg.beta = 1.0;
-          HPS_CUDA(gemm<T>(gg, st, pf));
+    // level by level: gathers of every merge of the level, one batched
+    // D^{-1} per group of equal sizes, then the B x products
+    for (size_t g0 = 0; g0 < h->ag.size();) {
+      size_t g1 = g0;
+      while (g1 < h->ag.size() && h->ag[g1].level == h->ag[g0].level) ++g1;
+      for (size_t gi = g0; gi < g1; ++gi)
+        for (int mi : h->ag[gi].members) {
+          AMergeDev& M = h->am[(size_t)mi];
+          const ANode& nd = at.nodes[M.node];
+          const int ne = M.n_ext, nI = M.n_int;
+          HPS_CUDA(fill<T>(bop<T>((T*)M.r, 0, nI), nI, nrhs, 1, 0.0, 0.0, st, pf));
+          for (int c = 0; c < 8; ++c) {
+            const AChildDev& CD = M.ch[c];
+            const ANode& K = at.nodes[nd.child[c]];
+            const T* hc;
+            int ldh;
+            if (K.leaf >= 0) { hc = (const T*)h->ws_hleaf + (int64_t)K.leaf * nb * nrhs; ldh = nb; }
+            else { const AMergeDev& C2 = h->am[h->node_merge[nd.child[c]]]; hc = (const T*)C2.hp; ldh = C2.n_ext; }
+            HPS_CUDA(proj_rows<T>(hc, ldh, nrhs, CD.pj, h->dF2C, vt, CD.pj.np, st, pf));
+            HPS_CUDA(merge_gather_h<T>(vt, 1, 1, CD.pj.np, ne, nI, nrhs, CD.ext, CD.var, CD.var, false, (T*)M.r,
+                                       (T*)M.hp, st, pf));
+          }
         }
+      for (size_t gi = g0; gi < g1; ++gi) {
+        const AGroup& G = h->ag[gi];
+        const int nbat = (int)G.members.size();
+        BOp<T> XB = bopp<T>(G.dx, G.n_int);
+        HPS_CUDA(permute_rows<T>(bopp<T>(G.dr, G.n_int), XB, G.perm, G.n_int, nrhs, nbat, st, pf));
+        HPS_CUDA(getrs_inplace<T>(bopp<T>(G.dD, G.n_int), G.n_int, XB, nrhs, nbat, st, pf));
       }
+      for (size_t gi = g0; gi < g1; ++gi) {
+        const AGroup& G = h->ag[gi];
+        HPS_TRY(group_b_products(h, G, G.dx, nrhs, G.dhp, false, st, pf));
+      }
+      g0 = g1;
     }
   }
   // downward pass, root first

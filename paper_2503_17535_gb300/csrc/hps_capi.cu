@@ -404,9 +404,13 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
 
 // --------------------------------------------------------------- solve -----
 
+void drop_graphs(hps_handle* h);
+
 template <typename T>
 hps_status ensure_ws(hps_handle* h, int nrhs) {
   if (h->ws_nrhs >= nrhs) return HPS_OK;
+  if (h->capturing) return HPS_ERR_INVALID;  // never allocate inside a capture
+  drop_graphs(h);                            // they refer to the old buffers
   for (void* pp : h->ws_allocs) { cudaFree(pp); }
   h->ws_allocs.clear();
   h->bytes -= h->ws_bytes;
@@ -450,7 +454,7 @@ hps_status apply_Dinv(hps_handle* h, int m, T* b, T* y, int nrhs, cudaStream_t s
   if (!Kind<T>::iti) {
     BOp<T> DD = bop<T>((T*)Lv.D, (int64_t)ni * ni, ni);
     HPS_CUDA(permute_rows<T>(bop<T>(b, (int64_t)ni * nrhs, ni), YB, Lv.perm, ni, nrhs, nm, st, pf));
-    if (trsv_flags_applicable<T>(ni, nrhs, nm, h->trsv))
+    if (!h->capturing && trsv_flags_applicable<T>(ni, nrhs, nm, h->trsv))
       HPS_CUDA(getrs_flags<T>((const T*)Lv.D, ni, ni, y, ni, nrhs, h->trsv, st, pf));
     else
       HPS_CUDA(getrs_inplace<T>(DD, ni, YB, nrhs, nm, st, pf));
@@ -481,7 +485,7 @@ hps_status apply_Dinv(hps_handle* h, int m, T* b, T* y, int nrhs, cudaStream_t s
   // b1 <- b1 - D12 b2 (odd children's interior blocks)
   HPS_CUDA(child_block(true, grouped(B1, 2), grouped(B1, 2)));
   HPS_CUDA(permute_rows<T>(B1, YB, Lv.perm, hn, nrhs, nm, st, pf));
-  if (trsv_flags_applicable<T>(hn, nrhs, nm, h->trsv))
+  if (!h->capturing && trsv_flags_applicable<T>(hn, nrhs, nm, h->trsv))
     HPS_CUDA(getrs_flags<T>((const T*)Lv.W, hn, hn, y, ni, nrhs, h->trsv, st, pf));
   else
     HPS_CUDA(getrs_inplace<T>(WW, hn, YB, nrhs, nm, st, pf));
@@ -505,17 +509,18 @@ hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_i
   const int64_t nl = h->nl;
   const int nb = h->nb, xr = h->xrows_leaf, nlu = h->nlu_leaf;
   // stage host inputs
+  // (a captured solve has checked its pointers before the capture began)
   const T* g = (const T*)g_in;
-  if (!is_device_ptr(g_in)) {
+  if (!h->capturing && !is_device_ptr(g_in)) {
     HPS_CUDA(cudaMemcpyAsync(h->ws_g, g_in, (size_t)h->nroot * nrhs * sizeof(T), cudaMemcpyHostToDevice, st));
     g = (const T*)h->ws_g;
   }
   const T* f = (const T*)f_in;
-  if (f_in && !is_device_ptr(f_in)) {
+  if (f_in && !h->capturing && !is_device_ptr(f_in)) {
     HPS_CUDA(cudaMemcpyAsync(h->ws_f, f_in, (size_t)nl * h->npts * nrhs * sizeof(T), cudaMemcpyHostToDevice, st));
     f = (const T*)h->ws_f;
   }
-  const bool host_u = !is_device_ptr(u_out);
+  const bool host_u = !h->capturing && !is_device_ptr(u_out);
   T* u = host_u ? (T*)h->ws_u : (T*)u_out;
   const bool newf = (f != nullptr);
 
@@ -599,13 +604,76 @@ hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_i
 
 thread_local int64_t g_last_err_node = -1;
 
+void drop_graphs(hps_handle* h) {
+  for (auto& e : h->graphs)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  h->graphs.clear();
+}
+
 void free_handle(hps_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  drop_graphs(h);
   for (void* p : h->ws_allocs) cudaFree(p);
   for (void* p : h->allocs) cudaFree(p);
   if (h->trsv_err_host) cudaFreeHost(h->trsv_err_host);
   delete h;
+}
+
+// Solve through a captured CUDA graph: the first call with a key runs
+// eagerly (allocating the workspace), the second captures the enqueued work
+// and every later call replays it.  The flag-ordered triangular solves are
+// not captured (their epochs are host state); the blocked solves are.
+hps_status graph_solve(hps_handle* h, int nrhs, const void* g, const void* f, void* u, cudaStream_t st) {
+  auto eager = [&]() {
+    return h->iti ? solve_impl<cplx>(h, nrhs, g, f, u, st) : solve_impl<double>(h, nrhs, g, f, u, st);
+  };
+  if (h->trsv_err_host && *(volatile int*)h->trsv_err_host) return HPS_ERR_TIMEOUT;
+  for (size_t i = 0; i < h->graphs.size(); ++i) {
+    auto& e = h->graphs[i];
+    if (e.nrhs != nrhs || e.g != g || e.f != f || e.u != u) continue;
+    if (e.exec) {
+      HPS_CUDA(cudaGraphLaunch(e.exec, st));
+      return HPS_OK;
+    }
+    // second call: capture
+    cudaGraph_t graph = nullptr;
+    HPS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    hps_status s = eager();
+    h->capturing = false;
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (s != HPS_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return s != HPS_OK ? s : HPS_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      cudaGetLastError();
+      return HPS_ERR_CUDA;
+    }
+    e.exec = exec;
+    HPS_CUDA(cudaGraphLaunch(e.exec, st));
+    return HPS_OK;
+  }
+  // first call with this key: run eagerly, remember the key
+  hps_status s = eager();
+  if (s != HPS_OK) return s;
+  if (h->graphs.size() >= 8) {
+    if (h->graphs.front().exec) cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  hps_handle::GraphEntry e;
+  e.nrhs = nrhs;
+  e.g = g;
+  e.f = f;
+  e.u = u;
+  e.warm = true;
+  h->graphs.push_back(e);
+  return HPS_OK;
 }
 
 }  // namespace
@@ -758,8 +826,12 @@ hps_status hps_solve_batched(hps_handle* h, int nrhs, const void* g, const void*
   hps_status s;
   try {
     if (h->adaptive) s = adaptive_solve(h, nrhs, g, f, u, st);
+    else if (h->opts.graph_solve && !h->opts.profile && st && is_device_ptr(g) && is_device_ptr(u) &&
+             (!f || is_device_ptr(f)))
+      s = graph_solve(h, nrhs, g, f, u, st);
     else s = h->iti ? solve_impl<cplx>(h, nrhs, g, f, u, st) : solve_impl<double>(h, nrhs, g, f, u, st);
   } catch (...) {
+    h->capturing = false;
     s = HPS_ERR_INVALID;
   }
   return s;

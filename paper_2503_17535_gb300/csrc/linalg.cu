@@ -79,7 +79,20 @@ template <typename T> struct GemmTile;
 template <> struct GemmTile<double> { enum { BM = 64, BN = 64, BK = 16, TM = 4, TN = 4 }; };
 template <> struct GemmTile<cplx> { enum { BM = 32, BN = 32, BK = 16, TM = 2, TN = 2 }; };
 
+// Epilogue modes: the LU / TRSM / Schur updates are C <- C - A B and the
+// leaf products C <- A B; handling those two forms apart keeps the general
+// alpha / beta arithmetic (a complex multiply and multiply-add per element)
+// off the FP64 pipe, where it costs as much as several steps of K.
+enum { EPI_GENERAL = 0, EPI_SUB = 1, EPI_SET = 2 };
+
 template <typename T>
+inline int epi_mode(const GemmArgs<T>& g) {
+  if (g.alpha == T(-1.0) && g.beta == T(1.0)) return EPI_SUB;
+  if (g.alpha == T(1.0) && is_zero(g.beta)) return EPI_SET;
+  return EPI_GENERAL;
+}
+
+template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
   constexpr int BM = GemmTile<T>::BM, BN = GemmTile<T>::BN, BK = GemmTile<T>::BK;
   constexpr int TM = GemmTile<T>::TM, TN = GemmTile<T>::TN;
@@ -97,7 +110,13 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
 #pragma unroll
     for (int r = 0; r < TM; ++r)
 #pragma unroll
-      for (int c = 0; c < TN; ++c) acc[r][c] = T(0.0);
+      for (int c = 0; c < TN; ++c) {
+        acc[r][c] = T(0.0);
+        if (MODE == EPI_SUB) {
+          const int gi = i0 + tx + RX * r, gj = j0 + ty + (256 / RX) * c;
+          if (gi < g.M && gj < g.N) acc[r][c] = C[(int64_t)g.crow.at(b, gi) + (int64_t)gj * g.C.ld];
+        }
+      }
     for (int k0 = 0; k0 < g.K; k0 += BK) {
       for (int e = tid; e < BM * BK; e += 256) {
         int i = e % BM, l = e / BM;
@@ -125,7 +144,8 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
 #pragma unroll
         for (int r = 0; r < TM; ++r)
 #pragma unroll
-          for (int c = 0; c < TN; ++c) acc[r][c] = fmac(acc[r][c], av[r], bv[c]);
+          for (int c = 0; c < TN; ++c)
+            acc[r][c] = MODE == EPI_SUB ? fmsc(acc[r][c], av[r], bv[c]) : fmac(acc[r][c], av[r], bv[c]);
       }
       __syncthreads();
     }
@@ -140,9 +160,13 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
         int gj = j0 + ty + (256 / RX) * c;
         if (gj >= g.N) continue;
         T* p = C + ci + (int64_t)gj * g.C.ld;
-        T v = g.alpha * acc[r][c];
-        if (use_beta) v = fmac(v, g.beta, *p);
-        *p = v;
+        if (MODE != EPI_GENERAL) {
+          *p = acc[r][c];
+        } else {
+          T v = g.alpha * acc[r][c];
+          if (use_beta) v = fmac(v, g.beta, *p);
+          *p = v;
+        }
       }
     }
   }
@@ -153,6 +177,10 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
 // C = (P1 - P2) + i (P3 - P1 - P2).  Each complex multiply-add costs three
 // real FMAs instead of four on the FP64 pipe; the sums Ar + Ai and Br + Bi
 // are formed once per element when the tile is staged in shared memory.
+// With MODE == EPI_SUB the accumulators start from C so that the update
+// needs three additions per element: p1 = 0, p2 = Re C, p3 = Re C - Im C give
+// Re(C - AB) = p2 - p1 and Im(C - AB) = p1 + p2 - p3 after the products.
+template <int MODE>
 __global__ void __launch_bounds__(256) k_gemm_c3m(GemmArgs<cplx> g) {
   constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2, RX = 16;
   __shared__ double Ar[BK][BM], Ai[BK][BM], As[BK][BM];
@@ -168,7 +196,17 @@ __global__ void __launch_bounds__(256) k_gemm_c3m(GemmArgs<cplx> g) {
 #pragma unroll
     for (int r = 0; r < TM; ++r)
 #pragma unroll
-      for (int c = 0; c < TN; ++c) p1[r][c] = p2[r][c] = p3[r][c] = 0.0;
+      for (int c = 0; c < TN; ++c) {
+        p1[r][c] = p2[r][c] = p3[r][c] = 0.0;
+        if (MODE == EPI_SUB) {
+          const int gi = i0 + tx + RX * r, gj = j0 + ty + 16 * c;
+          if (gi < g.M && gj < g.N) {
+            const cplx cv = C[(int64_t)g.crow.at(b, gi) + (int64_t)gj * g.C.ld];
+            p2[r][c] = cv.re;
+            p3[r][c] = cv.re - cv.im;
+          }
+        }
+      }
     for (int k0 = 0; k0 < g.K; k0 += BK) {
       for (int e = tid; e < BM * BK; e += 256) {
         const int i = e % BM, l = e / BM;
@@ -214,10 +252,16 @@ __global__ void __launch_bounds__(256) k_gemm_c3m(GemmArgs<cplx> g) {
         const int gj = j0 + ty + 16 * c;
         if (gj >= g.N) continue;
         cplx* p = C + ci + (int64_t)gj * g.C.ld;
-        const cplx acc(p1[r][c] - p2[r][c], p3[r][c] - p1[r][c] - p2[r][c]);
-        cplx v = g.alpha * acc;
-        if (use_beta) v = fmac(v, g.beta, *p);
-        *p = v;
+        if (MODE == EPI_SUB) {
+          *p = cplx(p2[r][c] - p1[r][c], (p1[r][c] + p2[r][c]) - p3[r][c]);
+        } else if (MODE == EPI_SET) {
+          *p = cplx(p1[r][c] - p2[r][c], p3[r][c] - (p1[r][c] + p2[r][c]));
+        } else {
+          const cplx acc(p1[r][c] - p2[r][c], p3[r][c] - p1[r][c] - p2[r][c]);
+          cplx v = g.alpha * acc;
+          if (use_beta) v = fmac(v, g.beta, *p);
+          *p = v;
+        }
       }
     }
   }
@@ -357,13 +401,22 @@ cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
     else k_gemm_skinny<T, 8><<<grid, 128, 0, st>>>(g);
   } else if (UseC3M<T>::value) {
     dim3 grid((g.M + 31) / 32, (g.N + 31) / 32, std::min(g.batch, 65535));
-    k_gemm_c3m<<<grid, 256, 0, st>>>(*reinterpret_cast<const GemmArgs<cplx>*>(&g));
+    const GemmArgs<cplx>& gc = *reinterpret_cast<const GemmArgs<cplx>*>(&g);
+    switch (epi_mode(gc)) {
+      case EPI_SUB: k_gemm_c3m<EPI_SUB><<<grid, 256, 0, st>>>(gc); break;
+      case EPI_SET: k_gemm_c3m<EPI_SET><<<grid, 256, 0, st>>>(gc); break;
+      default: k_gemm_c3m<EPI_GENERAL><<<grid, 256, 0, st>>>(gc); break;
+    }
     const double mnk = g.M * (double)g.N * g.K * g.batch;
     if (pf) pf->end(K_GEMM, 8.0 * mnk, st, 6.0 * mnk);
     return cudaGetLastError();
   } else {
     dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, std::min(g.batch, 65535));
-    k_gemm<T><<<grid, 256, 0, st>>>(g);
+    switch (epi_mode(g)) {
+      case EPI_SUB: k_gemm<T, EPI_SUB><<<grid, 256, 0, st>>>(g); break;
+      case EPI_SET: k_gemm<T, EPI_SET><<<grid, 256, 0, st>>>(g); break;
+      default: k_gemm<T, EPI_GENERAL><<<grid, 256, 0, st>>>(g); break;
+    }
   }
   if (pf) pf->end(K_GEMM, fma_flops<T>() * g.M * (double)g.N * g.K * g.batch, st);
   return cudaGetLastError();
@@ -403,10 +456,26 @@ cudaError_t fill(BOp<T> C, int M, int N, int batch, T value, T diag, cudaStream_
 // matrix's group; each CTA holds its chunk of the panel in shared memory
 // (column-major, `ch` rows).  Per column: local argmax, publish candidate,
 // group barrier, global pick (largest |.|, lowest row on ties), swap, update.
+// Pivot order: larger magnitude first, then the lower row.  Magnitudes are
+// non-negative (or -1 for "none"), so their IEEE bit patterns order like the
+// values as signed 64-bit integers; comparing those keeps the search on the
+// integer pipe instead of the FP64 pipe.
+__device__ __forceinline__ bool piv_better(double m, int r, double best_m, int best_r) {
+  const long long a = __double_as_longlong(m), b = __double_as_longlong(best_m);
+  return a > b || (a == b && r < best_r);
+}
+
 template <typename T, bool COOP>
 __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int nb, int G, int* ipiv,
                                                   int* info, unsigned* bars, T* pubv, double* pubm,
                                                   int* pubr, unsigned* dev_err) {
+  // Threads form RT row lanes x CT column lanes (CT > 1 when the chunk has
+  // fewer rows than threads); per column the pivot is reduced (warp
+  // shuffles, then every thread over the warp results), rows j and p are
+  // swapped one column per thread, every thread forms the multipliers of its
+  // rows, and after one more barrier updates its columns (cyclic from
+  // jj + 1), the lane of column jj + 1 tracking that column's largest entry
+  // for the next step: three block barriers per column.
   extern __shared__ unsigned char smem_raw[];
   T* Ps = reinterpret_cast<T*>(smem_raw);
   const int b = blockIdx.x / G, g = blockIdx.x % G;
@@ -416,83 +485,80 @@ __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int n
   const int rc = max(0, min(ch, n - r0));     // rows in this chunk
   T* Ab = A.item(b);
   const int lda = A.ld;
-  T* Wv = Ps + (size_t)ch * nb;               // winner row (nb)
+  T* Wv = Ps + (size_t)ch * nb;               // pivot row after the swap (nb)
   T* Rv = Wv + nb;                            // old row j (nb)
-  __shared__ double red_m[32];
-  __shared__ int red_r[32];
-  __shared__ int s_piv;
-  __shared__ double s_pmag;
-  __shared__ double s_inv_raw[2];
+  __shared__ double red_m[8];
+  __shared__ int red_r[8];
+  __shared__ int s_bg;
+  __shared__ double s_inv_raw[2];  // 1 / pivot, formed once per column
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5;
+  const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  int CT = 1;
+  while (CT < 16 && CT * 2 <= nb && (nth / (CT * 2)) >= rc && nth / (CT * 2) >= 32) CT *= 2;
+  const int RT = nth / CT, rt = tid % RT, ct = tid / RT;
 
-  for (int e = tid; e < rc * nb; e += nth) {
-    int r = e % rc, c = e / rc;
-    Ps[r + (size_t)c * ch] = Ab[(int64_t)(r0 + r) + (int64_t)(k0 + c) * lda];
-  }
+  for (int c = 0; c < nb; ++c)
+    for (int r = tid; r < rc; r += nth) Ps[r + (size_t)c * ch] = Ab[(int64_t)(r0 + r) + (int64_t)(k0 + c) * lda];
   __syncthreads();
   T* pv = COOP ? pubv + (size_t)b * 2 * (G + 1) * nb : nullptr;
   double* pm = COOP ? pubm + (size_t)b * 2 * G : nullptr;
   int* pr = COOP ? pubr + (size_t)b * 2 * G : nullptr;
   unsigned* bar = COOP ? bars + 2 * b : nullptr;
 
+  // this thread's best entry of the current column (rows >= j)
+  double best = -1.0;
+  int brow = 0x7fffffff;
+  for (int r = max(0, k0 - r0) + tid; r < rc; r += nth) {
+    const double m = mag1(Ps[r]);
+    if (piv_better(m, r0 + r, best, brow)) { best = m; brow = r0 + r; }
+  }
   for (int jj = 0; jj < nb; ++jj) {
     const int j = k0 + jj;
-    // local argmax over rows >= j in this chunk
-    double best = -1.0;
-    int brow = 0x7fffffff;
-    for (int r = max(0, j - r0) + tid; r < rc; r += nth) {
-      double m = mag1(Ps[r + (size_t)jj * ch]);
-      if (m > best || (m == best && r0 + r < brow)) { best = m; brow = r0 + r; }
-    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double m2 = __shfl_down_sync(0xffffffffu, best, o);
-      int r2 = __shfl_down_sync(0xffffffffu, brow, o);
-      if (m2 > best || (m2 == best && r2 < brow)) { best = m2; brow = r2; }
+      const double m2 = __shfl_down_sync(0xffffffffu, best, o);
+      const int r2 = __shfl_down_sync(0xffffffffu, brow, o);
+      if (piv_better(m2, r2, best, brow)) { best = m2; brow = r2; }
     }
     if (lane == 0) { red_m[wid] = best; red_r[wid] = brow; }
     __syncthreads();
-    if (tid == 0) {
-      for (int w = 1; w < (nth + 31) / 32; ++w)
-        if (red_m[w] > red_m[0] || (red_m[w] == red_m[0] && red_r[w] < red_r[0])) {
-          red_m[0] = red_m[w]; red_r[0] = red_r[w];
-        }
-    }
-    __syncthreads();
+    double pmag = red_m[0];
+    int p = red_r[0];
+    for (int w = 1; w < nw; ++w)
+      if (piv_better(red_m[w], red_r[w], pmag, p)) { pmag = red_m[w]; p = red_r[w]; }
     const bool own_j = (j >= r0 && j < r0 + rc);
     if (COOP) {
       const int slot = jj & 1;
-      if (tid == 0) { pm[slot * G + g] = red_m[0]; pr[slot * G + g] = red_r[0]; }
-      const int lr = red_r[0] - r0;
+      if (tid == 0) { pm[slot * G + g] = pmag; pr[slot * G + g] = p; }
+      const int lr = p - r0;
       for (int c = tid; c < nb; c += nth) {
-        if (red_m[0] >= 0.0 && lr >= 0 && lr < rc)
-          pv[((size_t)slot * (G + 1) + g) * nb + c] = Ps[lr + (size_t)c * ch];
+        if (pmag >= 0.0 && lr >= 0 && lr < rc) pv[((size_t)slot * (G + 1) + g) * nb + c] = Ps[lr + (size_t)c * ch];
         if (own_j) pv[((size_t)slot * (G + 1) + G) * nb + c] = Ps[(j - r0) + (size_t)c * ch];
       }
       if (!group_barrier(bar, G, dev_err)) return;
-      // pick the global pivot: warp 0 reduces the G published candidates
-      // (loads bypass L1: the values were written by other CTAs)
+      // the global pivot: warp 0 reduces the G published candidates (loads
+      // bypass L1: the values were written by other CTAs)
       if (wid == 0) {
         double bm = -1.0;
         int brr = 0x7fffffff, bg = 0;
         for (int q2 = lane; q2 < G; q2 += 32) {
           const double m = __ldcg(&pm[slot * G + q2]);
           const int rr = __ldcg(&pr[slot * G + q2]);
-          if (m > bm || (m == bm && rr < brr)) { bm = m; brr = rr; bg = q2; }
+          if (piv_better(m, rr, bm, brr)) { bm = m; brr = rr; bg = q2; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           const double m2 = __shfl_down_sync(0xffffffffu, bm, o);
           const int r2 = __shfl_down_sync(0xffffffffu, brr, o);
           const int g2 = __shfl_down_sync(0xffffffffu, bg, o);
-          if (m2 > bm || (m2 == bm && r2 < brr)) { bm = m2; brr = r2; bg = g2; }
+          if (piv_better(m2, r2, bm, brr)) { bm = m2; brr = r2; bg = g2; }
         }
-        if (lane == 0) { s_piv = brr; s_pmag = bm; red_r[1] = bg; }
+        if (lane == 0) { red_m[0] = bm; red_r[0] = brr; s_bg = bg; }
       }
       __syncthreads();
-      const int bg = red_r[1];
-      const double* wsrc = reinterpret_cast<const double*>(pv + ((size_t)slot * (G + 1) + bg) * nb);
+      pmag = red_m[0];
+      p = red_r[0];
+      const double* wsrc = reinterpret_cast<const double*>(pv + ((size_t)slot * (G + 1) + s_bg) * nb);
       const double* rsrc = reinterpret_cast<const double*>(pv + ((size_t)slot * (G + 1) + G) * nb);
       double* wdst = reinterpret_cast<double*>(Wv);
       double* rdst = reinterpret_cast<double*>(Rv);
@@ -501,51 +567,70 @@ __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int n
         wdst[c] = __ldcg(&wsrc[c]);
         rdst[c] = __ldcg(&rsrc[c]);
       }
-    } else {
-      if (tid == 0) { s_piv = red_r[0]; s_pmag = red_m[0]; }
       __syncthreads();
       for (int c = tid; c < nb; c += nth) {
-        Wv[c] = Ps[(s_piv - r0) + (size_t)c * ch];
-        Rv[c] = Ps[(j - r0) + (size_t)c * ch];
+        if (own_j) Ps[(j - r0) + (size_t)c * ch] = Wv[c];
+        if (p != j && p >= r0 && p < r0 + rc) Ps[(p - r0) + (size_t)c * ch] = Rv[c];
+        if (c == jj) *reinterpret_cast<T*>(s_inv_raw) = (pmag == 0.0) ? T(0.0) : recip(Wv[c]);
+      }
+    } else {
+      // one column per thread: read both rows, then write them swapped
+      for (int c = tid; c < nb; c += nth) {
+        const T wv = Ps[(p - r0) + (size_t)c * ch];
+        const T rv = Ps[(j - r0) + (size_t)c * ch];
+        Wv[c] = wv;
+        Ps[(j - r0) + (size_t)c * ch] = wv;
+        if (p != j) Ps[(p - r0) + (size_t)c * ch] = rv;
+        if (c == jj) *reinterpret_cast<T*>(s_inv_raw) = (pmag == 0.0) ? T(0.0) : recip(wv);
       }
     }
-    __syncthreads();
-    const int p = s_piv;
     if (g == 0 && tid == 0) {
       ipiv[(int64_t)b * n + j] = p;
-      if (s_pmag == 0.0 && info[b] == 0) info[b] = j + 1;
-    }
-    // swap rows j and p inside the chunk(s)
-    for (int c = tid; c < nb; c += nth) {
-      if (own_j) Ps[(j - r0) + (size_t)c * ch] = Wv[c];
-      if (p != j && p >= r0 && p < r0 + rc) Ps[(p - r0) + (size_t)c * ch] = Rv[c];
+      if (pmag == 0.0 && info[b] == 0) info[b] = j + 1;
     }
     __syncthreads();
-    // multipliers (one reciprocal of the pivot per column, computed once),
-    // then the rank-1 update of the columns right of jj, rows below j
-    if (tid == 0) {
-      const T inv0 = (s_pmag == 0.0) ? T(0.0) : recip(Wv[jj]);
-      *reinterpret_cast<T*>(s_inv_raw) = inv0;
-    }
-    __syncthreads();
+    // multipliers of this thread's rows (at most ch / RT + 1 of them are
+    // kept: the rows rlo + rt, rlo + rt + RT, ...), then the update of its
+    // columns; the next column's candidates are tracked by column lane 0
     const T inv = *reinterpret_cast<const T*>(s_inv_raw);
     const int rlo = max(0, j + 1 - r0);
-    const int nr = rc - rlo;
-    const int ncol = nb - jj - 1;
-    for (int r = rlo + tid; r < rc; r += nth) Ps[r + (size_t)jj * ch] = Ps[r + (size_t)jj * ch] * inv;
-    __syncthreads();
-    if (nr > 0 && ncol > 0) {
-      for (int e = tid; e < nr * ncol; e += nth) {
-        int r = rlo + e % nr, c = jj + 1 + e / nr;
-        Ps[r + (size_t)c * ch] = fmsc(Ps[r + (size_t)c * ch], Ps[r + (size_t)jj * ch], Wv[c]);
+    best = -1.0;
+    brow = 0x7fffffff;
+    if (CT == 1) {
+      for (int r = rlo + rt; r < rc; r += RT) {
+        const T l = Ps[r + (size_t)jj * ch] * inv;
+        Ps[r + (size_t)jj * ch] = l;
+        for (int c = jj + 1; c < nb; ++c) {
+          const T v = fmsc(Ps[r + (size_t)c * ch], l, Wv[c]);
+          Ps[r + (size_t)c * ch] = v;
+          if (c == jj + 1) {
+            const double m = mag1(v);
+            if (piv_better(m, r0 + r, best, brow)) { best = m; brow = r0 + r; }
+          }
+        }
+      }
+    } else {
+      // rc <= RT here: each thread has at most one row
+      const int r = rlo + rt;
+      T l = T(0.0);
+      if (r < rc) l = Ps[r + (size_t)jj * ch] * inv;
+      __syncthreads();
+      if (r < rc) {
+        if (ct == 0) Ps[r + (size_t)jj * ch] = l;
+        for (int c = jj + 1 + ct; c < nb; c += CT) {
+          const T v = fmsc(Ps[r + (size_t)c * ch], l, Wv[c]);
+          Ps[r + (size_t)c * ch] = v;
+          if (c == jj + 1) {
+            const double m = mag1(v);
+            if (piv_better(m, r0 + r, best, brow)) { best = m; brow = r0 + r; }
+          }
+        }
       }
     }
-    __syncthreads();
   }
-  for (int e = tid; e < rc * nb; e += nth) {
-    int r = e % rc, c = e / rc;
-    Ab[(int64_t)(r0 + r) + (int64_t)(k0 + c) * lda] = Ps[r + (size_t)c * ch];
-  }
+  __syncthreads();
+  for (int c = 0; c < nb; ++c)
+    for (int r = tid; r < rc; r += nth) Ab[(int64_t)(r0 + r) + (int64_t)(k0 + c) * lda] = Ps[r + (size_t)c * ch];
 }
 
 // Apply the panel's interchanges to every column outside the panel and

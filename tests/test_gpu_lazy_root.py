@@ -112,3 +112,33 @@ def test_lazy_root_full_size_helmholtz_residuals(P):
     torch.cuda.synchronize()
     P.hps_free(h)
     assert rel(ul, u.cpu().numpy()) <= 1e-11
+
+
+@pytest.mark.parametrize("lazy", [False, True], ids=["explicit", "lazy"])
+def test_graph_solve_replays_match_eager(P, lazy):
+    """hps_options.graph_solve: the third and later calls replay a captured
+    graph; results for changing data behind the same pointers equal eager
+    solves (the graph takes the blocked triangular solves at a lazy root,
+    so agreement is to roundoff, not bitwise)."""
+    pr = W.helmholtz_bumps_2d(seed=1)
+    p, L = 12, 3
+    t, x, a, b, c, f, g = sample_inputs(P, pr, p, L)
+    args = dict(a=dev(a), b=[dev(bk) for bk in b], c=dev(c), f=dev(f), eta=pr.eta, lazy_root=lazy)
+    hg = P.hps_build(t, p, p - 2, P.HPS_ITI, graph_solve=True, **args)
+    he = P.hps_build(t, p, p - 2, P.HPS_ITI, **args)
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(9)
+    gd = torch.zeros(g.shape, dtype=torch.complex128, device="cuda")
+    fd = torch.zeros(f.shape, dtype=torch.complex128, device="cuda")
+    ug = torch.zeros(f.shape, dtype=torch.complex128, device="cuda")
+    ue = torch.zeros(f.shape, dtype=torch.complex128, device="cuda")
+    with torch.cuda.stream(stream):
+        for k in range(5):
+            gd.copy_(dev(_rand(rng, g.shape, True)))
+            fd.copy_(dev(_rand(rng, f.shape, True)))
+            P.hps_solve(hg, gd, ug, f=fd if k % 2 else None, stream=stream.cuda_stream)
+            P.hps_solve(he, gd, ue, f=fd if k % 2 else None, stream=stream.cuda_stream)
+            stream.synchronize()
+            assert rel(ug.cpu().numpy(), ue.cpu().numpy()) <= 1e-12
+    P.hps_free(hg)
+    P.hps_free(he)

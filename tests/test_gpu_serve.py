@@ -33,6 +33,8 @@ def P():
 def _problem(P, mk, p, L):
     pr = mk()
     t, x, a, b, c, f, g = sample_inputs(P, pr, p, L)
+    cc = np.ascontiguousarray
+    a, b, c, f, g = cc(a), [cc(bk) for bk in b], cc(c), cc(f), cc(g)
     kind = P.HPS_ITI if pr.kind == "iti" else P.HPS_DTN
     return dict(pr=pr, t=t, p=p, L=L, kind=kind, a=a, b=b, c=c, f=f, g=g, eta=pr.eta or 0.0)
 
