@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="helmholtz2d", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--workload", default="helmholtz2d", choices=sorted(WORKLOADS) + ["serve", "diff"])
     ap.add_argument("--requests", type=int, default=None, help="serve: requests per arrival rate")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -98,6 +98,10 @@ def parse():
         args.spec = dict(SERVE)
         if args.requests:
             args.spec["requests"] = args.requests
+        return args
+    if args.workload == "diff":
+        args.spec = {"workload": "diff_helmholtz2d_theta64_depth5_p16", "depth": 5, "p": 16, "k": 20.0,
+                     "grid": 64, "seed": 5}
         return args
     spec = dict(WORKLOADS[args.workload])
     if args.depth is not None and spec["depth"] >= 0 and args.depth != spec["depth"]:
@@ -683,12 +687,82 @@ def run_serve(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------ differentiation --
+
+def run_diff(args, rank, world):
+    """Gradient of J(theta) = ||u(theta) - u(theta_true)||^2 over a 64 x 64
+    grid theta (Helmholtz operator, 1024 leaves, p = 16): one step = forward
+    (build + solve) and backward (adjoint solve + coefficient gradient +
+    interpolation transpose) through the autograd Function."""
+    import torch
+    import paper_2503_17535_gb300 as P
+    import workloads as W
+    from paper_2503_17535_gb300.autograd import hps_solve_fn
+
+    spec = args.spec
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    d = W.helmholtz_theta_2d(seed=spec["seed"], k=spec["k"], n=spec["grid"])
+    pr, k = d["problem"], d["k"]
+    p, L = spec["p"], spec["depth"]
+    t = P.uniform_tree(2, L, pr.lo, pr.hi)
+    x, xb = P.hps_nodes(t, p, p - 2)
+    nl, ppl, nr = P.hps_sizes(t, p, p - 2)
+    I = W.grid_interp_matrix(x, d["n"]).tocoo()
+    Imat = torch.sparse_coo_tensor(np.vstack([I.row, I.col]), I.data, I.shape, dtype=torch.float64,
+                                   device="cuda").coalesce()
+    f = torch.from_numpy(np.ascontiguousarray(pr.source(x).reshape(nl, ppl).astype(np.complex128))).cuda()
+    g = torch.from_numpy(np.ascontiguousarray(pr.boundary(xb).astype(np.complex128))).cuda()
+
+    def forward(theta):
+        c = (k ** 2 * (1.0 - torch.sparse.mm(Imat, theta[:, None])[:, 0])).reshape(nl, ppl)
+        return hps_solve_fn(c, g, f, t, p, P.HPS_ITI, eta=pr.eta, lazy_root=True)
+
+    with torch.no_grad():
+        u_obs = forward(torch.from_numpy(d["theta_true"]).cuda())
+    theta0 = torch.from_numpy(d["theta_0"]).cuda()
+
+    def step():
+        th = theta0.clone().requires_grad_(True)
+        J = ((forward(th) - u_obs).abs() ** 2).sum()
+        J.backward()
+        return th.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    total = t0.elapsed_time(t1)
+    per = sorted(a.elapsed_time(b) for a, b in evs)
+    line = {"metric": "gradients/s of J(theta) through the adjoint kernels", "value": round(args.steps / (total / 1e3), 4),
+            "unit": "gradients/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total / args.steps, 3), "p50_ms": round(pct(per, 50), 3),
+            "p99_ms": round(pct(per, 99), 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128", "data": "synthetic",
+            "config": {"workload": spec["workload"], "n_leaves": nl, "p": p, "grid": spec["grid"],
+                       "step": "forward (build + solve) + backward (adjoint solve + coefficient gradient)",
+                       "root": "lazy"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.workload == "serve":
         return run_serve(args, rank, world)
+    if args.workload == "diff":
+        return run_diff(args, rank, world)
     spec = args.spec
     if args.impl == "reference":
         line = run_reference(args, rank)

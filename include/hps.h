@@ -205,6 +205,33 @@ hps_status hps_solve(hps_handle* h, const void* g, const void* f, void* u,
 hps_status hps_solve_batched(hps_handle* h, int nrhs, const void* g, const void* f, void* u,
                              struct CUstream_st* stream);
 
+/* Adjoint solve (uniform trees).  The solve is a linear map
+ * u = A_g g + A_f f (Sections 3.2-3.4); this applies its conjugate
+ * transpose with the stored factors, every step of the solve reversed:
+ *   gbar = A_g^H ubar  ([nrhs][n_root_bdry], may be NULL),
+ *   fbar = A_f^H ubar  ([nrhs][n_leaves][p^d], may be NULL; zero except at
+ *                       each leaf's interior nodes),
+ * for ubar [nrhs][n_leaves][p^d], so that Re<ubar, u> = Re<gbar, g> +
+ * Re<fbar, f> for every (g, f).  fbar is the adjoint field of the leaf
+ * collocation equations (input to hps_coeff_gradient).  Host or device
+ * buffers as in hps_solve.  No counterpart in the paper, which computes
+ * gradients by automatic differentiation of its JAX solver.
+ * Errors: HPS_ERR_INVALID (adaptive handle, bad sizes), HPS_ERR_CUDA. */
+hps_status hps_solve_adjoint(hps_handle* h, int nrhs, const void* ubar, void* gbar, void* fbar,
+                             struct CUstream_st* stream);
+
+/* Derivatives of Re<ubar, u> with respect to the coefficients at the leaf
+ * interior nodes, from the solution u and the adjoint field fbar of
+ * hps_solve_adjoint (same ubar), summed over the nrhs columns:
+ *   gc = -Re(conj(fbar) u),  ga = -Re(conj(fbar) Lap u),
+ *   gb[k] = -Re(conj(fbar) d_k u)  (derivatives of the leaf's spectral
+ *   collocation, scaled to the leaf size);
+ * every output is [n_leaves][p^d] doubles (gb: [dim][n_leaves][p^d]), zero
+ * at leaf boundary nodes, and may be NULL.  u, fbar and the outputs must be
+ * device memory.  Uniform trees. */
+hps_status hps_coeff_gradient(hps_handle* h, int nrhs, const void* u, const void* fbar, double* ga,
+                              double* gb, double* gc, struct CUstream_st* stream);
+
 /* Release a handle (NULL is accepted).  Synchronises the handle's last stream. */
 void hps_free(hps_handle* h);
 

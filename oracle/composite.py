@@ -75,6 +75,13 @@ def _leaf_panels(dim, L):
 
 
 def solve_dtn(dim, p, L, lo, hi, a, b, c, f, g):
+    A, rhs, unpack = assemble_dtn(dim, p, L, lo, hi, a, b, c, f, g)
+    return unpack(np.linalg.solve(A, rhs), g)
+
+
+def assemble_dtn(dim, p, L, lo, hi, a, b, c, f, g):
+    """The composite DtN system (A, rhs) and unpack(sol, g) -> u on the leaf
+    nodes ([n_leaves][p^dim])."""
     q = p - 2
     corners, hvec = geo.uniform_leaf_boxes(dim, lo, hi, L)
     hlen = float(hvec[0])
@@ -128,19 +135,33 @@ def solve_dtn(dim, p, L, lo, hi, a, b, c, f, g):
                 else:
                     k2 = ent2[1]
                     A[rows, off_g + k2 * npan:off_g + (k2 + 1) * npan] += blk
-    sol = np.linalg.solve(A, rhs)
-    u = np.zeros((nl, p ** dim), dt)
-    for m in range(nl):
-        gl = np.zeros(nslot * npan, dt)
-        for s, (kind, k) in enumerate(panels[m]):
-            src = g if kind == "root" else sol[off_g:]
-            gl[s * npan:(s + 1) * npan] = src[k * npan:(k + 1) * npan]
-        u[m, Ie] = P @ gl
-        u[m, Ii] = sol[m * ni:(m + 1) * ni]
-    return u
+
+    def unpack(sol, g):
+        dt2 = np.result_type(sol, g)
+        u = np.zeros((nl, p ** dim), dt2)
+        for m in range(nl):
+            gl = np.zeros(nslot * npan, dt2)
+            for s, (kind, k) in enumerate(panels[m]):
+                src = g if kind == "root" else sol[off_g:]
+                gl[s * npan:(s + 1) * npan] = src[k * npan:(k + 1) * npan]
+            u[m, Ie] = P @ gl
+            u[m, Ii] = sol[m * ni:(m + 1) * ni]
+        return u
+
+    unpack.info = {"panels": panels, "off_g": off_g, "ni": ni, "npan": npan, "Ie": Ie, "Ii": Ii, "P": P,
+                   "nl": nl, "npts": p ** dim}
+    return A, rhs, unpack
 
 
 def solve_iti(p, L, lo, hi, a, b, c, f, g, eta):
+    A, rhs = assemble_iti(p, L, lo, hi, a, b, c, f, g, eta)
+    nl = (2 ** L) ** 2
+    return np.linalg.solve(A, rhs).reshape(nl, p * p)
+
+
+def assemble_iti(p, L, lo, hi, a, b, c, f, g, eta):
+    """The composite ItI system (A, rhs); the solution is u on the leaf nodes
+    ([n_leaves][p^2]) flattened."""
     dim = 2
     q = p - 2
     corners, hvec = geo.uniform_leaf_boxes(dim, lo, hi, L)
@@ -177,8 +198,7 @@ def solve_iti(p, L, lo, hi, a, b, c, f, g, eta):
                 (mb, sb), = [o for o in owners[k] if o[0] != m]
                 # G u^m = P_s g_in,  g_in = -(QH u^mb) on the neighbour's slot sb
                 A[r0:r0 + nown, mb * npl:(mb + 1) * npl] += Ps @ QH[sb * q:(sb + 1) * q, :]
-    sol = np.linalg.solve(A, rhs)
-    return sol.reshape(nl, npl)
+    return A, rhs
 
 
 def solve_dtn_adaptive(leaves, p, lo, hi, a, b, c, f, g):

@@ -451,3 +451,27 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def hps_solve_adjoint(h: Handle, ubar, gbar=None, fbar=None, nrhs: int = 1, stream=None):
+    """(gbar, fbar) <- conjugate transpose of the solve map applied to ubar."""
+    keep: list = []
+    n = nrhs * h.n_leaves * h.ppl
+    up = _ptr(ubar, h.complex, n, "ubar", keep)
+    gp = _ptr(gbar, h.complex, nrhs * h.n_root, "gbar", keep)
+    fp = _ptr(fbar, h.complex, n, "fbar", keep)
+    _check(_capi.lib().hps_solve_adjoint(h.ptr, nrhs, up, gp, fp, _stream(stream)), "hps_solve_adjoint")
+    return gbar, fbar
+
+
+def hps_coeff_gradient(h: Handle, u, fbar, ga=None, gb=None, gc=None, nrhs: int = 1, stream=None):
+    """Coefficient derivatives at the leaf interior nodes (device tensors)."""
+    keep: list = []
+    n = h.n_leaves * h.ppl
+    up = _ptr(u, h.complex, nrhs * n, "u", keep)
+    fp = _ptr(fbar, h.complex, nrhs * n, "fbar", keep)
+    ap = _ptr(ga, False, n, "ga", keep)
+    bp = _ptr(gb, False, h.dim * n, "gb", keep)
+    cp = _ptr(gc, False, n, "gc", keep)
+    _check(_capi.lib().hps_coeff_gradient(h.ptr, nrhs, up, fp, ap, bp, cp, _stream(stream)),
+           "hps_coeff_gradient")

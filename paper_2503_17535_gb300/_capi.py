@@ -22,7 +22,7 @@ EXPORTED = [
     "hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
     "hps_error_string", "hps_last_error_detail", "hps_device_bytes", "hps_last_launch_count",
     "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc", "hps_refine", "hps_trace_count",
-    "hps_trace_get", "hps_plan_bytes",
+    "hps_trace_get", "hps_plan_bytes", "hps_solve_adjoint", "hps_coeff_gradient",
     # request server (include/hps_serve.h)
     "hps_server_create", "hps_server_destroy", "hps_server_submit_build", "hps_server_submit_solve",
     "hps_server_wait", "hps_server_poll", "hps_server_get_stats", "hps_server_operator",
@@ -118,6 +118,10 @@ def lib() -> ctypes.CDLL:
     L.hps_trace_get.restype = c_int
     L.hps_plan_bytes.argtypes = [POINTER(hps_tree), c_int, c_int, c_int, POINTER(c_int64)]
     L.hps_plan_bytes.restype = c_int
+    L.hps_solve_adjoint.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.hps_solve_adjoint.restype = c_int
+    L.hps_coeff_gradient.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.hps_coeff_gradient.restype = c_int
     L.hps_server_create.argtypes = [POINTER(hps_server_options), POINTER(c_void_p)]
     L.hps_server_create.restype = c_int
     L.hps_server_destroy.argtypes = [c_void_p]

@@ -53,6 +53,8 @@ __host__ __device__ inline cplx recip(cplx a) {
 }
 __host__ __device__ inline bool is_zero(double a) { return a == 0.0; }
 __host__ __device__ inline bool is_zero(cplx a) { return a.re == 0.0 && a.im == 0.0; }
+__host__ __device__ inline double conj_of(double a) { return a; }
+__host__ __device__ inline cplx conj_of(cplx a) { return cplx(a.re, -a.im); }
 __host__ __device__ inline double scale(double a, double s) { return a * s; }
 __host__ __device__ inline cplx scale(cplx a, double s) { return cplx(a.re * s, a.im * s); }
 

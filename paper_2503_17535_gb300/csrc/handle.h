@@ -33,6 +33,12 @@ struct LevelDev {
   int G = 1;
   LuWork luw;
   bool lazy = false;    // root only: X holds [C | h_int]; D^{-1} is applied per solve
+  // adjoint B^H products of DtN levels, in two passes over the children of
+  // even / odd popcount (children sharing an interface differ in one bit, so
+  // no two products of one pass write the same interface rows): per pass a
+  // device array of child [T | h] pointers and the four maps in pass order
+  void* adj_ptrs[2] = {nullptr, nullptr};
+  int* adj_maps[2] = {nullptr, nullptr};
   // solve workspace (nrhs columns)
   void *r = nullptr, *hp = nullptr, *x = nullptr, *gint = nullptr, *gchild = nullptr;
   bool top() const { return nmerge == 1; }
@@ -162,6 +168,13 @@ namespace hps {
       return HPS_ERR_CUDA;                              \
     }                                                   \
   } while (0)
+
+// Solve workspace for nrhs columns (uniform trees); defined with the solve.
+hps_status ensure_solve_ws(hps_handle* h, int nrhs);
+// Adjoint solve and coefficient gradients (uniform trees), hps_adjoint.cu.
+hps_status adjoint_solve(hps_handle* h, int nrhs, const void* ubar, void* gbar, void* fbar, cudaStream_t st);
+hps_status coeff_gradient(hps_handle* h, int nrhs, const void* u, const void* fbar, double* ga, double* gb,
+                          double* gc, cudaStream_t st);
 
 #define HPS_TRY(call)                                   \
   do {                                                  \

@@ -678,6 +678,10 @@ hps_status graph_solve(hps_handle* h, int nrhs, const void* g, const void* f, vo
 
 }  // namespace
 
+hps_status hps::ensure_solve_ws(hps_handle* h, int nrhs) {
+  return h->iti ? ensure_ws<cplx>(h, nrhs) : ensure_ws<double>(h, nrhs);
+}
+
 extern "C" {
 
 const char* hps_error_string(hps_status s) {
@@ -839,6 +843,26 @@ hps_status hps_solve_batched(hps_handle* h, int nrhs, const void* g, const void*
 
 hps_status hps_solve(hps_handle* h, const void* g, const void* f, void* u, struct CUstream_st* stream) {
   return hps_solve_batched(h, 1, g, f, u, stream);
+}
+
+hps_status hps_solve_adjoint(hps_handle* h, int nrhs, const void* ubar, void* gbar, void* fbar,
+                             struct CUstream_st* stream) {
+  if (!h || !ubar || nrhs < 1 || h->adaptive) return HPS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last = st;
+  try {
+    return adjoint_solve(h, nrhs, ubar, gbar, fbar, st);
+  } catch (...) {
+    return HPS_ERR_INVALID;
+  }
+}
+
+hps_status hps_coeff_gradient(hps_handle* h, int nrhs, const void* u, const void* fbar, double* ga, double* gb,
+                              double* gc, struct CUstream_st* stream) {
+  if (!h || !u || !fbar || nrhs < 1 || h->adaptive) return HPS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last = st;
+  return coeff_gradient(h, nrhs, u, fbar, ga, gb, gc, st);
 }
 
 void hps_free(hps_handle* h) { free_handle(h); }

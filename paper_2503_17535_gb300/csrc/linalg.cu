@@ -379,6 +379,68 @@ __global__ void __launch_bounds__(256) k_gemm_skinny_kg(GemmArgs<T> g) {
   }
 }
 
+// Products with a conjugate-transposed left factor (the adjoint solves):
+// 32 x 32 output tiles, 16-deep slabs of both operands staged in shared
+// memory.  Kept apart from the forward kernels so that their code is not
+// touched by the transposed operand access.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_ta(GemmArgs<T> g) {
+  constexpr int BM = 32, BN = 32, BK = 16;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;  // 2 x 2 outputs per thread
+  for (int b = blockIdx.z; b < g.batch; b += gridDim.z) {
+    const T* A = g.A.item(b);
+    const T* B = g.B.item(b);
+    T* C = g.C.item(b);
+    const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
+    T acc[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) acc[r][c] = T(0.0);
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+      for (int e = tid; e < BM * BK; e += 256) {
+        const int l = e % BK, i = e / BK;  // consecutive threads walk A's column
+        const int gi = i0 + i, gl = k0 + l;
+        As[l][i] = (gi < g.M && gl < g.K) ? g.a_at(A, b, gi, gl) : T(0.0);
+      }
+      for (int e = tid; e < BK * BN; e += 256) {
+        const int l = e % BK, j = e / BK;
+        const int gl = k0 + l, gj = j0 + j;
+        Bs[l][j] = (gl < g.K && gj < g.N) ? B[(int64_t)g.brow.at(b, gl) + (int64_t)gj * g.B.ld] : T(0.0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        const T a0 = As[kk][tx], a1 = As[kk][tx + 16], b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
+        acc[0][0] = fmac(acc[0][0], a0, b0);
+        acc[0][1] = fmac(acc[0][1], a0, b1);
+        acc[1][0] = fmac(acc[1][0], a1, b0);
+        acc[1][1] = fmac(acc[1][1], a1, b1);
+      }
+      __syncthreads();
+    }
+    const bool use_beta = !is_zero(g.beta);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int gi = i0 + tx + 16 * r;
+      if (gi >= g.M) continue;
+      const int64_t ci = g.crow.at(b, gi);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int gj = j0 + ty + 16 * c;
+        if (gj >= g.N) continue;
+        T* p = C + ci + (int64_t)gj * g.C.ld;
+        T v = g.alpha * acc[r][c];
+        if (use_beta) v = fmac(v, g.beta, *p);
+        *p = v;
+      }
+    }
+  }
+}
+
 template <typename T>
 cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
@@ -387,7 +449,10 @@ cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
     pf->begin(st);
     pf->note(g.M, g.N, g.K, g.batch);
   }
-  if (g.N <= 8 && g.K >= 128 && (int64_t)((g.M + 127) / 128) * g.batch < 304) {
+  if (g.ta) {
+    dim3 grid((g.M + 31) / 32, (g.N + 31) / 32, std::min(g.batch, 65535));
+    k_gemm_ta<T><<<grid, 256, 0, st>>>(g);
+  } else if (g.N <= 8 && g.K >= 128 && (int64_t)((g.M + 127) / 128) * g.batch < 304) {
     dim3 grid((g.M + 31) / 32, 1, std::min(g.batch, 65535));
     if (g.N == 1) k_gemm_skinny_kg<T, 1><<<grid, 256, 0, st>>>(g);
     else if (g.N == 2) k_gemm_skinny_kg<T, 2><<<grid, 256, 0, st>>>(g);

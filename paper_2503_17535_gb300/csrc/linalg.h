@@ -89,6 +89,13 @@ struct GemmArgs {
   BOp<T> A, B, C;
   IMap arow, acol, brow, crow;
   T alpha = T(1.0), beta = T(0.0);
+  // A enters conjugate-transposed: the (i, l) entry of the product's left
+  // factor is conj(A(acol(l), arow(i))) (adjoint solves)
+  bool ta = false;
+  __device__ T a_at(const T* A, int b, int i, int l) const {
+    if (!ta) return A[(int64_t)arow.at(b, i) + (int64_t)acol.at(b, l) * this->A.ld];
+    return conj_of(A[(int64_t)acol.at(b, l) + (int64_t)arow.at(b, i) * this->A.ld]);
+  }
 };
 
 template <typename T>

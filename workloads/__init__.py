@@ -23,4 +23,6 @@ from .problems import (  # noqa: F401
     polynomial_field,
     sharp_source_3d,
     adaptive_3d,
+    grid_interp_matrix,
+    helmholtz_theta_2d,
 )

@@ -211,6 +211,64 @@ def helmholtz_bumps_2d(seed: int = 1, k: float = 20.0, eta: Optional[float] = No
                          "direction": d.tolist()})
 
 
+def grid_interp_matrix(x: np.ndarray, n: int = 64, lo=(-1.0, -1.0), hi=(1.0, 1.0)):
+    """Sparse (len(x) x n^2) matrix of tensor cubic Lagrange interpolation from
+    an n x n grid of values on [lo, hi] (grid point (i, j) at lo + (i, j) h,
+    h = (hi - lo) / (n - 1); flattened index i + n j) to the points x.  Each
+    point uses the 4 x 4 grid points around it (shifted inward at the edges).
+    Linear in the grid values, so its transpose is the exact adjoint."""
+    import scipy.sparse as sps
+    x = np.atleast_2d(x)
+    m = x.shape[0]
+    rows, cols, vals = [], [], []
+    w_axes, i_axes = [], []
+    for a in range(2):
+        h = (hi[a] - lo[a]) / (n - 1)
+        t = (x[:, a] - lo[a]) / h
+        i0 = np.clip(np.floor(t).astype(int) - 1, 0, n - 4)
+        loc = t - i0                       # position within the 4 stencil points 0..3
+        w = np.ones((m, 4))
+        for k in range(4):
+            for j in range(4):
+                if j != k:
+                    w[:, k] *= (loc - j) / (k - j)
+        w_axes.append(w)
+        i_axes.append(i0)
+    for kx in range(4):
+        for ky in range(4):
+            rows.append(np.arange(m))
+            cols.append((i_axes[0] + kx) + n * (i_axes[1] + ky))
+            vals.append(w_axes[0][:, kx] * w_axes[1][:, ky])
+    return sps.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(m, n * n))
+
+
+def helmholtz_theta_2d(seed: int = 5, k: float = 20.0, n: int = 64):
+    """Differentiation workload: the operator of helmholtz_bumps_2d(seed=1)
+    with its refractive field n(x) replaced by theta, an n x n grid of values
+    carried to the nodes by grid_interp_matrix; c = k^2 (1 - I theta).
+    Returns the base problem (source, boundary data, eta), theta_true (a
+    smooth seeded field: the sum of 6 Gaussian bumps of width 0.15 and
+    amplitude U[0.2, 0.5] sampled on the grid), theta_0 (zero field) and the
+    16 seeded grid entries and the seeded unit direction used for the
+    finite-difference check."""
+    base = helmholtz_bumps_2d(seed=1, k=k)
+    rng = np.random.default_rng(seed)
+    zc = rng.uniform(-0.7, 0.7, size=(6, 2))
+    am = rng.uniform(0.2, 0.5, size=6)
+    g1 = np.linspace(-1.0, 1.0, n)
+    X, Y = np.meshgrid(g1, g1, indexing="ij")
+    th = np.zeros((n, n))
+    for zi, ai in zip(zc, am):
+        th += ai * np.exp(-((X - zi[0]) ** 2 + (Y - zi[1]) ** 2) / (2 * 0.15 ** 2))
+    theta_true = th.reshape(-1, order="F")          # index i + n j
+    theta_0 = np.zeros(n * n)
+    probe = rng.choice(n * n, 16, replace=False)
+    direction = rng.standard_normal(n * n)
+    direction /= np.linalg.norm(direction)
+    return {"problem": base, "k": k, "n": n, "theta_true": theta_true, "theta_0": theta_0,
+            "probe": probe, "direction": direction}
+
+
 # ---------------------------------------------------------------------------
 # workload 3: 3D divergence-form elliptic problem
 # ---------------------------------------------------------------------------
