@@ -110,7 +110,7 @@ def parse():
         spec["workload"] = spec["workload"].replace(f"depth{WORKLOADS[args.workload]['depth']}",
                                                     f"depth{args.depth}")
         spec["cpu_depth"] = min(spec["cpu_depth"], args.depth)
-    spec["root"] = args.root if spec["depth"] >= 0 else "explicit"
+    spec["root"] = args.root
     args.spec = spec
     return args
 

@@ -113,8 +113,8 @@ typedef struct {
   int lazy_root;        /* 1: keep the root's [C | h_int] and D's factors instead of
                            forming S = -D^{-1} C (Eq. "merge outputs 2"); each
                            solve then applies D^{-1} to C g + h_int.  Saves the
-                           root's multi-RHS solve in hps_build; uniform trees,
-                           ignored with want_root_map.  With up to 8 right-hand
+                           root's multi-RHS solve in hps_build; uniform and
+                           adaptive trees, ignored with want_root_map.  With up to 8 right-hand
                            sides the root's triangular solves run as one
                            flag-ordered launch per triangle; if one of its
                            bounded waits gives up, that hps_solve (host u) or
@@ -126,7 +126,15 @@ typedef struct {
                            up to 8 graphs per handle.  Uniform trees; ignored
                            while profiling.  The caller may change the data
                            behind the pointers between calls, not the pointers. */
-  int reserved[3];
+  int iti_leaf;         /* ItI leaf solves: 0 automatic, 1 the complex LU of the whole
+                           leaf matrix B = [G; L(I_i,:)] (Algorithm "2D ItI local
+                           solve"), 2 elimination of the interior nodes (a real
+                           LU of L(I_i,I_i) and a complex Schur complement on the
+                           boundary nodes; same solution, about a third of the
+                           flops).  Automatic takes 2 when the leaf Dirichlet
+                           problem is far from resonance: max c <= min a * pi^2 /
+                           (2 h^2) and max |b| h <= min a, h the leaf side. */
+  int reserved[2];
 } hps_options;
 
 /* Kernel classes reported by hps_kernel_stats. */

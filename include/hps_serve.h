@@ -12,8 +12,9 @@
  *     (hps_plan_bytes) has room.
  * Solve requests that wait on the same operator are merged into one batched
  * solve (hps_solve_batched) of up to max_batch right-hand sides, and batches
- * of different operators run concurrently on n_streams CUDA streams; a build
- * runs on its own host thread and stream while solves continue.  Requests
+ * of different operators run concurrently on n_streams CUDA streams; builds
+ * run on n_builders host threads, each with its own stream, while solves
+ * continue.  Requests
  * that arrive while others run are admitted as soon as a stream and the
  * operator are free (continuous batching).  Requests on one slot take effect
  * in submission order: a solve submitted after a build of its slot uses the
@@ -24,7 +25,7 @@
  * until the request's ticket has completed (hps_server_wait or a poll that
  * does not return HPS_PENDING).
  *
- * Threads: the server runs two host threads (scheduler and builder).  The
+ * Threads: the server runs a scheduler thread and n_builders builder threads.  The
  * submit, wait and poll calls may be made from any thread.  Operators'
  * handles belong to the server.
  */
@@ -49,7 +50,9 @@ typedef struct {
                            device memory when the server is created                  */
   int lazy_root;        /* build operators with hps_options.lazy_root when the build
                            request passes no options                                 */
-  int reserved[7];
+  int n_builders;       /* builds that may run at once, each on its own host thread
+                           and stream (1..8; 0 -> 2)                                 */
+  int reserved[6];
 } hps_server_options;
 
 typedef struct {

@@ -175,7 +175,7 @@ def make_coeffs(kind: int, a=None, b=None, c=None, eta: float = 0.0, keep=None, 
 
 def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None, f=None,
               eta: float = 0.0, want_root_map: bool = False, profile: bool = False,
-              lazy_root: bool = False, graph_solve: bool = False, stream=None) -> Handle:
+              lazy_root: bool = False, graph_solve: bool = False, iti_leaf: int = 0, stream=None) -> Handle:
     """Build the solution operator; coefficient and source arrays hold
     n_leaves * p^dim values (leaf-major, tensor node order)."""
     nl, ppl, _ = hps_sizes(tree, p, q)
@@ -189,6 +189,7 @@ def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None,
     opts.profile = 1 if profile else 0
     opts.lazy_root = 1 if lazy_root else 0
     opts.graph_solve = 1 if graph_solve else 0
+    opts.iti_leaf = int(iti_leaf)
     out = c_void_p()
     st = _stream(stream)
     _check(_capi.lib().hps_build(byref(tree), p, q, byref(cf), fp, byref(opts), st, byref(out)),
@@ -344,12 +345,13 @@ class Server:
     waited for."""
 
     def __init__(self, n_slots: int = 16, n_streams: int = 4, max_batch: int = 8, hbm_budget: int = 0,
-                 lazy_root: bool = False):
+                 lazy_root: bool = False, n_builders: int = 2):
         o = _capi.hps_server_options()
         o.version = 1
         o.n_slots, o.n_streams, o.max_batch = n_slots, n_streams, max_batch
         o.hbm_budget = hbm_budget
         o.lazy_root = 1 if lazy_root else 0
+        o.n_builders = n_builders
         out = c_void_p()
         _check(_capi.lib().hps_server_create(byref(o), byref(out)), "hps_server_create")
         self.ptr = out.value

@@ -46,7 +46,7 @@ class hps_coeffs(ctypes.Structure):
 
 class hps_options(ctypes.Structure):
     _fields_ = [("version", c_int), ("want_root_map", c_int), ("profile", c_int),
-                ("lazy_root", c_int), ("graph_solve", c_int), ("reserved", c_int * 3)]
+                ("lazy_root", c_int), ("graph_solve", c_int), ("iti_leaf", c_int), ("reserved", c_int * 2)]
 
 
 class hps_kernel_stat(ctypes.Structure):
@@ -60,7 +60,7 @@ class hps_trace_rec(ctypes.Structure):
 
 class hps_server_options(ctypes.Structure):
     _fields_ = [("version", c_int), ("n_slots", c_int), ("n_streams", c_int), ("max_batch", c_int),
-                ("hbm_budget", c_int64), ("lazy_root", c_int), ("reserved", c_int * 7)]
+                ("hbm_budget", c_int64), ("lazy_root", c_int), ("n_builders", c_int), ("reserved", c_int * 6)]
 
 
 class hps_ticket_info(ctypes.Structure):

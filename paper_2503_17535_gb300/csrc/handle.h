@@ -54,6 +54,25 @@ struct AChildDev {
   void* Tp = nullptr;         // np x (np + 1) projected [T | h]
 };
 
+// ItI leaves solved by elimination of the interior nodes (iti_leaf.cu): the
+// real LU of L(I_i, I_i), W = L_ii^{-1} L(I_i, boundary), the complex LU of
+// the boundary Schur complement S, and the shared real impedance-row blocks.
+struct ItiElim {
+  bool on = false;
+  int ni = 0, no = 0;                      // interior nodes, boundary nodes (owner order)
+  double *Goe = nullptr, *Goi = nullptr;   // shared: no x no, no x ni (real parts)
+  double* LU = nullptr;                    // [leaf] ni x ni
+  int *ipiv = nullptr, *perm = nullptr;
+  double* W = nullptr;                     // [leaf] ni x no
+  cplx* S = nullptr;                       // [leaf] no x no (LU)
+  int *ipivS = nullptr, *permS = nullptr;
+  LuWork luw, luwS;
+  int G = 1, GS = 1;
+  int cap = 0;                             // columns the workspace holds
+  double *z = nullptr, *z2 = nullptr, *t = nullptr;
+  cplx *q = nullptr, *q2 = nullptr;
+};
+
 // Merges of one tree level with the same interface sizes: their dense
 // factorisations and solves run as one batched call (pointer arrays).
 struct AGroup {
@@ -82,6 +101,7 @@ struct AMergeDev {
   int *ipiv = nullptr, *perm = nullptr, *info = nullptr;
   int G = 1;
   LuWork luw;
+  bool lazy = false;  // root only: X holds [C | h_int]; D^{-1} is applied per solve
   // solve workspace (nrhs columns)
   void *r = nullptr, *x = nullptr, *hp = nullptr, *gint = nullptr, *g = nullptr;
 };
@@ -89,6 +109,7 @@ struct AMergeDev {
 }  // namespace hps
 
 using hps::ATree;
+using hps::ItiElim;
 using hps::cplx;
 using hps::DtnLeafRef;
 using hps::ItiLeafRef;
@@ -138,6 +159,7 @@ struct hps_handle {
   };
   std::vector<GraphEntry> graphs;
   bool capturing = false;
+  hps::ItiElim ie;               // ItI leaves by interior elimination (when on)
   hps::TrsvWork trsv;            // flag-ordered solves with a lazy root's factors
   int* trsv_err_host = nullptr;  // host-mapped error word of trsv (cudaHostAlloc)
   cudaStream_t last = nullptr;
@@ -175,6 +197,15 @@ hps_status ensure_solve_ws(hps_handle* h, int nrhs);
 hps_status adjoint_solve(hps_handle* h, int nrhs, const void* ubar, void* gbar, void* fbar, cudaStream_t st);
 hps_status coeff_gradient(hps_handle* h, int nrhs, const void* u, const void* fbar, double* ga, double* gb,
                           double* gc, cudaStream_t st);
+
+// ItI interior elimination (iti_leaf.cu): whether to use it for these
+// coefficients (hps_options.iti_leaf, or the resonance check), the setup
+// (factorisations), X = B^{-1} R and Rbar = B^{-H} Xbar per leaf (R in B's
+// rows order, X in node order; p^2 x m per leaf).
+bool iti_elim_safe(hps_handle* h, const Coeffs& co, cudaStream_t st, hps_status* err);
+hps_status iti_elim_setup(hps_handle* h, const Coeffs& co, cudaStream_t st, Prof* pf);
+hps_status iti_elim_apply(hps_handle* h, const cplx* R, cplx* X, int m, cudaStream_t st, Prof* pf);
+hps_status iti_elim_apply_h(hps_handle* h, const cplx* Xb, cplx* Rb, int m, cudaStream_t st, Prof* pf);
 
 #define HPS_TRY(call)                                   \
   do {                                                  \

@@ -351,8 +351,27 @@ hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs*
       BOp<T> DD = bopp<T>(A.dD, nI);
       BOp<T> XX = bopp<T>(A.dX, nI);
       HPS_CUDA(getrf<T>(DD, nI, nbat, A.ipiv, A.perm, A.info, h->dev_err, A.G, A.luw, st, pf));
-      HPS_CUDA(permute_rows<T>(bopp<T>(A.dR, nI), XX, A.perm, nI, ne + 1, nbat, st, pf));
-      HPS_CUDA(getrs_inplace<T>(DD, nI, XX, ne + 1, nbat, st, pf));
+      AMergeDev& M0 = h->am[(size_t)A.members[0]];
+      if (nbat == 1 && M0.node == 0 && h->opts.lazy_root && !h->opts.want_root_map) {
+        // lazy root: keep [C | h_int] (in X's storage) and D's factors
+        M0.lazy = true;
+        HPS_CUDA(cudaMemcpyAsync(M0.X, Rof[(size_t)A.members[0]], (size_t)nI * (ne + 1) * sizeof(T),
+                                 cudaMemcpyDeviceToDevice, st));
+        const int nf = (nI + 31) / 32;
+        h->trsv.flags = (unsigned*)dalloc(h, (size_t)nf * sizeof(unsigned));
+        if (!h->trsv.flags) return HPS_ERR_OOM;
+        HPS_CUDA(cudaMemsetAsync(h->trsv.flags, 0, (size_t)nf * sizeof(unsigned), st));
+        h->trsv.nflags = nf;
+        HPS_CUDA(cudaHostAlloc((void**)&h->trsv_err_host, sizeof(int), cudaHostAllocMapped));
+        *h->trsv_err_host = 0;
+        int* dp = nullptr;
+        HPS_CUDA(cudaHostGetDevicePointer((void**)&dp, h->trsv_err_host, 0));
+        h->trsv.host_err = h->trsv_err_host;
+        h->trsv.dev_err = dp;
+      } else {
+        HPS_CUDA(permute_rows<T>(bopp<T>(A.dR, nI), XX, A.perm, nI, ne + 1, nbat, st, pf));
+        HPS_CUDA(getrs_inplace<T>(DD, nI, XX, ne + 1, nbat, st, pf));
+      }
       std::vector<T*> vTP;
       for (int mi : A.members) vTP.push_back((T*)h->am[(size_t)mi].TP);
       A.dTP = upload(h, vTP, st);
@@ -467,6 +486,7 @@ static hps_status adaptive_ws(hps_handle* h, int nrhs) {
 hps_status adaptive_solve(hps_handle* h, int nrhs, const void* g_in, const void* f_in, void* u_out,
                           cudaStream_t st) {
   using T = double;
+  if (h->trsv_err_host && *(volatile int*)h->trsv_err_host) return HPS_ERR_TIMEOUT;
   hps_status rs = adaptive_ws(h, nrhs);
   if (rs != HPS_OK) return rs;
   Prof* pf = &h->prof;
@@ -532,6 +552,7 @@ hps_status adaptive_solve(hps_handle* h, int nrhs, const void* g_in, const void*
       for (size_t gi = g0; gi < g1; ++gi) {
         const AGroup& G = h->ag[gi];
         const int nbat = (int)G.members.size();
+        if (h->am[(size_t)G.members[0]].lazy) continue;  // the root's D^{-1} runs in the downward pass
         BOp<T> XB = bopp<T>(G.dx, G.n_int);
         HPS_CUDA(permute_rows<T>(bopp<T>(G.dr, G.n_int), XB, G.perm, G.n_int, nrhs, nbat, st, pf));
         HPS_CUDA(getrs_inplace<T>(bopp<T>(G.dD, G.n_int), G.n_int, XB, nrhs, nbat, st, pf));
@@ -548,8 +569,20 @@ hps_status adaptive_solve(hps_handle* h, int nrhs, const void* g_in, const void*
     AMergeDev& M = h->am[k2];
     const ANode& nd = at.nodes[M.node];
     const T* gpar = (M.node == 0) ? g : (const T*)M.g;
-    HPS_CUDA(down_gint<T>((const T*)M.X, newf ? (const T*)M.x : nullptr, gpar, 1, M.n_ext, M.n_int, nrhs,
-                          (T*)M.gint, st, pf));
+    if (M.lazy) {
+      // X holds [C | h_int]: t = -(C g + h), then g_int = D^{-1} t
+      HPS_CUDA(down_gint<T>((const T*)M.X, newf ? (const T*)M.r : nullptr, gpar, 1, M.n_ext, M.n_int, nrhs,
+                            (T*)M.x, st, pf));
+      BOp<T> GI = bop<T>((T*)M.gint, 0, M.n_int);
+      HPS_CUDA(permute_rows<T>(bop<T>((T*)M.x, 0, M.n_int), GI, M.perm, M.n_int, nrhs, 1, st, pf));
+      if (trsv_flags_applicable<T>(M.n_int, nrhs, 1, h->trsv))
+        HPS_CUDA(getrs_flags<T>((const T*)M.D, M.n_int, M.n_int, (T*)M.gint, M.n_int, nrhs, h->trsv, st, pf));
+      else
+        HPS_CUDA(getrs_inplace<T>(bop<T>((T*)M.D, 0, M.n_int), M.n_int, GI, nrhs, 1, st, pf));
+    } else {
+      HPS_CUDA(down_gint<T>((const T*)M.X, newf ? (const T*)M.x : nullptr, gpar, 1, M.n_ext, M.n_int, nrhs,
+                            (T*)M.gint, st, pf));
+    }
     for (int c = 0; c < 8; ++c) {
       const AChildDev& CD = M.ch[c];
       HPS_CUDA(down_children<T>(gpar, (const T*)M.gint, 1, 1, CD.pj.np, M.n_ext, M.n_int, nrhs, CD.ext, CD.var,

@@ -136,46 +136,6 @@ __global__ void k_particular_rhs_adj(LeafConsts k, int64_t nl, int nrhs, const T
   }
 }
 
-// dst(perm[i], j) = src(i, j): the inverse of permute_rows.
-template <typename T>
-__global__ void k_permute_rows_inv(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrhs, int batch) {
-  const int64_t per = (int64_t)n * nrhs;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch; e += (int64_t)gridDim.x * blockDim.x) {
-    const int b = (int)(e / per);
-    const int rc = (int)(e % per);
-    const int i = rc % n, j = rc / n;
-    dst.item(b)[perm[(int64_t)b * n + i] + (int64_t)j * dst.ld] = src.item(b)[i + (int64_t)j * src.ld];
-  }
-}
-
-// Diagonal-block solves with the conjugate transposes of the LU factors:
-// LOWER: U^H w = y (U^H is lower triangular); else L^H z = w (upper, unit).
-template <typename T, bool LOWER>
-__global__ void k_trsm_diag_h(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch) {
-  for (int b = blockIdx.y; b < batch; b += gridDim.y) {
-    const T* Lb = LU.item(b);
-    T* Xb = X.item(b);
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrhs; j += gridDim.x * blockDim.x) {
-      T* col = Xb + (int64_t)j * X.ld + p0;
-      if (LOWER) {
-        for (int r = 0; r < pb; ++r) {
-          T s = col[r];
-          for (int c = 0; c < r; ++c) s = fmsc(s, conj_of(Lb[(int64_t)(p0 + c) + (int64_t)(p0 + r) * LU.ld]), col[c]);
-          const T d = conj_of(Lb[(int64_t)(p0 + r) + (int64_t)(p0 + r) * LU.ld]);
-          col[r] = is_zero(d) ? T(0.0) : s * recip(d);
-        }
-      } else {
-        for (int r = pb - 1; r >= 0; --r) {
-          T s = col[r];
-          for (int c = r + 1; c < pb; ++c)
-            s = fmsc(s, conj_of(Lb[(int64_t)(p0 + c) + (int64_t)(p0 + r) * LU.ld]), col[c]);
-          col[r] = s;
-        }
-      }
-    }
-  }
-}
-
 // coefficient gradients at the interior nodes: -sum_c Re(conj(fbar) * (d/dcoef of L u))
 template <typename T>
 __global__ void k_coeff_grad(LeafConsts k, int64_t nl, int nrhs, const T* u, const T* fbar, double* ga, double* gb,
@@ -219,55 +179,6 @@ __global__ void k_coeff_grad(LeafConsts k, int64_t nl, int nrhs, const T* u, con
 }
 
 // ---- host helpers
-
-template <typename T>
-cudaError_t permute_rows_inv(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrhs, int batch, cudaStream_t st) {
-  k_permute_rows_inv<T><<<gridn((int64_t)n * nrhs * batch), 256, 0, st>>>(src, dst, perm, n, nrhs, batch);
-  return cudaGetLastError();
-}
-
-// X <- (U^H)^{-1} then (L^H)^{-1}: the conjugate transpose of getrs_inplace
-// (without the row permutation, which the caller applies after).
-template <typename T>
-cudaError_t getrs_h(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaStream_t st, Prof* pf) {
-  const int pb0 = 32;
-  const int by = std::min(batch, 65535);
-  const int bx = std::min((nrhs + 127) / 128, 1024);
-  cudaError_t e;
-  for (int p0 = 0; p0 < n; p0 += pb0) {
-    const int pb = std::min(pb0, n - p0);
-    k_trsm_diag_h<T, true><<<dim3(bx, by), 128, 0, st>>>(LU, X, p0, pb, nrhs, batch);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int rest = n - p0 - pb;
-    if (rest > 0) {
-      GemmArgs<T> g;
-      g.M = rest; g.N = nrhs; g.K = pb; g.batch = batch;
-      g.A = shifted(LU, (int64_t)p0 + (int64_t)(p0 + pb) * LU.ld);  // U(p0 .., p0 + pb ..)
-      g.ta = true;
-      g.B = shifted(X, (int64_t)p0);
-      g.C = shifted(X, (int64_t)(p0 + pb));
-      g.alpha = T(-1.0); g.beta = T(1.0);
-      if ((e = gemm<T>(g, st, pf)) != cudaSuccess) return e;
-    }
-  }
-  const int npan = (n + pb0 - 1) / pb0;
-  for (int pi = npan - 1; pi >= 0; --pi) {
-    const int p0 = pi * pb0, pb = std::min(pb0, n - p0);
-    k_trsm_diag_h<T, false><<<dim3(bx, by), 128, 0, st>>>(LU, X, p0, pb, nrhs, batch);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (p0 > 0) {
-      GemmArgs<T> g;
-      g.M = p0; g.N = nrhs; g.K = pb; g.batch = batch;
-      g.A = shifted(LU, (int64_t)p0);  // L(p0 .., 0 ..)
-      g.ta = true;
-      g.B = shifted(X, (int64_t)p0);
-      g.C = X;
-      g.alpha = T(-1.0); g.beta = T(1.0);
-      if ((e = gemm<T>(g, st, pf)) != cudaSuccess) return e;
-    }
-  }
-  return cudaSuccess;
-}
 
 // The transpose of one child-block product of the ItI D route:
 // forward C(eq) -= T_child(pts, pts) B(var); here Bbar(var) -= T^H Cbar(eq).
@@ -479,10 +390,14 @@ hps_status adjoint_impl(hps_handle* h, int nrhs, const void* ub_in, void* gbar_o
     HPS_CUDA(gemm<T>(gl, st, pf));
   }
   // (1) leaf particular solves: tmpbar = P^T L^{-H} U^{-H} xfbar; fbar
-  BOp<T> LA = bop<T>((T*)h->leafA, (int64_t)nlu * nlu, nlu);
-  BOp<T> XF = bop<T>(xf, (int64_t)xr * nrhs, xr);
-  HPS_CUDA(getrs_h<T>(LA, nlu, XF, nrhs, (int)nl, st, pf));
-  HPS_CUDA(permute_rows_inv<T>(XF, bop<T>(tmp, (int64_t)xr * nrhs, xr), h->leaf_perm, nlu, nrhs, (int)nl, st));
+  if (h->ie.on) {
+    HPS_TRY(iti_elim_apply_h(h, (const cplx*)xf, (cplx*)tmp, nrhs, st, pf));
+  } else {
+    BOp<T> LA = bop<T>((T*)h->leafA, (int64_t)nlu * nlu, nlu);
+    BOp<T> XF = bop<T>(xf, (int64_t)xr * nrhs, xr);
+    HPS_CUDA(getrs_h<T>(LA, nlu, XF, nrhs, (int)nl, st, pf));
+    HPS_CUDA(permute_rows_inv<T>(XF, bop<T>(tmp, (int64_t)xr * nrhs, xr), h->leaf_perm, nlu, nrhs, (int)nl, st));
+  }
   HPS_CUDA(cudaMemsetAsync(fbar, 0, ubytes, st));
   k_particular_rhs_adj<T><<<gridn(nl * nrhs * h->lc.ni), 256, 0, st>>>(h->lc, nl, nrhs, tmp, fbar, ITI);
   HPS_CUDA(cudaGetLastError());

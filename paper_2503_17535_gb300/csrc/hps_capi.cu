@@ -160,11 +160,20 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
   // ---- leaf stage (Algorithm "local solve")
   const int64_t nl = h->nl;
   const int nlu = h->nlu_leaf, nb = h->nb, xr = h->xrows_leaf;
-  h->leafA = dalloc(h, (size_t)nl * nlu * nlu * sizeof(T));
+  bool elim = false;
+  if (ITI) {
+    hps_status es = HPS_OK;
+    elim = iti_elim_safe(h, co, st, &es);
+    if (es != HPS_OK) return es;
+  }
+  if (!elim) {
+    h->leafA = dalloc(h, (size_t)nl * nlu * nlu * sizeof(T));
+    h->leaf_ipiv = (int*)dalloc(h, (size_t)nl * nlu * sizeof(int));
+    h->leaf_perm = (int*)dalloc(h, (size_t)nl * nlu * sizeof(int));
+    if (!h->leafA || !h->leaf_ipiv || !h->leaf_perm) return HPS_ERR_OOM;
+  }
   h->leafX = dalloc(h, (size_t)nl * xr * (nb + 1) * sizeof(T));
   h->leafTH = dalloc(h, (size_t)nl * nb * (nb + 1) * sizeof(T));
-  h->leaf_ipiv = (int*)dalloc(h, (size_t)nl * nlu * sizeof(int));
-  h->leaf_perm = (int*)dalloc(h, (size_t)nl * nlu * sizeof(int));
   h->leaf_info = (int*)dalloc(h, (size_t)nl * sizeof(int));
   // scratch: largest R / RHS buffer of any stage
   size_t scratch = (size_t)nl * xr * (nb + 1);
@@ -179,29 +188,35 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
     }
   }
   h->scratch = dalloc(h, scratch * sizeof(T));
-  if (!h->leafA || !h->leafX || !h->leafTH || !h->leaf_ipiv || !h->leaf_perm || !h->leaf_info || !h->scratch)
-    return HPS_ERR_OOM;
+  if (!h->leafX || !h->leafTH || !h->leaf_info || !h->scratch) return HPS_ERR_OOM;
   HPS_CUDA(cudaMemsetAsync(h->leaf_info, 0, (size_t)nl * sizeof(int), st));
   T* RHS = (T*)h->scratch;
-  if (!ITI) {
+  BOp<T> LX = bop<T>((T*)h->leafX, (int64_t)xr * (nb + 1), xr);
+  if (elim) {
+    // ItI by elimination of the interior nodes: X = B^{-1} [[P, 0], [0, f_i]]
+    HPS_TRY(iti_elim_setup(h, co, st, pf));
+    HPS_CUDA(leaf_iti_rhs(k, nl, (const cplx*)f, (cplx*)RHS, st, pf));
+    HPS_TRY(iti_elim_apply(h, (const cplx*)RHS, (cplx*)h->leafX, nb + 1, st, pf));
+  } else if (!ITI) {
     HPS_CUDA(leaf_dtn_assemble(k, nl, co, (const double*)f, (double*)h->leafA, (double*)RHS, st, pf));
   } else {
     HPS_CUDA(leaf_iti_assemble(k, nl, co, (const cplx*)f, (cplx*)h->leafA, (cplx*)RHS, st, pf));
   }
-  h->leaf_G = lu_group_size<T>(nlu, (int)std::min<int64_t>(nl, 1 << 30), h->num_sms);
-  if (h->leaf_G > 1) {
-    h->leaf_luw.bars = (unsigned*)dalloc(h, sizeof(unsigned) * 2 * nl);
-    h->leaf_luw.pub_bytes = lu_pub_bytes<T>(nlu, (int)nl, h->leaf_G);
-    h->leaf_luw.pub = dalloc(h, h->leaf_luw.pub_bytes);
-    if (!h->leaf_luw.bars || !h->leaf_luw.pub) return HPS_ERR_OOM;
-    HPS_CUDA(cudaMemsetAsync(h->leaf_luw.bars, 0, sizeof(unsigned) * 2 * nl, st));
+  if (!elim) {
+    h->leaf_G = lu_group_size<T>(nlu, (int)std::min<int64_t>(nl, 1 << 30), h->num_sms);
+    if (h->leaf_G > 1) {
+      h->leaf_luw.bars = (unsigned*)dalloc(h, sizeof(unsigned) * 2 * nl);
+      h->leaf_luw.pub_bytes = lu_pub_bytes<T>(nlu, (int)nl, h->leaf_G);
+      h->leaf_luw.pub = dalloc(h, h->leaf_luw.pub_bytes);
+      if (!h->leaf_luw.bars || !h->leaf_luw.pub) return HPS_ERR_OOM;
+      HPS_CUDA(cudaMemsetAsync(h->leaf_luw.bars, 0, sizeof(unsigned) * 2 * nl, st));
+    }
+    BOp<T> LA = bop<T>((T*)h->leafA, (int64_t)nlu * nlu, nlu);
+    HPS_CUDA(getrf<T>(LA, nlu, (int)nl, h->leaf_ipiv, h->leaf_perm, h->leaf_info, h->dev_err, h->leaf_G,
+                      h->leaf_luw, st, pf));
+    HPS_CUDA(permute_rows<T>(bop<T>(RHS, (int64_t)xr * (nb + 1), xr), LX, h->leaf_perm, nlu, nb + 1, (int)nl, st, pf));
+    HPS_CUDA(getrs_inplace<T>(LA, nlu, LX, nb + 1, (int)nl, st, pf));
   }
-  BOp<T> LA = bop<T>((T*)h->leafA, (int64_t)nlu * nlu, nlu);
-  HPS_CUDA(getrf<T>(LA, nlu, (int)nl, h->leaf_ipiv, h->leaf_perm, h->leaf_info, h->dev_err, h->leaf_G,
-                    h->leaf_luw, st, pf));
-  BOp<T> LX = bop<T>((T*)h->leafX, (int64_t)xr * (nb + 1), xr);
-  HPS_CUDA(permute_rows<T>(bop<T>(RHS, (int64_t)xr * (nb + 1), xr), LX, h->leaf_perm, nlu, nb + 1, (int)nl, st, pf));
-  HPS_CUDA(getrs_inplace<T>(LA, nlu, LX, nb + 1, (int)nl, st, pf));
   {
     GemmArgs<T> g;
     g.M = nb; g.N = nb + 1; g.batch = (int)nl;
@@ -529,10 +544,14 @@ hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_i
     T* xf = (T*)h->ws_xf;
     T* tmp = (T*)h->ws_rhs;
     HPS_CUDA(leaf_particular_rhs<T>(h->lc, nl, nrhs, f, tmp, ITI, st, pf));
-    BOp<T> LA = bop<T>((T*)h->leafA, (int64_t)nlu * nlu, nlu);
     BOp<T> XF = bop<T>(xf, (int64_t)xr * nrhs, xr);
-    HPS_CUDA(permute_rows<T>(bop<T>(tmp, (int64_t)xr * nrhs, xr), XF, h->leaf_perm, nlu, nrhs, (int)nl, st, pf));
-    HPS_CUDA(getrs_inplace<T>(LA, nlu, XF, nrhs, (int)nl, st, pf));
+    if (h->ie.on) {
+      HPS_TRY(iti_elim_apply(h, (const cplx*)tmp, (cplx*)xf, nrhs, st, pf));
+    } else {
+      BOp<T> LA = bop<T>((T*)h->leafA, (int64_t)nlu * nlu, nlu);
+      HPS_CUDA(permute_rows<T>(bop<T>(tmp, (int64_t)xr * nrhs, xr), XF, h->leaf_perm, nlu, nrhs, (int)nl, st, pf));
+      HPS_CUDA(getrs_inplace<T>(LA, nlu, XF, nrhs, (int)nl, st, pf));
+    }
     GemmArgs<T> gl;
     gl.M = nb; gl.N = nrhs; gl.K = ITI ? (int)h->npts : xr; gl.batch = (int)nl;
     gl.A = ITI ? bop<T>((T*)h->dQH, 0, nb) : bop<T>((T*)h->dQi, 0, nb);

@@ -163,6 +163,89 @@ __global__ void k_leaf_iti_rhs(LeafConsts k, int64_t nl, const cplx* f, cplx* rh
   }
 }
 
+// L(I_i, boundary nodes in owner order): the interior rows of the leaf
+// operator on the boundary columns, for the ItI interior elimination.
+__global__ void k_leaf_iti_Lie(LeafConsts k, int64_t nl, Coeffs cf, double* Lie) {
+  const int64_t per = (int64_t)k.ni * k.nown;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nl * per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t leaf = e / per;
+    const int rc = (int)(e % per);
+    const int r = rc % k.ni, c = rc / k.ni;
+    const int i = k.Ii[r], j = k.own_node[c];
+    double a, b[3], cc;
+    load_coeffs(cf, leaf * k.npts + i, k.dim, &a, b, &cc);
+    Lie[e] = L_entry(k, k.s, a, b, cc, i, j);
+  }
+}
+
+// Per-block bounds of the coefficients: out[3 * block + {0, 1, 2}] =
+// (min a, max |b|, max c) over this block's share of the nodes.
+__global__ void k_coef_bounds(Coeffs cf, int dim, int64_t n, double* out) {
+  __shared__ double sa[256], sb[256], sc[256];
+  double amin = 1e300, bmax = 0.0, cmax = -1e300;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    amin = fmin(amin, cf.a ? cf.a[e] : 1.0);
+    for (int ax = 0; ax < dim; ++ax) bmax = fmax(bmax, cf.b[ax] ? fabs(cf.b[ax][e]) : 0.0);
+    cmax = fmax(cmax, cf.c ? cf.c[e] : 0.0);
+  }
+  sa[threadIdx.x] = amin;
+  sb[threadIdx.x] = bmax;
+  sc[threadIdx.x] = cmax;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sa[threadIdx.x] = fmin(sa[threadIdx.x], sa[threadIdx.x + o]);
+      sb[threadIdx.x] = fmax(sb[threadIdx.x], sb[threadIdx.x + o]);
+      sc[threadIdx.x] = fmax(sc[threadIdx.x], sc[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[3 * blockIdx.x] = sa[0];
+    out[3 * blockIdx.x + 1] = sb[0];
+    out[3 * blockIdx.x + 2] = sc[0];
+  }
+}
+
+cudaError_t leaf_assemble_Lii(const LeafConsts& k, int64_t nl, Coeffs cf, double* Lii, cudaStream_t st, Prof* pf) {
+  if (pf) pf->begin(st);
+  k_leaf_dtn_Lii<<<grid_for(nl * k.ni * k.ni), 256, 0, st>>>(k, nl, cf, Lii);
+  if (pf) pf->end(K_ASSEMBLE, 0.0, st);
+  return cudaGetLastError();
+}
+
+cudaError_t leaf_iti_Lie(const LeafConsts& k, int64_t nl, Coeffs cf, double* Lie, cudaStream_t st, Prof* pf) {
+  if (pf) pf->begin(st);
+  k_leaf_iti_Lie<<<grid_for(nl * k.ni * k.nown), 256, 0, st>>>(k, nl, cf, Lie);
+  if (pf) pf->end(K_ASSEMBLE, 0.0, st);
+  return cudaGetLastError();
+}
+
+cudaError_t leaf_iti_rhs(const LeafConsts& k, int64_t nl, const cplx* f, cplx* rhs, cudaStream_t st, Prof* pf) {
+  if (pf) pf->begin(st);
+  k_leaf_iti_rhs<<<grid_for(nl * k.npts * (k.nb + 1)), 256, 0, st>>>(k, nl, f, rhs);
+  if (pf) pf->end(K_ASSEMBLE, 0.0, st);
+  return cudaGetLastError();
+}
+
+cudaError_t coef_bounds(Coeffs cf, int dim, int64_t n, double* d_out, double* h_out, cudaStream_t st) {
+  constexpr int nblk = 64;
+  k_coef_bounds<<<nblk, 256, 0, st>>>(cf, dim, n, d_out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  double tmp[3 * nblk];
+  if ((e = cudaMemcpyAsync(tmp, d_out, sizeof(tmp), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  h_out[0] = 1e300; h_out[1] = 0.0; h_out[2] = -1e300;
+  for (int b = 0; b < nblk; ++b) {
+    h_out[0] = std::min(h_out[0], tmp[3 * b]);
+    h_out[1] = std::max(h_out[1], tmp[3 * b + 1]);
+    h_out[2] = std::max(h_out[2], tmp[3 * b + 2]);
+  }
+  return cudaSuccess;
+}
+
 cudaError_t leaf_iti_assemble(const LeafConsts& k, int64_t nl, Coeffs cf, const cplx* f, cplx* B,
                               cplx* rhs, cudaStream_t st, Prof* pf) {
   if (pf) pf->begin(st);

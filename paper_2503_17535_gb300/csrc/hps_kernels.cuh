@@ -40,6 +40,16 @@ cudaError_t leaf_dtn_assemble(const LeafConsts& k, int64_t nl, Coeffs cf, const 
 // ItI leaf: B = [G; L(I_i, :)] (nl x npts x npts) and RHS = [[P, 0], [0, f_i]].
 cudaError_t leaf_iti_assemble(const LeafConsts& k, int64_t nl, Coeffs cf, const cplx* f,
                               cplx* B, cplx* rhs, cudaStream_t st, Prof* pf);
+// Pieces of the ItI interior elimination: L(I_i, I_i) (as for DtN leaves),
+// L(I_i, boundary nodes in owner order) (nl x ni x nown) and the right-hand
+// sides [[P, 0], [0, f_i]] alone.
+cudaError_t leaf_assemble_Lii(const LeafConsts& k, int64_t nl, Coeffs cf, double* Lii, cudaStream_t st, Prof* pf);
+cudaError_t leaf_iti_Lie(const LeafConsts& k, int64_t nl, Coeffs cf, double* Lie, cudaStream_t st, Prof* pf);
+cudaError_t leaf_iti_rhs(const LeafConsts& k, int64_t nl, const cplx* f, cplx* rhs, cudaStream_t st, Prof* pf);
+// Bounds of the coefficients over n nodes: h_out = (min a, max |b_k|, max c)
+// (defaults a = 1, b = 0, c = 0 for missing arrays); d_out holds 192
+// doubles of device scratch.  Synchronises the stream.
+cudaError_t coef_bounds(Coeffs cf, int dim, int64_t n, double* d_out, double* h_out, cudaStream_t st);
 // Right-hand sides of the upward particular pass: DtN -f_i; ItI [0; f_i].
 // f is [nrhs][nl][npts]; out is per leaf an (rows x nrhs) column-major block.
 template <typename T>

@@ -781,6 +781,27 @@ size_t lu_pub_bytes(int n, int batch, int G) {
   return v + m + r + 256;
 }
 
+// Allow the panel kernel the device's whole opt-in shared memory once per
+// process.  Setting the attribute per launch to the launch's own size would
+// race between host threads that build concurrently (one thread's smaller
+// value landing between another's set and launch).
+template <typename T, bool COOP>
+cudaError_t panel_smem_limit() {
+  static const cudaError_t err = [] {
+    int dev = 0, mx = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_lu_panel<T, COOP>);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_lu_panel<T, COOP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               mx - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
+  }();
+  return err;
+}
+
 template <typename T>
 cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, unsigned* dev_err,
                   int G, const LuWork& w, cudaStream_t st, Prof* pf) {
@@ -808,9 +829,7 @@ cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, u
       T* pubv = reinterpret_cast<T*>(w.pub);
       double* pubm = reinterpret_cast<double*>(pubv + (size_t)batch * 2 * (G + 1) * nb0);
       int* pubr = reinterpret_cast<int*>(pubm + (size_t)batch * 2 * G);
-      e = cudaFuncSetAttribute(k_lu_panel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)std::max<size_t>(sm, 1024));
-      if (e != cudaSuccess) return e;
+      if ((e = panel_smem_limit<T, true>()) != cudaSuccess) return e;
       BOp<T> Aa = A;
       int nn = n, kk = k0, nbb = nb, GG = Gk;
       unsigned* bars = w.bars;
@@ -819,9 +838,7 @@ cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, u
                                       sm, st);
       if (e != cudaSuccess) return e;
     } else {
-      e = cudaFuncSetAttribute(k_lu_panel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)std::max<size_t>(sm, 1024));
-      if (e != cudaSuccess) return e;
+      if ((e = panel_smem_limit<T, false>()) != cudaSuccess) return e;
       k_lu_panel<T, false><<<batch, 256, sm, st>>>(A, n, k0, nb, 1, ipiv, info, nullptr, nullptr,
                                                    nullptr, nullptr, dev_err);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1222,6 +1239,104 @@ cudaError_t getrs_flags(const T* LU, int n, int ld, T* X, int ldx, int nrhs, Trs
   return cudaSuccess;
 }
 
+// ------------------------------------------------- conjugate transposes ----
+
+namespace {
+inline int grid_n(int64_t total, int threads = 256) {
+  int64_t b = (total + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 65535 * 8));
+}
+}  // namespace
+
+// dst(perm[i], j) = src(i, j): the inverse of permute_rows.
+template <typename T>
+__global__ void k_permute_rows_inv(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrhs, int batch) {
+  const int64_t per = (int64_t)n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * batch; e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / per);
+    const int rc = (int)(e % per);
+    const int i = rc % n, j = rc / n;
+    dst.item(b)[perm[(int64_t)b * n + i] + (int64_t)j * dst.ld] = src.item(b)[i + (int64_t)j * src.ld];
+  }
+}
+
+// Diagonal-block solves with the conjugate transposes of the LU factors:
+// LOWER: U^H w = y (U^H is lower triangular); else L^H z = w (upper, unit).
+template <typename T, bool LOWER>
+__global__ void k_trsm_diag_h(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch) {
+  for (int b = blockIdx.y; b < batch; b += gridDim.y) {
+    const T* Lb = LU.item(b);
+    T* Xb = X.item(b);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nrhs; j += gridDim.x * blockDim.x) {
+      T* col = Xb + (int64_t)j * X.ld + p0;
+      if (LOWER) {
+        for (int r = 0; r < pb; ++r) {
+          T s = col[r];
+          for (int c = 0; c < r; ++c) s = fmsc(s, conj_of(Lb[(int64_t)(p0 + c) + (int64_t)(p0 + r) * LU.ld]), col[c]);
+          const T d = conj_of(Lb[(int64_t)(p0 + r) + (int64_t)(p0 + r) * LU.ld]);
+          col[r] = is_zero(d) ? T(0.0) : s * recip(d);
+        }
+      } else {
+        for (int r = pb - 1; r >= 0; --r) {
+          T s = col[r];
+          for (int c = r + 1; c < pb; ++c)
+            s = fmsc(s, conj_of(Lb[(int64_t)(p0 + c) + (int64_t)(p0 + r) * LU.ld]), col[c]);
+          col[r] = s;
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t permute_rows_inv(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrhs, int batch, cudaStream_t st) {
+  k_permute_rows_inv<T><<<grid_n((int64_t)n * nrhs * batch), 256, 0, st>>>(src, dst, perm, n, nrhs, batch);
+  return cudaGetLastError();
+}
+
+// X <- (U^H)^{-1} then (L^H)^{-1}: the conjugate transpose of getrs_inplace
+// (without the row permutation, which the caller applies after).
+template <typename T>
+cudaError_t getrs_h(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaStream_t st, Prof* pf) {
+  const int pb0 = 32;
+  const int by = std::min(batch, 65535);
+  const int bx = std::min((nrhs + 127) / 128, 1024);
+  cudaError_t e;
+  for (int p0 = 0; p0 < n; p0 += pb0) {
+    const int pb = std::min(pb0, n - p0);
+    k_trsm_diag_h<T, true><<<dim3(bx, by), 128, 0, st>>>(LU, X, p0, pb, nrhs, batch);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int rest = n - p0 - pb;
+    if (rest > 0) {
+      GemmArgs<T> g;
+      g.M = rest; g.N = nrhs; g.K = pb; g.batch = batch;
+      g.A = shifted(LU, (int64_t)p0 + (int64_t)(p0 + pb) * LU.ld);  // U(p0 .., p0 + pb ..)
+      g.ta = true;
+      g.B = shifted(X, (int64_t)p0);
+      g.C = shifted(X, (int64_t)(p0 + pb));
+      g.alpha = T(-1.0); g.beta = T(1.0);
+      if ((e = gemm<T>(g, st, pf)) != cudaSuccess) return e;
+    }
+  }
+  const int npan = (n + pb0 - 1) / pb0;
+  for (int pi = npan - 1; pi >= 0; --pi) {
+    const int p0 = pi * pb0, pb = std::min(pb0, n - p0);
+    k_trsm_diag_h<T, false><<<dim3(bx, by), 128, 0, st>>>(LU, X, p0, pb, nrhs, batch);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (p0 > 0) {
+      GemmArgs<T> g;
+      g.M = p0; g.N = nrhs; g.K = pb; g.batch = batch;
+      g.A = shifted(LU, (int64_t)p0);  // L(p0 .., 0 ..)
+      g.ta = true;
+      g.B = shifted(X, (int64_t)p0);
+      g.C = X;
+      g.alpha = T(-1.0); g.beta = T(1.0);
+      if ((e = gemm<T>(g, st, pf)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
 // ------------------------------------------------------- instantiation ----
 
 #define HPS_INST(T)                                                                              \
@@ -1235,7 +1350,9 @@ cudaError_t getrs_flags(const T* LU, int n, int ld, T* X, int ldx, int nrhs, Trs
                                        Prof*);                                                   \
   template cudaError_t getrs_inplace<T>(BOp<T>, int, BOp<T>, int, int, cudaStream_t, Prof*);                   \
   template bool trsv_flags_applicable<T>(int, int, int, const TrsvWork&);                        \
-  template cudaError_t getrs_flags<T>(const T*, int, int, T*, int, int, TrsvWork&, cudaStream_t, Prof*);
+  template cudaError_t getrs_flags<T>(const T*, int, int, T*, int, int, TrsvWork&, cudaStream_t, Prof*); \
+  template cudaError_t permute_rows_inv<T>(BOp<T>, BOp<T>, const int*, int, int, int, cudaStream_t);    \
+  template cudaError_t getrs_h<T>(BOp<T>, int, BOp<T>, int, int, cudaStream_t, Prof*);
 
 HPS_INST(double)
 HPS_INST(cplx)

@@ -156,6 +156,15 @@ template <typename T>
 cudaError_t getrs_flags(const T* LU, int n, int ld, T* X, int ldx, int nrhs, TrsvWork& w, cudaStream_t st,
                         Prof* pf);
 
+// Conjugate transposes for the adjoint solves: dst(perm[i], j) = src(i, j),
+// and X <- (U^H)^{-1} then (L^H)^{-1} with the LU factors of getrf (the
+// caller applies the inverse row permutation afterwards).
+template <typename T>
+cudaError_t permute_rows_inv(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrhs, int batch,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t getrs_h(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaStream_t st, Prof* pf);
+
 // C = alpha * C + beta (identity added on the diagonal when diag != 0) helpers
 template <typename T>
 cudaError_t fill(BOp<T> C, int M, int N, int batch, T value, T diag, cudaStream_t st, Prof* pf);

@@ -8,9 +8,10 @@
 // to max_batch solve requests (all with or all without a new source) becomes
 // one hps_solve_batched on a free stream; a build is handed to the builder
 // thread.  Only one batch or build per slot is in flight, which keeps each
-// handle single-threaded, as hps.h requires.  The builder thread runs
+// handle single-threaded, as hps.h requires.  Each builder thread runs
 // hps_build on its own stream and releases the slot's previous operator
-// (hps_free synchronises the device, so that wait is kept off the scheduler).
+// (hps_free synchronises the device, so that wait is kept off the scheduler);
+// with several builders a small rebuild does not wait behind a large one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -117,17 +118,23 @@ struct hps_server {
   int64_t next_id = 1;
   std::vector<Slot> slots;
   std::vector<StreamCtx> streams;
-  std::thread sched, builder;
+  std::thread sched;
   bool stop = false;          // destroy: the scheduler drains, then exits
   bool builder_stop = false;  // set once the scheduler has exited
   int64_t outstanding = 0;    // submitted, not yet finished
   // builder hand-off (under mu)
-  Req* build_req = nullptr;
-  hps_handle* build_old = nullptr;
-  bool build_free_first = false;
-  bool build_done = false;
-  hps_handle* build_out = nullptr;
-  hps_status build_status = HPS_OK;
+  struct BuildJob {
+    Req* r = nullptr;
+    hps_handle* old = nullptr;  // the slot's operator while the build runs
+    bool free_first = false;    // old released before building (memory)
+    int64_t need = 0;           // reserved bytes
+    hps_handle* out = nullptr;
+    hps_status status = HPS_OK;
+  };
+  std::deque<BuildJob*> build_queue;
+  std::vector<BuildJob*> build_done_list;
+  int active_builds = 0;
+  std::vector<std::thread> builders;
   // accounting
   int64_t resident = 0;
   hps_server_stats stats{};
@@ -216,15 +223,16 @@ void complete_batch(hps_server* s, StreamCtx& sc) {
   sc.busy = false;
 }
 
-// Hand the build at the head of slot si to the builder, if memory admits it.
-// Returns false when the builder is busy.
+// Hand the build at the head of slot si to a builder, if memory admits it.
+// Returns false when nothing changed (every builder busy, or waiting for
+// memory that builds in flight still hold).
 bool dispatch_build(hps_server* s, int si) {
   Slot& sl = s->slots[si];
   Req* r = sl.q.front();
   int64_t need = 0;
   hps_status st = hps_plan_bytes(&r->tree, r->p, r->q, r->cf.kind, &need);
   std::unique_lock<std::mutex> lk(s->mu);
-  if (s->build_req) return false;
+  if (s->active_builds >= s->opts.n_builders) return false;
   if (st != HPS_OK) {
     sl.q.pop_front();
     lk.unlock();
@@ -235,20 +243,22 @@ bool dispatch_build(hps_server* s, int si) {
   if (s->resident + need > s->opts.hbm_budget) {
     if (sl.h && s->resident - sl.bytes + need <= s->opts.hbm_budget) {
       free_first = true;
-    } else if (s->resident - sl.bytes + need > s->opts.hbm_budget) {
+    } else if (s->active_builds > 0) {
+      return false;  // memory reserved by builds in flight comes back when they end
+    } else {
       sl.q.pop_front();
       lk.unlock();
       finish(s, r, HPS_ERR_OOM);
       return true;
-    } else {
-      return true;  // wait for memory held by builds in flight elsewhere
     }
   }
   sl.q.pop_front();
   r->t_start = s->now_ms();
-  s->build_req = r;
-  s->build_old = sl.h;
-  s->build_free_first = free_first;
+  hps_server::BuildJob* job = new hps_server::BuildJob();
+  job->r = r;
+  job->old = sl.h;
+  job->free_first = free_first;
+  job->need = need;
   if (free_first) {
     s->resident -= sl.bytes;
     sl.h = nullptr;
@@ -256,46 +266,44 @@ bool dispatch_build(hps_server* s, int si) {
   }
   s->resident += need;  // reserved until the build reports its real size
   sl.busy = true;
-  s->cv_build.notify_all();
+  ++s->active_builds;
+  s->build_queue.push_back(job);
+  s->cv_build.notify_one();
   return true;
 }
 
-void complete_build(hps_server* s) {
-  Req* r = nullptr;
-  hps_handle* h = nullptr;
-  hps_status st = HPS_OK;
+void complete_builds(hps_server* s) {
+  std::vector<hps_server::BuildJob*> done;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    if (!s->build_done) return;
-    r = s->build_req;
-    h = s->build_out;
-    st = s->build_status;
-    s->build_req = nullptr;
-    s->build_out = nullptr;
-    s->build_done = false;
-    int64_t need = 0;
-    hps_plan_bytes(&r->tree, r->p, r->q, r->cf.kind, &need);
-    s->resident -= need;
-    Slot& sl = s->slots[r->slot];
-    if (!s->build_free_first && s->build_old) {  // the builder released it after building
-      s->resident -= sl.bytes;
-      sl.h = nullptr;
-      sl.bytes = 0;
+    done.swap(s->build_done_list);
+    for (hps_server::BuildJob* job : done) {
+      Req* r = job->r;
+      --s->active_builds;
+      s->resident -= job->need;
+      Slot& sl = s->slots[r->slot];
+      if (job->status == HPS_OK) {
+        if (!job->free_first && job->old) {  // the builder released it after building
+          s->resident -= sl.bytes;
+          sl.h = nullptr;
+          sl.bytes = 0;
+        }
+        sl.h = job->out;
+        sl.bytes = hps_device_bytes(job->out);
+        sl.iti = r->cf.kind == HPS_ITI;
+        int64_t nl = 0, ppl = 0, nr = 0;
+        hps_sizes(&r->tree, r->p, r->q, &nl, &ppl, &nr);
+        sl.n_root = nr;
+        sl.n_pts = nl * ppl;
+        s->resident += sl.bytes;
+      }
+      sl.busy = false;
     }
-    s->build_old = nullptr;
-    if (st == HPS_OK) {
-      sl.h = h;
-      sl.bytes = hps_device_bytes(h);
-      sl.iti = r->cf.kind == HPS_ITI;
-      int64_t nl = 0, ppl = 0, nr = 0;
-      hps_sizes(&r->tree, r->p, r->q, &nl, &ppl, &nr);
-      sl.n_root = nr;
-      sl.n_pts = nl * ppl;
-      s->resident += sl.bytes;
-    }
-    sl.busy = false;
   }
-  finish(s, r, st);
+  for (hps_server::BuildJob* job : done) {
+    finish(s, job->r, job->status);
+    delete job;
+  }
 }
 
 void builder_main(hps_server* s) {
@@ -303,21 +311,16 @@ void builder_main(hps_server* s) {
   cudaStream_t bs = nullptr;
   cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
   for (;;) {
-    Req* r = nullptr;
-    hps_handle* old = nullptr;
-    bool free_first = false;
+    hps_server::BuildJob* job = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_build.wait(lk, [&] { return s->builder_stop || (s->build_req && !s->build_done); });
-      if (!s->build_req || s->build_done) {
-        if (s->builder_stop) break;
-        continue;
-      }
-      r = s->build_req;
-      old = s->build_old;
-      free_first = s->build_free_first;
+      s->cv_build.wait(lk, [&] { return s->builder_stop || !s->build_queue.empty(); });
+      if (s->build_queue.empty()) break;  // builder_stop
+      job = s->build_queue.front();
+      s->build_queue.pop_front();
     }
-    if (free_first && old) hps_free(old);
+    Req* r = job->r;
+    if (job->free_first && job->old) hps_free(job->old);
     hps_options o{};
     const hps_options* op = nullptr;
     if (r->has_opts) {
@@ -333,14 +336,13 @@ void builder_main(hps_server* s) {
       hps_free(h);
       h = nullptr;
     }
-    if (!free_first && old && st == HPS_OK) hps_free(old);
-    if (!free_first && old && st != HPS_OK) old = nullptr;  // keep the old operator
+    // on success the old operator goes; on failure the slot keeps it
+    if (!job->free_first && job->old && st == HPS_OK) hps_free(job->old);
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      s->build_out = h;
-      s->build_status = st;
-      if (!free_first && old == nullptr) s->build_old = nullptr;
-      s->build_done = true;
+      job->out = h;
+      job->status = st;
+      s->build_done_list.push_back(job);
     }
     s->cv_sched.notify_all();
   }
@@ -372,11 +374,11 @@ void sched_main(hps_server* s) {
       bool bd;
       {
         std::lock_guard<std::mutex> lk(s->mu);
-        bd = s->build_done;
-        inflight = inflight || s->build_req != nullptr;
+        bd = !s->build_done_list.empty();
+        inflight = inflight || s->active_builds > 0;
       }
       if (bd) {
-        complete_build(s);
+        complete_builds(s);
         progress = true;
       }
     }
@@ -413,7 +415,7 @@ void sched_main(hps_server* s) {
       if (inflight)
         s->cv_sched.wait_for(lk, std::chrono::microseconds(20));
       else
-        s->cv_sched.wait(lk, [&] { return s->stop || !s->incoming.empty() || s->build_done; });
+        s->cv_sched.wait(lk, [&] { return s->stop || !s->incoming.empty() || !s->build_done_list.empty(); });
     }
   }
 }
@@ -465,8 +467,9 @@ hps_status hps_server_create(const hps_server_options* opts, hps_server** out) {
   if (o.n_slots == 0) o.n_slots = 16;
   if (o.n_streams == 0) o.n_streams = 4;
   if (o.max_batch == 0) o.max_batch = 8;
+  if (o.n_builders == 0) o.n_builders = 2;
   if (o.n_slots < 1 || o.n_slots > 1024 || o.n_streams < 1 || o.n_streams > 64 || o.max_batch < 1 ||
-      o.max_batch > 256 || o.hbm_budget < 0)
+      o.max_batch > 256 || o.hbm_budget < 0 || o.n_builders < 1 || o.n_builders > 8)
     return HPS_ERR_INVALID;
   hps_server* s = new (std::nothrow) hps_server();
   if (!s) return HPS_ERR_OOM;
@@ -502,7 +505,7 @@ hps_status hps_server_create(const hps_server_options* opts, hps_server** out) {
     }
   }
   s->sched = std::thread(sched_main, s);
-  s->builder = std::thread(builder_main, s);
+  for (int i = 0; i < o.n_builders; ++i) s->builders.emplace_back(builder_main, s);
   *out = s;
   return HPS_OK;
 }
@@ -521,7 +524,8 @@ void hps_server_destroy(hps_server* s) {
     s->builder_stop = true;
   }
   s->cv_build.notify_all();
-  if (s->builder.joinable()) s->builder.join();
+  for (std::thread& b : s->builders)
+    if (b.joinable()) b.join();
   cudaSetDevice(s->device);
   for (StreamCtx& sc : s->streams) {
     if (sc.s) cudaStreamSynchronize(sc.s);

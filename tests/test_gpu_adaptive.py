@@ -45,7 +45,7 @@ def d(v):
     return torch.from_numpy(np.ascontiguousarray(v)).cuda()
 
 
-def gpu_solve(P, pr, leaves, p, f_solve=None):
+def gpu_solve(P, pr, leaves, p, f_solve=None, lazy=False):
     t = P.adaptive_tree(leaves, pr.lo, pr.hi)
     x, xb = P.hps_nodes(t, p, p - 2)
     nl, ppl, nr = P.hps_sizes(t, p, p - 2)
@@ -55,7 +55,7 @@ def gpu_solve(P, pr, leaves, p, f_solve=None):
     c = cf["c"].reshape(nl, ppl)
     f = pr.source(x).reshape(nl, ppl)
     g = pr.boundary(xb)
-    h = P.hps_build(t, p, p - 2, P.HPS_DTN, a=d(a), b=[d(bk) for bk in b], c=d(c), f=d(f))
+    h = P.hps_build(t, p, p - 2, P.HPS_DTN, a=d(a), b=[d(bk) for bk in b], c=d(c), f=d(f), lazy_root=lazy)
     u = torch.zeros((nl, ppl), dtype=torch.float64, device="cuda")
     P.hps_solve(h, d(g), u, f=None if f_solve is None else d(f_solve))
     torch.cuda.synchronize()
@@ -63,11 +63,12 @@ def gpu_solve(P, pr, leaves, p, f_solve=None):
     return u.cpu().numpy(), (x, a, b, c, f, g)
 
 
+@pytest.mark.parametrize("lazy", [False, True], ids=["explicit", "lazy"])
 @pytest.mark.parametrize("p", [6, 8])
-def test_adaptive_parity_two_one_tree(P, p):
+def test_adaptive_parity_two_one_tree(P, p, lazy):
     pr = W.elliptic_3d(seed=2)
     leaves = two_one_tree()
-    ug, (x, a, b, c, f, g) = gpu_solve(P, pr, leaves, p)
+    ug, (x, a, b, c, f, g) = gpu_solve(P, pr, leaves, p, lazy=lazy)
     uo = np.array(ad.solve_adaptive(ad.build_adaptive(leaves, p, pr.lo, pr.hi, a, b, c, f), g))
     assert rel(ug, uo) <= TOL
 
@@ -82,14 +83,15 @@ def test_adaptive_polynomial_exact_on_gpu(P):
     assert rel(ug.reshape(-1), poly.value(inputs[0])) < 1e-11
 
 
-def test_adaptive_new_source(P):
+@pytest.mark.parametrize("lazy", [False, True], ids=["explicit", "lazy"])
+def test_adaptive_new_source(P, lazy):
     pr = W.elliptic_3d(seed=2)
     p = 6
     leaves = two_one_tree()
     rng = np.random.default_rng(5)
     nl = len(leaves)
     f2 = rng.standard_normal((nl, p ** 3))
-    ug, (x, a, b, c, f, g) = gpu_solve(P, pr, leaves, p, f_solve=f2)
+    ug, (x, a, b, c, f, g) = gpu_solve(P, pr, leaves, p, f_solve=f2, lazy=lazy)
     uo = np.array(ad.solve_adaptive(ad.build_adaptive(leaves, p, pr.lo, pr.hi, a, b, c, f2), g))
     assert rel(ug, uo) <= TOL
 
