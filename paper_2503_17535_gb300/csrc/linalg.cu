@@ -75,9 +75,14 @@ template <> constexpr double fma_flops<cplx>() { return 8.0; }
 
 // ---------------------------------------------------------------- GEMM ----
 
-template <typename T> struct GemmTile;
-template <> struct GemmTile<double> { enum { BM = 64, BN = 64, BK = 16, TM = 4, TN = 4 }; };
-template <> struct GemmTile<cplx> { enum { BM = 32, BN = 32, BK = 16, TM = 2, TN = 2 }; };
+// Tile shapes: 64 x 64 (4 x 4 outputs per thread) for large FP64 products,
+// 32 x 32 (2 x 2 per thread) where 64-wide tiles would leave much of the
+// last tile row / column empty (the leaf updates of (p-2)^2-sized blocks).
+template <typename T, int WIDE> struct GemmTile;
+template <> struct GemmTile<double, 1> { enum { BM = 64, BN = 64, BK = 16, TM = 4, TN = 4 }; };
+template <> struct GemmTile<double, 0> { enum { BM = 32, BN = 32, BK = 16, TM = 2, TN = 2 }; };
+template <> struct GemmTile<cplx, 1> { enum { BM = 32, BN = 32, BK = 16, TM = 2, TN = 2 }; };
+template <> struct GemmTile<cplx, 0> { enum { BM = 32, BN = 32, BK = 16, TM = 2, TN = 2 }; };
 
 // Epilogue modes: the LU / TRSM / Schur updates are C <- C - A B and the
 // leaf products C <- A B; handling those two forms apart keeps the general
@@ -92,10 +97,10 @@ inline int epi_mode(const GemmArgs<T>& g) {
   return EPI_GENERAL;
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, int WIDE>
 __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g) {
-  constexpr int BM = GemmTile<T>::BM, BN = GemmTile<T>::BN, BK = GemmTile<T>::BK;
-  constexpr int TM = GemmTile<T>::TM, TN = GemmTile<T>::TN;
+  constexpr int BM = GemmTile<T, WIDE>::BM, BN = GemmTile<T, WIDE>::BN, BK = GemmTile<T, WIDE>::BK;
+  constexpr int TM = GemmTile<T, WIDE>::TM, TN = GemmTile<T, WIDE>::TN;
   constexpr int RX = BM / TM;  // threads along M (16)
   __shared__ T As[BK][BM];
   __shared__ T Bs[BK][BN];
@@ -441,10 +446,19 @@ __global__ void __launch_bounds__(256) k_gemm_ta(GemmArgs<T> g) {
   }
 }
 
+// Wide (64 x 64) tiles unless they leave more than 1/8 of the computed
+// outputs empty where 32 x 32 tiles would not: the padded area decides.
+inline bool wide_tiles(int M, int N, int BM, int BN) {
+  if (BM == 32) return false;
+  auto padded = [](int n, int b) { return (double)((n + b - 1) / b) * b; };
+  const double wide = padded(M, BM) * padded(N, BN), narrow = padded(M, 32) * padded(N, 32);
+  return wide <= 1.125 * narrow;
+}
+
 template <typename T>
 cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
-  constexpr int BM = GemmTile<T>::BM, BN = GemmTile<T>::BN;
+  constexpr int BM = GemmTile<T, 1>::BM, BN = GemmTile<T, 1>::BN;
   if (pf) {
     pf->begin(st);
     pf->note(g.M, g.N, g.K, g.batch);
@@ -475,12 +489,19 @@ cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
     const double mnk = g.M * (double)g.N * g.K * g.batch;
     if (pf) pf->end(K_GEMM, 8.0 * mnk, st, 6.0 * mnk);
     return cudaGetLastError();
-  } else {
+  } else if (wide_tiles(g.M, g.N, BM, BN)) {
     dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, std::min(g.batch, 65535));
     switch (epi_mode(g)) {
-      case EPI_SUB: k_gemm<T, EPI_SUB><<<grid, 256, 0, st>>>(g); break;
-      case EPI_SET: k_gemm<T, EPI_SET><<<grid, 256, 0, st>>>(g); break;
-      default: k_gemm<T, EPI_GENERAL><<<grid, 256, 0, st>>>(g); break;
+      case EPI_SUB: k_gemm<T, EPI_SUB, 1><<<grid, 256, 0, st>>>(g); break;
+      case EPI_SET: k_gemm<T, EPI_SET, 1><<<grid, 256, 0, st>>>(g); break;
+      default: k_gemm<T, EPI_GENERAL, 1><<<grid, 256, 0, st>>>(g); break;
+    }
+  } else {
+    dim3 grid((g.M + 31) / 32, (g.N + 31) / 32, std::min(g.batch, 65535));
+    switch (epi_mode(g)) {
+      case EPI_SUB: k_gemm<T, EPI_SUB, 0><<<grid, 256, 0, st>>>(g); break;
+      case EPI_SET: k_gemm<T, EPI_SET, 0><<<grid, 256, 0, st>>>(g); break;
+      default: k_gemm<T, EPI_GENERAL, 0><<<grid, 256, 0, st>>>(g); break;
     }
   }
   if (pf) pf->end(K_GEMM, fma_flops<T>() * g.M * (double)g.N * g.K * g.batch, st);
