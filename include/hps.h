@@ -134,7 +134,14 @@ typedef struct {
                            flops).  Automatic takes 2 when the leaf Dirichlet
                            problem is far from resonance: max c <= min a * pi^2 /
                            (2 h^2) and max |b| h <= min a, h the leaf side. */
-  int reserved[2];
+  int fp64_gemm;        /* 0: hps_build runs its large real and complex products
+                           on the tensor cores as exact bf16 digit-slice
+                           products (FP64 accuracy: operands cut into nine 6-bit
+                           digits, products accumulated exactly and recombined
+                           in 64-bit integers; it needs a transient device
+                           workspace of up to about 1 GB); 1: every product on
+                           the FP64 pipe.  Solves always use the FP64 pipe. */
+  int reserved[1];
 } hps_options;
 
 /* Kernel classes reported by hps_kernel_stats. */
@@ -147,7 +154,9 @@ enum {
   HPS_KCLASS_GATHER = 5,      /* merge gathers, row permutations, scatters           */
   HPS_KCLASS_DOWN = 6,        /* downward-pass and leaf-output products              */
   HPS_KCLASS_OTHER = 7,       /* fills and copies                                    */
-  HPS_KCLASS_COUNT = 8
+  HPS_KCLASS_GEMM_TC = 8,     /* FP64 / complex GEMM on the tensor cores (digit slices) */
+  HPS_KCLASS_SPLIT = 9,       /* cutting GEMM operands into bf16 digit slices        */
+  HPS_KCLASS_COUNT = 10
 };
 
 typedef struct {
@@ -242,6 +251,25 @@ hps_status hps_coeff_gradient(hps_handle* h, int nrhs, const void* u, const void
 
 /* Release a handle (NULL is accepted).  Synchronises the handle's last stream. */
 void hps_free(hps_handle* h);
+
+/* Batched dense product C = alpha A B + beta C (no counterpart in the paper:
+ * the GEMM every merge and leaf stage of hps_build is made of, exposed so
+ * that callers and tests can run it alone).  `batch` column-major matrices:
+ * A item b at A + b*strideA (m x k, leading dimension lda), B item b at
+ * B + b*strideB (k x n, ldb), C item b at C + b*strideC (m x n, ldc); strides
+ * and leading dimensions in elements.  dtype HPS_F64 (double) or HPS_C128
+ * (interleaved complex; alpha and beta are real).  mode 0: the tensor-core
+ * digit-slice product that hps_build uses (operands cut into nine 6-bit bf16
+ * digits per row of A / column of B, 53 digit products accumulated exactly
+ * in fp32, recombined in 64-bit integers; a transient device workspace of up
+ * to about 1 GB); mode 1: the FP64-pipe kernels.  Device pointers only; C must
+ * not overlap A or B.  Enqueued on `stream` and synchronised before return.
+ * HPS_ERR_INVALID for bad sizes, dtype or mode; HPS_ERR_OOM when the
+ * workspace cannot be allocated; HPS_ERR_TIMEOUT when a bounded wait inside
+ * the tensor-core kernel gave up (C is then undefined). */
+hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double alpha, const void* A, int lda,
+                    int64_t strideA, const void* B, int ldb, int64_t strideB, double beta, void* C, int ldc,
+                    int64_t strideC, struct CUstream_st* stream);
 
 /* Static, NUL-terminated description of a status code. */
 const char* hps_error_string(hps_status s);

@@ -175,9 +175,12 @@ def make_coeffs(kind: int, a=None, b=None, c=None, eta: float = 0.0, keep=None, 
 
 def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None, f=None,
               eta: float = 0.0, want_root_map: bool = False, profile: bool = False,
-              lazy_root: bool = False, graph_solve: bool = False, iti_leaf: int = 0, stream=None) -> Handle:
+              lazy_root: bool = False, graph_solve: bool = False, iti_leaf: int = 0, fp64_gemm: bool = False,
+              stream=None) -> Handle:
     """Build the solution operator; coefficient and source arrays hold
-    n_leaves * p^dim values (leaf-major, tensor node order)."""
+    n_leaves * p^dim values (leaf-major, tensor node order).  fp64_gemm=True
+    keeps every product on the FP64 pipe (default: large products on the
+    tensor cores as exact digit-slice products)."""
     nl, ppl, _ = hps_sizes(tree, p, q)
     n = nl * ppl
     keep: list = []
@@ -190,6 +193,7 @@ def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None,
     opts.lazy_root = 1 if lazy_root else 0
     opts.graph_solve = 1 if graph_solve else 0
     opts.iti_leaf = int(iti_leaf)
+    opts.fp64_gemm = 1 if fp64_gemm else 0
     out = c_void_p()
     st = _stream(stream)
     _check(_capi.lib().hps_build(byref(tree), p, q, byref(cf), fp, byref(opts), st, byref(out)),
@@ -477,3 +481,28 @@ def hps_coeff_gradient(h: Handle, u, fbar, ga=None, gb=None, gc=None, nrhs: int 
     cp = _ptr(gc, False, n, "gc", keep)
     _check(_capi.lib().hps_coeff_gradient(h.ptr, nrhs, up, fp, ap, bp, cp, _stream(stream)),
            "hps_coeff_gradient")
+
+
+def hps_gemm(A, B, C, alpha: float = 1.0, beta: float = 0.0, mode: int = 0, stream=None):
+    """C <- alpha A B + beta C for batches of column-major matrices held as
+    contiguous device tensors of shape (batch, cols, rows) (that is, each
+    item's columns are contiguous): A (batch, k, m), B (batch, n, k),
+    C (batch, n, m); float64 or complex128.  mode 0: tensor-core digit-slice
+    product; mode 1: FP64 pipe.  Synchronises the stream."""
+    if not (_is_torch(A) and _is_torch(B) and _is_torch(C)):
+        raise TypeError("hps_gemm: A, B and C must be device tensors")
+    if A.dim() != 3 or B.dim() != 3 or C.dim() != 3:
+        raise ValueError("hps_gemm: tensors must be (batch, cols, rows)")
+    batch, k, m = A.shape
+    _, n, k2 = B.shape
+    if B.shape[0] != batch or tuple(C.shape) != (batch, n, m) or k2 != k:
+        raise ValueError("hps_gemm: shapes do not match")
+    cp = A.is_complex()
+    keep: list = []
+    ap = _ptr(A, cp, A.numel(), "A", keep)
+    bp = _ptr(B, cp, B.numel(), "B", keep)
+    cq = _ptr(C, cp, C.numel(), "C", keep)
+    _check(_capi.lib().hps_gemm(HPS_C128 if cp else HPS_F64, int(mode), m, n, k, batch, float(alpha), ap,
+                                max(m, 1), m * k, bp, max(k, 1), k * n, float(beta), cq, max(m, 1), m * n,
+                                _stream(stream)), "hps_gemm")
+    return C

@@ -22,7 +22,7 @@ EXPORTED = [
     "hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
     "hps_error_string", "hps_last_error_detail", "hps_device_bytes", "hps_last_launch_count",
     "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc", "hps_refine", "hps_trace_count",
-    "hps_trace_get", "hps_plan_bytes", "hps_solve_adjoint", "hps_coeff_gradient",
+    "hps_trace_get", "hps_plan_bytes", "hps_solve_adjoint", "hps_coeff_gradient", "hps_gemm",
     # request server (include/hps_serve.h)
     "hps_server_create", "hps_server_destroy", "hps_server_submit_build", "hps_server_submit_solve",
     "hps_server_wait", "hps_server_poll", "hps_server_get_stats", "hps_server_operator",
@@ -30,7 +30,8 @@ EXPORTED = [
 
 EVAL_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_int64, POINTER(c_double), POINTER(c_double))
 
-KCLASSES = ["gemm", "lu_panel", "laswp_trsm", "trsm_diag", "assemble", "gather", "down", "other"]
+KCLASSES = ["gemm", "lu_panel", "laswp_trsm", "trsm_diag", "assemble", "gather", "down", "other", "gemm_tc",
+            "split"]
 
 
 class hps_tree(ctypes.Structure):
@@ -46,7 +47,8 @@ class hps_coeffs(ctypes.Structure):
 
 class hps_options(ctypes.Structure):
     _fields_ = [("version", c_int), ("want_root_map", c_int), ("profile", c_int),
-                ("lazy_root", c_int), ("graph_solve", c_int), ("iti_leaf", c_int), ("reserved", c_int * 2)]
+                ("lazy_root", c_int), ("graph_solve", c_int), ("iti_leaf", c_int), ("fp64_gemm", c_int),
+                ("reserved", c_int * 1)]
 
 
 class hps_kernel_stat(ctypes.Structure):
@@ -122,6 +124,9 @@ def lib() -> ctypes.CDLL:
     L.hps_solve_adjoint.restype = c_int
     L.hps_coeff_gradient.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     L.hps_coeff_gradient.restype = c_int
+    L.hps_gemm.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_int64,
+                           c_void_p, c_int, c_int64, c_double, c_void_p, c_int, c_int64, c_void_p]
+    L.hps_gemm.restype = c_int
     L.hps_server_create.argtypes = [POINTER(hps_server_options), POINTER(c_void_p)]
     L.hps_server_create.restype = c_int
     L.hps_server_destroy.argtypes = [c_void_p]

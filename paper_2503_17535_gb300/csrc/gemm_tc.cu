@@ -1,0 +1,641 @@
+// FP64 and complex128 GEMMs on the tcgen05 tensor cores by exact digit
+// slicing (an Ozaki-type splitting of each operand into bf16 digit matrices).
+//
+// Why: the FP64 FMA pipe of this GPU does 4 flop/clk/SM, while the bf16
+// tensor cores do ~7000.  A real product C = A B is computed as
+//
+//   A(i, k) ~ 2^{e_i} sum_p a_p(i, k) 2^{-6p},   B(k, j) ~ 2^{f_j} sum_q b_q(k, j) 2^{-6q},
+//
+// p, q = 1..10, where 2^{e_i} (2^{f_j}) is the power of two above the
+// largest |A(i, :)| (|B(:, j)|) and the digits are the balanced base-64
+// digits of the scaled value rounded to 60 fraction bits: the leading digit
+// in [-64, 64], the others in [-32, 31].  Integers of that size are exact in
+// bf16, their products are exact in the fp32 accumulators of tcgen05.mma, and
+// so are sums of up to 2^22 / 12288 of the products that share one
+// anti-diagonal d = p + q (weight 2^{-6d}).  The product keeps the pairs with
+// p + q <= 11 and accumulates each diagonal exactly in its own TMEM
+// accumulator over K chunks of up to 256.  The epilogue converts the ten
+// diagonal sums to integers, adds them in a 64-bit fixed-point integer (the
+// low diagonals first at full precision, then rounded once) and scales by
+// 2^{e_i + f_j} into FP64.  Errors: operand rounding 2^{-61} 2^{e_i} per
+// entry (unbiased), dropped pairs about 2^{-59} K 2^{e_i + f_j}, half a unit
+// of the fixed point (2^{-lsb}, lsb = 62 - ceil(log2 K)) per chunk, and the
+// final rounding to FP64: at or below FP64's own rounding error for a dot
+// product of length K when rows and columns are not far from their largest
+// entries.
+//
+// Layout: the slicing kernel writes each operand's digits, K-major, in the
+// tensor core's canonical no-swizzle layout (8-row x 16-byte core matrices;
+// a 16-deep k step of a 128-row A tile is one 4 KB block per digit, of a
+// 48-column B tile one 1.5 KB block), so that one k step of all digits is one
+// contiguous bulk copy (cp.async.bulk) per operand.  The GEMM kernel runs one
+// 128 x 48 output tile per CTA: a producer warp streams the digit blocks
+// through a 4-stage shared-memory ring, one thread issues the 55 MMAs per k
+// step into 10 TMEM accumulators (480 of 512 columns), and eight epilogue
+// warps (two per TMEM lane quarter, one per half of the columns) read the
+// accumulators back.
+//
+// Complex products are four real products (re*re, im*im, re*im, im*re),
+// each written into its component of C.
+#include "linalg.h"
+
+#include <algorithm>
+#include <mutex>
+#include <type_traits>
+
+namespace hps {
+namespace tc {
+
+constexpr int DIG = 10;             // digits per operand
+constexpr int BITS = 6;             // bits per digit
+constexpr int FRAC = DIG * BITS;    // fraction bits of the scaled operands
+constexpr int DSUM = 11;            // keep digit pairs with p + q <= DSUM (1-based)
+constexpr int NDIAG = DSUM - 1;     // accumulators: d = 2 .. DSUM
+constexpr int TM = 128, TN = 48, TK = 16;
+constexpr int KC = 256;             // k per exact fp32 accumulation chunk
+constexpr int KCT = KC / TK;        // k steps per chunk
+constexpr int ABLK = TM * TK * 2;   // bytes of one digit of an A tile k step
+constexpr int BBLK = TN * TK * 2;
+constexpr int ASTG = DIG * ABLK;
+constexpr int BSTG = DIG * BBLK;
+constexpr int STAGE = ASTG + BSTG;
+constexpr int NST = 3;
+constexpr int CSTG = TN * TM * 8;     // the C tile staged for the epilogue (column-major)
+constexpr int SMEM = NST * STAGE + CSTG;
+constexpr int TMEM_COLS = 512;
+constexpr int EPI_WARPS = 8;        // two per TMEM lane quarter, each half of the tile's columns
+constexpr int ECOLS = TN / 2;       // columns per epilogue thread
+constexpr int THREADS = 32 * EPI_WARPS + 64;   // + producer warp + MMA-issue warp
+constexpr long SPIN = 1L << 22;     // polls before a wait gives up
+
+static_assert(NDIAG * TN <= TMEM_COLS, "accumulators exceed TMEM");
+static_assert(ECOLS % 4 == 0, "epilogue column groups of 4");
+// largest |sum of the digit products on one diagonal| per k: the two pairs
+// with a leading digit (64 * 32 each) and the others (32 * 32), or 64 * 64
+// (below 2^22 the epilogue converts them to integers with one fp32 add)
+static_assert((long)KC * (2 * 64 * 32 + (DIG - 2) * 32 * 32) < (1L << 22), "diagonal sums must stay exact in fp32");
+static_assert((long)KC * 64 * 64 < (1L << 22), "diagonal sums must stay exact in fp32");
+static_assert(SMEM <= 227 * 1024, "shared memory ring too large");
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading byte
+// offset (between core matrices adjacent in K) and stride byte offset
+// (between core matrices adjacent in M / N), version bits 46-48 = 0b001.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; gives up when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  for (long it = 0; it < SPIN; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+    if (it > 32) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ inline double part_of(double v, int) { return v; }
+__device__ inline double part_of(const cplx& v, int part) { return part ? v.im : v.re; }
+
+// One real operand as rows x K: element (r, k) = part(X[rmap(r) * rs + kmap(k) * ks]).
+template <typename T>
+struct Src {
+  BOp<T> X;
+  IMap rmap, kmap;
+  int64_t rs = 1, ks = 1;
+  int part = 0;
+};
+
+// Row maxima of an operand, as biased FP64 exponents: thread per (row,
+// k range of KSPAN); atomicMax into ex (zeroed beforehand).  A zero or
+// subnormal row keeps 0 (all its digits are then 0).
+constexpr int KSPAN = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_split_max(Src<T> s, int R, int K, int* ex, int exstride, int b0) {
+  const int bl = blockIdx.z, b = b0 + bl;
+  const int r = blockIdx.x * 128 + threadIdx.x;
+  if (r >= R) return;
+  const int k0 = blockIdx.y * KSPAN, k1 = min(K, k0 + KSPAN);
+  const T* X = s.X.item(b);
+  const int64_t roff = (int64_t)s.rmap.at(b, r) * s.rs;
+  unsigned long long mx = 0;
+  for (int k = k0; k < k1; ++k) {
+    const double v = part_of(X[roff + (int64_t)s.kmap.at(b, k) * s.ks], s.part);
+    mx = max(mx, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
+  }
+  const int evm = (int)(mx >> 52);
+  if (evm) atomicMax(ex + (int64_t)bl * exstride + r, evm);
+}
+
+// exponent e of a row (max |x| < 2^e) from its biased maximum exponent
+__device__ __forceinline__ int row_exp(int evm) { return evm ? evm - 1022 : 0; }
+
+// Digits of a K-major operand: thread per (padded row, 8-deep k group).
+template <typename T, int TR>
+__global__ void __launch_bounds__(128) k_split(Src<T> s, int R, int K, int RT, int KT, uint8_t* out,
+                                               const int* ex, int exstride, int b0) {
+  constexpr int BLK = TR * TK * 2;
+  const int bl = blockIdx.z, b = b0 + bl;
+  const int r = blockIdx.x * 128 + threadIdx.x;
+  const int Rpad = RT * TR;
+  if (r >= Rpad) return;
+  const int k0 = blockIdx.y * 8;
+  const T* X = s.X.item(b);
+  const bool live = r < R;
+  const int evm = live ? ex[(int64_t)bl * exstride + r] : 0;
+  const bool zero = evm == 0;
+  const int e = row_exp(evm);
+  const int64_t roff = live ? (int64_t)s.rmap.at(b, r) * s.rs : 0;
+  const int tile = r / TR, rr = r % TR;
+  uint8_t* blk = out + ((int64_t)bl * RT + tile) * KT * (int64_t)(DIG * BLK) + (rr >> 3) * 256 + (rr & 7) * 16 +
+                 (int64_t)(k0 >> 4) * (DIG * BLK) + ((k0 >> 3) & 1) * 128;
+  int dg[8][DIG];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int k = k0 + c;
+    double v = 0.0;
+    if (live && !zero && k < K) v = part_of(X[roff + (int64_t)s.kmap.at(b, k) * s.ks], s.part);
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const int ev = (int)((u >> 52) & 0x7FF);
+    // |v| 2^{FRAC - e} rounded to an integer (<= 2^FRAC), then signed
+    const long long m = (long long)((u & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+    const int sh = ev - (1075 - FRAC) - e;
+    long long x = 0;
+    if (ev != 0) {
+      if (sh >= 0) x = m << sh;
+      else if (sh > -62) x = ((m >> (-sh - 1)) + 1) >> 1;
+    }
+    if (u >> 63) x = -x;
+    // balanced base-64 digits, least significant first
+#pragma unroll
+    for (int p = DIG - 1; p > 0; --p) {
+      const int d = (int)((x + 32) & 63) - 32;
+      dg[c][p] = d;
+      x = (x - d) >> BITS;
+    }
+    dg[c][0] = (int)x;
+  }
+#pragma unroll
+  for (int p = 0; p < DIG; ++p) {
+    uint32_t w[4];
+#pragma unroll
+    for (int c = 0; c < 8; c += 2) {
+      uint32_t h[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int d = dg[c + t][p];
+        const uint32_t a = (uint32_t)(d < 0 ? -d : d);
+        // |d| <= 64 as an exact float; its upper 16 bits are the bf16 encoding
+        const float f = __uint_as_float(0x4B000000u | a) - 8388608.0f;
+        h[t] = (__float_as_uint(f) >> 16) | (d < 0 ? 0x8000u : 0u);
+      }
+      w[c >> 1] = h[0] | (h[1] << 16);
+    }
+    *reinterpret_cast<uint4*>(blk + (int64_t)p * BLK) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// R 2^es as the nearest double (ties to even), from the integer's bits;
+// falls back to ldexp outside the normal range.
+__device__ __forceinline__ double fixed_to_double(long long R, int es) {
+  if (R == 0) return 0.0;
+  const unsigned long long sgn = R < 0 ? (1ull << 63) : 0ull;
+  unsigned long long a = R < 0 ? (unsigned long long)(-R) : (unsigned long long)R;
+  const int lz = __clzll((long long)a);
+  a <<= lz;                                    // leading one at bit 63
+  unsigned long long m = a >> 11;              // 53 significant bits
+  const unsigned long long rem = a & 0x7FFull;
+  m += (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) ? 1ull : 0ull;
+  const int e2 = es + 63 - lz;                 // value in [2^e2, 2^(e2+1))
+  if (e2 + 1023 < 1 || e2 + 1023 > 2046) return ldexp((double)R, es);
+  // m carries the hidden bit: adding it to (exponent - 1) sets the exponent
+  // (and carries once more when rounding reached 2^53)
+  return __longlong_as_double((long long)(sgn | (((unsigned long long)(e2 + 1022) << 52) + m)));
+}
+
+template <typename T>
+struct GemmP {
+  const uint8_t* As;
+  const uint8_t* Bs;
+  const int* ea;
+  const int* eb;
+  int MT, NT, KT, M, N;
+  int lsb;             // fraction bits of the fixed-point result
+  double alpha, beta;
+  int amode;                 // 1: alpha = +-1 (applied as a sign flip)
+  long long asign;           // sign bit to flip when amode = 1
+  BOp<T> C;
+  IMap crow;
+  int cpart;           // complex C: component written (0 re, 1 im)
+  int b0;              // first batch item of this launch
+  unsigned* err;
+};
+
+template <typename T, bool BETA0>
+__global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[NST], empty[NST], acc_full, acc_empty;
+  __shared__ int s_eb[TN];
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bl = blockIdx.y;
+  const int mt = blockIdx.x % g.MT, nt = blockIdx.x / g.MT;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 32) {
+    for (int i = 0; i < NST; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&acc_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acc_empty)), "r"(32 * EPI_WARPS));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tslot;
+  volatile int* abrt = &abort_flag;
+  const int nchunk = (g.KT + KCT - 1) / KCT;
+  const uint32_t sbase = su32(smem);
+
+  if (warp == EPI_WARPS) {
+    // producer: one bulk copy per operand per k step
+    if (lane == 0) {
+      const uint8_t* a_src = g.As + ((int64_t)bl * g.MT + mt) * g.KT * (int64_t)ASTG;
+      const uint8_t* b_src = g.Bs + ((int64_t)bl * g.NT + nt) * g.KT * (int64_t)BSTG;
+      for (int it = 0; it < g.KT; ++it) {
+        const int s = it % NST;
+        if (it >= NST && !mbar_wait(su32(&empty[s]), ((it / NST) & 1) ^ 1, abrt)) {
+          *abrt = 1;
+          atomicOr(g.err, DEV_ERR_TIMEOUT);
+          break;
+        }
+        const uint32_t fb = su32(&full[s]), dst = sbase + s * STAGE;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(dst), "l"(a_src + (int64_t)it * ASTG), "r"(ASTG), "r"(fb) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(dst + ASTG), "l"(b_src + (int64_t)it * BSTG), "r"(BSTG), "r"(fb) : "memory");
+      }
+    }
+  } else if (warp == EPI_WARPS + 1) {
+    // MMA issue: 53 digit-pair products per k step into the 10 diagonal accumulators
+    if (lane == 0) {
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                             ((uint32_t)(TM >> 4) << 24);
+      int it = 0;
+      bool ok = true;
+      for (int c = 0; c < nchunk && ok; ++c) {
+        if (c > 0 && !mbar_wait(su32(&acc_empty), (c - 1) & 1, abrt)) { ok = false; break; }
+        fence_after();
+        const int kend = min(g.KT, (c + 1) * KCT);
+        uint32_t touched = 0;
+        for (; it < kend; ++it) {
+          const int s = it % NST;
+          if (!mbar_wait(su32(&full[s]), (it / NST) & 1, abrt)) { ok = false; break; }
+          fence_after();
+          const uint32_t a0 = sbase + s * STAGE, b0 = a0 + ASTG;
+#pragma unroll
+          for (int p = 0; p < DIG; ++p) {
+            const uint64_t ad = sdesc(a0 + p * ABLK, 128, 256);
+#pragma unroll
+            for (int q = 0; q < DIG; ++q) {
+              if (p + q > DSUM - 2) continue;
+              const int di = p + q;
+              const uint32_t acc = (touched >> di) & 1u;
+              touched |= 1u << di;
+              const uint64_t bd = sdesc(b0 + q * BBLK, 128, 256);
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(di * TN)),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           su32(&empty[s]))
+                       : "memory");
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         su32(&acc_full))
+                     : "memory");
+      }
+      if (!ok) {
+        *abrt = 1;
+        atomicOr(g.err, DEV_ERR_TIMEOUT);
+      }
+    }
+  } else {
+    // epilogue: warp w reads TMEM lane quarter w % 4 (its rows) and column
+    // half w / 4; thread = row, 24 fixed-point sums.  While the MMAs run, the
+    // C tile (beta != 0) and the columns' exponents are staged in shared
+    // memory with asynchronous copies.
+    const int quarter = warp & 3, c0 = (warp >> 2) * ECOLS;
+    const int row = quarter * 32 + lane;
+    const int i = mt * TM + row;
+    const int b = g.b0 + bl;
+    double* Cb = reinterpret_cast<double*>(g.C.item(b));
+    constexpr int W = (int)(sizeof(T) / sizeof(double));
+    const int64_t ci = i < g.M ? (int64_t)g.crow.at(b, i) : 0;
+    double* s_c = reinterpret_cast<double*>(smem + NST * STAGE);
+    if (threadIdx.x < TN)
+      s_eb[threadIdx.x] = nt * TN + threadIdx.x < g.N ? row_exp(g.eb[(int64_t)bl * g.NT * TN + nt * TN + threadIdx.x]) : 0;
+    if (!BETA0 && i < g.M) {
+#pragma unroll 4
+      for (int j = c0; j < c0 + ECOLS; ++j) {
+        const int col = nt * TN + j;
+        if (col >= g.N) break;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(s_c + j * TM + row)),
+                     "l"(Cb + (ci + (int64_t)col * g.C.ld) * W + g.cpart)
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    long long R[ECOLS];
+#pragma unroll
+    for (int j = 0; j < ECOLS; ++j) R[j] = 0;
+    // diagonal d = di + 2 has weight 2^{-6d}; R counts units of 2^{-lsb}.
+    // Diagonals with 6d <= lsb enter R exactly; the others are first summed
+    // exactly in units of 2^{-6 DSUM} and then rounded into R once.
+    int shl[NDIAG];
+#pragma unroll
+    for (int di = 0; di < NDIAG; ++di) {
+      const int sh = g.lsb - BITS * (di + 2);
+      shl[di] = sh >= 0 ? sh : -1 - BITS * (DSUM - 2 - di);   // < 0: low part, shift -1 - sh
+    }
+    const int low_sh = BITS * DSUM - g.lsb;   // units 2^{-6 DSUM} -> 2^{-lsb}
+    bool ok = true;
+    for (int c = 0; c < nchunk; ++c) {
+      if (!mbar_wait(su32(&acc_full), c & 1, abrt)) { ok = false; break; }
+      fence_after();
+#pragma unroll
+      for (int cg = 0; cg < ECOLS / 4; ++cg) {
+        uint32_t v[NDIAG][4];
+#pragma unroll
+        for (int di = 0; di < NDIAG; ++di) {
+          const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(di * TN + c0 + cg * 4);
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                       : "=r"(v[di][0]), "=r"(v[di][1]), "=r"(v[di][2]), "=r"(v[di][3])
+                       : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          long long hi = R[cg * 4 + j], lo = 0;
+#pragma unroll
+          for (int di = 0; di < NDIAG; ++di) {
+            // exact integer below 2^22: adding 1.5 * 2^23 leaves it in the low mantissa bits
+            const long long x = (long long)(__float_as_int(__uint_as_float(v[di][j]) + 12582912.0f) - 0x4B400000);
+            if (shl[di] >= 0) hi += x << shl[di];
+            else lo += x << (-1 - shl[di]);
+          }
+          R[cg * 4 + j] = hi + ((lo + (1ll << (low_sh - 1))) >> low_sh);
+        }
+      }
+      fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&acc_empty)) : "memory");
+    }
+    if (!ok) {
+      *abrt = 1;
+      atomicOr(g.err, DEV_ERR_TIMEOUT);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");   // s_eb from other epilogue warps
+    if (ok && i < g.M) {
+      const int er = row_exp(g.ea[(int64_t)bl * g.MT * TM + i]);
+#pragma unroll
+      for (int jj = 0; jj < ECOLS; ++jj) {
+        const int j = c0 + jj;
+        const int col = nt * TN + j;
+        if (col >= g.N) break;
+        double val = fixed_to_double(R[jj], er + s_eb[j] - g.lsb);
+        double* cp = Cb + (ci + (int64_t)col * g.C.ld) * W + g.cpart;
+        if (g.amode == 1) {          // alpha = +-1: a sign flip
+          val = __longlong_as_double(__double_as_longlong(val) ^ g.asign);
+          if (BETA0) *cp = val;
+          else if (g.beta == 1.0) *cp = s_c[j * TM + row] + val;
+          else *cp = fma(g.beta, s_c[j * TM + row], val);
+        } else {
+          if (BETA0) *cp = g.alpha * val;
+          else *cp = fma(g.alpha, val, g.beta * s_c[j * TM + row]);
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+int ceil_log2(int64_t x) {
+  int c = 0;
+  while ((int64_t(1) << c) < x) ++c;
+  return c;
+}
+
+template <typename T, bool BETA0>
+void set_smem_attr() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_gemm_tc<T, BETA0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  });
+}
+
+struct Sizes {
+  int MT, NT, KT;
+  size_t a_item, b_item, ea_item, eb_item;
+};
+
+Sizes sizes(int M, int N, int K) {
+  Sizes z;
+  z.MT = (M + TM - 1) / TM;
+  z.NT = (N + TN - 1) / TN;
+  z.KT = (K + TK - 1) / TK;
+  z.a_item = (size_t)z.MT * z.KT * ASTG;
+  z.b_item = (size_t)z.NT * z.KT * BSTG;
+  z.ea_item = (size_t)z.MT * TM * sizeof(int);
+  z.eb_item = (size_t)z.NT * TN * sizeof(int);
+  return z;
+}
+
+constexpr size_t WS_CAP = size_t(1) << 30;  // workspace bytes a launch group may use
+
+}  // namespace tc
+
+TcWorkspace*& tc_workspace() {
+  static thread_local TcWorkspace* w = nullptr;
+  return w;
+}
+
+size_t tc_workspace_cap() { return tc::WS_CAP; }
+
+void tc_release(TcWorkspace* w) {
+  if (w && w->p) cudaFree(w->p);
+  if (w) { w->p = nullptr; w->bytes = 0; }
+}
+
+template <typename T>
+bool tc_applicable(const GemmArgs<T>& g) {
+  const TcWorkspace* w = tc_workspace();
+  if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta) return false;
+  if (w->force) return true;
+  if (g.M < 64 || g.N < 32 || g.K < 16) return false;
+  if ((double)g.M * g.N * g.K * g.batch < 1.0e7) return false;
+  return true;
+}
+
+template <>
+bool tc_applicable<cplx>(const GemmArgs<cplx>& g) {
+  const TcWorkspace* w = tc_workspace();
+  if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta) return false;
+  if (g.alpha.im != 0.0 || g.beta.im != 0.0) return false;
+  if (w->force) return true;
+  if (g.M < 64 || g.N < 32 || g.K < 16) return false;
+  if ((double)g.M * g.N * g.K * g.batch < 2.5e6) return false;
+  return true;
+}
+
+namespace {
+
+template <typename T>
+cudaError_t ensure_ws(TcWorkspace* w, size_t bytes, cudaStream_t st) {
+  if (w->bytes >= bytes) return cudaSuccess;
+  if (w->p) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    cudaFree(w->p);
+    w->p = nullptr;
+    w->bytes = 0;
+  }
+  const size_t nb = std::max(bytes, (size_t)64 << 20);
+  cudaError_t e = cudaMalloc(&w->p, nb);
+  if (e != cudaSuccess) { w->p = nullptr; return e; }
+  w->bytes = nb;
+  return cudaSuccess;
+}
+
+template <typename T, int TR>
+void launch_split(const tc::Src<T>& s, int R, int K, int RT, int KT, uint8_t* out, int* ex, int b0, int nb,
+                  cudaStream_t st, Prof* pf) {
+  const int Rpad = RT * TR;
+  cudaMemsetAsync(ex, 0, sizeof(int) * (size_t)Rpad * nb, st);
+  if (pf) {
+    pf->begin(st);
+    pf->note(R, 0, K, nb);
+  }
+  tc::k_split_max<T><<<dim3((R + 127) / 128, (K + tc::KSPAN - 1) / tc::KSPAN, nb), 128, 0, st>>>(s, R, K, ex, Rpad,
+                                                                                                 b0);
+  if (pf) {
+    pf->end(K_SPLIT, 0.0, st);
+    pf->begin(st);
+    pf->note(R, 0, K, nb);
+  }
+  tc::k_split<T, TR><<<dim3((Rpad + 127) / 128, KT * 2, nb), 128, 0, st>>>(s, R, K, RT, KT, out, ex, Rpad, b0);
+  if (pf) pf->end(K_SPLIT, 0.0, st);
+}
+
+template <typename T>
+void launch_mma(const tc::GemmP<T>& p, int nb, int K, cudaStream_t st, Prof* pf) {
+  if (pf) {
+    pf->begin(st);
+    pf->note(p.M, p.N, K, nb);
+  }
+  dim3 grid(p.MT * p.NT, nb);
+  if (p.beta == 0.0) {
+    tc::set_smem_attr<T, true>();
+    tc::k_gemm_tc<T, true><<<grid, tc::THREADS, tc::SMEM, st>>>(p);
+  } else {
+    tc::set_smem_attr<T, false>();
+    tc::k_gemm_tc<T, false><<<grid, tc::THREADS, tc::SMEM, st>>>(p);
+  }
+  if (pf) pf->end(K_GEMM_TC, 2.0 * p.M * (double)p.N * K * nb, st, 0.0);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
+  using namespace tc;
+  constexpr int NP = std::is_same<T, cplx>::value ? 2 : 1;
+  TcWorkspace* w = tc_workspace();
+  const Sizes z = sizes(g.M, g.N, g.K);
+  const size_t per_item = NP * (z.a_item + z.b_item + z.ea_item + z.eb_item);
+  const int nb_max = (int)std::max<size_t>(1, std::min<size_t>(std::min(g.batch, 65535), WS_CAP / per_item));
+  cudaError_t e = ensure_ws<T>(w, per_item * nb_max, st);
+  if (e != cudaSuccess) return e;
+  uint8_t* base = static_cast<uint8_t*>(w->p);
+  uint8_t* As[2];
+  uint8_t* Bs[2];
+  int* ea[2];
+  int* eb[2];
+  {
+    uint8_t* q = base;
+    for (int pt = 0; pt < NP; ++pt) {
+      As[pt] = q; q += z.a_item * nb_max;
+      Bs[pt] = q; q += z.b_item * nb_max;
+    }
+    for (int pt = 0; pt < NP; ++pt) {
+      ea[pt] = reinterpret_cast<int*>(q); q += z.ea_item * nb_max;
+      eb[pt] = reinterpret_cast<int*>(q); q += z.eb_item * nb_max;
+    }
+  }
+  const int lsb = 62 - ceil_log2(std::max(g.K, 1));
+  double alpha, beta;
+  if constexpr (NP == 2) { alpha = g.alpha.re; beta = g.beta.re; }
+  else { alpha = g.alpha; beta = g.beta; }
+  for (int b0 = 0; b0 < g.batch; b0 += nb_max) {
+    const int nb = std::min(nb_max, g.batch - b0);
+    for (int pt = 0; pt < NP; ++pt) {
+      Src<T> sa;
+      sa.X = g.A; sa.rmap = g.arow; sa.kmap = g.acol; sa.rs = 1; sa.ks = g.A.ld; sa.part = pt;
+      launch_split<T, TM>(sa, g.M, g.K, z.MT, z.KT, As[pt], ea[pt], b0, nb, st, pf);
+      Src<T> sb;
+      sb.X = g.B; sb.kmap = g.brow; sb.rs = g.B.ld; sb.ks = 1; sb.part = pt;
+      launch_split<T, TN>(sb, g.N, g.K, z.NT, z.KT, Bs[pt], eb[pt], b0, nb, st, pf);
+    }
+    GemmP<T> p;
+    p.MT = z.MT; p.NT = z.NT; p.KT = z.KT; p.M = g.M; p.N = g.N; p.lsb = lsb;
+    p.C = g.C; p.crow = g.crow; p.b0 = b0; p.err = *w->err_slot;
+    // real: C = alpha A B + beta C; complex (real alpha, beta):
+    //   C.re = alpha (Ar Br - Ai Bi) + beta C.re,  C.im = alpha (Ar Bi + Ai Br) + beta C.im
+    const int npr = NP == 2 ? 4 : 1;
+    for (int k = 0; k < npr; ++k) {
+      static const int pa[4] = {0, 1, 0, 1}, pb[4] = {0, 1, 1, 0}, pc[4] = {0, 0, 1, 1};
+      p.As = As[pa[k]]; p.ea = ea[pa[k]];
+      p.Bs = Bs[pb[k]]; p.eb = eb[pb[k]];
+      p.cpart = pc[k];
+      p.alpha = (k == 1) ? -alpha : alpha;
+      p.beta = (k == 1 || k == 3) ? 1.0 : beta;
+      p.amode = (p.alpha == 1.0 || p.alpha == -1.0) ? 1 : 0;
+      p.asign = p.alpha == -1.0 ? (long long)(1ull << 63) : 0ll;
+      launch_mma<T>(p, nb, g.K, st, pf);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template bool tc_applicable<double>(const GemmArgs<double>&);
+template cudaError_t gemm_tc<double>(const GemmArgs<double>&, cudaStream_t, Prof*);
+template cudaError_t gemm_tc<cplx>(const GemmArgs<cplx>&, cudaStream_t, Prof*);
+
+}  // namespace hps

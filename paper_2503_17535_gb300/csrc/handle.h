@@ -147,6 +147,7 @@ struct hps_handle {
   std::vector<void*> allocs;
   int64_t bytes = 0;
   Prof prof;
+  hps::TcWorkspace tcw;           // digit slices of tensor-core products (build only)
   int64_t err_node = -1;
   int num_sms = 0;
   // captured solves (hps_options.graph_solve): key -> executable graph

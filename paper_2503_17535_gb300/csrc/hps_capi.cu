@@ -819,11 +819,19 @@ hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeff
   }
   cudaStream_t st = (cudaStream_t)stream;
   h->last = st;
+  h->tcw.err_slot = &h->dev_err;
+  h->tcw.enabled = h->opts.fp64_gemm == 0;
   try {
+    hps::TcScope tc_scope(&h->tcw);
     if (h->adaptive) s = adaptive_build(h, tree, coeffs, f, st);
     else s = h->iti ? build_impl<cplx>(h, coeffs, f, st) : build_impl<double>(h, coeffs, f, st);
   } catch (...) {
     s = HPS_ERR_INVALID;
+  }
+  // the digit-slice workspace only lives through the build
+  if (h->tcw.p) {
+    cudaStreamSynchronize(st);
+    hps::tc_release(&h->tcw);
   }
   if (s != HPS_OK && s != HPS_ERR_SINGULAR) {
     free_handle(h);
@@ -874,6 +882,51 @@ hps_status hps_solve_adjoint(hps_handle* h, int nrhs, const void* ubar, void* gb
   } catch (...) {
     return HPS_ERR_INVALID;
   }
+}
+
+hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double alpha, const void* A, int lda,
+                    int64_t strideA, const void* B, int ldb, int64_t strideB, double beta, void* C, int ldc,
+                    int64_t strideC, struct CUstream_st* stream) {
+  if ((dtype != HPS_F64 && dtype != HPS_C128) || (mode != 0 && mode != 1)) return HPS_ERR_INVALID;
+  if (m < 0 || n < 0 || k < 0 || batch < 0 || !A || !B || !C) return HPS_ERR_INVALID;
+  if (lda < std::max(m, 1) || ldb < std::max(k, 1) || ldc < std::max(m, 1)) return HPS_ERR_INVALID;
+  if (m == 0 || n == 0 || batch == 0) return HPS_OK;
+  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C)) return HPS_ERR_INVALID;
+  // an empty inner dimension leaves C = beta C; only beta 0 or 1 is supported there
+  if (k == 0 && beta != 0.0 && beta != 1.0) return HPS_ERR_INVALID;
+  if (k == 0 && beta == 1.0) return HPS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* derr = nullptr;
+  HPS_CUDA(cudaMalloc(&derr, sizeof(unsigned)));
+  hps::TcWorkspace w;
+  w.err_slot = &derr;
+  w.enabled = mode == 0;
+  w.force = true;
+  cudaError_t e = cudaMemsetAsync(derr, 0, sizeof(unsigned), st);
+  {
+    hps::TcScope scope(&w);
+    auto run = [&](auto* tag) -> cudaError_t {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      hps::GemmArgs<T> g;
+      g.M = m; g.N = n; g.K = k; g.batch = batch;
+      g.A = hps::bop<T>((T*)A, strideA, lda);
+      g.B = hps::bop<T>((T*)B, strideB, ldb);
+      g.C = hps::bop<T>((T*)C, strideC, ldc);
+      g.alpha = T(alpha);
+      g.beta = T(beta);
+      if (k == 0) return hps::fill<T>(g.C, m, n, batch, T(0.0), T(0.0), st, nullptr);
+      return hps::gemm<T>(g, st, nullptr);
+    };
+    if (e == cudaSuccess) e = dtype == HPS_F64 ? run((double*)nullptr) : run((hps::cplx*)nullptr);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  unsigned herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  hps::tc_release(&w);
+  cudaFree(derr);
+  if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return HPS_ERR_OOM; }
+  if (e != cudaSuccess) { cudaGetLastError(); return HPS_ERR_CUDA; }
+  return (herr & hps::DEV_ERR_TIMEOUT) ? HPS_ERR_TIMEOUT : HPS_OK;
 }
 
 hps_status hps_coeff_gradient(hps_handle* h, int nrhs, const void* u, const void* fbar, double* ga, double* gb,

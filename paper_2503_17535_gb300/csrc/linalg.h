@@ -18,7 +18,7 @@ namespace hps {
 
 // Kernel classes for launch / flop accounting and optional event timing.
 enum KClass { K_GEMM = 0, K_LU_PANEL, K_LASWP_TRSM, K_TRSM_DIAG, K_ASSEMBLE, K_GATHER, K_DOWN,
-              K_OTHER, K_COUNT };
+              K_OTHER, K_GEMM_TC, K_SPLIT, K_COUNT };
 
 // Launch accounting.  Every launch adds its class's algorithmic FP64 flops
 // (a complex multiply-add counts 8); with `on` set each launch is also
@@ -100,6 +100,33 @@ struct GemmArgs {
 
 template <typename T>
 cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf);
+
+// Tensor-core FP64 products (gemm_tc.cu): workspace for the operands' bf16
+// digit slices.  gemm() routes a product to the tensor cores when the calling
+// thread has an enabled workspace installed (TcScope) and the shape is large
+// enough; otherwise it runs on the FP64 pipe.  Kernel timeouts set
+// DEV_ERR_TIMEOUT in *err_slot.
+struct TcWorkspace {
+  void* p = nullptr;
+  size_t bytes = 0;
+  unsigned* const* err_slot = nullptr;
+  bool enabled = false;
+  bool force = false;   // every product with K >= 1 (no size threshold)
+};
+TcWorkspace*& tc_workspace();
+void tc_release(TcWorkspace* w);
+// bytes the digit slices of one launch group may take (the allocation is at
+// least 64 MB and at most this, unless a single matrix needs more)
+size_t tc_workspace_cap();
+struct TcScope {
+  TcWorkspace* prev;
+  explicit TcScope(TcWorkspace* w) : prev(tc_workspace()) { tc_workspace() = w; }
+  ~TcScope() { tc_workspace() = prev; }
+};
+template <typename T>
+bool tc_applicable(const GemmArgs<T>& g);
+template <typename T>
+cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf);
 
 // LU with partial pivoting of `batch` n x n matrices (in place), LAPACK
 // semantics: ipiv[j] = row swapped with row j (0-based), perm = the row
