@@ -163,9 +163,12 @@ typedef struct {
   int64_t launches;  /* launches of this class in the last build or solve          */
   double flops;      /* algorithmic FP64 flops (complex multiply-add = 8)          */
   double ms;         /* summed CUDA-event time, or -1 when profiling is off         */
-  double exec_flops; /* flops the FP64 pipe executes: equal to flops except for the
-                        complex GEMM, which takes 3 real products per complex
-                        multiply-add (Gauss / 3M form: 6 flops instead of 8)   */
+  double exec_flops; /* flops the executing pipe performs: the FP64 pipe's equal
+                        flops except for the complex GEMM, which takes 3 real
+                        products per complex multiply-add (Gauss / 3M form: 6
+                        flops instead of 8); for HPS_KCLASS_GEMM_TC the bf16
+                        tensor-core flops of the digit products over the padded
+                        128 x 48 x 16 tiles (55 products per real product)    */
 } hps_kernel_stat;
 
 typedef struct hps_handle hps_handle;

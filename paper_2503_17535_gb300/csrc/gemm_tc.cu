@@ -30,10 +30,11 @@
 // 48-column B tile one 1.5 KB block), so that one k step of all digits is one
 // contiguous bulk copy (cp.async.bulk) per operand.  The GEMM kernel runs one
 // 128 x 48 output tile per CTA: a producer warp streams the digit blocks
-// through a 4-stage shared-memory ring, one thread issues the 55 MMAs per k
-// step into 10 TMEM accumulators (480 of 512 columns), and eight epilogue
-// warps (two per TMEM lane quarter, one per half of the columns) read the
-// accumulators back.
+// through a 3-stage shared-memory ring, one thread issues the products as
+// 15 MMAs per k step (digits of B stacked along N, up to 5 per MMA, land in
+// adjacent diagonal accumulators), ten TMEM accumulators take 480 of the 512
+// columns, and eight epilogue warps (two per TMEM lane quarter, one per half
+// of the columns) read them back while the C tile waits in shared memory.
 //
 // Complex products are four real products (re*re, im*im, re*im, im*re),
 // each written into its component of C.
@@ -59,6 +60,7 @@ constexpr int BBLK = TN * TK * 2;
 constexpr int ASTG = DIG * ABLK;
 constexpr int BSTG = DIG * BBLK;
 constexpr int STAGE = ASTG + BSTG;
+constexpr int QGRP = 5;             // B digits stacked into one MMA (N = 5 * 48 = 240 <= 256)
 constexpr int NST = 3;
 constexpr int CSTG = TN * TM * 8;     // the C tile staged for the epilogue (column-major)
 constexpr int SMEM = NST * STAGE + CSTG;
@@ -70,6 +72,7 @@ constexpr long SPIN = 1L << 22;     // polls before a wait gives up
 
 static_assert(NDIAG * TN <= TMEM_COLS, "accumulators exceed TMEM");
 static_assert(ECOLS % 4 == 0, "epilogue column groups of 4");
+static_assert(NDIAG == 10 && DSUM == 11 && BITS == 6, "the epilogue pairs diagonals 2..11 into H (2..7) and L (8..11)");
 // largest |sum of the digit products on one diagonal| per k: the two pairs
 // with a leading digit (64 * 32 each) and the others (32 * 32), or 64 * 64
 // (below 2^22 the epilogue converts them to integers with one fp32 add)
@@ -119,95 +122,108 @@ struct Src {
   int part = 0;
 };
 
-// Row maxima of an operand, as biased FP64 exponents: thread per (row,
-// k range of KSPAN); atomicMax into ex (zeroed beforehand).  A zero or
-// subnormal row keeps 0 (all its digits are then 0).
-constexpr int KSPAN = 64;
-
-template <typename T>
-__global__ void __launch_bounds__(128) k_split_max(Src<T> s, int R, int K, int* ex, int exstride, int b0) {
-  const int bl = blockIdx.z, b = b0 + bl;
-  const int r = blockIdx.x * 128 + threadIdx.x;
-  if (r >= R) return;
-  const int k0 = blockIdx.y * KSPAN, k1 = min(K, k0 + KSPAN);
-  const T* X = s.X.item(b);
-  const int64_t roff = (int64_t)s.rmap.at(b, r) * s.rs;
-  unsigned long long mx = 0;
-  for (int k = k0; k < k1; ++k) {
-    const double v = part_of(X[roff + (int64_t)s.kmap.at(b, k) * s.ks], s.part);
-    mx = max(mx, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
-  }
-  const int evm = (int)(mx >> 52);
-  if (evm) atomicMax(ex + (int64_t)bl * exstride + r, evm);
-}
-
 // exponent e of a row (max |x| < 2^e) from its biased maximum exponent
 __device__ __forceinline__ int row_exp(int evm) { return evm ? evm - 1022 : 0; }
 
-// Digits of a K-major operand: thread per (padded row, 8-deep k group).
-template <typename T, int TR>
-__global__ void __launch_bounds__(128) k_split(Src<T> s, int R, int K, int RT, int KT, uint8_t* out,
-                                               const int* ex, int exstride, int b0) {
-  constexpr int BLK = TR * TK * 2;
-  const int bl = blockIdx.z, b = b0 + bl;
-  const int r = blockIdx.x * 128 + threadIdx.x;
-  const int Rpad = RT * TR;
-  if (r >= Rpad) return;
-  const int k0 = blockIdx.y * 8;
+// The operands of one product call (A and B, and for complex data their
+// real and imaginary parts): rows x K each, cut into digit blocks with
+// row tiles of TR rows.
+constexpr int MAXOPS = 4;
+template <typename T>
+struct SplitSet {
+  Src<T> s[MAXOPS];
+  int R[MAXOPS], TR[MAXOPS], RT[MAXOPS];
+  uint8_t* out[MAXOPS];
+  int* ex[MAXOPS];    // biased exponent of each row's largest |entry| (0: zero row)
+};
+
+// One launch for all operands: CTA = 32 rows x 8 warps; warp w takes the
+// 8-deep k groups w, w+8, ...  Pass 1 finds each row's largest magnitude
+// (compared as bit patterns, which order like the values), pass 2 writes
+// the balanced base-64 digits of the row scaled by 2^{FRAC - e}, rounded to
+// an integer.
+template <typename T>
+__global__ void __launch_bounds__(256) k_split(SplitSet<T> ss, int K, int KT, int b0, int nb) {
+  const int op = blockIdx.z / nb, bl = blockIdx.z % nb, b = b0 + bl;
+  const int R = ss.R[op], TR = ss.TR[op], Rpad = ss.RT[op] * TR;
+  if (blockIdx.x * 32 >= Rpad) return;                 // uniform over the CTA
+  const Src<T>& s = ss.s[op];
+  const int lr = threadIdx.x & 31, kw = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + lr;
   const T* X = s.X.item(b);
   const bool live = r < R;
-  const int evm = live ? ex[(int64_t)bl * exstride + r] : 0;
+  const int64_t roff = live ? (int64_t)s.rmap.at(b, r) * s.rs : 0;
+  const int ngrp = KT * 2;
+  __shared__ unsigned long long smax[8][32];
+  unsigned long long mx = 0;
+  if (live)
+    for (int gi = kw; gi < ngrp; gi += 8)
+      for (int c = 0; c < 8; ++c) {
+        const int k = gi * 8 + c;
+        if (k >= K) break;
+        const double v = part_of(X[roff + (int64_t)s.kmap.at(b, k) * s.ks], s.part);
+        mx = max(mx, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
+      }
+  smax[kw][lr] = mx;
+  __syncthreads();
+#pragma unroll
+  for (int w = 0; w < 8; ++w) mx = max(mx, smax[w][lr]);
+  const int evm = (int)(mx >> 52);
+  if (kw == 0 && r < Rpad) ss.ex[op][(int64_t)bl * Rpad + r] = evm;
+  if (r >= Rpad) return;
   const bool zero = evm == 0;
   const int e = row_exp(evm);
-  const int64_t roff = live ? (int64_t)s.rmap.at(b, r) * s.rs : 0;
+  const int BLK = TR * TK * 2;
   const int tile = r / TR, rr = r % TR;
-  uint8_t* blk = out + ((int64_t)bl * RT + tile) * KT * (int64_t)(DIG * BLK) + (rr >> 3) * 256 + (rr & 7) * 16 +
-                 (int64_t)(k0 >> 4) * (DIG * BLK) + ((k0 >> 3) & 1) * 128;
-  int dg[8][DIG];
+  uint8_t* base = ss.out[op] + ((int64_t)bl * ss.RT[op] + tile) * KT * (int64_t)(DIG * BLK) + (rr >> 3) * 256 +
+                  (rr & 7) * 16;
+  for (int gi = kw; gi < ngrp; gi += 8) {
+    const int k0 = gi * 8;
+    int dg[8][DIG];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int k = k0 + c;
-    double v = 0.0;
-    if (live && !zero && k < K) v = part_of(X[roff + (int64_t)s.kmap.at(b, k) * s.ks], s.part);
-    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    const int ev = (int)((u >> 52) & 0x7FF);
-    // |v| 2^{FRAC - e} rounded to an integer (<= 2^FRAC), then signed
-    const long long m = (long long)((u & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-    const int sh = ev - (1075 - FRAC) - e;
-    long long x = 0;
-    if (ev != 0) {
-      if (sh >= 0) x = m << sh;
-      else if (sh > -62) x = ((m >> (-sh - 1)) + 1) >> 1;
-    }
-    if (u >> 63) x = -x;
-    // balanced base-64 digits, least significant first
-#pragma unroll
-    for (int p = DIG - 1; p > 0; --p) {
-      const int d = (int)((x + 32) & 63) - 32;
-      dg[c][p] = d;
-      x = (x - d) >> BITS;
-    }
-    dg[c][0] = (int)x;
-  }
-#pragma unroll
-  for (int p = 0; p < DIG; ++p) {
-    uint32_t w[4];
-#pragma unroll
-    for (int c = 0; c < 8; c += 2) {
-      uint32_t h[2];
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int d = dg[c + t][p];
-        const uint32_t a = (uint32_t)(d < 0 ? -d : d);
-        // |d| <= 64 as an exact float; its upper 16 bits are the bf16 encoding
-        const float f = __uint_as_float(0x4B000000u | a) - 8388608.0f;
-        h[t] = (__float_as_uint(f) >> 16) | (d < 0 ? 0x8000u : 0u);
+    for (int c = 0; c < 8; ++c) {
+      const int k = k0 + c;
+      double v = 0.0;
+      if (live && !zero && k < K) v = part_of(X[roff + (int64_t)s.kmap.at(b, k) * s.ks], s.part);
+      const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+      const int ev = (int)((u >> 52) & 0x7FF);
+      // |v| 2^{FRAC - e} rounded to an integer (<= 2^FRAC), then signed
+      const long long m = (long long)((u & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+      const int sh = ev - (1075 - FRAC) - e;
+      long long x = 0;
+      if (ev != 0) {
+        if (sh >= 0) x = m << sh;
+        else if (sh > -62) x = ((m >> (-sh - 1)) + 1) >> 1;
       }
-      w[c >> 1] = h[0] | (h[1] << 16);
+      if (u >> 63) x = -x;
+      // balanced base-64 digits, least significant first
+#pragma unroll
+      for (int p = DIG - 1; p > 0; --p) {
+        const int d = (int)((x + 32) & 63) - 32;
+        dg[c][p] = d;
+        x = (x - d) >> BITS;
+      }
+      dg[c][0] = (int)x;
     }
-    *reinterpret_cast<uint4*>(blk + (int64_t)p * BLK) = make_uint4(w[0], w[1], w[2], w[3]);
+    uint8_t* blk = base + (int64_t)(k0 >> 4) * (DIG * BLK) + ((k0 >> 3) & 1) * 128;
+#pragma unroll
+    for (int p = 0; p < DIG; ++p) {
+      uint32_t w[4];
+#pragma unroll
+      for (int c = 0; c < 8; c += 2) {
+        // d (|d| <= 64) as an exact float: 1.5 * 2^23 + d has d in its low
+        // mantissa bits; subtracting 1.5 * 2^23 leaves d, whose upper 16
+        // bits are its bf16 encoding (d has at most 7 significant bits)
+        const float f0 = __int_as_float(0x4B400000 + dg[c][p]) - 12582912.0f;
+        const float f1 = __int_as_float(0x4B400000 + dg[c + 1][p]) - 12582912.0f;
+        w[c >> 1] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+      }
+      *reinterpret_cast<uint4*>(blk + (int64_t)p * BLK) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
   }
 }
+
+__device__ __noinline__ double scale_slow(long long R, int es) { return ldexp((double)R, es); }
 
 // R 2^es as the nearest double (ties to even), from the integer's bits;
 // falls back to ldexp outside the normal range.
@@ -221,7 +237,7 @@ __device__ __forceinline__ double fixed_to_double(long long R, int es) {
   const unsigned long long rem = a & 0x7FFull;
   m += (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) ? 1ull : 0ull;
   const int e2 = es + 63 - lz;                 // value in [2^e2, 2^(e2+1))
-  if (e2 + 1023 < 1 || e2 + 1023 > 2046) return ldexp((double)R, es);
+  if (e2 + 1023 < 1 || e2 + 1023 > 2046) return scale_slow(R, es);
   // m carries the hidden bit: adding it to (exponent - 1) sets the exponent
   // (and carries once more when rounding reached 2^53)
   return __longlong_as_double((long long)(sgn | (((unsigned long long)(e2 + 1022) << 52) + m)));
@@ -301,15 +317,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
   } else if (warp == EPI_WARPS + 1) {
     // MMA issue: 53 digit-pair products per k step into the 10 diagonal accumulators
     if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                             ((uint32_t)(TM >> 4) << 24);
+      // B's digit blocks lie one after another with the same row-group stride,
+      // so digits q0 .. q0+n-1 form one operand of n * 48 rows, and A_p times
+      // it lands in the accumulators of diagonals p+q0 .. p+q0+n-1, which are
+      // adjacent in TMEM: one MMA (N <= 240) per (p, group of <= 5 digits).
+      const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TM >> 4) << 24);
       int it = 0;
       bool ok = true;
       for (int c = 0; c < nchunk && ok; ++c) {
         if (c > 0 && !mbar_wait(su32(&acc_empty), (c - 1) & 1, abrt)) { ok = false; break; }
         fence_after();
-        const int kend = min(g.KT, (c + 1) * KCT);
-        uint32_t touched = 0;
+        const int kbeg = it, kend = min(g.KT, (c + 1) * KCT);
         for (; it < kend; ++it) {
           const int s = it % NST;
           if (!mbar_wait(su32(&full[s]), (it / NST) & 1, abrt)) { ok = false; break; }
@@ -318,16 +336,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
 #pragma unroll
           for (int p = 0; p < DIG; ++p) {
             const uint64_t ad = sdesc(a0 + p * ABLK, 128, 256);
+            const int nq_all = (DSUM - 1 - p) < DIG ? (DSUM - 1 - p) : DIG;   // q = 0 .. nq_all-1
 #pragma unroll
-            for (int q = 0; q < DIG; ++q) {
-              if (p + q > DSUM - 2) continue;
-              const int di = p + q;
-              const uint32_t acc = (touched >> di) & 1u;
-              touched |= 1u << di;
-              const uint64_t bd = sdesc(b0 + q * BBLK, 128, 256);
+            for (int q0 = 0; q0 < nq_all; q0 += QGRP) {
+              const int nq = (nq_all - q0) < QGRP ? (nq_all - q0) : QGRP;
+              // the first k step of a chunk overwrites: p = 0 covers every diagonal once
+              const uint32_t acc = (it != kbeg || p != 0) ? 1u : 0u;
+              const uint64_t bd = sdesc(b0 + q0 * BBLK, 128, 256);
+              const uint32_t idesc = idesc0 | ((uint32_t)((nq * TN) >> 3) << 17);
               asm volatile(
                   "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(di * TN)),
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)((p + q0) * TN)),
                   "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
           }
@@ -375,15 +394,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
 #pragma unroll
     for (int j = 0; j < ECOLS; ++j) R[j] = 0;
     // diagonal d = di + 2 has weight 2^{-6d}; R counts units of 2^{-lsb}.
-    // Diagonals with 6d <= lsb enter R exactly; the others are first summed
-    // exactly in units of 2^{-6 DSUM} and then rounded into R once.
-    int shl[NDIAG];
-#pragma unroll
-    for (int di = 0; di < NDIAG; ++di) {
-      const int sh = g.lsb - BITS * (di + 2);
-      shl[di] = sh >= 0 ? sh : -1 - BITS * (DSUM - 2 - di);   // < 0: low part, shift -1 - sh
-    }
-    const int low_sh = BITS * DSUM - g.lsb;   // units 2^{-6 DSUM} -> 2^{-lsb}
+    // Adjacent diagonals pair up exactly in 32 bits (y = x_d * 64 + x_{d+1},
+    // |y| < 2^29), the pairs of d = 2..7 form H (units 2^{-42}) and those of
+    // d = 8..11 form L (units 2^{-66}) in 64 bits; H enters R exactly and L
+    // rounded once.  lsb is at least 42 (K <= 2^20).
+    const int shH = g.lsb - 42, shL = 66 - g.lsb;
+    const long long halfL = 1ll << (shL - 1);
     bool ok = true;
     for (int c = 0; c < nchunk; ++c) {
       if (!mbar_wait(su32(&acc_full), c & 1, abrt)) { ok = false; break; }
@@ -401,15 +417,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          long long hi = R[cg * 4 + j], lo = 0;
+          // an fp32 holding an integer below 2^22, plus 1.5 * 2^23, has the
+          // integer in its low mantissa bits: x = bits - 0x4B400000
+          int y[NDIAG / 2];
 #pragma unroll
-          for (int di = 0; di < NDIAG; ++di) {
-            // exact integer below 2^22: adding 1.5 * 2^23 leaves it in the low mantissa bits
-            const long long x = (long long)(__float_as_int(__uint_as_float(v[di][j]) + 12582912.0f) - 0x4B400000);
-            if (shl[di] >= 0) hi += x << shl[di];
-            else lo += x << (-1 - shl[di]);
+          for (int k = 0; k < NDIAG / 2; ++k) {
+            const uint32_t a = __float_as_uint(__uint_as_float(v[2 * k][j]) + 12582912.0f);
+            const uint32_t c2 = __float_as_uint(__uint_as_float(v[2 * k + 1][j]) + 12582912.0f);
+            y[k] = (int)(a * 64u + c2 - 65u * 0x4B400000u);
           }
-          R[cg * 4 + j] = hi + ((lo + (1ll << (low_sh - 1))) >> low_sh);
+          const long long H = ((long long)y[0] << 24) + ((long long)y[1] << 12) + (long long)y[2];
+          const long long L = ((long long)y[3] << 12) + (long long)y[4];
+          R[cg * 4 + j] += (H << shH) + ((L + halfL) >> shL);
         }
       }
       fence_before();
@@ -421,6 +440,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");   // s_eb from other epilogue warps
+    const bool amode1 = g.amode == 1, beta1 = g.beta == 1.0;
     if (ok && i < g.M) {
       const int er = row_exp(g.ea[(int64_t)bl * g.MT * TM + i]);
 #pragma unroll
@@ -430,10 +450,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
         if (col >= g.N) break;
         double val = fixed_to_double(R[jj], er + s_eb[j] - g.lsb);
         double* cp = Cb + (ci + (int64_t)col * g.C.ld) * W + g.cpart;
-        if (g.amode == 1) {          // alpha = +-1: a sign flip
+        if (amode1) {                // alpha = +-1: a sign flip
           val = __longlong_as_double(__double_as_longlong(val) ^ g.asign);
           if (BETA0) *cp = val;
-          else if (g.beta == 1.0) *cp = s_c[j * TM + row] + val;
+          else if (beta1) *cp = s_c[j * TM + row] + val;
           else *cp = fma(g.beta, s_c[j * TM + row], val);
         } else {
           if (BETA0) *cp = g.alpha * val;
@@ -446,6 +466,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
+
+// digit pairs (p, q), 1 <= p, q <= DIG, with p + q <= DSUM
+constexpr int npairs() {
+  int n = 0;
+  for (int p = 1; p <= DIG; ++p)
+    for (int q = 1; q <= DIG; ++q) n += (p + q <= DSUM) ? 1 : 0;
+  return n;
+}
+static_assert(npairs() == 55, "digit pair count");
+static_assert(QGRP * TN <= 256 && (QGRP * TN) % 16 == 0, "MMA N for M = 128");
 
 int ceil_log2(int64_t x) {
   int c = 0;
@@ -497,9 +527,9 @@ void tc_release(TcWorkspace* w) {
 template <typename T>
 bool tc_applicable(const GemmArgs<T>& g) {
   const TcWorkspace* w = tc_workspace();
-  if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta) return false;
+  if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta || g.K > (1 << 20)) return false;
   if (w->force) return true;
-  if (g.M < 64 || g.N < 32 || g.K < 16) return false;
+  if (g.M < 32 || g.N < 16 || g.K < 16) return false;
   if ((double)g.M * g.N * g.K * g.batch < 1.0e7) return false;
   return true;
 }
@@ -507,10 +537,10 @@ bool tc_applicable(const GemmArgs<T>& g) {
 template <>
 bool tc_applicable<cplx>(const GemmArgs<cplx>& g) {
   const TcWorkspace* w = tc_workspace();
-  if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta) return false;
+  if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta || g.K > (1 << 20)) return false;
   if (g.alpha.im != 0.0 || g.beta.im != 0.0) return false;
   if (w->force) return true;
-  if (g.M < 64 || g.N < 32 || g.K < 16) return false;
+  if (g.M < 32 || g.N < 16 || g.K < 16) return false;
   if ((double)g.M * g.N * g.K * g.batch < 2.5e6) return false;
   return true;
 }
@@ -534,23 +564,15 @@ cudaError_t ensure_ws(TcWorkspace* w, size_t bytes, cudaStream_t st) {
   return cudaSuccess;
 }
 
-template <typename T, int TR>
-void launch_split(const tc::Src<T>& s, int R, int K, int RT, int KT, uint8_t* out, int* ex, int b0, int nb,
-                  cudaStream_t st, Prof* pf) {
-  const int Rpad = RT * TR;
-  cudaMemsetAsync(ex, 0, sizeof(int) * (size_t)Rpad * nb, st);
+template <typename T>
+void launch_split(const tc::SplitSet<T>& ss, int nops, int K, int KT, int b0, int nb, cudaStream_t st, Prof* pf) {
+  int rmax = 0;
+  for (int o = 0; o < nops; ++o) rmax = std::max(rmax, ss.RT[o] * ss.TR[o]);
   if (pf) {
     pf->begin(st);
-    pf->note(R, 0, K, nb);
+    pf->note(rmax, nops, K, nb);
   }
-  tc::k_split_max<T><<<dim3((R + 127) / 128, (K + tc::KSPAN - 1) / tc::KSPAN, nb), 128, 0, st>>>(s, R, K, ex, Rpad,
-                                                                                                 b0);
-  if (pf) {
-    pf->end(K_SPLIT, 0.0, st);
-    pf->begin(st);
-    pf->note(R, 0, K, nb);
-  }
-  tc::k_split<T, TR><<<dim3((Rpad + 127) / 128, KT * 2, nb), 128, 0, st>>>(s, R, K, RT, KT, out, ex, Rpad, b0);
+  tc::k_split<T><<<dim3((rmax + 31) / 32, 1, nops * nb), 256, 0, st>>>(ss, K, KT, b0, nb);
   if (pf) pf->end(K_SPLIT, 0.0, st);
 }
 
@@ -568,7 +590,10 @@ void launch_mma(const tc::GemmP<T>& p, int nb, int K, cudaStream_t st, Prof* pf)
     tc::set_smem_attr<T, false>();
     tc::k_gemm_tc<T, false><<<grid, tc::THREADS, tc::SMEM, st>>>(p);
   }
-  if (pf) pf->end(K_GEMM_TC, 2.0 * p.M * (double)p.N * K * nb, st, 0.0);
+  // executed: bf16 tensor-core flops of the digit products over the padded tiles
+  const double npairs = tc::npairs();
+  const double exec = 2.0 * npairs * (double)p.MT * tc::TM * (double)p.NT * tc::TN * (double)p.KT * tc::TK * nb;
+  if (pf) pf->end(K_GEMM_TC, 2.0 * p.M * (double)p.N * K * nb, st, exec);
 }
 
 }  // namespace
@@ -580,7 +605,7 @@ cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   TcWorkspace* w = tc_workspace();
   const Sizes z = sizes(g.M, g.N, g.K);
   const size_t per_item = NP * (z.a_item + z.b_item + z.ea_item + z.eb_item);
-  const int nb_max = (int)std::max<size_t>(1, std::min<size_t>(std::min(g.batch, 65535), WS_CAP / per_item));
+  const int nb_max = (int)std::max<size_t>(1, std::min<size_t>(std::min(g.batch, 65535 / (2 * NP)), WS_CAP / per_item));
   cudaError_t e = ensure_ws<T>(w, per_item * nb_max, st);
   if (e != cudaSuccess) return e;
   uint8_t* base = static_cast<uint8_t*>(w->p);
@@ -605,14 +630,19 @@ cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   else { alpha = g.alpha; beta = g.beta; }
   for (int b0 = 0; b0 < g.batch; b0 += nb_max) {
     const int nb = std::min(nb_max, g.batch - b0);
+    SplitSet<T> ss;
+    int nops = 0;
     for (int pt = 0; pt < NP; ++pt) {
       Src<T> sa;
       sa.X = g.A; sa.rmap = g.arow; sa.kmap = g.acol; sa.rs = 1; sa.ks = g.A.ld; sa.part = pt;
-      launch_split<T, TM>(sa, g.M, g.K, z.MT, z.KT, As[pt], ea[pt], b0, nb, st, pf);
+      ss.s[nops] = sa; ss.R[nops] = g.M; ss.TR[nops] = TM; ss.RT[nops] = z.MT; ss.out[nops] = As[pt];
+      ss.ex[nops] = ea[pt]; ++nops;
       Src<T> sb;
       sb.X = g.B; sb.kmap = g.brow; sb.rs = g.B.ld; sb.ks = 1; sb.part = pt;
-      launch_split<T, TN>(sb, g.N, g.K, z.NT, z.KT, Bs[pt], eb[pt], b0, nb, st, pf);
+      ss.s[nops] = sb; ss.R[nops] = g.N; ss.TR[nops] = TN; ss.RT[nops] = z.NT; ss.out[nops] = Bs[pt];
+      ss.ex[nops] = eb[pt]; ++nops;
     }
+    launch_split<T>(ss, nops, g.K, z.KT, b0, nb, st, pf);
     GemmP<T> p;
     p.MT = z.MT; p.NT = z.NT; p.KT = z.KT; p.M = g.M; p.N = g.N; p.lsb = lsb;
     p.C = g.C; p.crow = g.crow; p.b0 = b0; p.err = *w->err_slot;
