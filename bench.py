@@ -93,7 +93,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="helmholtz2d", choices=sorted(WORKLOADS) + ["serve", "diff"])
+    ap.add_argument("--workload", default="helmholtz2d", choices=sorted(WORKLOADS) + ["serve", "diff", "gemm"])
     ap.add_argument("--requests", type=int, default=None, help="serve: requests per arrival rate")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -116,6 +116,9 @@ def parse():
     if args.workload == "diff":
         args.spec = {"workload": "diff_helmholtz2d_theta64_depth5_p16", "depth": 5, "p": 16, "k": 20.0,
                      "grid": 64, "seed": 5}
+        return args
+    if args.workload == "gemm":
+        args.spec = {"workload": "gemm_lu_update_and_schur_shapes"}
         return args
     spec = dict(WORKLOADS[args.workload])
     if args.depth is not None and spec["depth"] >= 0 and args.depth != spec["depth"]:
@@ -788,6 +791,52 @@ def run_diff(args, rank, world):
     return 0
 
 
+def run_gemm(args, rank, world):
+    """The build's two product shapes alone through hps_gemm: an LU / triangular
+    update (inner dimension 32) and a Schur complement (inner dimension 448),
+    C -= A B in FP64, on the tensor cores (mode 0) and on the FP64 pipe
+    (mode 1); checks mode 0 against mode 1 and times both with CUDA events
+    (each call synchronises and allocates its workspace, so the times include
+    that host overhead; ncu gives the kernel alone)."""
+    import torch
+    import paper_2503_17535_gb300 as P
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    out = {}
+    for name, (m, n, k, b) in {"lu_update": (1696, 3457, 32, 2), "schur": (448, 1793, 448, 4)}.items():
+        g = torch.Generator(device="cuda").manual_seed(m + n + k)
+        A = torch.randn(b, k, m, dtype=torch.float64, device="cuda", generator=g)
+        B = torch.randn(b, n, k, dtype=torch.float64, device="cuda", generator=g)
+        C0 = torch.randn(b, n, m, dtype=torch.float64, device="cuda", generator=g)
+        res = {}
+        for mode in (0, 1):
+            C = C0.clone()
+            P.hps_gemm(A, B, C, alpha=-1.0, beta=1.0, mode=mode)   # warm-up (and result)
+            ts = []
+            for _ in range(max(args.steps, 1)):
+                Ct = C0.clone()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                P.hps_gemm(A, B, Ct, alpha=-1.0, beta=1.0, mode=mode)
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            res[mode] = (C, statistics.median(ts))
+        mag = torch.bmm(A.abs().transpose(1, 2), B.abs().transpose(1, 2))
+        err = ((res[0][0] - res[1][0]).abs().transpose(1, 2) / (mag + 1.0)).max().item()
+        if err >= 1e-13:
+            raise SystemExit(f"gemm {name}: tensor-core result differs from the FP64 pipe by {err:.3e}")
+        fl = 2.0 * m * n * k * b
+        out[name] = {"m": m, "n": n, "k": k, "batch": b, "max_err_rel_AB": err,
+                     "tc_ms": round(res[0][1], 4), "fp64_ms": round(res[1][1], 4),
+                     "tc_fp64_equiv_tflops": round(fl / res[0][1] / 1e9, 3),
+                     "fp64_tflops": round(fl / res[1][1] / 1e9, 3)}
+    if rank == 0:
+        print(json.dumps({"metric": "hps_gemm FP64 products: tensor-core digit slices vs FP64 pipe",
+                          "unit": "ms", "higher_is_better": False, "data": "synthetic",
+                          "config": {"workload": args.spec["workload"]}, "shapes": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -796,6 +845,8 @@ def main():
         return run_serve(args, rank, world)
     if args.workload == "diff":
         return run_diff(args, rank, world)
+    if args.workload == "gemm":
+        return run_gemm(args, rank, world)
     spec = args.spec
     if args.impl == "reference":
         line = run_reference(args, rank)

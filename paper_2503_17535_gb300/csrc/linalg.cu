@@ -721,9 +721,10 @@ __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int n
 }
 
 // Apply the panel's interchanges to every column outside the panel and
-// solve U12 = L11^{-1} A12 for the columns right of it.
+// solve U12 = L11^{-1} A12 for the columns in [k0 + nb, trsm_end).
 template <typename T>
-__global__ void __launch_bounds__(128) k_laswp_trsm(BOp<T> A, int n, int k0, int nb, const int* ipiv) {
+__global__ void __launch_bounds__(128) k_laswp_trsm(BOp<T> A, int n, int k0, int nb, const int* ipiv,
+                                                    int trsm_end) {
   extern __shared__ unsigned char smem_raw[];
   T* L11 = reinterpret_cast<T*>(smem_raw);  // nb x nb, column-major
   __shared__ int piv[64];
@@ -745,7 +746,7 @@ __global__ void __launch_bounds__(128) k_laswp_trsm(BOp<T> A, int n, int k0, int
       int j = k0 + jj;
       if (p != j) { T tmp = col[j]; col[j] = col[p]; col[p] = tmp; }
     }
-    if (c >= k0 + nb) {
+    if (c >= k0 + nb && c < trsm_end) {
       T x[64];
 #pragma unroll 8
       for (int jj = 0; jj < nb; ++jj) x[jj] = col[k0 + jj];
@@ -824,71 +825,125 @@ cudaError_t panel_smem_limit() {
   return err;
 }
 
+// Factor the panel A[k0:n, k0:k0+nb), apply its interchanges to every other
+// column and solve U12 = L11^{-1} A12 for the columns [k0 + nb, trsm_end).
+template <typename T>
+static cudaError_t lu_leaf(BOp<T> A, int n, int k0, int nb, int trsm_end, int batch, int* ipiv, int* info,
+                           unsigned* dev_err, int G, const LuWork& w, cudaStream_t st, Prof* pf) {
+  constexpr double F = fma_flops<T>();
+  const int nb0 = LuNB<T>::NB;
+  cudaError_t e;
+  const int rows = n - k0;
+  int Gk = std::min(G, std::max(1, rows / 8));
+  const int ch = (rows + Gk - 1) / Gk;
+  size_t sm = ((size_t)ch * nb + 2 * nb) * sizeof(T);
+  double pfl = 0.0;  // panel: rank-1 updates and multipliers (FMA-equivalents)
+  for (int jj = 0; jj < nb; ++jj) {
+    const double below = (double)(n - (k0 + jj) - 1);
+    pfl += below * (nb - jj - 1) + below;
+  }
+  pfl *= F * batch;
+  if (pf) {
+    pf->begin(st);
+    pf->note(rows, nb, Gk, batch);  // k: CTAs per matrix
+  }
+  if (Gk > 1) {
+    T* pubv = reinterpret_cast<T*>(w.pub);
+    double* pubm = reinterpret_cast<double*>(pubv + (size_t)batch * 2 * (G + 1) * nb0);
+    int* pubr = reinterpret_cast<int*>(pubm + (size_t)batch * 2 * G);
+    if ((e = panel_smem_limit<T, true>()) != cudaSuccess) return e;
+    BOp<T> Aa = A;
+    int nn = n, kk = k0, nbb = nb, GG = Gk;
+    unsigned* bars = w.bars;
+    void* args[] = {&Aa, &nn, &kk, &nbb, &GG, &ipiv, &info, &bars, &pubv, &pubm, &pubr, &dev_err};
+    e = cudaLaunchCooperativeKernel((void*)k_lu_panel<T, true>, dim3(batch * Gk), dim3(256), args, sm, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    if ((e = panel_smem_limit<T, false>()) != cudaSuccess) return e;
+    k_lu_panel<T, false><<<batch, 256, sm, st>>>(A, n, k0, nb, 1, ipiv, info, nullptr, nullptr, nullptr,
+                                                 nullptr, dev_err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (pf) pf->end(K_LU_PANEL, pfl, st);
+  if (n > nb) {
+    const int ncols = n - nb;
+    int bx = std::min((ncols + 127) / 128, 1024);
+    size_t sm2 = (size_t)nb * nb * sizeof(T);
+    if (pf) {
+      pf->begin(st);
+      pf->note(nb, ncols, nb, batch);
+    }
+    k_laswp_trsm<T><<<dim3(bx, batch), 128, sm2, st>>>(A, n, k0, nb, ipiv, trsm_end);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (pf) pf->end(K_LASWP_TRSM, F * 0.5 * nb * (nb - 1) * (double)std::max(0, trsm_end - k0 - nb) * batch, st);
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t rtrsm_lower(BOp<T> LU, BOp<T> X, int p0, int n1, int nrhs, int batch, cudaStream_t st,
+                               Prof* pf);
+
+// Recursive LU with partial pivoting of the columns [c0, c1) (rows c0..n):
+// factor the left half, U12 = L11^{-1} A12 by the recursive triangular
+// solve, A22 -= A21 U12 as one product of inner dimension ~(c1 - c0) / 2,
+// factor the right half.  Ranges of at most 4 panels are factored blocked
+// right-looking (panel, interchanges + U12 within the range, update of the
+// range's remaining columns), which keeps the launch count of the blocked
+// algorithm; so are whole matrices when there are few of them (base_w = n).  The same pivots and operations as the blocked right-looking
+// order; the bulk of the trailing updates becomes a few large-K products
+// (on the tensor cores) instead of n / nb products of inner dimension nb.
+template <typename T>
+static cudaError_t rgetrf(BOp<T> A, int n, int c0, int c1, int base_w, int batch, int* ipiv, int* info,
+                          unsigned* dev_err, int G, const LuWork& w, cudaStream_t st, Prof* pf) {
+  const int nb0 = LuNB<T>::NB;
+  const int wdt = c1 - c0;
+  cudaError_t e;
+  if (wdt <= base_w) {
+    for (int k0 = c0; k0 < c1; k0 += nb0) {
+      const int nb = std::min(nb0, c1 - k0);
+      if ((e = lu_leaf<T>(A, n, k0, nb, c1, batch, ipiv, info, dev_err, G, w, st, pf)) != cudaSuccess) return e;
+      const int m2 = n - k0 - nb, n2 = c1 - k0 - nb;
+      if (m2 > 0 && n2 > 0) {
+        GemmArgs<T> g;
+        g.M = m2; g.N = n2; g.K = nb; g.batch = batch;
+        g.A = shifted(A, (int64_t)(k0 + nb) + (int64_t)k0 * A.ld);
+        g.B = shifted(A, (int64_t)k0 + (int64_t)(k0 + nb) * A.ld);
+        g.C = shifted(A, (int64_t)(k0 + nb) + (int64_t)(k0 + nb) * A.ld);
+        g.alpha = T(-1.0); g.beta = T(1.0);
+        if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
+      }
+    }
+    return cudaSuccess;
+  }
+  const int cm = c0 + ((wdt / 2 + nb0 - 1) / nb0) * nb0;
+  if ((e = rgetrf<T>(A, n, c0, cm, base_w, batch, ipiv, info, dev_err, G, w, st, pf)) != cudaSuccess) return e;
+  // U12: rows [c0, cm), columns [cm, c1)
+  BOp<T> L11 = shifted(A, (int64_t)c0 + (int64_t)c0 * A.ld);
+  BOp<T> A12 = shifted(A, (int64_t)c0 + (int64_t)cm * A.ld);
+  if ((e = rtrsm_lower<T>(L11, A12, 0, cm - c0, c1 - cm, batch, st, pf)) != cudaSuccess) return e;
+  if (n > cm) {
+    GemmArgs<T> g;
+    g.M = n - cm; g.N = c1 - cm; g.K = cm - c0; g.batch = batch;
+    g.A = shifted(A, (int64_t)cm + (int64_t)c0 * A.ld);
+    g.B = A12;
+    g.C = shifted(A, (int64_t)cm + (int64_t)cm * A.ld);
+    g.alpha = T(-1.0); g.beta = T(1.0);
+    if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
+  }
+  return rgetrf<T>(A, n, cm, c1, base_w, batch, ipiv, info, dev_err, G, w, st, pf);
+}
+
 template <typename T>
 cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, unsigned* dev_err,
                   int G, const LuWork& w, cudaStream_t st, Prof* pf) {
   if (n <= 0 || batch <= 0) return cudaSuccess;
-  constexpr double F = fma_flops<T>();
-  const int nb0 = LuNB<T>::NB;
   cudaError_t e;
-  for (int k0 = 0; k0 < n; k0 += nb0) {
-    const int nb = std::min(nb0, n - k0);
-    const int rows = n - k0;
-    int Gk = std::min(G, std::max(1, rows / 8));
-    const int ch = (rows + Gk - 1) / Gk;
-    size_t sm = ((size_t)ch * nb + 2 * nb) * sizeof(T);
-    double pfl = 0.0;  // panel: rank-1 updates and multipliers (FMA-equivalents)
-    for (int jj = 0; jj < nb; ++jj) {
-      const double below = (double)(n - (k0 + jj) - 1);
-      pfl += below * (nb - jj - 1) + below;
-    }
-    pfl *= F * batch;
-    if (pf) {
-      pf->begin(st);
-      pf->note(rows, nb, Gk, batch);  // k: CTAs per matrix
-    }
-    if (Gk > 1) {
-      T* pubv = reinterpret_cast<T*>(w.pub);
-      double* pubm = reinterpret_cast<double*>(pubv + (size_t)batch * 2 * (G + 1) * nb0);
-      int* pubr = reinterpret_cast<int*>(pubm + (size_t)batch * 2 * G);
-      if ((e = panel_smem_limit<T, true>()) != cudaSuccess) return e;
-      BOp<T> Aa = A;
-      int nn = n, kk = k0, nbb = nb, GG = Gk;
-      unsigned* bars = w.bars;
-      void* args[] = {&Aa, &nn, &kk, &nbb, &GG, &ipiv, &info, &bars, &pubv, &pubm, &pubr, &dev_err};
-      e = cudaLaunchCooperativeKernel((void*)k_lu_panel<T, true>, dim3(batch * Gk), dim3(256), args,
-                                      sm, st);
-      if (e != cudaSuccess) return e;
-    } else {
-      if ((e = panel_smem_limit<T, false>()) != cudaSuccess) return e;
-      k_lu_panel<T, false><<<batch, 256, sm, st>>>(A, n, k0, nb, 1, ipiv, info, nullptr, nullptr,
-                                                   nullptr, nullptr, dev_err);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if (pf) pf->end(K_LU_PANEL, pfl, st);
-    if (n > nb) {
-      const int ncols = n - nb;
-      int bx = std::min((ncols + 127) / 128, 1024);
-      size_t sm2 = (size_t)nb * nb * sizeof(T);
-      if (pf) {
-        pf->begin(st);
-        pf->note(nb, n - k0 - nb, nb, batch);
-      }
-      k_laswp_trsm<T><<<dim3(bx, batch), 128, sm2, st>>>(A, n, k0, nb, ipiv);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      if (pf) pf->end(K_LASWP_TRSM, F * 0.5 * nb * (nb - 1) * (double)(n - k0 - nb) * batch, st);
-    }
-    const int m2 = n - k0 - nb;
-    if (m2 > 0) {
-      GemmArgs<T> g;
-      g.M = m2; g.N = m2; g.K = nb; g.batch = batch;
-      g.A = shifted(A, (int64_t)(k0 + nb) + (int64_t)k0 * A.ld);
-      g.B = shifted(A, (int64_t)k0 + (int64_t)(k0 + nb) * A.ld);
-      g.C = shifted(A, (int64_t)(k0 + nb) + (int64_t)(k0 + nb) * A.ld);
-      g.alpha = T(-1.0); g.beta = T(1.0);
-      if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
-    }
-  }
+  // Few matrices: the recursion's triangular solves become many small
+  // launches on a few SMs, so the blocked right-looking order (one fused
+  // interchange + U12 launch per panel) is kept there.
+  const int base_w = batch < 8 ? n : 4 * LuNB<T>::NB;
+  if ((e = rgetrf<T>(A, n, 0, n, base_w, batch, ipiv, info, dev_err, G, w, st, pf)) != cudaSuccess) return e;
   if (pf) pf->begin(st);
   k_ipiv_to_perm<<<(batch + 127) / 128, 128, 0, st>>>(ipiv, perm, n, batch);
   if (pf) pf->end(K_OTHER, 0.0, st);
@@ -1033,56 +1088,73 @@ cudaError_t trsm_diag(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch, 
   return cudaGetLastError();
 }
 
+// Recursive triangular solves on rows [p0, p0 + n1) of X: split at a
+// multiple of 32 near the middle, solve the first half, update the second
+// with one product of inner dimension ~n1/2, solve the second half; 32-row
+// diagonal blocks at the leaves.  Same operations as the blocked
+// right-looking order, but the updates are few large-K products (the bulk
+// runs on the tensor cores) instead of n/32 products of inner dimension 32
+// that each re-read the rest of X.
+template <typename T>
+static cudaError_t rtrsm_lower(BOp<T> LU, BOp<T> X, int p0, int n1, int nrhs, int batch, cudaStream_t st,
+                               Prof* pf) {
+  constexpr double F = fma_flops<T>();
+  cudaError_t e;
+  if (n1 <= 32) {
+    if (pf) {
+      pf->begin(st);
+      pf->note(n1, nrhs, n1, batch);
+    }
+    if ((e = trsm_diag<T, false>(LU, X, p0, n1, nrhs, batch, st)) != cudaSuccess) return e;
+    if (pf) pf->end(K_TRSM_DIAG, F * 0.5 * n1 * (n1 - 1) * (double)nrhs * batch, st);
+    return cudaSuccess;
+  }
+  const int h = ((n1 / 2 + 31) / 32) * 32;
+  if ((e = rtrsm_lower<T>(LU, X, p0, h, nrhs, batch, st, pf)) != cudaSuccess) return e;
+  GemmArgs<T> g;
+  g.M = n1 - h; g.N = nrhs; g.K = h; g.batch = batch;
+  g.A = shifted(LU, (int64_t)(p0 + h) + (int64_t)p0 * LU.ld);
+  g.B = shifted(X, (int64_t)p0);
+  g.C = shifted(X, (int64_t)(p0 + h));
+  g.alpha = T(-1.0); g.beta = T(1.0);
+  if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
+  return rtrsm_lower<T>(LU, X, p0 + h, n1 - h, nrhs, batch, st, pf);
+}
+
+template <typename T>
+static cudaError_t rtrsm_upper(BOp<T> LU, BOp<T> X, int p0, int n1, int nrhs, int batch, cudaStream_t st,
+                               Prof* pf) {
+  constexpr double F = fma_flops<T>();
+  cudaError_t e;
+  if (n1 <= 32) {
+    if (pf) {
+      pf->begin(st);
+      pf->note(n1, nrhs, n1, batch);
+    }
+    if ((e = trsm_diag<T, true>(LU, X, p0, n1, nrhs, batch, st)) != cudaSuccess) return e;
+    if (pf) pf->end(K_TRSM_DIAG, F * (0.5 * n1 * (n1 - 1) + n1) * (double)nrhs * batch, st);
+    return cudaSuccess;
+  }
+  const int h = ((n1 / 2 + 31) / 32) * 32;
+  if ((e = rtrsm_upper<T>(LU, X, p0 + h, n1 - h, nrhs, batch, st, pf)) != cudaSuccess) return e;
+  GemmArgs<T> g;
+  g.M = h; g.N = nrhs; g.K = n1 - h; g.batch = batch;
+  g.A = shifted(LU, (int64_t)p0 + (int64_t)(p0 + h) * LU.ld);
+  g.B = shifted(X, (int64_t)(p0 + h));
+  g.C = shifted(X, (int64_t)p0);
+  g.alpha = T(-1.0); g.beta = T(1.0);
+  if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
+  return rtrsm_upper<T>(LU, X, p0, h, nrhs, batch, st, pf);
+}
+
 template <typename T>
 cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaStream_t st,
                           Prof* pf) {
   if (n <= 0 || nrhs <= 0 || batch <= 0) return cudaSuccess;
-  constexpr double F = fma_flops<T>();
-  const int pb0 = 32;
   cudaError_t e;
-
-  // forward: unit lower
-  for (int p0 = 0; p0 < n; p0 += pb0) {
-    const int pb = std::min(pb0, n - p0);
-    if (pf) {
-      pf->begin(st);
-      pf->note(pb, nrhs, pb, batch);
-    }
-    if ((e = trsm_diag<T, false>(LU, X, p0, pb, nrhs, batch, st)) != cudaSuccess) return e;
-    if (pf) pf->end(K_TRSM_DIAG, F * 0.5 * pb * (pb - 1) * (double)nrhs * batch, st);
-    const int rest = n - p0 - pb;
-    if (rest > 0) {
-      GemmArgs<T> g;
-      g.M = rest; g.N = nrhs; g.K = pb; g.batch = batch;
-      g.A = shifted(LU, (int64_t)(p0 + pb) + (int64_t)p0 * LU.ld);
-      g.B = shifted(X, (int64_t)p0);
-      g.C = shifted(X, (int64_t)(p0 + pb));
-      g.alpha = T(-1.0); g.beta = T(1.0);
-      if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
-    }
-  }
-  // backward: non-unit upper
-  const int npan = (n + pb0 - 1) / pb0;
-  for (int pi = npan - 1; pi >= 0; --pi) {
-    const int p0 = pi * pb0;
-    const int pb = std::min(pb0, n - p0);
-    if (pf) {
-      pf->begin(st);
-      pf->note(pb, nrhs, pb, batch);
-    }
-    if ((e = trsm_diag<T, true>(LU, X, p0, pb, nrhs, batch, st)) != cudaSuccess) return e;
-    if (pf) pf->end(K_TRSM_DIAG, F * (0.5 * pb * (pb - 1) + pb) * (double)nrhs * batch, st);
-    if (p0 > 0) {
-      GemmArgs<T> g;
-      g.M = p0; g.N = nrhs; g.K = pb; g.batch = batch;
-      g.A = shifted(LU, (int64_t)p0 * LU.ld);
-      g.B = shifted(X, (int64_t)p0);
-      g.C = X;
-      g.alpha = T(-1.0); g.beta = T(1.0);
-      if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
-    }
-  }
-  return cudaSuccess;
+  // forward: unit lower; backward: non-unit upper
+  if ((e = rtrsm_lower<T>(LU, X, 0, n, nrhs, batch, st, pf)) != cudaSuccess) return e;
+  return rtrsm_upper<T>(LU, X, 0, n, nrhs, batch, st, pf);
 }
 
 // --------------------------------------------- flag-ordered solve ----
