@@ -1074,11 +1074,69 @@ __global__ void __launch_bounds__(128) k_trsm_diag_cols(BOp<T> LU, BOp<T> X, int
   }
 }
 
+// Full 32-row diagonal blocks: a CTA takes CT right-hand sides of one
+// matrix, loads the 32 x CT tile of X coalesced (a warp per column) into
+// shared memory (stride 33: conflict-free per-thread columns), solves one
+// column per thread in registers (fully unrolled), and stores coalesced.
+template <typename T, bool UPPER, int CT>
+__global__ void __launch_bounds__(CT) k_trsm32(BOp<T> LU, BOp<T> X, int p0, int nrhs, int batch) {
+  __shared__ T Ls[32 * 32];
+  __shared__ T Dinv[32];
+  __shared__ T Xs[CT * 33];
+  const int b = blockIdx.y;
+  const T* Lb = LU.item(b);
+  T* Xb = X.item(b);
+  const int j0 = blockIdx.x * CT;
+  const int ncol = min(CT, nrhs - j0);
+  for (int e = threadIdx.x; e < 32 * 32; e += CT) {
+    const int r = e & 31, c = e >> 5;
+    Ls[e] = Lb[(int64_t)(p0 + r) + (int64_t)(p0 + c) * LU.ld];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = wid; c < ncol; c += CT / 32) Xs[c * 33 + lane] = Xb[(int64_t)(j0 + c) * X.ld + p0 + lane];
+  __syncthreads();
+  if (UPPER && threadIdx.x < 32) {
+    const T d = Ls[threadIdx.x * 33];
+    Dinv[threadIdx.x] = is_zero(d) ? T(0.0) : recip(d);
+  }
+  __syncthreads();
+  if (threadIdx.x < ncol) {
+    T x[32];
+    T* xc = Xs + threadIdx.x * 33;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) x[r] = xc[r];
+    if (!UPPER) {
+#pragma unroll
+      for (int r = 1; r < 32; ++r) {
+        T s2 = x[r];
+#pragma unroll
+        for (int c = 0; c < r; ++c) s2 = fmsc(s2, Ls[r + c * 32], x[c]);
+        x[r] = s2;
+      }
+    } else {
+#pragma unroll
+      for (int r = 31; r >= 0; --r) {
+        T s2 = x[r];
+#pragma unroll
+        for (int c = r + 1; c < 32; ++c) s2 = fmsc(s2, Ls[r + c * 32], x[c]);
+        x[r] = s2 * Dinv[r];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) xc[r] = x[r];
+  }
+  __syncthreads();
+  for (int c = wid; c < ncol; c += CT / 32) Xb[(int64_t)(j0 + c) * X.ld + p0 + lane] = Xs[c * 33 + lane];
+}
+
 template <typename T, bool UPPER>
 cudaError_t trsm_diag(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch, cudaStream_t st) {
   const size_t sm = ((size_t)pb * pb + pb) * sizeof(T);
   const int by = std::min(batch, 65535);
-  if (nrhs >= 16) {
+  if (pb == 32 && nrhs >= 16 && batch <= 65535) {
+    constexpr int CT = sizeof(T) == 8 ? 128 : 32;   // static shared memory stays below 48 KB
+    k_trsm32<T, UPPER, CT><<<dim3((nrhs + CT - 1) / CT, batch), CT, 0, st>>>(LU, X, p0, nrhs, batch);
+  } else if (nrhs >= 16) {
     const int bx = std::min((nrhs + 127) / 128, 1024);
     k_trsm_diag_cols<T, UPPER><<<dim3(bx, by), 128, sm, st>>>(LU, X, p0, pb, nrhs, batch);
   } else {
