@@ -196,14 +196,26 @@ __global__ void __launch_bounds__(256) k_split(SplitSet<T> ss, int K, int KT, in
         else if (sh > -62) x = ((m >> (-sh - 1)) + 1) >> 1;
       }
       if (u >> 63) x = -x;
-      // balanced base-64 digits, least significant first
+      // balanced base-64 digits, least significant first, in 32-bit halves:
+      // x = hi 2^30 + lo with 0 <= lo < 2^30.  A digit is d = (t & 63) - 32
+      // with t = v + 32, and the rest is (v - d) / 64 = t >> 6.  Five digits
+      // of lo leave a carry of 0 or 1 into hi; four of hi leave the leading
+      // digit (|.| <= 64).
+      int lo = (int)(x & 0x3FFFFFFFll), hi = (int)(x >> 30);
 #pragma unroll
-      for (int p = DIG - 1; p > 0; --p) {
-        const int d = (int)((x + 32) & 63) - 32;
-        dg[c][p] = d;
-        x = (x - d) >> BITS;
+      for (int p = DIG - 1; p >= DIG - 5; --p) {
+        const int t = lo + 32;
+        dg[c][p] = (t & 63) - 32;
+        lo = t >> BITS;
       }
-      dg[c][0] = (int)x;
+      hi += lo;
+#pragma unroll
+      for (int p = DIG - 6; p > 0; --p) {
+        const int t = hi + 32;
+        dg[c][p] = (t & 63) - 32;
+        hi = t >> BITS;
+      }
+      dg[c][0] = hi;
     }
     uint8_t* blk = base + (int64_t)(k0 >> 4) * (DIG * BLK) + ((k0 >> 3) & 1) * 128;
 #pragma unroll
@@ -475,6 +487,7 @@ constexpr int npairs() {
   return n;
 }
 static_assert(npairs() == 55, "digit pair count");
+static_assert(DIG == 10 && BITS == 6 && FRAC == 60, "the slicing splits 60 bits into 30 + 30");
 static_assert(QGRP * TN <= 256 && (QGRP * TN) % 16 == 0, "MMA N for M = 128");
 
 int ceil_log2(int64_t x) {
