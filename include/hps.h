@@ -290,7 +290,10 @@ int64_t hps_device_bytes(const hps_handle* h);
 /* Planned device bytes of a handle that hps_build would create for a uniform
  * tree (factors, operators and a one-right-hand-side solve workspace), before
  * building it: the figure a caller admits work by.  Pure host computation.
- * HPS_ERR_INVALID for adaptive trees and bad arguments. */
+ * Not included: the transient digit-slice workspace of the tensor-core
+ * products (hps_options.fp64_gemm = 0), at most about 1 GB while hps_build
+ * runs and freed before it returns.  HPS_ERR_INVALID for adaptive trees and
+ * bad arguments. */
 hps_status hps_plan_bytes(const hps_tree* tree, int p, int q, int kind, int64_t* bytes);
 
 /* Number of CUDA kernel launches issued by the last hps_build / hps_solve on h. */

@@ -147,3 +147,22 @@ def test_plan_bytes_grows_with_the_tree(pkg):
     assert 3.5 < b[2] / b[1] < 4.5
     with pytest.raises(pkg.HPSError):
         pkg.hps_plan_bytes(pkg.uniform_tree(3, 1), 8, 6, pkg.HPS_ITI)
+
+
+def test_gemm_arguments_are_validated_before_any_device_work(pkg):
+    """hps_gemm rejects bad dtype, mode and sizes, and returns for empty
+    products, without touching a device (these run on a host with no GPU)."""
+    from paper_2503_17535_gb300 import _capi
+    L = _capi.lib()
+    ok, bad = pkg.HPS_OK, -1
+    # dtype / mode
+    assert L.hps_gemm(7, 0, 4, 4, 4, 1, 1.0, None, 4, 16, None, 4, 16, 0.0, None, 4, 16, None) == bad
+    assert L.hps_gemm(pkg.HPS_F64, 2, 4, 4, 4, 1, 1.0, None, 4, 16, None, 4, 16, 0.0, None, 4, 16, None) == bad
+    # negative sizes, missing pointers, too-small leading dimensions
+    assert L.hps_gemm(pkg.HPS_F64, 0, -1, 4, 4, 1, 1.0, 8, 4, 16, 8, 4, 16, 0.0, 8, 4, 16, None) == bad
+    assert L.hps_gemm(pkg.HPS_F64, 0, 4, 4, 4, 1, 1.0, None, 4, 16, 8, 4, 16, 0.0, 8, 4, 16, None) == bad
+    assert L.hps_gemm(pkg.HPS_F64, 0, 4, 4, 4, 1, 1.0, 8, 3, 16, 8, 4, 16, 0.0, 8, 4, 16, None) == bad
+    assert L.hps_gemm(pkg.HPS_C128, 1, 4, 4, 4, 1, 1.0, 8, 4, 16, 8, 2, 16, 0.0, 8, 4, 16, None) == bad
+    # empty products are no-ops
+    assert L.hps_gemm(pkg.HPS_F64, 0, 0, 4, 4, 1, 1.0, 8, 1, 0, 8, 4, 16, 0.0, 8, 1, 0, None) == ok
+    assert L.hps_gemm(pkg.HPS_F64, 0, 4, 4, 4, 0, 1.0, 8, 4, 16, 8, 4, 16, 0.0, 8, 4, 16, None) == ok
