@@ -139,8 +139,10 @@ typedef struct {
                            products (FP64 accuracy: operands cut into nine 6-bit
                            digits, products accumulated exactly and recombined
                            in 64-bit integers; it needs a transient device
-                           workspace of up to about 1 GB); 1: every product on
-                           the FP64 pipe.  Solves always use the FP64 pipe. */
+                           workspace of up to about 1 GB, and a product whose
+                           workspace cannot be allocated runs on the FP64
+                           pipe); 1: every product on the FP64 pipe.  Solves
+                           always use the FP64 pipe. */
   int reserved[1];
 } hps_options;
 
@@ -267,9 +269,10 @@ void hps_free(hps_handle* h);
  * in fp32, recombined in 64-bit integers; a transient device workspace of up
  * to about 1 GB); mode 1: the FP64-pipe kernels.  Device pointers only; C must
  * not overlap A or B.  Enqueued on `stream` and synchronised before return.
- * HPS_ERR_INVALID for bad sizes, dtype or mode; HPS_ERR_OOM when the
- * workspace cannot be allocated; HPS_ERR_TIMEOUT when a bounded wait inside
- * the tensor-core kernel gave up (C is then undefined). */
+ * HPS_ERR_INVALID for bad sizes, dtype or mode; HPS_ERR_OOM when device
+ * memory cannot be allocated (mode 0 runs the product on the FP64 pipe when
+ * its digit workspace does not fit); HPS_ERR_TIMEOUT when a bounded wait
+ * inside the tensor-core kernel gave up (C is then undefined). */
 hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double alpha, const void* A, int lda,
                     int64_t strideA, const void* B, int ldb, int64_t strideB, double beta, void* C, int ldc,
                     int64_t strideC, struct CUstream_st* stream);

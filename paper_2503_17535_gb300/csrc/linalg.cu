@@ -458,7 +458,13 @@ inline bool wide_tiles(int M, int N, int BM, int BN) {
 template <typename T>
 cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
-  if (g.K > 0 && tc_applicable(g)) return gemm_tc(g, st, pf);
+  if (g.K > 0 && tc_applicable(g)) {
+    const cudaError_t e = gemm_tc(g, st, pf);
+    if (e != cudaErrorMemoryAllocation) return e;
+    // the digit-slice workspace could not grow (nothing was launched): the
+    // product runs on the FP64 pipe instead
+    cudaGetLastError();
+  }
   constexpr int BM = GemmTile<T, 1>::BM, BN = GemmTile<T, 1>::BN;
   if (pf) {
     pf->begin(st);

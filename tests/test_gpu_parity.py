@@ -57,7 +57,7 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def gpu_solve(P, pr, p, L, inputs, f_solve=None, host=False):
+def gpu_solve(P, pr, p, L, inputs, f_solve=None, host=False, fp64_gemm=False, stats=None):
     t, x, a, b, c, f, g = inputs
     kind = P.HPS_ITI if pr.kind == "iti" else P.HPS_DTN
     if host:
@@ -67,7 +67,9 @@ def gpu_solve(P, pr, p, L, inputs, f_solve=None, host=False):
         P.hps_free(h)
         return u
     h = P.hps_build(t, p, p - 2, kind, a=dev(a), b=[dev(bk) for bk in b], c=dev(c), f=dev(f),
-                    eta=pr.eta or 0.0)
+                    eta=pr.eta or 0.0, fp64_gemm=fp64_gemm)
+    if stats is not None:
+        stats.update(P.hps_kernel_stats(h))
     u = torch.zeros(f.shape, dtype=torch.complex128 if pr.kind == "iti" else torch.float64,
                     device="cuda")
     P.hps_solve(h, dev(g), u, f=None if f_solve is None else dev(f_solve))
@@ -108,6 +110,24 @@ def test_parity_against_oracle(P, name, mk, p, L):
     ug = gpu_solve(P, pr, p, L, inputs)
     uo = oracle_solve(pr, p, L, inputs)
     assert rel(ug, uo) <= TOL, rel(ug, uo)
+
+
+@pytest.mark.parametrize("name,mk,p,L", [CASES[2], CASES[6], CASES[11]], ids=[CASES[2][0], CASES[6][0], CASES[11][0]])
+def test_products_on_either_pipe_match_the_oracle(P, name, mk, p, L):
+    """The build's products on the tensor cores (default) and on the FP64
+    pipe (fp64_gemm) both meet the parity bar; the default build really ran
+    tensor-core products where they are large enough, the other none."""
+    pr = mk()
+    inputs = sample_inputs(P, pr, p, L)
+    uo = oracle_solve(pr, p, L, inputs)
+    st_tc, st_fp = {}, {}
+    u_tc = gpu_solve(P, pr, p, L, inputs, stats=st_tc)
+    u_fp = gpu_solve(P, pr, p, L, inputs, fp64_gemm=True, stats=st_fp)
+    assert rel(u_tc, uo) <= TOL, rel(u_tc, uo)
+    assert rel(u_fp, uo) <= TOL, rel(u_fp, uo)
+    assert st_fp["gemm_tc"]["launches"] == 0 and st_fp["split"]["launches"] == 0
+    if name.startswith("helmholtz"):
+        assert st_tc["gemm_tc"]["launches"] > 0 and st_tc["split"]["launches"] > 0
 
 
 @pytest.mark.parametrize("name,mk,p,L", [CASES[0], CASES[5], CASES[9]], ids=["dtn2d", "iti", "dtn3d"])
