@@ -560,7 +560,6 @@ bool tc_applicable<cplx>(const GemmArgs<cplx>& g) {
 
 namespace {
 
-template <typename T>
 cudaError_t ensure_ws(TcWorkspace* w, size_t bytes, cudaStream_t st) {
   if (w->bytes >= bytes) return cudaSuccess;
   if (w->p) {
@@ -619,7 +618,7 @@ cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   const Sizes z = sizes(g.M, g.N, g.K);
   const size_t per_item = NP * (z.a_item + z.b_item + z.ea_item + z.eb_item);
   const int nb_max = (int)std::max<size_t>(1, std::min<size_t>(std::min(g.batch, 65535 / (2 * NP)), WS_CAP / per_item));
-  cudaError_t e = ensure_ws<T>(w, per_item * nb_max, st);
+  cudaError_t e = ensure_ws(w, per_item * nb_max, st);
   if (e != cudaSuccess) return e;
   uint8_t* base = static_cast<uint8_t*>(w->p);
   uint8_t* As[2];
