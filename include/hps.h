@@ -277,6 +277,16 @@ hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double 
                     int64_t strideA, const void* B, int ldb, int64_t strideB, double beta, void* C, int ldc,
                     int64_t strideC, struct CUstream_st* stream);
 
+/* Fault injection for tests (no counterpart in the paper).  Host side only:
+ * no device fault, trap or hang is involved.  After hps_debug_fail_alloc(n)
+ * with n > 0, the n-th device allocation of a handle (build buffers,
+ * operators, solve workspaces) from then on fails as if cudaMalloc had
+ * reported out-of-memory; the call that made it unwinds with HPS_ERR_OOM and
+ * frees what it had allocated.  n <= 0 disarms.  hps_debug_alloc_count
+ * returns the number of handle allocations made so far in this process. */
+void hps_debug_fail_alloc(int64_t n);
+int64_t hps_debug_alloc_count(void);
+
 /* Static, NUL-terminated description of a status code. */
 const char* hps_error_string(hps_status s);
 

@@ -506,3 +506,14 @@ def hps_gemm(A, B, C, alpha: float = 1.0, beta: float = 0.0, mode: int = 0, stre
                                 max(m, 1), m * k, bp, max(k, 1), k * n, float(beta), cq, max(m, 1), m * n,
                                 _stream(stream)), "hps_gemm")
     return C
+
+
+def hps_debug_fail_alloc(n: int) -> None:
+    """Fault injection for tests: the n-th handle allocation from now on fails
+    as out-of-memory (host side); n <= 0 disarms."""
+    _capi.lib().hps_debug_fail_alloc(int(n))
+
+
+def hps_debug_alloc_count() -> int:
+    """Handle allocations made so far in this process."""
+    return int(_capi.lib().hps_debug_alloc_count())

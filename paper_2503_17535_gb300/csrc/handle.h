@@ -2,6 +2,8 @@
 // the C ABI translation units.
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -214,8 +216,21 @@ hps_status iti_elim_apply_h(hps_handle* h, const cplx* Xb, cplx* Rb, int m, cuda
     if (s_ != HPS_OK) return s_;                        \
   } while (0)
 
+// Host-side fault injection for tests (hps_debug_fail_alloc): a countdown
+// of handle allocations; the allocation that takes it from 1 to 0 fails as
+// if cudaMalloc had run out of memory.  Also counts all handle allocations.
+std::atomic<int64_t>& alloc_fail_countdown();
+std::atomic<int64_t>& alloc_counter();
+
 inline void* dalloc(hps_handle* h, size_t bytes, std::vector<void*>* list = nullptr) {
   if (bytes == 0) bytes = 16;
+  alloc_counter().fetch_add(1);
+  {
+    std::atomic<int64_t>& c = alloc_fail_countdown();
+    int64_t v = c.load();
+    while (v > 0 && !c.compare_exchange_weak(v, v - 1)) {}
+    if (v == 1) return nullptr;
+  }
   void* p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();

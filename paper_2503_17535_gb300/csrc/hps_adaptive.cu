@@ -187,6 +187,9 @@ hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs*
   for (int a = 0; a < 3; ++a) co.b[a] = (const double*)stage(cf->b[a], cbytes);
   co.c = (const double*)stage(cf->c, cbytes);
   const T* f = (const T*)stage(f_in, cbytes);
+  if ((cf->a && !co.a) || (cf->c && !co.c) || (f_in && !f)) return HPS_ERR_OOM;
+  for (int a = 0; a < 3; ++a)
+    if (cf->b[a] && !co.b[a]) return HPS_ERR_OOM;
 
   // ---- leaf stage
   h->leafA = dalloc(h, (size_t)nl * ni * ni * sizeof(T));

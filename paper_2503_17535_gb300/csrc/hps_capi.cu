@@ -136,6 +136,8 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
   h->diidx = upload(h, iidx, st);
   k.iidx = h->diidx;
   if (!h->dD || !h->dDD || !h->dIi || !h->dP || !h->diidx || !h->dprow) return HPS_ERR_OOM;
+  if (!ITI && (!h->dQi || !h->dQP)) return HPS_ERR_OOM;
+  if (ITI && (!h->downn || !h->downa || !h->dsgn || !h->dQH)) return HPS_ERR_OOM;
   h->dev_err = (unsigned*)dalloc(h, sizeof(unsigned) * 4);
   if (!h->dev_err) return HPS_ERR_OOM;
   HPS_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(unsigned) * 4, st));
@@ -156,6 +158,8 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
   co.c = (const double*)stage(cf->c, cbytes);
   const T* f = (const T*)stage(f_in, (size_t)h->nl * h->npts * sizeof(T));
   if ((cf->a && !co.a) || (cf->c && !co.c) || (f_in && !f)) return HPS_ERR_OOM;
+  for (int a = 0; a < dim; ++a)
+    if (cf->b[a] && !co.b[a]) return HPS_ERR_OOM;
 
   // ---- leaf stage (Algorithm "local solve")
   const int64_t nl = h->nl;
@@ -701,6 +705,17 @@ hps_status hps::ensure_solve_ws(hps_handle* h, int nrhs) {
   return h->iti ? ensure_ws<cplx>(h, nrhs) : ensure_ws<double>(h, nrhs);
 }
 
+namespace hps {
+std::atomic<int64_t>& alloc_fail_countdown() {
+  static std::atomic<int64_t> c{0};
+  return c;
+}
+std::atomic<int64_t>& alloc_counter() {
+  static std::atomic<int64_t> c{0};
+  return c;
+}
+}  // namespace hps
+
 extern "C" {
 
 const char* hps_error_string(hps_status s) {
@@ -883,6 +898,10 @@ hps_status hps_solve_adjoint(hps_handle* h, int nrhs, const void* ubar, void* gb
     return HPS_ERR_INVALID;
   }
 }
+
+void hps_debug_fail_alloc(int64_t n) { hps::alloc_fail_countdown().store(n > 0 ? n : 0); }
+
+int64_t hps_debug_alloc_count(void) { return hps::alloc_counter().load(); }
 
 hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double alpha, const void* A, int lda,
                     int64_t strideA, const void* B, int ldb, int64_t strideB, double beta, void* C, int ldc,

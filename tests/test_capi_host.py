@@ -166,3 +166,13 @@ def test_gemm_arguments_are_validated_before_any_device_work(pkg):
     # empty products are no-ops
     assert L.hps_gemm(pkg.HPS_F64, 0, 0, 4, 4, 1, 1.0, 8, 1, 0, 8, 4, 16, 0.0, 8, 1, 0, None) == ok
     assert L.hps_gemm(pkg.HPS_F64, 0, 4, 4, 4, 0, 1.0, 8, 4, 16, 8, 4, 16, 0.0, 8, 4, 16, None) == ok
+
+
+def test_fault_injection_hook_is_host_only(pkg):
+    """Arming and disarming the allocation-failure hook and reading the
+    allocation counter need no device."""
+    n = pkg.hps_debug_alloc_count()
+    pkg.hps_debug_fail_alloc(3)
+    pkg.hps_debug_fail_alloc(0)
+    pkg.hps_debug_fail_alloc(-5)
+    assert pkg.hps_debug_alloc_count() == n
