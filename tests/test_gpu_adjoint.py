@@ -1,6 +1,6 @@
 """GPU adjoint solve and coefficient gradients against the oracle adjoint
 (dense composite system), the adjoint identity at larger sizes, and the
-differentiation workload (config 5: Helmholtz, 1024 leaves, p = 16, theta on
+differentiation workload (Helmholtz, 1024 leaves, p = 16, theta on
 a 64 x 64 grid) against central finite differences through the
 torch.autograd.Function."""
 
@@ -98,7 +98,7 @@ def test_adjoint_identity_two_rhs(P, name, mk, p, L, lazy):
 
 
 def test_differentiation_workload_matches_finite_differences(P):
-    """Config 5: J(theta) = ||u(theta) - u(theta_true)||^2, 1024 leaves,
+    """Helmholtz coefficient fit: J(theta) = ||u(theta) - u(theta_true)||^2, 1024 leaves,
     p = 16, complex128; autograd gradient (adjoint kernels) against central
     differences (h = 1e-6) on 16 seeded grid entries and one seeded direction."""
     from paper_2503_17535_gb300.autograd import hps_solve_fn
