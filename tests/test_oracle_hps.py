@@ -73,6 +73,23 @@ def test_polynomial_exactness(dim, kind, p, L):
     assert rel(u2, P2.value(x)) > 1e-9
 
 
+
+@pytest.mark.parametrize("dim,kind,p,L", [(2, "dtn", 8, 0), (2, "dtn", 8, 2), (2, "dtn", 12, 1),
+                                          (2, "iti", 8, 0), (2, "iti", 8, 2), (2, "iti", 10, 1),
+                                          (3, "dtn", 6, 0), (3, "dtn", 6, 1)])
+def test_polynomial_exactness_variable_coefficients(dim, kind, p, L):
+    """The same exactness with seeded non-constant a(x), b(x), c(x): f is
+    formed from u's closed-form derivatives, so the collocation equations
+    hold exactly for u in Q_{p-3} whatever the coefficients are.  This pins
+    how a, b and c enter the leaf operator (Section 3.2: diag(a) times the
+    spectral Laplacian, diag(b_k) times the k-th derivative, diag(c))."""
+    pr = W.poly_varcoef(dim, p - 3, 10 + p, kind)
+    x, u = hps.solve_problem(pr, p, L)
+    assert rel(u, pr.u_exact(x)) < 1e-11
+    pr2 = W.poly_varcoef(dim, p - 2, 20 + p, kind)
+    x, u2 = hps.solve_problem(pr2, p, max(L, 1))
+    assert rel(u2, pr2.u_exact(x)) > 1e-9
+
 # ------------------------------------------------------- O1 against O2 ----
 
 @pytest.mark.parametrize("L,p", [(1, 8), (2, 8), (2, 10)])
@@ -175,6 +192,23 @@ def test_e2_hp_convergence():
     assert errs[1] < 1e-2
 
 
+def test_e1_spectral_convergence_in_p():
+    """Section 5.1 at a fixed tree: for the smooth E1 solution the error
+    falls faster than any fixed power of p (spectral convergence).  At depth
+    3 each step of 4 in p gains a growing factor: more than 30x from 8 to 12
+    and more than 300x from 12 to 16; an algebraic rate p^-k would give a
+    shrinking gain, (8/12)^k then (12/16)^k."""
+    pr = W.e1_dtn_2d()
+    errs = {}
+    for p in (8, 12, 16):
+        x, u = hps.solve_problem(pr, p, 3)
+        errs[p] = rel(u, pr.u_exact(x))
+    assert errs[12] / errs[8] < 1 / 30
+    assert errs[16] / errs[12] < 1 / 300
+    assert errs[16] < 1e-7
+
+
+
 def test_top_merge_sizes_match_table():
     """Table "merge_sizes": the top-level D of a uniform octree of depth L has
     12 q^2 4^(L-1) rows.  The oracle's D for small trees follows the same
@@ -230,3 +264,30 @@ def test_planted_transposed_block_is_caught(monkeypatch):
     monkeypatch.setattr(mg, "merge_2d_dtn", bad)
     s = hps.build(2, "dtn", p, q, L, pr.lo, pr.hi, a, b, c, f)
     assert rel(hps.solve(s, g), u2) > 1e-6
+
+
+@pytest.mark.parametrize("mistake", ["a_on_columns", "a_on_one_derivative", "b_on_columns"])
+def test_planted_coefficient_mistakes_are_caught(monkeypatch, mistake):
+    """A plausible slip in how the coefficients enter L -- a scaling columns
+    instead of rows, a multiplying only one second derivative, b scaling
+    columns -- leaves every constant-coefficient pin green but fails the
+    variable-coefficient exactness pin."""
+    def bad(dim, p, hlen, a, b, c):
+        Ds = lf.derivative_matrices(dim, p, hlen)
+        n = p ** dim
+        if mistake == "a_on_columns":
+            L = sum(Dk @ Dk for Dk in Ds) * a[None, :] + c[:, None] * np.eye(n)
+        elif mistake == "a_on_one_derivative":
+            L = a[:, None] * (Ds[0] @ Ds[0]) + sum(Dk @ Dk for Dk in Ds[1:]) + c[:, None] * np.eye(n)
+        else:
+            L = a[:, None] * sum(Dk @ Dk for Dk in Ds) + c[:, None] * np.eye(n)
+        for k in range(dim):
+            L = L + (Ds[k] * b[k][None, :] if mistake == "b_on_columns" else b[k][:, None] * Ds[k])
+        return L
+
+    pr = W.poly_varcoef(2, 5, 18, "dtn")
+    x, u = hps.solve_problem(pr, 8, 1)
+    assert rel(u, pr.u_exact(x)) < 1e-11
+    monkeypatch.setattr(lf, "assemble_L", bad)
+    x, u = hps.solve_problem(pr, 8, 1)
+    assert rel(u, pr.u_exact(x)) > 1e-4

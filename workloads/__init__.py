@@ -21,6 +21,7 @@ from .problems import (  # noqa: F401
     e2_iti_2d,
     e7_wavefront_3d,
     polynomial_field,
+    poly_varcoef,
     sharp_source_3d,
     adaptive_3d,
     grid_interp_matrix,

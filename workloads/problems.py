@@ -137,6 +137,49 @@ def _const_coeffs(dim, a=1.0, c=0.0):
     return f
 
 
+
+def poly_varcoef(dim: int, degree: int, seed: int, kind: str = "dtn", eta: float = 2.0) -> Problem:
+    """A tensor polynomial u in Q_degree with smooth, seeded, non-constant
+    coefficients: a = 1 + 0.3 sin(k_a . x + phi_a) in [0.7, 1.3],
+    b_j = 0.5 cos(k_b . x + phi_b + j), c = 0.7 + 0.5 sin(k_c . x + phi_c),
+    wave vectors U[-2, 2]^dim and phases U[0, 2 pi) from ``seed + 100``.
+    f = a Lap u + b . grad u + c u is formed from the closed-form derivatives
+    of u, so a collocation that reproduces u exactly also reproduces f
+    exactly at every node, whatever a, b and c are.  Boundary data:
+    Dirichlet values (dtn) or incoming impedance u_n + i eta u (iti)."""
+    P = polynomial_field(dim, degree, seed, tensor=True)
+    rng = np.random.default_rng(seed + 100)
+    kv = rng.uniform(-2.0, 2.0, (3, dim))
+    ph = rng.uniform(0.0, 2.0 * np.pi, 3)
+    lo, hi = (-1.0,) * dim, (1.0,) * dim
+
+    def coeffs(x):
+        x = np.atleast_2d(x)
+        return {"a": 1.0 + 0.3 * np.sin(x @ kv[0] + ph[0]),
+                "b": [0.5 * np.cos(x @ kv[1] + ph[1] + j) for j in range(dim)],
+                "c": 0.7 + 0.5 * np.sin(x @ kv[2] + ph[2])}
+
+    def f(x):
+        x = np.atleast_2d(x)
+        co = coeffs(x)
+        gr = P.grad(x)
+        out = co["a"] * P.lap(x) + co["c"] * P.value(x)
+        for j in range(dim):
+            out = out + co["b"][j] * gr[j]
+        return out if kind == "dtn" else out.astype(complex)
+
+    if kind == "dtn":
+        return Problem(f"poly_varcoef{dim}d_deg{degree}_seed{seed}", dim, lo, hi, "dtn", seed,
+                       coeffs, f, P.value, P.value, info={"poly": P})
+
+    def g(xb):
+        nn = box_normals(xb, lo, hi)
+        gr = P.grad(xb)
+        return sum(nn[:, k] * gr[k] for k in range(dim)) + 1j * eta * P.value(xb)
+
+    return Problem(f"poly_varcoef{dim}d_deg{degree}_seed{seed}", dim, lo, hi, "iti", seed,
+                   coeffs, f, g, P.value, eta=eta, info={"poly": P})
+
 # ---------------------------------------------------------------------------
 # workload 1: 2D Poisson, Dirichlet, u = sin(pi x) sin(pi y) + P5
 # ---------------------------------------------------------------------------
