@@ -136,9 +136,10 @@ typedef struct {
                            (2 h^2) and max |b| h <= min a, h the leaf side. */
   int fp64_gemm;        /* 0: hps_build runs its large real and complex products
                            on the tensor cores as exact bf16 digit-slice
-                           products (FP64 accuracy: operands cut into nine 6-bit
-                           digits, products accumulated exactly and recombined
-                           in 64-bit integers; it needs a transient device
+                           products (FP64 accuracy: operands cut into ten 6-bit
+                           digits, the 55 digit products of weight above 2^-66
+                           accumulated exactly and recombined in 64-bit
+                           integers; it needs a transient device
                            workspace of up to about 1 GB, and a product whose
                            workspace cannot be allocated runs on the FP64
                            pipe); 1: every product on the FP64 pipe.  Solves
@@ -264,9 +265,10 @@ void hps_free(hps_handle* h);
  * B + b*strideB (k x n, ldb), C item b at C + b*strideC (m x n, ldc); strides
  * and leading dimensions in elements.  dtype HPS_F64 (double) or HPS_C128
  * (interleaved complex; alpha and beta are real).  mode 0: the tensor-core
- * digit-slice product that hps_build uses (operands cut into nine 6-bit bf16
- * digits per row of A / column of B, 53 digit products accumulated exactly
- * in fp32, recombined in 64-bit integers; a transient device workspace of up
+ * digit-slice product that hps_build uses (operands cut into ten 6-bit bf16
+ * digits per row of A / column of B, the 55 digit products whose digit
+ * indices sum to at most 11 accumulated exactly in fp32, recombined in
+ * 64-bit integers; a transient device workspace of up
  * to about 1 GB); mode 1: the FP64-pipe kernels.  Device pointers only; C must
  * not overlap A or B.  Enqueued on `stream` and synchronised before return.
  * HPS_ERR_INVALID for bad sizes, dtype or mode; HPS_ERR_OOM when device
@@ -286,6 +288,22 @@ hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double 
  * returns the number of handle allocations made so far in this process. */
 void hps_debug_fail_alloc(int64_t n);
 int64_t hps_debug_alloc_count(void);
+
+/* Bounded-wait check for tests (no counterpart in the paper).  Every wait
+ * inside the library's kernels -- the inter-CTA barrier of the cooperative
+ * panel LU (which = 0), the flag wait of the flag-ordered triangular solves
+ * of a lazy root (which = 1) and the mbarrier wait of the tensor-core product
+ * pipeline (which = 2) -- gives up after a bounded number of polls, records
+ * a timeout in a device status word and lets its kernel end, so that a wait
+ * that can never be satisfied costs an error status, not a hung GPU.  This
+ * call runs the chosen wait in a one-CTA kernel on a word that nothing else
+ * writes (satisfied = 0: the wait must run out) or on one already holding
+ * the awaited value (satisfied = 1: the wait must pass at once), with at most
+ * limit_polls polls (1 .. 2^24; the kernels' own limits are 2^22 to 2*10^7).
+ * Returns HPS_ERR_TIMEOUT when the wait gave up, HPS_OK when it passed;
+ * synchronises `stream`; uses 16 bytes of device memory for the call.
+ * HPS_ERR_INVALID for a bad `which` or limit. */
+hps_status hps_debug_wait_timeout(int which, int satisfied, int64_t limit_polls, struct CUstream_st* stream);
 
 /* Static, NUL-terminated description of a status code. */
 const char* hps_error_string(hps_status s);
@@ -349,7 +367,9 @@ hps_status hps_trace_get(hps_handle* h, int64_t i, hps_trace_rec* out);
  * loads it, until the process exits; no cudaMalloc, cudaFree or allocating
  * routine is called.
  *   g: [n_root_bdry] and u: [n_leaves][p^d] must be device memory.
- *   HPS_ERR_INVALID if g or u is host memory, if the handle keeps a lazy
+ *   HPS_ERR_INVALID if g or u is host memory or memory of another device
+ *   than the current one, if the handle was built on another device, if
+ *   the handle keeps a lazy
  *   root (hps_options.lazy_root), or if the handle's downward
  *   pass needs more than the 16 MiB array (the sum over merge levels of
  *   n_merges x (interior unknowns + children's boundary points) elements,

@@ -517,3 +517,12 @@ def hps_debug_fail_alloc(n: int) -> None:
 def hps_debug_alloc_count() -> int:
     """Handle allocations made so far in this process."""
     return int(_capi.lib().hps_debug_alloc_count())
+
+
+def hps_debug_wait_timeout(which: int, satisfied: bool, limit_polls: int, stream=None) -> int:
+    """Run one of the library's bounded device waits on a word nothing writes
+    (which 0: inter-CTA group barrier, 1: triangular-solve flag wait,
+    2: tensor-core pipeline mbarrier wait).  Returns the status code:
+    HPS_ERR_TIMEOUT when the wait gave up, HPS_OK when it passed."""
+    return int(_capi.lib().hps_debug_wait_timeout(int(which), 1 if satisfied else 0, int(limit_polls),
+                                                   _stream(stream)))

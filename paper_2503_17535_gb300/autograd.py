@@ -23,8 +23,10 @@ class HPSSolve(torch.autograd.Function):
 
     c: float64 [n_leaves, p^d] (device), g: [n_root_bdry], f: [n_leaves, p^d]
     (float64 for DtN, complex128 for ItI); a and b: fixed coefficient arrays
-    (or None for a = 1, b = 0).  The handle built in forward is kept for the
-    backward pass and released after it."""
+    (or None for a = 1, b = 0).  The handle built in forward stays on the
+    autograd context, so every backward through the graph (retain_graph=True,
+    or torch.autograd.grad called more than once) reuses its factors; it is
+    released when the graph is freed (Handle.__del__ calls hps_free)."""
 
     @staticmethod
     def forward(ctx, c, g, f, tree, p, kind, a=None, b=None, eta=0.0, lazy_root=False):
@@ -46,8 +48,6 @@ class HPSSolve(torch.autograd.Function):
         hps_solve_adjoint(h, grad_u.contiguous(), gbar, fbar)
         gc = torch.empty(u.shape, dtype=torch.float64, device=u.device)
         hps_coeff_gradient(h, u, fbar, gc=gc)
-        hps_free(h)
-        ctx.h = None
         return gc, gbar, fbar, None, None, None, None, None, None, None
 
 

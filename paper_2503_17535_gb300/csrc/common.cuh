@@ -111,4 +111,16 @@ __device__ inline bool group_barrier(unsigned* bar, unsigned G, unsigned* err,
   return ok != 0;
 }
 
+// Bounded wait until *f == want (another CTA publishes it with a fence).
+// Gives up after `limit` polls and returns false; the caller records the
+// timeout in its status word and leaves.
+__device__ inline bool wait_flag(const volatile unsigned* f, unsigned want, unsigned long long limit) {
+  unsigned long long it = 0;
+  while (*f != want) {
+    if (++it > limit) return false;
+    __nanosleep(32);
+  }
+  return true;
+}
+
 }  // namespace hps

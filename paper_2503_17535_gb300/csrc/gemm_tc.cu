@@ -98,8 +98,8 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait on an mbarrier phase; gives up when another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
-  for (long it = 0; it < SPIN; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, long limit = SPIN) {
+  for (long it = 0; it < limit; ++it) {
     if (mbar_try(bar, parity)) return true;
     if (*abort) return false;
     if (it > 32) __nanosleep(64);
@@ -673,6 +673,31 @@ cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
       launch_mma<T>(p, nb, g.K, st, pf);
     }
   }
+  return cudaGetLastError();
+}
+
+// Bounded-wait check (hps_debug_wait_timeout, which 2): one CTA waits with
+// the pipeline's mbarrier wait on phase 0 of a barrier that expects one
+// arrival; nothing arrives unless `satisfied`.  A wait that gives up sets
+// DEV_ERR_TIMEOUT in *err.
+__global__ void k_debug_mbar_wait(int satisfied, long limit, unsigned* err) {
+  using namespace tc;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (satisfied) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&bar)) : "memory");
+    if (!mbar_wait(su32(&bar), 0, &abort_flag, limit)) atomicOr(err, DEV_ERR_TIMEOUT);
+  }
+}
+
+cudaError_t debug_mbar_wait(int satisfied, long limit, unsigned* err, cudaStream_t st) {
+  k_debug_mbar_wait<<<1, 32, 0, st>>>(satisfied, limit, err);
   return cudaGetLastError();
 }
 

@@ -152,6 +152,7 @@ struct hps_handle {
   hps::TcWorkspace tcw;           // digit slices of tensor-core products (build only)
   int64_t err_node = -1;
   int num_sms = 0;
+  int device = -1;               // CUDA device the handle was built on
   // captured solves (hps_options.graph_solve): key -> executable graph
   struct GraphEntry {
     int nrhs = 0;

@@ -1,5 +1,6 @@
 // C ABI of the HPS solver: planning, storage, build (leaf stage + merges)
 // and solve (upward particular pass, downward pass, leaf output).
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -832,6 +833,7 @@ hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeff
     delete h;
     return HPS_ERR_CUDA;
   }
+  h->device = dev;
   cudaStream_t st = (cudaStream_t)stream;
   h->last = st;
   h->tcw.err_slot = &h->dev_err;
@@ -897,6 +899,26 @@ hps_status hps_solve_adjoint(hps_handle* h, int nrhs, const void* ubar, void* gb
   } catch (...) {
     return HPS_ERR_INVALID;
   }
+}
+
+hps_status hps_debug_wait_timeout(int which, int satisfied, int64_t limit_polls, struct CUstream_st* stream) {
+  if (which < 0 || which > 2 || limit_polls < 1 || limit_polls > ((int64_t)1 << 24)) return HPS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* d = nullptr;  // words[0..2] waited on, words[3] the status word
+  HPS_CUDA(cudaMalloc(&d, 4 * sizeof(unsigned)));
+  cudaError_t e = cudaMemsetAsync(d, 0, 4 * sizeof(unsigned), st);
+  if (e == cudaSuccess)
+    e = which == 2 ? hps::debug_mbar_wait(satisfied ? 1 : 0, (long)limit_polls, d + 3, st)
+                   : hps::debug_wait(which, satisfied ? 1 : 0, d, (unsigned long long)limit_polls, d + 3, st);
+  unsigned herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return HPS_ERR_CUDA;
+  }
+  return (herr & hps::DEV_ERR_TIMEOUT) ? HPS_ERR_TIMEOUT : HPS_OK;
 }
 
 void hps_debug_fail_alloc(int64_t n) { hps::alloc_fail_countdown().store(n > 0 ? n : 0); }
@@ -1041,29 +1063,42 @@ constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB per device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
-void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+// Per-device address cache.  Two host threads making the first call on one
+// device at the same time may both look the address up; they store the same
+// value, and the atomics keep that free of data races.
+std::atomic<void*> g_noalloc_addr[kNoAllocMaxDevices] = {};
 
-// Device address of the static array on the current device.  In host code the
-// symbol names a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
-hps_status noalloc_scratch(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return HPS_ERR_CUDA;
+// Device address of the static array on device `dev` (the current device).
+// In host code the symbol names a host-side stand-in, so the address must
+// come from cudaGetSymbolAddress, once per device, with that device current.
+hps_status noalloc_scratch(int dev, void** out) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) return HPS_ERR_INVALID;
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
+  void* p = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!p) {
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return HPS_ERR_CUDA;
     }
-    g_noalloc_addr[dev] = p;
+    g_noalloc_addr[dev].store(p, std::memory_order_release);
   }
-  *out = g_noalloc_addr[dev];
+  *out = p;
   return HPS_OK;
 }
 
+// True when p is device (or managed) memory that the current device `dev`
+// can use directly: allocated on dev, or managed.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 template <typename T>
-hps_status solve_noalloc_impl(hps_handle* h, const T* g, T* u, cudaStream_t st) {
+hps_status solve_noalloc_impl(hps_handle* h, int dev, const T* g, T* u, cudaStream_t st) {
   // scratch layout: per level (from the root down) g_int then the children's g
   const size_t al = 256 / sizeof(T);
   auto up = [&](size_t n) { return (n + al - 1) / al * al; };
@@ -1074,7 +1109,7 @@ hps_status solve_noalloc_impl(hps_handle* h, const T* g, T* u, cudaStream_t st) 
   }
   if (need * sizeof(T) > kNoAllocScratchBytes) return HPS_ERR_INVALID;
   void* base = nullptr;
-  hps_status s = noalloc_scratch(&base);
+  hps_status s = noalloc_scratch(dev, &base);
   if (s != HPS_OK) return s;
   T* cur = reinterpret_cast<T*>(base);
   const T* gpar = g;
@@ -1096,11 +1131,18 @@ hps_status solve_noalloc_impl(hps_handle* h, const T* g, T* u, cudaStream_t st) 
 
 extern "C" hps_status hps_solve_noalloc(hps_handle* h, const void* g, void* u, struct CUstream_st* stream) {
   if (!h || !g || !u || h->adaptive || (h->L > 0 && h->lev[h->L - 1].lazy)) return HPS_ERR_INVALID;
-  if (!is_device_ptr(g) || !is_device_ptr(u)) return HPS_ERR_INVALID;
+  // the handle, g and u must all live on the current device: a kernel given
+  // pointers of another device would fault
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HPS_ERR_CUDA;
+  }
+  if (dev != h->device || !on_device(g, dev) || !on_device(u, dev)) return HPS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   try {
-    return h->iti ? solve_noalloc_impl<cplx>(h, (const cplx*)g, (cplx*)u, st)
-                  : solve_noalloc_impl<double>(h, (const double*)g, (double*)u, st);
+    return h->iti ? solve_noalloc_impl<cplx>(h, dev, (const cplx*)g, (cplx*)u, st)
+                  : solve_noalloc_impl<double>(h, dev, (const double*)g, (double*)u, st);
   } catch (...) {
     return HPS_ERR_INVALID;
   }

@@ -1262,15 +1262,7 @@ __global__ void __launch_bounds__(256) k_trsv_flags(const T* __restrict__ LU, in
 #pragma unroll
         for (int q = 0; q < 32; ++q) a[q] = (rv && q < qn) ? col[(int64_t)q * ld] : T(0.0);
         if (lane == 0) {
-          const volatile unsigned* f = flags + i;
-          unsigned long long it = 0;
-          while (*f != epoch) {
-            if (++it > (1ull << 24)) {
-              *err = 1;
-              break;
-            }
-            __nanosleep(32);
-          }
+          if (!wait_flag(flags + i, epoch, 1ull << 24)) *err = 1;
           __threadfence();
         }
         __syncwarp();
@@ -1514,5 +1506,30 @@ cudaError_t getrs_h(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaStream_
 
 HPS_INST(double)
 HPS_INST(cplx)
+
+
+// ----------------------------------------------------------------------------
+// Bounded-wait check (hps_debug_wait_timeout): one CTA runs one of the
+// library's bounded waits on a word that nothing else writes.  which 0: the
+// inter-CTA group barrier with a group of two CTAs of which only this one
+// arrives (satisfied: a group of one); which 1: the flag wait of the
+// flag-ordered triangular solves on a flag nothing sets (satisfied: the flag
+// already holds the awaited value).  A wait that gives up sets
+// DEV_ERR_TIMEOUT in *err.
+__global__ void k_debug_wait(int which, int satisfied, unsigned* words, unsigned long long limit, unsigned* err) {
+  if (which == 0) {
+    group_barrier(words, satisfied ? 1u : 2u, err, limit);
+  } else if (threadIdx.x == 0) {
+    if (satisfied) words[2] = 7u;
+    __threadfence();
+    if (!wait_flag(words + 2, 7u, limit)) atomicOr(err, DEV_ERR_TIMEOUT);
+  }
+}
+
+cudaError_t debug_wait(int which, int satisfied, unsigned* words, unsigned long long limit, unsigned* err,
+                       cudaStream_t st) {
+  k_debug_wait<<<1, 128, 0, st>>>(which, satisfied, words, limit, err);
+  return cudaGetLastError();
+}
 
 }  // namespace hps

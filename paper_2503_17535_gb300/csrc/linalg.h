@@ -106,6 +106,14 @@ cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf);
 // thread has an enabled workspace installed (TcScope) and the shape is large
 // enough; otherwise it runs on the FP64 pipe.  Kernel timeouts set
 // DEV_ERR_TIMEOUT in *err_slot.
+// Bounded-wait checks (hps_debug_wait_timeout): one CTA runs one of the
+// library's bounded waits on a word nothing else writes (linalg.cu: the group
+// barrier, which 0, and the triangular solves' flag wait, which 1, on the
+// zeroed words[0..2]; gemm_tc.cu: the tensor-core pipeline's mbarrier wait).
+cudaError_t debug_wait(int which, int satisfied, unsigned* words, unsigned long long limit, unsigned* err,
+                       cudaStream_t st);
+cudaError_t debug_mbar_wait(int satisfied, long limit, unsigned* err, cudaStream_t st);
+
 struct TcWorkspace {
   void* p = nullptr;
   size_t bytes = 0;

@@ -176,3 +176,13 @@ def test_fault_injection_hook_is_host_only(pkg):
     pkg.hps_debug_fail_alloc(0)
     pkg.hps_debug_fail_alloc(-5)
     assert pkg.hps_debug_alloc_count() == n
+
+
+def test_debug_wait_timeout_rejects_bad_arguments(pkg):
+    """Argument checks of hps_debug_wait_timeout happen on the host, before
+    any device call."""
+    from paper_2503_17535_gb300 import _capi
+    assert pkg.hps_debug_wait_timeout(3, False, 1000, 0) == _capi.HPS_ERR_INVALID
+    assert pkg.hps_debug_wait_timeout(-1, False, 1000, 0) == _capi.HPS_ERR_INVALID
+    assert pkg.hps_debug_wait_timeout(0, False, 0, 0) == _capi.HPS_ERR_INVALID
+    assert pkg.hps_debug_wait_timeout(0, False, (1 << 24) + 1, 0) == _capi.HPS_ERR_INVALID

@@ -151,3 +151,31 @@ def test_differentiation_workload_matches_finite_differences(P):
     ad = float(grad @ v)
     assert abs(fd(v, 1e-6) - ad) <= 1e-10 * abs(J0) / 1e-6 + 1e-6 * scale
     assert abs(fd(v, 1e-4) - ad) <= 1e-10 * abs(J0) / 1e-4 + 1e-6 * scale, (fd(v, 1e-4), ad, J0)
+
+
+@pytest.mark.parametrize("name,mk,p,L", [SMALL[2], SMALL[1]], ids=["iti_L1", "dtn2d_L2"])
+def test_autograd_backward_twice_reuses_the_factors(P, name, mk, p, L):
+    """Two backward passes through one graph (retain_graph=True, then
+    torch.autograd.grad) reuse the handle built in forward; both coefficient
+    gradients of J = Re<ubar, u> equal the oracle adjoint's."""
+    from paper_2503_17535_gb300.autograd import hps_solve_fn
+    pr = mk()
+    inputs = sample_inputs(P, pr, p, L)
+    t, x, a, b, c, f, g = inputs
+    cp = pr.kind == "iti"
+    rng = np.random.default_rng(7)
+    ubar = rng.standard_normal(f.shape) + (1j * rng.standard_normal(f.shape) if cp else 0.0)
+    if cp:
+        _, _, oc, _ = OA.adjoint_iti(p, L, pr.lo, pr.hi, a, b, c, f, g, ubar, pr.eta)
+    else:
+        _, _, oc, _ = OA.adjoint_dtn(pr.dim, p, L, pr.lo, pr.hi, a, b, c, f, g, ubar, with_gbar=False)
+    cd = dev(c).requires_grad_(True)
+    u = hps_solve_fn(cd, dev(g), dev(f), t, p, P.HPS_ITI if cp else P.HPS_DTN, a=dev(a),
+                     b=[dev(bk) for bk in b], eta=pr.eta or 0.0)
+    J = (torch.conj(dev(ubar)) * u).real.sum()
+    J.backward(retain_graph=True)
+    g1 = cd.grad.detach().cpu().numpy().copy()
+    (g2,) = torch.autograd.grad(J, cd)
+    g2 = g2.detach().cpu().numpy()
+    assert rel(g1, oc) <= TOL, rel(g1, oc)
+    assert rel(g2, oc) <= TOL, rel(g2, oc)
