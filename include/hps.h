@@ -38,8 +38,17 @@
  * Streams: work is enqueued on the stream passed in (NULL = legacy default
  * stream).  hps_build and hps_solve are asynchronous with respect to the host
  * for device buffers, except that hps_build synchronises the stream once at
- * its end to read the pivot status.  A handle must not be used from two host
- * threads at the same time.
+ * its end to read the pivot status.  Calls on one handle made on different
+ * streams are ordered on the device: each call's stream first waits for the
+ * handle's previous work (an event the handle records), so they never
+ * overlap on the handle's buffers (not while the caller captures the stream
+ * into a graph, where the caller's graph orders the work).  A handle must
+ * not be used from two host threads at the same time.
+ *
+ * Device memory of handles and their workspaces comes from a stream-ordered
+ * pool per device (cudaMallocFromPoolAsync / cudaFreeAsync, release
+ * threshold 0): building, growing a workspace or freeing a handle never
+ * waits for other streams.
  *
  * Errors: every call returns an hps_status; nothing is thrown across the ABI.
  * On failure *out handles are set to NULL and no memory is leaked.
@@ -228,6 +237,27 @@ hps_status hps_solve(hps_handle* h, const void* g, const void* f, void* u,
 hps_status hps_solve_batched(hps_handle* h, int nrhs, const void* g, const void* f, void* u,
                              struct CUstream_st* stream);
 
+/* Apply-only solves of n different operators at once (uniform trees; their
+ * dimensions, kinds, depths and orders may all differ): for each i,
+ * u[i] = solution of operator hs[i] for root data g[i] with the build-time
+ * source, as hps_solve_batched(hs[i], nrhs[i], g[i], NULL, u[i]) computes it.
+ * The downward passes share launches: one launch per tree level counted
+ * from the roots serves every operator that has that level, and one launch
+ * forms every leaf output (Section 3.4, Algorithm "down pass", over many
+ * trees; the paper's remark that further sources cost only matrix-vector
+ * products, Section 5.2).  Real and complex operators take separate
+ * launches; a lazy root is applied per operator before the shared levels.
+ *   hs: n distinct handles built on the current device;
+ *   nrhs[i] >= 1; g[i]: [nrhs[i]][n_root_bdry_i], u[i]: [nrhs[i]][n_leaves_i]
+ *   [p_i^d] device memory of the current device (dtype of hs[i]).
+ * Each handle's previous work is waited for on `stream` first.  Results
+ * equal hps_solve's up to rounding (the level products sum in another
+ * order).  Errors: HPS_ERR_INVALID (n outside 1..1024, a NULL or repeated
+ * handle, an adaptive handle, host buffers, another device), HPS_ERR_OOM
+ * (a solve workspace), HPS_ERR_TIMEOUT, HPS_ERR_CUDA. */
+hps_status hps_solve_multi(int n, hps_handle* const* hs, const int* nrhs, const void* const* g, void* const* u,
+                           struct CUstream_st* stream);
+
 /* Adjoint solve (uniform trees).  The solve is a linear map
  * u = A_g g + A_f f (Sections 3.2-3.4); this applies its conjugate
  * transpose with the stored factors, every step of the solve reversed:
@@ -255,7 +285,10 @@ hps_status hps_solve_adjoint(hps_handle* h, int nrhs, const void* ubar, void* gb
 hps_status hps_coeff_gradient(hps_handle* h, int nrhs, const void* u, const void* fbar, double* ga,
                               double* gb, double* gc, struct CUstream_st* stream);
 
-/* Release a handle (NULL is accepted).  Synchronises the handle's last stream. */
+/* Release a handle (NULL is accepted).  Waits on the host for the handle's
+ * own queued work (not for other work on the device) and returns its memory
+ * to the library's stream-ordered pool, so a free never stalls unrelated
+ * streams. */
 void hps_free(hps_handle* h);
 
 /* Batched dense product C = alpha A B + beta C (no counterpart in the paper:

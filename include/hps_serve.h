@@ -11,8 +11,11 @@
  *     coefficients, admitted only when the server's device-memory budget
  *     (hps_plan_bytes) has room.
  * Solve requests that wait on the same operator are merged into one batched
- * solve (hps_solve_batched) of up to max_batch right-hand sides, and batches
- * of different operators run concurrently on n_streams CUDA streams; builds
+ * solve of up to max_batch right-hand sides; apply-only requests (the
+ * build-time source) waiting on up to max_group different operators --
+ * whatever their depths, orders and kinds -- are served together by one
+ * hps_solve_multi, whose downward passes share launches level by level;
+ * batches run concurrently on n_streams CUDA streams; builds
  * run on n_builders host threads, each with its own stream, while solves
  * continue.  Requests
  * that arrive while others run are admitted as soon as a stream and the
@@ -52,7 +55,11 @@ typedef struct {
                            request passes no options                                 */
   int n_builders;       /* builds that may run at once, each on its own host thread
                            and stream (1..8; 0 -> 2)                                 */
-  int reserved[6];
+  int max_group;        /* operators whose apply-only solves (build-time source) are
+                           served by one hps_solve_multi: their downward passes
+                           share launches across depths, orders and kinds
+                           (1..24; 0 -> 8; 1 turns cross-operator batching off)    */
+  int reserved[5];
 } hps_server_options;
 
 typedef struct {
@@ -67,7 +74,9 @@ typedef struct {
 
 typedef struct {
   int64_t solves, builds, batches;  /* completed                                       */
-  int64_t max_batch_seen;
+  int64_t max_batch_seen;           /* requests in one dispatched batch                */
+  int64_t multi_batches;            /* batches that served more than one operator      */
+  int64_t max_group_seen;           /* operators in one dispatched batch               */
   int64_t resident_bytes;           /* device bytes of the resident operators          */
   int64_t hbm_budget;
 } hps_server_stats;

@@ -24,6 +24,7 @@ from ._capi import (HPS_C128, HPS_DTN, HPS_F64, HPS_ITI, HPS_OK, hps_coeffs,  # 
 __all__ = ["hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
            "hps_error_string", "hps_last_error_detail", "hps_device_bytes",
            "hps_last_launch_count", "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc",
+           "hps_solve_multi",
            "uniform_tree", "adaptive_tree", "hps_refine",
            "make_coeffs", "HPSError", "Handle"]
 
@@ -216,6 +217,25 @@ def hps_solve(h: Handle, g, u, f=None, stream=None):
     return hps_solve_batched(h, 1, g, u, f=f, stream=stream)
 
 
+def hps_solve_multi(handles, gs, us, nrhs=None, stream=None):
+    """Apply-only solves (build-time source) of several different operators
+    in shared launches: us[i] <- solution of handles[i] for gs[i] (nrhs[i]
+    right-hand sides each, default 1).  Device tensors only."""
+    n = len(handles)
+    if len(gs) != n or len(us) != n:
+        raise ValueError("handles, gs and us must have the same length")
+    nr = [1] * n if nrhs is None else [int(k) for k in nrhs]
+    keep: list = []
+    hp = (c_void_p * n)(*[h.ptr for h in handles])
+    gp = (c_void_p * n)(*[_ptr(gs[i], handles[i].complex, nr[i] * handles[i].n_root, "g", keep)
+                          for i in range(n)])
+    up = (c_void_p * n)(*[_ptr(us[i], handles[i].complex, nr[i] * handles[i].n_leaves * handles[i].ppl, "u",
+                               keep) for i in range(n)])
+    npr = (ctypes.c_int * n)(*nr)
+    _check(_capi.lib().hps_solve_multi(n, hp, npr, gp, up, _stream(stream)), "hps_solve_multi")
+    return us
+
+
 def hps_solve_noalloc(h: Handle, g, u, stream=None):
     """Allocation-free variant of hps_solve with the build-time source: g and u
     must be device tensors; the library uses its static 16 MiB device array
@@ -349,13 +369,14 @@ class Server:
     waited for."""
 
     def __init__(self, n_slots: int = 16, n_streams: int = 4, max_batch: int = 8, hbm_budget: int = 0,
-                 lazy_root: bool = False, n_builders: int = 2):
+                 lazy_root: bool = False, n_builders: int = 2, max_group: int = 8):
         o = _capi.hps_server_options()
         o.version = 1
         o.n_slots, o.n_streams, o.max_batch = n_slots, n_streams, max_batch
         o.hbm_budget = hbm_budget
         o.lazy_root = 1 if lazy_root else 0
         o.n_builders = n_builders
+        o.max_group = max_group
         out = c_void_p()
         _check(_capi.lib().hps_server_create(byref(o), byref(out)), "hps_server_create")
         self.ptr = out.value
@@ -410,8 +431,11 @@ class Server:
 
     def wait(self, ticket: int, check: bool = True) -> dict:
         ti = _capi.hps_ticket_info()
+        ti.status = 1  # stays set when the ticket is unknown (nothing filled in)
         st = _capi.lib().hps_server_wait(self.ptr, ticket, byref(ti))
         self._keep.pop(ticket, None)
+        if ti.status == 1:
+            ti.status = st
         if st == HPS_OK or not check:
             return self._info(ti)
         raise HPSError(st, "hps_server_wait")

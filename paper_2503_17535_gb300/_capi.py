@@ -19,7 +19,7 @@ HPS_DTN, HPS_ITI = 0, 1
 HPS_F64, HPS_C128 = 0, 1
 
 EXPORTED = [
-    "hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_free",
+    "hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_solve_multi", "hps_free",
     "hps_error_string", "hps_last_error_detail", "hps_device_bytes", "hps_last_launch_count",
     "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc", "hps_refine", "hps_trace_count",
     "hps_trace_get", "hps_plan_bytes", "hps_solve_adjoint", "hps_coeff_gradient", "hps_gemm",
@@ -63,7 +63,8 @@ class hps_trace_rec(ctypes.Structure):
 
 class hps_server_options(ctypes.Structure):
     _fields_ = [("version", c_int), ("n_slots", c_int), ("n_streams", c_int), ("max_batch", c_int),
-                ("hbm_budget", c_int64), ("lazy_root", c_int), ("n_builders", c_int), ("reserved", c_int * 6)]
+                ("hbm_budget", c_int64), ("lazy_root", c_int), ("n_builders", c_int), ("max_group", c_int),
+                ("reserved", c_int * 5)]
 
 
 class hps_ticket_info(ctypes.Structure):
@@ -73,7 +74,8 @@ class hps_ticket_info(ctypes.Structure):
 
 class hps_server_stats(ctypes.Structure):
     _fields_ = [("solves", c_int64), ("builds", c_int64), ("batches", c_int64), ("max_batch_seen", c_int64),
-                ("resident_bytes", c_int64), ("hbm_budget", c_int64)]
+                ("multi_batches", c_int64), ("max_group_seen", c_int64), ("resident_bytes", c_int64),
+                ("hbm_budget", c_int64)]
 
 
 _lib = None
@@ -101,6 +103,8 @@ def lib() -> ctypes.CDLL:
     L.hps_solve.restype = c_int
     L.hps_solve_batched.argtypes = [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]
     L.hps_solve_batched.restype = c_int
+    L.hps_solve_multi.argtypes = [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.hps_solve_multi.restype = c_int
     L.hps_free.argtypes = [c_void_p]
     L.hps_free.restype = None
     L.hps_error_string.argtypes = [c_int]

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhps_gb300.so")
 
 SOURCES = ["linalg.cu", "hps_kernels.cu", "adaptive_kernels.cu", "hps_capi.cu", "hps_adaptive.cu", "plan.cpp", "adaptive.cpp",
-           "serve.cpp", "hps_adjoint.cu", "iti_leaf.cu", "gemm_tc.cu"]
+           "serve.cpp", "hps_adjoint.cu", "iti_leaf.cu", "gemm_tc.cu", "devmem.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -38,6 +38,7 @@
 //
 // Complex products are four real products (re*re, im*im, re*im, im*re),
 // each written into its component of C.
+#include "devmem.h"
 #include "linalg.h"
 
 #include <algorithm>
@@ -533,7 +534,7 @@ TcWorkspace*& tc_workspace() {
 size_t tc_workspace_cap() { return tc::WS_CAP; }
 
 void tc_release(TcWorkspace* w) {
-  if (w && w->p) cudaFree(w->p);
+  if (w && w->p) dev_free(w->p, w->st);
   if (w) { w->p = nullptr; w->bytes = 0; }
 }
 
@@ -561,18 +562,27 @@ bool tc_applicable<cplx>(const GemmArgs<cplx>& g) {
 namespace {
 
 cudaError_t ensure_ws(TcWorkspace* w, size_t bytes, cudaStream_t st) {
-  if (w->bytes >= bytes) return cudaSuccess;
+  if (w->bytes >= bytes) {
+    if (w->st != st && w->p) {
+      // the buffer moves to another stream: order it after its last use
+      cudaError_t e = cudaStreamSynchronize(w->st);
+      if (e != cudaSuccess) return e;
+      w->st = st;
+    }
+    return cudaSuccess;
+  }
   if (w->p) {
-    cudaError_t e = cudaStreamSynchronize(st);
+    cudaError_t e = cudaStreamSynchronize(w->st);
     if (e != cudaSuccess) return e;
-    cudaFree(w->p);
+    dev_free(w->p, st);
     w->p = nullptr;
     w->bytes = 0;
   }
   const size_t nb = std::max(bytes, (size_t)64 << 20);
-  cudaError_t e = cudaMalloc(&w->p, nb);
+  cudaError_t e = dev_malloc(&w->p, nb, st);
   if (e != cudaSuccess) { w->p = nullptr; return e; }
   w->bytes = nb;
+  w->st = st;
   return cudaSuccess;
 }
 

@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "devmem.h"
 #include "adaptive.h"
 #include "adaptive_kernels.cuh"
 #include "hps.h"
@@ -167,6 +168,13 @@ struct hps_handle {
   hps::TrsvWork trsv;            // flag-ordered solves with a lazy root's factors
   int* trsv_err_host = nullptr;  // host-mapped error word of trsv (cudaHostAlloc)
   cudaStream_t last = nullptr;
+  // Completion of the handle's latest work, whatever stream it ran on: each
+  // call that enqueues work on the handle first orders its stream after this
+  // event and records it again at its end, so calls made on different
+  // streams never overlap on the handle's buffers, and hps_free waits for
+  // exactly the handle's own work.
+  cudaEvent_t done = nullptr;
+  bool done_recorded = false;
   // solve workspace
   int ws_nrhs = 0;
   // adaptive trees
@@ -233,7 +241,7 @@ inline void* dalloc(hps_handle* h, size_t bytes, std::vector<void*>* list = null
     if (v == 1) return nullptr;
   }
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  if (dev_malloc(&p, bytes, h->last) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }

@@ -141,7 +141,7 @@ hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs*
   {
     size_t fr = 0, tot = 0;
     HPS_CUDA(cudaMemGetInfo(&fr, &tot));
-    if (need > fr) return HPS_ERR_OOM;
+    if (need > fr + dev_pool_idle_bytes()) return HPS_ERR_OOM;
   }
   h->max_np = max_np;
   // ---- constants
@@ -419,7 +419,7 @@ hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs*
     i0 = i1;
   }
   HPS_CUDA(cudaStreamSynchronize(st));
-  for (void* tb : tmpbufs) cudaFree(tb);
+  for (void* tb : tmpbufs) dev_free(tb, st);
   unsigned derr = 0;
   HPS_CUDA(cudaMemcpy(&derr, h->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (derr & DEV_ERR_TIMEOUT) return HPS_ERR_TIMEOUT;
@@ -438,7 +438,8 @@ hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs*
 static hps_status adaptive_ws(hps_handle* h, int nrhs) {
   using T = double;
   if (h->ws_nrhs >= nrhs) return HPS_OK;
-  for (void* pp : h->ws_allocs) cudaFree(pp);
+  // the call has ordered h->last after the handle's earlier work
+  for (void* pp : h->ws_allocs) dev_free(pp, h->last);
   h->ws_allocs.clear();
   h->bytes -= h->ws_bytes;
   const int64_t before = h->bytes;

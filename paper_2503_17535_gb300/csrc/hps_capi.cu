@@ -97,7 +97,7 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
     size_t need = plan_bytes<T>(h, false) + ((size_t)64 << 20);
     size_t fr = 0, tot = 0;
     HPS_CUDA(cudaMemGetInfo(&fr, &tot));
-    if (need > fr) return HPS_ERR_OOM;
+    if (need > fr + dev_pool_idle_bytes()) return HPS_ERR_OOM;
   }
   // ---- constants
   h->dD = upload(h, h->spec.D, st);
@@ -401,7 +401,7 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
 
   // ---- status: singular pivots / timeouts
   HPS_CUDA(cudaStreamSynchronize(st));
-  for (void* t : tmp) { cudaFree(t); }
+  for (void* t : tmp) { dev_free(t, st); }
   unsigned derr = 0;
   HPS_CUDA(cudaMemcpy(&derr, h->dev_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (derr & DEV_ERR_TIMEOUT) return HPS_ERR_TIMEOUT;
@@ -431,7 +431,8 @@ hps_status ensure_ws(hps_handle* h, int nrhs) {
   if (h->ws_nrhs >= nrhs) return HPS_OK;
   if (h->capturing) return HPS_ERR_INVALID;  // never allocate inside a capture
   drop_graphs(h);                            // they refer to the old buffers
-  for (void* pp : h->ws_allocs) { cudaFree(pp); }
+  // the call has ordered h->last after the handle's earlier work
+  for (void* pp : h->ws_allocs) { dev_free(pp, h->last); }
   h->ws_allocs.clear();
   h->bytes -= h->ws_bytes;
   const int64_t before = h->bytes;
@@ -626,6 +627,88 @@ hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_i
   return HPS_OK;
 }
 
+// Apply-only solves (build-time source) of several operators, the same
+// level of every tree in one launch (Section 3.4, Algorithm "down pass", for
+// many trees at once): per level counted from the roots one grouped gint
+// launch and one grouped children launch, then one grouped leaf output.  A
+// lazy root is applied per operator first (its D^{-1} is a factored solve).
+template <typename T>
+hps_status solve_multi_impl(const std::vector<int>& idx, hps_handle* const* hs, const int* nrhs,
+                            const void* const* g, void* const* u, cudaStream_t st) {
+  int maxL = 0;
+  for (int i : idx) {
+    hps_handle* h = hs[i];
+    if (h->trsv_err_host && *(volatile int*)h->trsv_err_host) return HPS_ERR_TIMEOUT;
+    HPS_TRY(ensure_ws<T>(h, nrhs[i]));
+    maxL = std::max(maxL, h->L);
+    if (h->L > 0 && h->lev[h->L - 1].lazy) {
+      LevelDev& Lv = h->lev[h->L - 1];
+      T* gchild = (h->L == 1) ? (T*)h->ws_gleaf : (T*)Lv.gchild;
+      HPS_CUDA(down_gint<T>((const T*)Lv.X, nullptr, (const T*)g[i], Lv.nmerge, Lv.n_ext, Lv.n_int, nrhs[i],
+                            (T*)Lv.x, st, nullptr));
+      HPS_TRY(apply_Dinv<T>(h, h->L - 1, (T*)Lv.x, (T*)Lv.gint, nrhs[i], st, nullptr));
+      HPS_CUDA(down_children<T>((const T*)g[i], (const T*)Lv.gint, Lv.nmerge, Lv.nch, Lv.nbc, Lv.n_ext, Lv.n_int,
+                                nrhs[i], Lv.ext, Lv.var, gchild, st, nullptr));
+    }
+  }
+  DownGroup<T> grp;
+  auto flush_down = [&]() -> cudaError_t {
+    cudaError_t e = down_level_group<T>(grp, st);
+    grp.n = 0;
+    grp.tiles = grp.elems = 0;
+    return e;
+  };
+  for (int d = 0; d < maxL; ++d) {
+    grp.n = 0;
+    grp.tiles = grp.elems = 0;
+    for (int i : idx) {
+      hps_handle* h = hs[i];
+      if (h->L <= d) continue;
+      const int m = h->L - 1 - d;
+      LevelDev& Lv = h->lev[m];
+      if (d == 0 && Lv.lazy) continue;
+      DownTask<T>& tk = grp.t[grp.n++];
+      tk.X = (const T*)Lv.X;
+      tk.gpar = d == 0 ? (const T*)g[i] : (const T*)h->lev[m + 1].gchild;
+      tk.gint = (T*)Lv.gint;
+      tk.gchild = m == 0 ? (T*)h->ws_gleaf : (T*)Lv.gchild;
+      tk.ext = Lv.ext;
+      tk.var = Lv.var;
+      tk.nmerge = Lv.nmerge; tk.nch = Lv.nch; tk.nbc = Lv.nbc;
+      tk.n_ext = Lv.n_ext; tk.n_int = Lv.n_int; tk.nrhs = nrhs[i];
+      tk.tile0 = grp.tiles;
+      tk.elem0 = grp.elems;
+      grp.tiles += (int64_t)Lv.nmerge * ((Lv.n_int + 31) / 32) * nrhs[i];
+      grp.elems += (int64_t)Lv.nmerge * Lv.nch * Lv.nbc * nrhs[i];
+      if (grp.n == kMaxGroup) HPS_CUDA(flush_down());
+    }
+    HPS_CUDA(flush_down());
+  }
+  LeafGroup<T> lg;
+  lg.n = 0;
+  lg.iti = Kind<T>::iti;
+  lg.elems = 0;
+  for (int i : idx) {
+    hps_handle* h = hs[i];
+    LeafTask<T>& tk = lg.t[lg.n++];
+    tk.k = h->lc;
+    tk.nl = h->nl;
+    tk.nrhs = nrhs[i];
+    tk.X = (const T*)h->leafX;
+    tk.g = h->L > 0 ? (const T*)h->ws_gleaf : (const T*)g[i];
+    tk.u = (T*)u[i];
+    tk.elem0 = lg.elems;
+    lg.elems += (int64_t)nrhs[i] * h->nl * h->npts;
+    if (lg.n == kMaxGroup) {
+      HPS_CUDA(leaf_output_group<T>(lg, st));
+      lg.n = 0;
+      lg.elems = 0;
+    }
+  }
+  HPS_CUDA(leaf_output_group<T>(lg, st));
+  return HPS_OK;
+}
+
 thread_local int64_t g_last_err_node = -1;
 
 void drop_graphs(hps_handle* h) {
@@ -634,14 +717,45 @@ void drop_graphs(hps_handle* h) {
   h->graphs.clear();
 }
 
+// Wait for the handle's own work (not the whole device: other streams keep
+// running), then give its memory back to the pool.
 void free_handle(hps_handle* h) {
   if (!h) return;
-  cudaDeviceSynchronize();
+  if (h->done && h->done_recorded) cudaEventSynchronize(h->done);
   drop_graphs(h);
-  for (void* p : h->ws_allocs) cudaFree(p);
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->ws_allocs) dev_free_idle(p);
+  for (void* p : h->allocs) dev_free_idle(p);
   if (h->trsv_err_host) cudaFreeHost(h->trsv_err_host);
+  if (h->done) cudaEventDestroy(h->done);
+  cudaGetLastError();
   delete h;
+}
+
+// Order stream st after the handle's earlier work, and mark the end of the
+// work a call enqueues.  Skipped while the stream is being captured into a
+// graph by the caller (an event recorded outside a capture cannot be waited
+// on inside it; the caller's graph orders the work itself).
+static bool capturing_stream(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+void handle_begin(hps_handle* h, cudaStream_t st) {
+  if (h->done && h->done_recorded && !capturing_stream(st)) {
+    if (cudaStreamWaitEvent(st, h->done, 0) != cudaSuccess) cudaGetLastError();
+  }
+  h->last = st;
+}
+
+void handle_end(hps_handle* h, cudaStream_t st) {
+  if (h->done && !capturing_stream(st)) {
+    if (cudaEventRecord(h->done, st) == cudaSuccess) h->done_recorded = true;
+    else cudaGetLastError();
+  }
 }
 
 // Solve through a captured CUDA graph: the first call with a key runs
@@ -834,8 +948,14 @@ hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeff
     return HPS_ERR_CUDA;
   }
   h->device = dev;
+  if (cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return HPS_ERR_CUDA;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   h->last = st;
+  h->tcw.st = st;
   h->tcw.err_slot = &h->dev_err;
   h->tcw.enabled = h->opts.fp64_gemm == 0;
   try {
@@ -850,6 +970,8 @@ hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeff
     cudaStreamSynchronize(st);
     hps::tc_release(&h->tcw);
   }
+  // a failed build may leave work queued on st: free_handle waits for it
+  if (s != HPS_OK) handle_end(h, st);
   if (s != HPS_OK && s != HPS_ERR_SINGULAR) {
     free_handle(h);
     return s;
@@ -862,6 +984,7 @@ hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeff
     return s;
   }
   g_last_err_node = -1;
+  handle_end(h, st);
   *out = h;
   return HPS_OK;
 }
@@ -870,7 +993,7 @@ hps_status hps_solve_batched(hps_handle* h, int nrhs, const void* g, const void*
                              struct CUstream_st* stream) {
   if (!h || !g || !u || nrhs < 1) return HPS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
-  h->last = st;
+  handle_begin(h, st);
   hps_status s;
   try {
     if (h->adaptive) s = adaptive_solve(h, nrhs, g, f, u, st);
@@ -882,6 +1005,37 @@ hps_status hps_solve_batched(hps_handle* h, int nrhs, const void* g, const void*
     h->capturing = false;
     s = HPS_ERR_INVALID;
   }
+  handle_end(h, st);
+  return s;
+}
+
+hps_status hps_solve_multi(int n, hps_handle* const* hs, const int* nrhs, const void* const* g, void* const* u,
+                           struct CUstream_st* stream) {
+  if (n < 1 || n > 1024 || !hs || !nrhs || !g || !u) return HPS_ERR_INVALID;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HPS_ERR_CUDA;
+  }
+  std::vector<int> real_idx, cplx_idx;
+  for (int i = 0; i < n; ++i) {
+    hps_handle* h = hs[i];
+    if (!h || h->adaptive || nrhs[i] < 1 || !g[i] || !u[i] || h->device != dev) return HPS_ERR_INVALID;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == h) return HPS_ERR_INVALID;
+    if (!is_device_ptr(g[i]) || !is_device_ptr(u[i])) return HPS_ERR_INVALID;
+    (h->iti ? cplx_idx : real_idx).push_back(i);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < n; ++i) handle_begin(hs[i], st);
+  hps_status s = HPS_OK;
+  try {
+    if (!real_idx.empty()) s = solve_multi_impl<double>(real_idx, hs, nrhs, g, u, st);
+    if (s == HPS_OK && !cplx_idx.empty()) s = solve_multi_impl<cplx>(cplx_idx, hs, nrhs, g, u, st);
+  } catch (...) {
+    s = HPS_ERR_INVALID;
+  }
+  for (int i = 0; i < n; ++i) handle_end(hs[i], st);
   return s;
 }
 
@@ -893,12 +1047,15 @@ hps_status hps_solve_adjoint(hps_handle* h, int nrhs, const void* ubar, void* gb
                              struct CUstream_st* stream) {
   if (!h || !ubar || nrhs < 1 || h->adaptive) return HPS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
-  h->last = st;
+  handle_begin(h, st);
+  hps_status s;
   try {
-    return adjoint_solve(h, nrhs, ubar, gbar, fbar, st);
+    s = adjoint_solve(h, nrhs, ubar, gbar, fbar, st);
   } catch (...) {
-    return HPS_ERR_INVALID;
+    s = HPS_ERR_INVALID;
   }
+  handle_end(h, st);
+  return s;
 }
 
 hps_status hps_debug_wait_timeout(int which, int satisfied, int64_t limit_polls, struct CUstream_st* stream) {
@@ -974,8 +1131,10 @@ hps_status hps_coeff_gradient(hps_handle* h, int nrhs, const void* u, const void
                               double* gc, struct CUstream_st* stream) {
   if (!h || !u || !fbar || nrhs < 1 || h->adaptive) return HPS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
-  h->last = st;
-  return coeff_gradient(h, nrhs, u, fbar, ga, gb, gc, st);
+  handle_begin(h, st);
+  const hps_status s = coeff_gradient(h, nrhs, u, fbar, ga, gb, gc, st);
+  handle_end(h, st);
+  return s;
 }
 
 void hps_free(hps_handle* h) { free_handle(h); }
@@ -1140,10 +1299,14 @@ extern "C" hps_status hps_solve_noalloc(hps_handle* h, const void* g, void* u, s
   }
   if (dev != h->device || !on_device(g, dev) || !on_device(u, dev)) return HPS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
+  handle_begin(h, st);
+  hps_status s;
   try {
-    return h->iti ? solve_noalloc_impl<cplx>(h, dev, (const cplx*)g, (cplx*)u, st)
-                  : solve_noalloc_impl<double>(h, dev, (const double*)g, (double*)u, st);
+    s = h->iti ? solve_noalloc_impl<cplx>(h, dev, (const cplx*)g, (cplx*)u, st)
+               : solve_noalloc_impl<double>(h, dev, (const double*)g, (double*)u, st);
   } catch (...) {
-    return HPS_ERR_INVALID;
+    s = HPS_ERR_INVALID;
   }
+  handle_end(h, st);
+  return s;
 }

@@ -608,6 +608,117 @@ cudaError_t scale_copy(const T* src, T* dst, int64_t n, double alpha, cudaStream
   return cudaGetLastError();
 }
 
+// ------------------------------------------------- grouped downward pass ----
+
+// gint = -(X_C gpar + x) for one 32-row tile of one merge and right-hand
+// side of one task per CTA: 32 lanes own the rows, 8 warps split the columns
+// (coalesced 32-row column reads), partial sums added in shared memory in a
+// fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_down_gint_group(DownGroup<T> grp) {
+  __shared__ T part[8][33];
+  const int lane = threadIdx.x, cg = threadIdx.y;
+  const int64_t tile = blockIdx.x;
+  int ti = 0;
+  while (ti + 1 < grp.n && grp.t[ti + 1].tile0 <= tile) ++ti;
+  const DownTask<T>& tk = grp.t[ti];
+  const int rtiles = (tk.n_int + 31) / 32;
+  const int64_t loc = tile - tk.tile0;
+  const int r = (int)(loc % rtiles) * 32 + lane;
+  const int64_t bc = loc / rtiles;
+  const int c = (int)(bc % tk.nrhs);
+  const int64_t b = bc / tk.nrhs;
+  const T* Xb = tk.X + b * (int64_t)tk.n_int * (tk.n_ext + 1);
+  const T* g = tk.gpar + b * (int64_t)tk.n_ext * tk.nrhs + (int64_t)c * tk.n_ext;
+  T acc = T(0.0);
+  if (r < tk.n_int) {
+#pragma unroll 4
+    for (int j = cg; j < tk.n_ext; j += 8) acc = fmac(acc, Xb[r + (int64_t)j * tk.n_int], g[j]);
+  }
+  part[cg][lane] = acc;
+  __syncthreads();
+  if (cg == 0 && r < tk.n_int) {
+    T s = Xb[r + (int64_t)tk.n_ext * tk.n_int];
+    for (int k = 0; k < 8; ++k) s = s + part[k][lane];
+    tk.gint[b * (int64_t)tk.n_int * tk.nrhs + r + (int64_t)c * tk.n_int] = -s;
+  }
+}
+
+template <typename T>
+__global__ void k_down_children_group(DownGroup<T> grp) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < grp.elems;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int ti = 0;
+    while (ti + 1 < grp.n && grp.t[ti + 1].elem0 <= e) ++ti;
+    const DownTask<T>& tk = grp.t[ti];
+    const int64_t le = e - tk.elem0;
+    const int64_t per_child = (int64_t)tk.nbc * tk.nrhs;
+    const int64_t cidx = le / per_child;
+    const int rc = (int)(le % per_child);
+    const int i = rc % tk.nbc, c = rc / tk.nbc;
+    const int k = (int)(cidx % tk.nch);
+    const int64_t b = cidx / tk.nch;
+    const int ei = tk.ext[k * tk.nbc + i];
+    T v;
+    if (ei >= 0) v = tk.gpar[b * (int64_t)tk.n_ext * tk.nrhs + ei + (int64_t)c * tk.n_ext];
+    else v = tk.gint[b * (int64_t)tk.n_int * tk.nrhs + tk.var[k * tk.nbc + i] + (int64_t)c * tk.n_int];
+    tk.gchild[le] = v;
+  }
+}
+
+template <typename T>
+cudaError_t down_level_group(const DownGroup<T>& grp, cudaStream_t st) {
+  if (grp.n <= 0) return cudaSuccess;
+  if (grp.tiles > 0) k_down_gint_group<T><<<(unsigned)grp.tiles, dim3(32, 8), 0, st>>>(grp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (grp.elems > 0) k_down_children_group<T><<<grid_for(grp.elems), 256, 0, st>>>(grp);
+  return cudaGetLastError();
+}
+
+// u = Y g + v with the build-time v, for the leaves of every task.
+template <typename T>
+__global__ void k_leaf_output_group(LeafGroup<T> grp) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < grp.elems;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int ti = 0;
+    while (ti + 1 < grp.n && grp.t[ti + 1].elem0 <= e) ++ti;
+    const LeafTask<T>& tk = grp.t[ti];
+    const LeafConsts& k = tk.k;
+    const int64_t le = e - tk.elem0;
+    const int node = (int)(le % k.npts);
+    const int64_t lc = le / k.npts;
+    const int64_t leaf = lc % tk.nl;
+    const int c = (int)(lc / tk.nl);
+    const int xrows = grp.iti ? k.npts : k.ni;
+    const T* gl = tk.g + (leaf * tk.nrhs + c) * (int64_t)k.nb;
+    const T* Xl = tk.X + leaf * (int64_t)xrows * (k.nb + 1);
+    T acc = T(0.0);
+    if (grp.iti) {
+      acc = Xl[node + (int64_t)k.nb * xrows];
+      for (int j = 0; j < k.nb; ++j) acc = fmac(acc, Xl[node + (int64_t)j * xrows], gl[j]);
+    } else {
+      const int pr = k.prow[node];
+      if (pr >= 0) {
+        for (int j = 0; j < k.nb; ++j) acc = fmac(acc, T(k.P[pr + (int64_t)j * k.ne]), gl[j]);
+      } else {
+        const int r = k.iidx[node];
+        acc = Xl[r + (int64_t)k.nb * xrows];
+        for (int j = 0; j < k.nb; ++j) acc = fmac(acc, Xl[r + (int64_t)j * xrows], gl[j]);
+        acc = -acc;
+      }
+    }
+    tk.u[le] = acc;
+  }
+}
+
+template <typename T>
+cudaError_t leaf_output_group(const LeafGroup<T>& grp, cudaStream_t st) {
+  if (grp.n <= 0 || grp.elems <= 0) return cudaSuccess;
+  k_leaf_output_group<T><<<grid_for(grp.elems), 256, 0, st>>>(grp);
+  return cudaGetLastError();
+}
+
 #define HPS_KINST(T)                                                                                  \
   template cudaError_t leaf_particular_rhs<T>(const LeafConsts&, int64_t, int, const T*, T*, bool,    \
                                               cudaStream_t, Prof*);                                   \
@@ -625,7 +736,9 @@ cudaError_t scale_copy(const T* src, T* dst, int64_t n, double alpha, cudaStream
   template cudaError_t down_gint<T>(const T*, const T*, const T*, int, int, int, int, T*, cudaStream_t,     \
                                     Prof*);                                                                 \
   template cudaError_t down_children<T>(const T*, const T*, int, int, int, int, int, int, const int*,       \
-                                        const int*, T*, cudaStream_t, Prof*);
+                                        const int*, T*, cudaStream_t, Prof*);                                 \
+  template cudaError_t down_level_group<T>(const DownGroup<T>&, cudaStream_t);                               \
+  template cudaError_t leaf_output_group<T>(const LeafGroup<T>&, cudaStream_t);
 
 HPS_KINST(double)
 HPS_KINST(cplx)

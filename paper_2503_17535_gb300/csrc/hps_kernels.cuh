@@ -99,6 +99,56 @@ template <typename T>
 cudaError_t leaf_output(const LeafConsts& k, int64_t nl, int nrhs, const T* X, const T* xp,
                         const T* g, T* u, bool iti, cudaStream_t st, Prof* pf);
 
+// Grouped downward pass and leaf output: one launch serves the same level
+// (counted from each tree's root) of up to kMaxGroup different operators,
+// whose depths, orders and sizes may all differ (Section 3.4, Algorithm
+// "down pass", applied to many trees at once).  Each task carries its own
+// pointers and sizes; the launch's tiles / elements are laid out task after
+// task and every CTA or thread finds its task from the prefix offsets.
+constexpr int kMaxGroup = 24;
+
+template <typename T>
+struct DownTask {
+  const T* X;        // n_int x (n_ext+1) per merge; the last column is x
+  const T* gpar;     // n_ext x nrhs per merge
+  T* gint;           // n_int x nrhs per merge
+  T* gchild;         // children's boundary data, nbc x nrhs per child
+  const int* ext;
+  const int* var;
+  int nmerge, nch, nbc, n_ext, n_int, nrhs;
+  int64_t tile0;     // first 32-row tile of this task in the gint launch
+  int64_t elem0;     // first element of this task in the children launch
+};
+template <typename T>
+struct DownGroup {
+  int n;
+  int64_t tiles, elems;  // totals
+  DownTask<T> t[kMaxGroup];
+};
+template <typename T>
+struct LeafTask {
+  LeafConsts k;
+  int64_t nl;
+  int nrhs;
+  const T* X;
+  const T* g;        // per leaf nb x nrhs
+  T* u;              // [nrhs][nl][npts]
+  int64_t elem0;
+};
+template <typename T>
+struct LeafGroup {
+  int n;
+  bool iti;
+  int64_t elems;
+  LeafTask<T> t[kMaxGroup];
+};
+// gint of every task, then the children's data (two launches).
+template <typename T>
+cudaError_t down_level_group(const DownGroup<T>& grp, cudaStream_t st);
+// u = Y g + v (build-time source) for every task (one launch).
+template <typename T>
+cudaError_t leaf_output_group(const LeafGroup<T>& grp, cudaStream_t st);
+
 // Copy rows [r0, r0+m) of src blocks into dst blocks (same column count).
 template <typename T>
 cudaError_t copy_block(const T* src, int64_t sstride, int sld, T* dst, int64_t dstride, int dld,

@@ -117,6 +117,7 @@ cudaError_t debug_mbar_wait(int satisfied, long limit, unsigned* err, cudaStream
 struct TcWorkspace {
   void* p = nullptr;
   size_t bytes = 0;
+  cudaStream_t st = nullptr;  // stream the buffer was last allocated / used on
   unsigned* const* err_slot = nullptr;
   bool enabled = false;
   bool force = false;   // every product with K >= 1 (no size threshold)

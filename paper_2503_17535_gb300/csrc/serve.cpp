@@ -10,8 +10,11 @@
 // thread.  Only one batch or build per slot is in flight, which keeps each
 // handle single-threaded, as hps.h requires.  Each builder thread runs
 // hps_build on its own stream and releases the slot's previous operator
-// (hps_free synchronises the device, so that wait is kept off the scheduler);
+// (hps_free waits for that operator's last work, so that wait is kept off
+// the scheduler);
 // with several builders a small rebuild does not wait behind a large one.
+// Handle memory and staging buffers are stream-ordered (devmem.h), so builds,
+// frees and buffer growth never wait for the solves on other streams.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +29,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "devmem.h"
 #include "hps.h"
 #include "hps_serve.h"
 
@@ -73,19 +77,23 @@ struct StreamCtx {
   cudaEvent_t ev = nullptr;
   DevBuf dg, df, du;  // device
   DevBuf hg, hf, hu;  // pinned host
-  std::vector<Req*> batch;
-  int slot = -1;
+  std::vector<Req*> batch;     // requests in flight, in staging order
+  std::vector<size_t> uoff;    // byte offset of each request's u in hu
+  std::vector<size_t> ubytes;  // its size
+  std::vector<int> slots;      // slots whose work is in flight here
   bool busy = false;
-  size_t elem = 0;
 };
 
-bool grow_dev(DevBuf& b, size_t bytes) {
+// Device staging buffers of a stream: allocated and freed in that stream's
+// order (a regrowth does not wait for the other streams).
+bool grow_dev(DevBuf& b, size_t bytes, cudaStream_t st) {
   if (b.cap >= bytes) return true;
-  if (b.p) cudaFree(b.p);
+  if (b.p) hps::dev_free(b.p, st);
   b.p = nullptr;
   b.cap = 0;
-  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+  if (hps::dev_malloc(&b.p, bytes, st) != cudaSuccess) {
     cudaGetLastError();
+    b.p = nullptr;
     return false;
   }
   b.cap = bytes;
@@ -170,9 +178,9 @@ void dispatch_solves(hps_server* s, int si, StreamCtx& sc) {
   const size_t es = sl.iti ? 16 : 8;
   const size_t gb = (size_t)sl.n_root * es, ub = (size_t)sl.n_pts * es;
   const int nb = (int)b.size();
-  bool ok = grow_dev(sc.dg, gb * nb) && grow_dev(sc.du, ub * nb) && grow_host(sc.hg, gb * nb) &&
+  bool ok = grow_dev(sc.dg, gb * nb, sc.s) && grow_dev(sc.du, ub * nb, sc.s) && grow_host(sc.hg, gb * nb) &&
             grow_host(sc.hu, ub * nb);
-  if (ok && with_f) ok = grow_dev(sc.df, ub * nb) && grow_host(sc.hf, ub * nb);
+  if (ok && with_f) ok = grow_dev(sc.df, ub * nb, sc.s) && grow_host(sc.hf, ub * nb);
   hps_status st = ok ? HPS_OK : HPS_ERR_OOM;
   const double t = s->now_ms();
   if (st == HPS_OK) {
@@ -197,14 +205,107 @@ void dispatch_solves(hps_server* s, int si, StreamCtx& sc) {
     for (Req* r : b) finish(s, r, st);
     return;
   }
+  sc.uoff.clear();
+  sc.ubytes.clear();
+  for (int i = 0; i < nb; ++i) {
+    sc.uoff.push_back((size_t)i * ub);
+    sc.ubytes.push_back(ub);
+  }
   sc.batch = std::move(b);
-  sc.slot = si;
+  sc.slots.assign(1, si);
   sc.busy = true;
-  sc.elem = ub;
   sl.busy = true;
   std::lock_guard<std::mutex> lk(s->mu);
   ++s->stats.batches;
   s->stats.max_batch_seen = std::max<int64_t>(s->stats.max_batch_seen, nb);
+}
+
+// Dispatch the apply-only solves (build-time source) waiting at the heads of
+// several slots as one hps_solve_multi on a free stream: up to max_batch
+// requests per slot, up to max_group slots, whatever their depths, orders
+// and kinds.  The operators' downward passes then share their launches.
+void dispatch_group(hps_server* s, const std::vector<int>& cand, StreamCtx& sc) {
+  std::vector<int> gs;
+  std::vector<std::vector<Req*>> reqs;
+  for (int si : cand) {
+    if ((int)gs.size() >= s->opts.max_group) break;
+    Slot& sl = s->slots[si];
+    std::vector<Req*> b;
+    while (!sl.q.empty() && (int)b.size() < s->opts.max_batch) {
+      Req* r = sl.q.front();
+      if (r->kind != 0 || r->f != nullptr) break;
+      b.push_back(r);
+      sl.q.pop_front();
+    }
+    if (b.empty()) continue;
+    gs.push_back(si);
+    reqs.push_back(std::move(b));
+  }
+  const int n = (int)gs.size();
+  if (n == 0) return;
+  // staging layout: per slot its requests' g (and u) back to back
+  std::vector<size_t> goff(n), uoff_slot(n);
+  size_t gtot = 0, utot = 0;
+  for (int k = 0; k < n; ++k) {
+    const Slot& sl = s->slots[gs[k]];
+    const size_t es = sl.iti ? 16 : 8;
+    goff[k] = gtot;
+    uoff_slot[k] = utot;
+    gtot += (size_t)sl.n_root * es * reqs[k].size();
+    utot += (size_t)sl.n_pts * es * reqs[k].size();
+  }
+  bool ok = grow_dev(sc.dg, gtot, sc.s) && grow_dev(sc.du, utot, sc.s) && grow_host(sc.hg, gtot) &&
+            grow_host(sc.hu, utot);
+  hps_status st = ok ? HPS_OK : HPS_ERR_OOM;
+  const double t = s->now_ms();
+  std::vector<hps_handle*> hs(n);
+  std::vector<int> nrhs(n);
+  std::vector<const void*> gp(n);
+  std::vector<void*> up(n);
+  sc.batch.clear();
+  sc.uoff.clear();
+  sc.ubytes.clear();
+  int nreq = 0;
+  for (int k = 0; k < n; ++k) {
+    const Slot& sl = s->slots[gs[k]];
+    const size_t es = sl.iti ? 16 : 8;
+    const size_t gb = (size_t)sl.n_root * es, ub = (size_t)sl.n_pts * es;
+    for (size_t i = 0; i < reqs[k].size(); ++i) {
+      Req* r = reqs[k][i];
+      if (st == HPS_OK) std::memcpy((char*)sc.hg.p + goff[k] + i * gb, r->g, gb);
+      r->t_start = t;
+      r->batch = (int)reqs[k].size();
+      sc.batch.push_back(r);
+      sc.uoff.push_back(uoff_slot[k] + i * ub);
+      sc.ubytes.push_back(ub);
+      ++nreq;
+    }
+    hs[k] = sl.h;
+    nrhs[k] = (int)reqs[k].size();
+    gp[k] = (const char*)sc.dg.p + goff[k];
+    up[k] = (char*)sc.du.p + uoff_slot[k];
+  }
+  if (st == HPS_OK && cudaMemcpyAsync(sc.dg.p, sc.hg.p, gtot, cudaMemcpyHostToDevice, sc.s) != cudaSuccess)
+    st = HPS_ERR_CUDA;
+  if (st == HPS_OK) st = hps_solve_multi(n, hs.data(), nrhs.data(), gp.data(), up.data(), sc.s);
+  if (st == HPS_OK && (cudaMemcpyAsync(sc.hu.p, sc.du.p, utot, cudaMemcpyDeviceToHost, sc.s) != cudaSuccess ||
+                       cudaEventRecord(sc.ev, sc.s) != cudaSuccess))
+    st = HPS_ERR_CUDA;
+  if (st != HPS_OK) {
+    cudaGetLastError();
+    std::vector<Req*> b = std::move(sc.batch);
+    sc.batch.clear();
+    for (Req* r : b) finish(s, r, st);
+    return;
+  }
+  sc.slots = gs;
+  sc.busy = true;
+  for (int si : gs) s->slots[si].busy = true;
+  std::lock_guard<std::mutex> lk(s->mu);
+  ++s->stats.batches;
+  if (n > 1) ++s->stats.multi_batches;
+  s->stats.max_batch_seen = std::max<int64_t>(s->stats.max_batch_seen, nreq);
+  s->stats.max_group_seen = std::max<int64_t>(s->stats.max_group_seen, n);
 }
 
 void complete_batch(hps_server* s, StreamCtx& sc) {
@@ -214,12 +315,12 @@ void complete_batch(hps_server* s, StreamCtx& sc) {
   if (e != cudaSuccess) cudaGetLastError();
   for (size_t i = 0; i < sc.batch.size(); ++i) {
     Req* r = sc.batch[i];
-    if (st == HPS_OK) std::memcpy(r->u, (const char*)sc.hu.p + i * sc.elem, sc.elem);
+    if (st == HPS_OK) std::memcpy(r->u, (const char*)sc.hu.p + sc.uoff[i], sc.ubytes[i]);
     finish(s, r, st);
   }
   sc.batch.clear();
-  s->slots[sc.slot].busy = false;
-  sc.slot = -1;
+  for (int si : sc.slots) s->slots[si].busy = false;
+  sc.slots.clear();
   sc.busy = false;
 }
 
@@ -383,6 +484,12 @@ void sched_main(hps_server* s) {
       }
     }
     const size_t ns = s->slots.size();
+    auto free_stream = [&]() -> StreamCtx* {
+      for (StreamCtx& sc : s->streams)
+        if (!sc.busy) return &sc;
+      return nullptr;
+    };
+    std::vector<int> apply_only;  // idle slots whose head is a solve with the build-time source
     for (size_t k = 0; k < ns; ++k) {
       const int si = (int)((rr + k) % ns);
       Slot& sl = s->slots[si];
@@ -398,17 +505,25 @@ void sched_main(hps_server* s) {
         progress = true;
         continue;
       }
-      StreamCtx* free_sc = nullptr;
-      for (StreamCtx& sc : s->streams)
-        if (!sc.busy) {
-          free_sc = &sc;
-          break;
-        }
+      if (head->f == nullptr && s->opts.max_group > 1) {
+        apply_only.push_back(si);
+        continue;
+      }
+      StreamCtx* free_sc = free_stream();
       if (!free_sc) break;
       dispatch_solves(s, si, *free_sc);
       progress = true;
       inflight = true;
       rr = (size_t)si + 1;
+    }
+    if (!apply_only.empty()) {
+      StreamCtx* free_sc = free_stream();
+      if (free_sc) {
+        dispatch_group(s, apply_only, *free_sc);
+        progress = true;
+        inflight = true;
+        rr = (size_t)apply_only.back() + 1;
+      }
     }
     if (!progress) {
       std::unique_lock<std::mutex> lk(s->mu);
@@ -468,8 +583,10 @@ hps_status hps_server_create(const hps_server_options* opts, hps_server** out) {
   if (o.n_streams == 0) o.n_streams = 4;
   if (o.max_batch == 0) o.max_batch = 8;
   if (o.n_builders == 0) o.n_builders = 2;
+  if (o.max_group == 0) o.max_group = 8;
   if (o.n_slots < 1 || o.n_slots > 1024 || o.n_streams < 1 || o.n_streams > 64 || o.max_batch < 1 ||
-      o.max_batch > 256 || o.hbm_budget < 0 || o.n_builders < 1 || o.n_builders > 8)
+      o.max_batch > 256 || o.hbm_budget < 0 || o.n_builders < 1 || o.n_builders > 8 || o.max_group < 1 ||
+      o.max_group > 24)
     return HPS_ERR_INVALID;
   hps_server* s = new (std::nothrow) hps_server();
   if (!s) return HPS_ERR_OOM;
@@ -530,7 +647,8 @@ void hps_server_destroy(hps_server* s) {
   for (StreamCtx& sc : s->streams) {
     if (sc.s) cudaStreamSynchronize(sc.s);
     for (DevBuf* b : {&sc.dg, &sc.df, &sc.du})
-      if (b->p) cudaFree(b->p);
+      if (b->p) hps::dev_free(b->p, sc.s);
+    if (sc.s) cudaStreamSynchronize(sc.s);
     for (DevBuf* b : {&sc.hg, &sc.hf, &sc.hu})
       if (b->p) cudaFreeHost(b->p);
     if (sc.ev) cudaEventDestroy(sc.ev);

@@ -2,14 +2,16 @@
 
 The server must return, for every request, the same solution as the plain
 path (hps_build + hps_solve of the same operator, one request at a time)
-within the parity bar (relative L-infinity <= 1e-10), whatever batches and
-streams the request shared; builds are admitted by device footprint.
+and as the oracle, within the parity bar (relative L-infinity <= 1e-10),
+whatever batches, operator groups and streams the request shared; builds are
+admitted by device footprint.
 """
 
 import numpy as np
 import pytest
 
 import workloads as W
+from oracle import hps as O
 from test_gpu_parity import TOL, rel, sample_inputs
 
 pytestmark = pytest.mark.gpu
@@ -56,6 +58,20 @@ def _alone(P, op, g, f):
     return u
 
 
+_ORACLE_OPS = {}
+
+
+def _oracle(op, g, f):
+    """The oracle's u for the operator's coefficients, boundary data g and
+    source f (the build-time source when f is None)."""
+    pr = op["pr"]
+    key = (id(op), None if f is None else f.tobytes())
+    if key not in _ORACLE_OPS:
+        _ORACLE_OPS[key] = O.build(pr.dim, pr.kind, op["p"], op["p"] - 2, op["L"], pr.lo, pr.hi, op["a"],
+                                   op["b"], op["c"], op["f"] if f is None else f, eta=pr.eta)
+    return O.solve(_ORACLE_OPS[key], g)
+
+
 def _submit_build(S, slot, op):
     return S.submit_build(slot, op["t"], op["p"], op["p"] - 2, op["kind"], a=op["a"], b=op["b"], c=op["c"],
                           f=op["f"], eta=op["eta"])
@@ -82,16 +98,50 @@ def test_results_same_alone_and_in_mix(P):
             f = _rand_like(rng, op["f"]) if rng.random() < 0.4 else None
             u = np.zeros(op["f"].shape, op["f"].dtype)
             reqs.append((S.submit_solve(slot, g, u, f=f), op, g, f, u))
-        infos = [S.wait(t) for t, *_ in reqs]
-        for t in builds:
-            S.wait(t)
+        infos = [S.wait(t, check=False) for t, *_ in reqs]
+        binfos = [S.wait(t, check=False) for t in builds]
         st = S.stats()
+    assert all(i["status"] == 0 for i in binfos), binfos
+    assert all(i["status"] == 0 for i in infos), [(t, i) for (t, *_), i in zip(reqs, infos) if i["status"]]
     assert st["solves"] == 40 and st["builds"] == 5
     assert max(i["batch"] for i in infos) >= 2, "no request was batched"
     for (t, op, g, f, u), info in zip(reqs, infos):
         assert info["status"] == 0
         ua = _alone(P, op, g, f)
         assert rel(u, ua) <= TOL, (info, rel(u, ua))
+        uo = _oracle(op, g, f)
+        assert rel(u, uo) <= TOL, (info, rel(u, uo))
+
+
+def test_apply_only_solves_of_different_operators_share_launches(P):
+    """Apply-only requests queued on operators of different kinds, depths
+    and orders are served by one grouped solve; each result equals the
+    oracle's and the plain path's."""
+    ops = [
+        _problem(P, W.e1_dtn_2d, 8, 3),
+        _problem(P, W.e2_iti_2d, 12, 2),
+        _problem(P, lambda: W.elliptic_3d(seed=2), 6, 1),
+        _problem(P, lambda: W.helmholtz_bumps_2d(seed=1), 16, 2),
+        _problem(P, lambda: W.poisson_poly_2d(seed=0), 8, 0),
+    ]
+    rng = np.random.default_rng(77)
+    with P.Server(n_slots=len(ops), n_streams=1, max_batch=3, max_group=8) as S:
+        for t in [_submit_build(S, i, op) for i, op in enumerate(ops)]:
+            S.wait(t)
+        reqs = []
+        for k in range(30):
+            slot = k % len(ops)
+            op = ops[slot]
+            g = _rand_like(rng, op["g"])
+            u = np.zeros(op["f"].shape, op["f"].dtype)
+            reqs.append((S.submit_solve(slot, g, u), op, g, u))
+        infos = [S.wait(t) for t, *_ in reqs]
+        st = S.stats()
+    assert st["multi_batches"] >= 1 and st["max_group_seen"] >= 2, st
+    for (t, op, g, u), info in zip(reqs, infos):
+        assert info["status"] == 0
+        assert rel(u, _alone(P, op, g, None)) <= TOL
+        assert rel(u, _oracle(op, g, None)) <= TOL
 
 
 def test_queued_solves_share_one_batch(P):
