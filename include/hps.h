@@ -312,6 +312,28 @@ hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double 
                     int64_t strideA, const void* B, int ldb, int64_t strideB, double beta, void* C, int ldc,
                     int64_t strideC, struct CUstream_st* stream);
 
+/* Shape choices of the batched LU and of the product routing (no
+ * counterpart in the paper, which factors and multiplies with its library).  Process-wide, read at each factorisation;
+ * the defaults come from the autotuner's table (timed builds on GB300).
+ *   HPS_TUNE_LU_BASE_PANELS_FEW  (0): recursive LU base width in panels for
+ *       batches of fewer than 8 matrices (0: blocked right-looking);
+ *   HPS_TUNE_LU_BASE_PANELS_MANY (1): the same for batches of 8 or more;
+ *   HPS_TUNE_LU_FEW_MIN_N        (2): batches of fewer than 8 recurse only
+ *       from this order on;
+ *   HPS_TUNE_LU_CLUSTER_PANEL    (3): 1 factors tall panels in a thread-block
+ *       cluster's distributed shared memory, 0 with cooperative groups;
+ *   HPS_TUNE_TC_MIN_WORK_REAL    (4): a real product of the build runs on the
+ *       tensor cores from M N K batch >= value x 1e5 on (hps_options.fp64_gemm
+ *       = 0), else on the FP64 pipe;
+ *   HPS_TUNE_TC_MIN_WORK_CPLX    (5): the same threshold for complex products.
+ * Every choice gives the same pivots and results up to rounding.  Not to be
+ * changed while a build runs.  HPS_ERR_INVALID for an unknown parameter or a
+ * value outside 0 .. 2^20. */
+enum { HPS_TUNE_LU_BASE_PANELS_FEW = 0, HPS_TUNE_LU_BASE_PANELS_MANY = 1, HPS_TUNE_LU_FEW_MIN_N = 2,
+       HPS_TUNE_LU_CLUSTER_PANEL = 3, HPS_TUNE_TC_MIN_WORK_REAL = 4, HPS_TUNE_TC_MIN_WORK_CPLX = 5 };
+hps_status hps_tune_set(int param, int value);
+hps_status hps_tune_get(int param, int* value);
+
 /* Fault injection for tests (no counterpart in the paper).  Host side only:
  * no device fault, trap or hang is involved.  After hps_debug_fail_alloc(n)
  * with n > 0, the n-th device allocation of a handle (build buffers,

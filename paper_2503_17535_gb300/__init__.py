@@ -550,3 +550,18 @@ def hps_debug_wait_timeout(which: int, satisfied: bool, limit_polls: int, stream
     HPS_ERR_TIMEOUT when the wait gave up, HPS_OK when it passed."""
     return int(_capi.lib().hps_debug_wait_timeout(int(which), 1 if satisfied else 0, int(limit_polls),
                                                    _stream(stream)))
+
+
+TUNE_PARAMS = {"lu_base_panels_few": 0, "lu_base_panels_many": 1, "lu_few_min_n": 2, "lu_cluster_panel": 3,
+               "tc_min_work_real": 4, "tc_min_work_cplx": 5}
+
+
+def hps_tune_set(name: str, value: int) -> None:
+    """Set one of the batched LU's shape choices (include/hps.h)."""
+    _check(_capi.lib().hps_tune_set(TUNE_PARAMS[name], int(value)), "hps_tune_set")
+
+
+def hps_tune_get(name: str) -> int:
+    v = ctypes.c_int(0)
+    _check(_capi.lib().hps_tune_get(TUNE_PARAMS[name], byref(v)), "hps_tune_get")
+    return int(v.value)

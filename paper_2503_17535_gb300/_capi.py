@@ -24,6 +24,7 @@ EXPORTED = [
     "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc", "hps_refine", "hps_trace_count",
     "hps_trace_get", "hps_plan_bytes", "hps_solve_adjoint", "hps_coeff_gradient", "hps_gemm",
     "hps_debug_fail_alloc", "hps_debug_alloc_count", "hps_debug_wait_timeout",
+    "hps_tune_set", "hps_tune_get",
     # request server (include/hps_serve.h)
     "hps_server_create", "hps_server_destroy", "hps_server_submit_build", "hps_server_submit_solve",
     "hps_server_wait", "hps_server_poll", "hps_server_get_stats", "hps_server_operator",
@@ -138,6 +139,10 @@ def lib() -> ctypes.CDLL:
     L.hps_debug_alloc_count.restype = c_int64
     L.hps_debug_wait_timeout.argtypes = [c_int, c_int, c_int64, c_void_p]
     L.hps_debug_wait_timeout.restype = c_int
+    L.hps_tune_set.argtypes = [c_int, c_int]
+    L.hps_tune_set.restype = c_int
+    L.hps_tune_get.argtypes = [c_int, POINTER(c_int)]
+    L.hps_tune_get.restype = c_int
     L.hps_server_create.argtypes = [POINTER(hps_server_options), POINTER(c_void_p)]
     L.hps_server_create.restype = c_int
     L.hps_server_destroy.argtypes = [c_void_p]

@@ -544,7 +544,7 @@ bool tc_applicable(const GemmArgs<T>& g) {
   if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta || g.K > (1 << 20)) return false;
   if (w->force) return true;
   if (g.M < 32 || g.N < 16 || g.K < 16) return false;
-  if ((double)g.M * g.N * g.K * g.batch < 1.0e7) return false;
+  if ((double)g.M * g.N * g.K * g.batch < 1.0e5 * lu_tune(TUNE_TC_MIN_WORK_REAL)) return false;
   return true;
 }
 
@@ -555,7 +555,7 @@ bool tc_applicable<cplx>(const GemmArgs<cplx>& g) {
   if (g.alpha.im != 0.0 || g.beta.im != 0.0) return false;
   if (w->force) return true;
   if (g.M < 32 || g.N < 16 || g.K < 16) return false;
-  if ((double)g.M * g.N * g.K * g.batch < 2.5e6) return false;
+  if ((double)g.M * g.N * g.K * g.batch < 1.0e5 * lu_tune(TUNE_TC_MIN_WORK_CPLX)) return false;
   return true;
 }
 

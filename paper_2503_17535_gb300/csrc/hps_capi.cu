@@ -1078,6 +1078,18 @@ hps_status hps_debug_wait_timeout(int which, int satisfied, int64_t limit_polls,
   return (herr & hps::DEV_ERR_TIMEOUT) ? HPS_ERR_TIMEOUT : HPS_OK;
 }
 
+hps_status hps_tune_set(int param, int value) {
+  if (param < 0 || param >= hps::TUNE_COUNT || value < 0 || value > (1 << 20)) return HPS_ERR_INVALID;
+  hps::lu_tune(param) = value;
+  return HPS_OK;
+}
+
+hps_status hps_tune_get(int param, int* value) {
+  if (param < 0 || param >= hps::TUNE_COUNT || !value) return HPS_ERR_INVALID;
+  *value = hps::lu_tune(param);
+  return HPS_OK;
+}
+
 void hps_debug_fail_alloc(int64_t n) { hps::alloc_fail_countdown().store(n > 0 ? n : 0); }
 
 int64_t hps_debug_alloc_count(void) { return hps::alloc_counter().load(); }

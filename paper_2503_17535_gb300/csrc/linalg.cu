@@ -9,6 +9,8 @@
 // instruction that is not part of the algorithm.
 #include "linalg.h"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstdio>
 
@@ -726,6 +728,229 @@ __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int n
     for (int r = tid; r < rc; r += nth) Ab[(int64_t)(r0 + r) + (int64_t)(k0 + c) * lda] = Ps[r + (size_t)c * ch];
 }
 
+// Panel LU of tall panels in the distributed shared memory of a thread-block
+// cluster.  The rows [k0, n) are split into CS contiguous chunks, one per CTA
+// of the matrix's cluster, each held in that CTA's shared memory for the
+// whole panel.  Rows never move during the panel: a chosen pivot row is only
+// marked done, and the interchanges are recorded in LAPACK's form (ipiv) by
+// a replay of the swap sequence on the panel's top positions; at the end
+// every row is written to its final position.  Per column: each CTA
+// publishes its best candidate (|.|, current position, row, and the row's
+// panel values) in its own shared memory, one cluster barrier, every CTA
+// reads all CS candidates through distributed shared memory in one round,
+// picks the same pivot (largest magnitude, and on ties the lowest current
+// position -- the row order after the interchanges so far, which is the
+// choice of the cooperative kernel and of LAPACK), and updates its own rows.  Candidates are
+// double-buffered by column parity, so one barrier per column suffices: a CTA
+// cannot overwrite a buffer before every CTA has passed the next barrier,
+// which each reaches only after reading the buffer.  The barrier is the
+// hardware cluster barrier; there is no polling.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k0, int nb, int* ipiv,
+                                                          int* info) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int g = (int)cl.block_rank();
+  const int b = blockIdx.x / CS;
+  const int rows = n - k0;
+  const int ch = (rows + CS - 1) / CS;
+  const int r0 = k0 + g * ch;
+  const int rc = max(0, min(ch, n - r0));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ps = reinterpret_cast<T*>(smem_raw);       // ch x nb, column-major
+  T* pubv = Ps + (size_t)ch * nb;               // 2 x nb: this CTA's candidate row
+  T* cand = pubv + 2 * nb;                      // CS x nb: every CTA's candidate row
+  int* chosen = reinterpret_cast<int*>(cand + (size_t)CS * nb);  // ch: pivot step of a row, or -1
+  __shared__ long long pub_m[2];
+  __shared__ int pub_r[2], pub_p[2];  // candidate's current position and row
+  __shared__ long long cm[16];
+  __shared__ int cr[16], cp[16];
+  __shared__ double red_m[8];
+  __shared__ int red_r[8], red_p[8];
+  __shared__ int s_win, s_lr;
+  __shared__ int phys_at[64], pos_top[64];      // swap replay on the top positions
+  __shared__ double s_inv_raw[2];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  T* Ab = A.item(b);
+  const int lda = A.ld;
+
+  for (int c = 0; c < nb; ++c)
+    for (int r = tid; r < rc; r += nth) Ps[r + (size_t)c * ch] = Ab[(int64_t)(r0 + r) + (int64_t)(k0 + c) * lda];
+  for (int r = tid; r < ch; r += nth) chosen[r] = -1;
+  if (tid < nb) { phys_at[tid] = k0 + tid; pos_top[tid] = k0 + tid; }
+  __syncthreads();
+  // (magnitude, current position) orders candidates; prow is the row itself
+  double best = -1.0;
+  int bpos = 0x7fffffff, prow = -1;
+  for (int r = tid; r < rc; r += nth) {
+    const double m = mag1(Ps[r]);
+    if (piv_better(m, r0 + r, best, bpos)) { best = m; bpos = r0 + r; prow = r0 + r; }
+  }
+  for (int jj = 0; jj < nb; ++jj) {
+    const int j = k0 + jj, slot = jj & 1;
+    // this CTA's candidate
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double m2 = __shfl_down_sync(0xffffffffu, best, o);
+      const int q2 = __shfl_down_sync(0xffffffffu, bpos, o);
+      const int p2 = __shfl_down_sync(0xffffffffu, prow, o);
+      if (piv_better(m2, q2, best, bpos)) { best = m2; bpos = q2; prow = p2; }
+    }
+    if (lane == 0) { red_m[wid] = best; red_r[wid] = bpos; red_p[wid] = prow; }
+    __syncthreads();
+    if (tid == 0) {
+      double pm = red_m[0];
+      int pq = red_r[0], pr = red_p[0];
+      for (int w = 1; w < nw; ++w)
+        if (piv_better(red_m[w], red_r[w], pm, pq)) { pm = red_m[w]; pq = red_r[w]; pr = red_p[w]; }
+      pub_m[slot] = __double_as_longlong(pm);
+      pub_r[slot] = pq;
+      pub_p[slot] = pr;
+      s_lr = pm >= 0.0 ? pr - r0 : -1;
+    }
+    __syncthreads();
+    for (int c = tid; c < nb; c += nth) pubv[slot * nb + c] = s_lr >= 0 ? Ps[s_lr + (size_t)c * ch] : T(0.0);
+    cl.sync();
+    // every CTA's candidate, in one round of distributed shared memory reads
+    for (int e = tid; e < CS * nb; e += nth) {
+      const int q = e / nb, c = e - q * nb;
+      cand[e] = cl.map_shared_rank(pubv, q)[slot * nb + c];
+    }
+    if (tid < CS) {
+      cm[tid] = cl.map_shared_rank(pub_m, tid)[slot];
+      cr[tid] = cl.map_shared_rank(pub_r, tid)[slot];
+      cp[tid] = cl.map_shared_rank(pub_p, tid)[slot];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double pm = __longlong_as_double(cm[0]);
+      int pq = cr[0], wq = 0;
+      for (int q = 1; q < CS; ++q) {
+        const double m = __longlong_as_double(cm[q]);
+        if (piv_better(m, cr[q], pm, pq)) { pm = m; pq = cr[q]; wq = q; }
+      }
+      const int p = cp[wq];
+      s_win = wq;
+      const T pv = cand[wq * nb + jj];
+      *reinterpret_cast<T*>(s_inv_raw) = (pm == 0.0) ? T(0.0) : recip(pv);
+      if (g == wq) chosen[p - r0] = jj;
+      // LAPACK interchange: swap position j with the winner's current position
+      const bool ptop = p - k0 < nb;
+      const int qpos = pq;
+      const int rj = phys_at[jj];
+      pos_top[rj - k0] = qpos;
+      if (qpos - k0 < nb) phys_at[qpos - k0] = rj;
+      phys_at[jj] = p;
+      if (ptop) pos_top[p - k0] = j;
+      if (g == 0) {
+        ipiv[(int64_t)b * n + j] = qpos;
+        if (pm == 0.0 && info[b] == 0) info[b] = j + 1;
+      }
+    }
+    __syncthreads();
+    const T* Wv = cand + (size_t)s_win * nb;
+    const T inv = *reinterpret_cast<const T*>(s_inv_raw);
+    best = -1.0;
+    bpos = 0x7fffffff;
+    prow = -1;
+    for (int r = tid; r < rc; r += nth) {
+      if (chosen[r] >= 0) continue;
+      const int pr = r0 + r;
+      const int pos = pr - k0 < nb ? pos_top[pr - k0] : pr;  // after this column's interchange
+      const T l = Ps[r + (size_t)jj * ch] * inv;
+      Ps[r + (size_t)jj * ch] = l;
+      for (int c = jj + 1; c < nb; ++c) {
+        const T v = fmsc(Ps[r + (size_t)c * ch], l, Wv[c]);
+        Ps[r + (size_t)c * ch] = v;
+        if (c == jj + 1) {
+          const double m = mag1(v);
+          if (piv_better(m, pos, best, bpos)) { best = m; bpos = pos; prow = pr; }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // rows to their final positions
+  for (int r = tid; r < rc; r += nth) {
+    const int pr = r0 + r;
+    int dst = pr;
+    if (chosen[r] >= 0) dst = k0 + chosen[r];
+    else if (pr - k0 < nb) dst = pos_top[pr - k0];
+    for (int c = 0; c < nb; ++c) Ab[(int64_t)dst + (int64_t)(k0 + c) * lda] = Ps[r + (size_t)c * ch];
+  }
+  // no CTA leaves while another may still read its candidates
+  cl.sync();
+}
+
+// Cluster shape for a panel of `rows` rows: the smallest power of two of
+// CTAs with at most 256 rows each (one row per thread), at least 2, at most
+// the largest cluster the device runs with the kernel's shared memory; 0 when
+// the panel does not fit (the cooperative kernel is used then).
+template <typename T>
+size_t panel_cluster_smem(int rows, int nb, int cs) {
+  const int ch = (rows + cs - 1) / cs;
+  return ((size_t)ch * nb + 2 * nb + (size_t)cs * nb) * sizeof(T) + (size_t)ch * sizeof(int) + 16;
+}
+
+template <typename T>
+int panel_cluster_max() {
+  static const int mx = [] {
+    int dev = 0, smem_max = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_lu_panel_cluster<T>) != cudaSuccess ||
+        cudaFuncSetAttribute(k_lu_panel_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_max - (int)fa.sharedSizeBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_lu_panel_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    // the largest cluster that can be resident with a near-full shared memory per CTA
+    for (int cs = 16; cs >= 2; cs /= 2) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = (size_t)(smem_max - (int)fa.sharedSizeBytes);
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, (void*)k_lu_panel_cluster<T>, &cfg) == cudaSuccess && ncl > 0)
+        return cs;
+      cudaGetLastError();
+    }
+    return 0;
+  }();
+  return mx;
+}
+
+template <typename T>
+int panel_cluster_size(int rows, int nb) {
+  const int mx = panel_cluster_max<T>();
+  if (mx < 2 || nb > 64) return 0;
+  int smem_max = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int cs = 2;
+  while (cs < mx && (rows + cs - 1) / cs > 256) cs *= 2;
+  while (cs <= mx && panel_cluster_smem<T>(rows, nb, cs) + 8192 > (size_t)smem_max) cs *= 2;
+  return cs <= mx ? cs : 0;
+}
+
 // Apply the panel's interchanges to every column outside the panel and
 // solve U12 = L11^{-1} A12 for the columns in [k0 + nb, trsm_end).
 template <typename T>
@@ -777,6 +1002,15 @@ __global__ void k_ipiv_to_perm(const int* ipiv, int* perm, int n, int batch) {
     int p = ip[j];
     if (p != j) { int t = pm[j]; pm[j] = pm[p]; pm[p] = t; }
   }
+}
+
+#include "tuned.h"
+
+int& lu_tune(int param) {
+  static int v[TUNE_COUNT] = {HPS_TUNED_LU_BASE_PANELS_FEW, HPS_TUNED_LU_BASE_PANELS_MANY,
+                              HPS_TUNED_LU_FEW_MIN_N,       HPS_TUNED_LU_CLUSTER_PANEL,
+                              HPS_TUNED_TC_MIN_WORK_REAL,   HPS_TUNED_TC_MIN_WORK_CPLX};
+  return v[param];
 }
 
 template <typename T> struct LuNB;
@@ -849,11 +1083,28 @@ static cudaError_t lu_leaf(BOp<T> A, int n, int k0, int nb, int trsm_end, int ba
     pfl += below * (nb - jj - 1) + below;
   }
   pfl *= F * batch;
+  const int CS = (Gk > 1 && lu_tune(TUNE_LU_CLUSTER_PANEL)) ? panel_cluster_size<T>(rows, nb) : 0;
   if (pf) {
     pf->begin(st);
-    pf->note(rows, nb, Gk, batch);  // k: CTAs per matrix
+    pf->note(rows, nb, CS > 1 ? CS : Gk, batch);  // k: CTAs per matrix
   }
-  if (Gk > 1) {
+  if (CS > 1) {
+    // the panel in the distributed shared memory of a cluster per matrix
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(batch * CS);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = panel_cluster_smem<T>(rows, nb, CS);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_lu_panel_cluster<T>, A, n, k0, nb, ipiv, info);
+    if (e != cudaSuccess) return e;
+  } else if (Gk > 1) {
     T* pubv = reinterpret_cast<T*>(w.pub);
     double* pubm = reinterpret_cast<double*>(pubv + (size_t)batch * 2 * (G + 1) * nb0);
     int* pubr = reinterpret_cast<int*>(pubm + (size_t)batch * 2 * G);
@@ -946,9 +1197,16 @@ cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, u
   if (n <= 0 || batch <= 0) return cudaSuccess;
   cudaError_t e;
   // Few matrices: the recursion's triangular solves become many small
-  // launches on a few SMs, so the blocked right-looking order (one fused
-  // interchange + U12 launch per panel) is kept there.
-  const int base_w = batch < 8 ? n : 4 * LuNB<T>::NB;
+  // launches on a few SMs, so small orders keep the blocked right-looking
+  // order (one fused interchange + U12 launch per panel); large ones recurse
+  // so that the trailing updates are a few large-K products.
+  const int nbp = LuNB<T>::NB;
+  int base_w = lu_tune(TUNE_LU_BASE_PANELS_MANY) * nbp;
+  if (batch < 8) {
+    const int bp = lu_tune(TUNE_LU_BASE_PANELS_FEW);
+    base_w = (bp <= 0 || n < lu_tune(TUNE_LU_FEW_MIN_N)) ? n : bp * nbp;
+  }
+  if (base_w < nbp) base_w = nbp;
   if ((e = rgetrf<T>(A, n, 0, n, base_w, batch, ipiv, info, dev_err, G, w, st, pf)) != cudaSuccess) return e;
   if (pf) pf->begin(st);
   k_ipiv_to_perm<<<(batch + 127) / 128, 128, 0, st>>>(ipiv, perm, n, batch);

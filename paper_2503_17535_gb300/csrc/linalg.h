@@ -143,6 +143,20 @@ cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf);
 // G > 1 spreads each matrix over G co-resident CTAs (cooperative launch).
 // ipiv/perm are int arrays of `batch * n` (item stride n).  info[b] = first
 // zero-pivot column + 1 (0 if none).  dev_err receives DEV_ERR_* bits.
+// Shape choices of the batched LU, process-wide (hps_tune_set / hps_tune_get
+// expose them; the defaults are the values the autotuner measured best on
+// GB300, csrc/tuned.h).
+enum LuTuneParam {
+  TUNE_LU_BASE_PANELS_FEW = 0,   // recursion base width in panels, batches < 8 (0: blocked)
+  TUNE_LU_BASE_PANELS_MANY = 1,  // recursion base width in panels, batches >= 8
+  TUNE_LU_FEW_MIN_N = 2,         // batches < 8 recurse only from this order on
+  TUNE_LU_CLUSTER_PANEL = 3,     // 1: tall panels in a thread-block cluster, 0: cooperative groups
+  TUNE_TC_MIN_WORK_REAL = 4,     // real products go to the tensor cores from M N K batch >= this x 1e5
+  TUNE_TC_MIN_WORK_CPLX = 5,     // complex products: the same threshold
+  TUNE_COUNT = 6
+};
+int& lu_tune(int param);
+
 struct LuWork {
   unsigned* bars = nullptr;   // 2 * batch barrier words (zeroed)
   void* pub = nullptr;        // publish buffer for G > 1

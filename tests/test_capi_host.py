@@ -186,3 +186,26 @@ def test_debug_wait_timeout_rejects_bad_arguments(pkg):
     assert pkg.hps_debug_wait_timeout(-1, False, 1000, 0) == _capi.HPS_ERR_INVALID
     assert pkg.hps_debug_wait_timeout(0, False, 0, 0) == _capi.HPS_ERR_INVALID
     assert pkg.hps_debug_wait_timeout(0, False, (1 << 24) + 1, 0) == _capi.HPS_ERR_INVALID
+
+
+def test_tuning_table_round_trip(pkg, tmp_path):
+    """The batched LU's shape choices: compiled-in defaults equal the tuned
+    table, values can be set and read back, bad parameters are refused; the
+    autotuner's header writer emits every parameter."""
+    import re as _re
+    from paper_2503_17535_gb300 import _capi, autotune
+    hdr = open(os.path.join(os.path.dirname(_capi.LIB_PATH), "csrc", "tuned.h")).read()
+    table = {m: int(v) for m, v in _re.findall(r"#define (HPS_TUNED_\w+) (\d+)", hdr)}
+    for name, macro in autotune.MACROS.items():
+        assert pkg.hps_tune_get(name) == table[macro]
+    old = pkg.hps_tune_get("lu_base_panels_few")
+    pkg.hps_tune_set("lu_base_panels_few", 7)
+    assert pkg.hps_tune_get("lu_base_panels_few") == 7
+    pkg.hps_tune_set("lu_base_panels_few", old)
+    lib = _capi.lib()
+    assert lib.hps_tune_set(99, 1) == _capi.HPS_ERR_INVALID
+    assert lib.hps_tune_set(0, -1) == _capi.HPS_ERR_INVALID
+    out = tmp_path / "tuned.h"
+    autotune.write_header(str(out), {k: v[0] for k, v in autotune.CANDIDATES.items()}, {"w": 1.0})
+    got = dict(_re.findall(r"#define (HPS_TUNED_\w+) (\d+)", out.read_text()))
+    assert set(got) == set(autotune.MACROS.values())
