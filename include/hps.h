@@ -153,7 +153,21 @@ typedef struct {
                            workspace cannot be allocated runs on the FP64
                            pipe); 1: every product on the FP64 pipe.  Solves
                            always use the FP64 pipe. */
-  int reserved[1];
+  int recompute_budget_mb; /* > 0: device-memory budget (MiB) of the handle.  When the
+                           planned footprint of a uniform tree (hps_plan_bytes)
+                           exceeds it, the build keeps only the merges above the
+                           largest complete subtrees that fit (each subtree's
+                           root T and h, and device copies of the coefficients
+                           and the source) and every hps_solve rebuilds each
+                           subtree on its way down: Section 4.1, Algorithm
+                           "our_recomputation", on the device.  Solves with a
+                           new f also rebuild each subtree once per right-hand
+                           side for its root's h.  Such a handle supports
+                           hps_solve / hps_solve_batched only (not the adjoint,
+                           hps_coeff_gradient, hps_solve_multi or
+                           hps_solve_noalloc: HPS_ERR_INVALID); a singular pivot
+                           inside a subtree is reported without the node.  If
+                           no subtree depth fits, HPS_ERR_OOM.  0: off. */
 } hps_options;
 
 /* Kernel classes reported by hps_kernel_stats. */

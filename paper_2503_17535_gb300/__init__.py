@@ -177,7 +177,7 @@ def make_coeffs(kind: int, a=None, b=None, c=None, eta: float = 0.0, keep=None, 
 def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None, f=None,
               eta: float = 0.0, want_root_map: bool = False, profile: bool = False,
               lazy_root: bool = False, graph_solve: bool = False, iti_leaf: int = 0, fp64_gemm: bool = False,
-              stream=None) -> Handle:
+              recompute_budget_mb: int = 0, stream=None) -> Handle:
     """Build the solution operator; coefficient and source arrays hold
     n_leaves * p^dim values (leaf-major, tensor node order).  fp64_gemm=True
     keeps every product on the FP64 pipe (default: large products on the
@@ -195,6 +195,7 @@ def hps_build(tree: hps_tree, p: int, q: int, kind: int, a=None, b=None, c=None,
     opts.graph_solve = 1 if graph_solve else 0
     opts.iti_leaf = int(iti_leaf)
     opts.fp64_gemm = 1 if fp64_gemm else 0
+    opts.recompute_budget_mb = int(recompute_budget_mb)
     out = c_void_p()
     st = _stream(stream)
     _check(_capi.lib().hps_build(byref(tree), p, q, byref(cf), fp, byref(opts), st, byref(out)),

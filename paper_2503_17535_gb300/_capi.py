@@ -50,7 +50,7 @@ class hps_coeffs(ctypes.Structure):
 class hps_options(ctypes.Structure):
     _fields_ = [("version", c_int), ("want_root_map", c_int), ("profile", c_int),
                 ("lazy_root", c_int), ("graph_solve", c_int), ("iti_leaf", c_int), ("fp64_gemm", c_int),
-                ("reserved", c_int * 1)]
+                ("recompute_budget_mb", c_int)]
 
 
 class hps_kernel_stat(ctypes.Structure):

@@ -154,6 +154,22 @@ struct hps_handle {
   int64_t err_node = -1;
   int num_sms = 0;
   int device = -1;               // CUDA device the handle was built on
+  // Subtree recomputation (hps_options.recompute_budget_mb; paper Section
+  // 4.1, Algorithm "our_recomputation").  A composite handle (recompute)
+  // keeps only `top` -- a handle whose leaves are the roots of the complete
+  // subtrees of depth sub_depth (ext_depth > 0 there, their T and h in
+  // leafTH) -- and device copies of the coefficients and the build-time
+  // source; every solve rebuilds each subtree on its way down.
+  int ext_depth = 0;             // leaves of this handle: roots of subtrees of this depth
+  int n0 = 0;                    // Gauss points per side (2D) / face panel (3D) at the first merge; 0: q (q^2)
+  bool ext_newf = false;         // solve: the leaves' h for the new sources are already in ws_hleaf
+  bool recompute = false;
+  hps_handle* top = nullptr;
+  int sub_depth = 0;
+  const double* rc_coef[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // a, b[0..2], c
+  void* rc_f = nullptr;          // build-time source (null: f = 0)
+  void* rc_u = nullptr;          // one subtree's solutions for nrhs right-hand sides
+  int64_t rc_u_elems = 0;
   // captured solves (hps_options.graph_solve): key -> executable graph
   struct GraphEntry {
     int nrhs = 0;

@@ -50,7 +50,7 @@ size_t plan_bytes(const hps_handle* h, bool with_solve_ws) {
   b += (size_t)nl * h->nb * (h->nb + 1) * es;                // leaf T|h
   b += (size_t)nl * h->nlu_leaf * 3 * sizeof(int);
   size_t scratch = (size_t)nl * h->xrows_leaf * (h->nb + 1) * es;
-  int n = h->dim == 2 ? h->q : h->q * h->q;
+  int n = h->n0 > 0 ? h->n0 : (h->dim == 2 ? h->q : h->q * h->q);
   int64_t nm = nl;
   for (int m = 0; m < h->L; ++m) {
     nm /= (h->dim == 2 ? 4 : 8);
@@ -91,6 +91,14 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
     h->nb = h->iref.nb;
     h->nlu_leaf = h->iref.npts;
     h->xrows_leaf = h->iref.npts;
+  }
+  if (h->ext_depth > 0) {
+    // the leaves are subtree roots whose [T | h] the caller has put in leafTH
+    const int side = 1 << h->ext_depth;
+    h->nb = dim == 2 ? 4 * q * side : 6 * q * q * side * side;
+    h->n0 = dim == 2 ? q * side : q * q * side * side;
+    h->nlu_leaf = 0;
+    h->xrows_leaf = 0;
   }
   // footprint check before any large allocation
   {
@@ -165,25 +173,28 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
   // ---- leaf stage (Algorithm "local solve")
   const int64_t nl = h->nl;
   const int nlu = h->nlu_leaf, nb = h->nb, xr = h->xrows_leaf;
+  const bool ext = h->ext_depth > 0;
   bool elim = false;
-  if (ITI) {
+  if (ITI && !ext) {
     hps_status es = HPS_OK;
     elim = iti_elim_safe(h, co, st, &es);
     if (es != HPS_OK) return es;
   }
-  if (!elim) {
+  if (!elim && !ext) {
     h->leafA = dalloc(h, (size_t)nl * nlu * nlu * sizeof(T));
     h->leaf_ipiv = (int*)dalloc(h, (size_t)nl * nlu * sizeof(int));
     h->leaf_perm = (int*)dalloc(h, (size_t)nl * nlu * sizeof(int));
     if (!h->leafA || !h->leaf_ipiv || !h->leaf_perm) return HPS_ERR_OOM;
   }
-  h->leafX = dalloc(h, (size_t)nl * xr * (nb + 1) * sizeof(T));
-  h->leafTH = dalloc(h, (size_t)nl * nb * (nb + 1) * sizeof(T));
+  if (!ext) {
+    h->leafX = dalloc(h, (size_t)nl * xr * (nb + 1) * sizeof(T));
+    h->leafTH = dalloc(h, (size_t)nl * nb * (nb + 1) * sizeof(T));
+  }
   h->leaf_info = (int*)dalloc(h, (size_t)nl * sizeof(int));
   // scratch: largest R / RHS buffer of any stage
   size_t scratch = (size_t)nl * xr * (nb + 1);
   {
-    int n = dim == 2 ? q : q * q;
+    int n = h->n0 > 0 ? h->n0 : (dim == 2 ? q : q * q);
     int64_t nm = nl;
     for (int m = 0; m < h->L; ++m) {
       nm /= (dim == 2 ? 4 : 8);
@@ -192,12 +203,14 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
       n *= (dim == 2 ? 2 : 4);
     }
   }
-  h->scratch = dalloc(h, scratch * sizeof(T));
-  if (!h->leafX || !h->leafTH || !h->leaf_info || !h->scratch) return HPS_ERR_OOM;
+  h->scratch = dalloc(h, std::max<size_t>(scratch, 1) * sizeof(T));
+  if ((!ext && !h->leafX) || !h->leafTH || !h->leaf_info || !h->scratch) return HPS_ERR_OOM;
   HPS_CUDA(cudaMemsetAsync(h->leaf_info, 0, (size_t)nl * sizeof(int), st));
   T* RHS = (T*)h->scratch;
   BOp<T> LX = bop<T>((T*)h->leafX, (int64_t)xr * (nb + 1), xr);
-  if (elim) {
+  if (ext) {
+    // nothing to do at the leaves
+  } else if (elim) {
     // ItI by elimination of the interior nodes: X = B^{-1} [[P, 0], [0, f_i]]
     HPS_TRY(iti_elim_setup(h, co, st, pf));
     HPS_CUDA(leaf_iti_rhs(k, nl, (const cplx*)f, (cplx*)RHS, st, pf));
@@ -207,7 +220,7 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
   } else {
     HPS_CUDA(leaf_iti_assemble(k, nl, co, (const cplx*)f, (cplx*)h->leafA, (cplx*)RHS, st, pf));
   }
-  if (!elim) {
+  if (!elim && !ext) {
     h->leaf_G = lu_group_size<T>(nlu, (int)std::min<int64_t>(nl, 1 << 30), h->num_sms);
     if (h->leaf_G > 1) {
       h->leaf_luw.bars = (unsigned*)dalloc(h, sizeof(unsigned) * 2 * nl);
@@ -222,7 +235,7 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
     HPS_CUDA(permute_rows<T>(bop<T>(RHS, (int64_t)xr * (nb + 1), xr), LX, h->leaf_perm, nlu, nb + 1, (int)nl, st, pf));
     HPS_CUDA(getrs_inplace<T>(LA, nlu, LX, nb + 1, (int)nl, st, pf));
   }
-  {
+  if (!ext) {
     GemmArgs<T> g;
     g.M = nb; g.N = nb + 1; g.batch = (int)nl;
     g.B = LX;
@@ -243,7 +256,7 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
   }
 
   // ---- merge stage (Algorithm "merge"), level by level
-  int n = dim == 2 ? q : q * q;
+  int n = h->n0 > 0 ? h->n0 : (dim == 2 ? q : q * q);
   int64_t nm = nl;
   const T* Tc = (const T*)h->leafTH;
   int64_t cstride = (int64_t)nb * (nb + 1);
@@ -541,12 +554,13 @@ hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_i
     HPS_CUDA(cudaMemcpyAsync(h->ws_f, f_in, (size_t)nl * h->npts * nrhs * sizeof(T), cudaMemcpyHostToDevice, st));
     f = (const T*)h->ws_f;
   }
-  const bool host_u = !h->capturing && !is_device_ptr(u_out);
+  const bool ext = h->ext_depth > 0;  // leaves are subtree roots: no leaf solves, no leaf output
+  const bool host_u = !ext && !h->capturing && !is_device_ptr(u_out);
   T* u = host_u ? (T*)h->ws_u : (T*)u_out;
-  const bool newf = (f != nullptr);
+  const bool newf = (f != nullptr) || (ext && h->ext_newf);
 
   // ---- upward particular pass (new f): leaf and merge triangular solves
-  if (newf) {
+  if (newf && !ext) {
     T* xf = (T*)h->ws_xf;
     T* tmp = (T*)h->ws_rhs;
     HPS_CUDA(leaf_particular_rhs<T>(h->lc, nl, nrhs, f, tmp, ITI, st, pf));
@@ -566,6 +580,9 @@ hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_i
     gl.alpha = ITI ? T(1.0) : T(-h->s);
     gl.beta = T(0.0);
     HPS_CUDA(gemm<T>(gl, st, pf));
+  }
+  if (newf) {
+    // leaves' h (for subtree roots: put in ws_hleaf by the caller)
     const T* hc = (const T*)h->ws_hleaf;
     for (int m = 0; m < h->L; ++m) {
       LevelDev& Lv = h->lev[m];
@@ -616,7 +633,8 @@ hps_status solve_impl(hps_handle* h, int nrhs, const void* g_in, const void* f_i
     }
     gpar = gchild;
   }
-  // leaf output u = Y g + v
+  // leaf output u = Y g + v (subtree roots: their g stays in ws_gleaf)
+  if (ext) return HPS_OK;
   HPS_CUDA(leaf_output<T>(h->lc, nl, nrhs, (const T*)h->leafX, newf ? (const T*)h->ws_xf : nullptr, gpar, u,
                           ITI, st, pf));
   if (host_u) {
@@ -709,6 +727,265 @@ hps_status solve_multi_impl(const std::vector<int>& idx, hps_handle* const* hs, 
   return HPS_OK;
 }
 
+// ------------------------------------------------ subtree recomputation ----
+
+void handle_begin(hps_handle* h, cudaStream_t st);
+void handle_end(hps_handle* h, cudaStream_t st);
+//
+// Paper Section 4.1, Algorithm "our_recomputation", on the device only: the
+// tree below level L - d is cut into its complete subtrees of depth d (the
+// largest d whose peak footprint fits the budget, as the paper picks the
+// largest subtrees that fit).  The build runs each subtree's leaf stage and
+// merges to its root, keeps only the root's T and h, and releases the rest;
+// the merges above the subtree roots are kept as usual.  A solve runs the
+// upward pass above the roots (new sources: each subtree is rebuilt with the
+// new source to get its root's h), the downward pass to the roots, then
+// rebuilds each subtree and runs its own downward pass and leaf output.  A
+// subtree's leaves are a contiguous range of leaves (Morton order), so its
+// coefficients, sources and solutions are slices of the caller's arrays.
+
+namespace {
+
+int64_t uniform_plan(int dim, int depth, int p, int q, bool iti, int ext_depth, bool with_ws) {
+  hps_handle t;
+  t.dim = dim; t.p = p; t.q = q; t.L = depth; t.iti = iti;
+  t.nl = (int64_t)1 << (dim * depth);
+  t.npts = dim == 2 ? (int64_t)p * p : (int64_t)p * p * p;
+  const int64_t ni = dim == 2 ? (int64_t)(p - 2) * (p - 2) : (int64_t)(p - 2) * (p - 2) * (p - 2);
+  t.nb = dim == 2 ? 4 * q : 6 * q * q;
+  t.nlu_leaf = (int)(iti ? t.npts : ni);
+  t.xrows_leaf = t.nlu_leaf;
+  if (ext_depth > 0) {
+    const int side = 1 << ext_depth;
+    t.nb = dim == 2 ? 4 * q * side : 6 * q * q * side * side;
+    t.n0 = dim == 2 ? q * side : q * q * side * side;
+    t.nlu_leaf = 0;
+    t.xrows_leaf = 0;
+  }
+  return (int64_t)(iti ? plan_bytes<cplx>(&t, with_ws) : plan_bytes<double>(&t, with_ws));
+}
+
+// Peak device bytes of a recomputing handle with subtrees of depth d: the
+// kept merges and subtree roots, the input copies, and one subtree built.
+int64_t recompute_peak(int dim, int L, int p, int q, bool iti, int d, int64_t copies) {
+  return uniform_plan(dim, L - d, p, q, iti, d, true) + uniform_plan(dim, d, p, q, iti, 0, true) + copies;
+}
+
+hps_tree subtree_of(const hps_handle* C, int64_t s, int d) {
+  const int dim = C->dim, Ls = C->L - d;
+  int64_t ix[3] = {0, 0, 0};
+  for (int l = 0; l < Ls; ++l) {
+    const int64_t c = (s >> (dim * (Ls - 1 - l))) & ((1 << dim) - 1);
+    for (int a = 0; a < dim; ++a) ix[a] = 2 * ix[a] + ((c >> a) & 1);
+  }
+  hps_tree t{};
+  t.dim = dim;
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      const double side = (C->hi[a] - C->lo[a]) / (double)((int64_t)1 << Ls);
+      t.lo[a] = C->lo[a] + (double)ix[a] * side;
+      t.hi[a] = t.lo[a] + side;
+    } else {
+      t.lo[a] = t.hi[a] = 0.0;
+    }
+  }
+  t.uniform_depth = d;
+  t.n_leaves = (int64_t)1 << (dim * d);
+  t.morton = nullptr;
+  t.level = nullptr;
+  return t;
+}
+
+// Build subtree s (depth d) with the stored coefficients and source `f`
+// (a full-tree array, or null); root_map asks for the root's T and h.
+template <typename T>
+hps_status build_subtree(hps_handle* C, int64_t s, const T* f, bool root_map, cudaStream_t st, hps_handle** out) {
+  const int d = C->sub_depth;
+  const int64_t lps = (int64_t)1 << (C->dim * d);
+  const int64_t off = s * lps * C->npts;
+  hps_tree t = subtree_of(C, s, d);
+  hps_coeffs cf{};
+  cf.kind = C->kind;
+  cf.dtype = C->iti ? HPS_C128 : HPS_F64;
+  cf.eta = C->eta;
+  cf.a = C->rc_coef[0] ? C->rc_coef[0] + off : nullptr;
+  for (int a = 0; a < 3; ++a) cf.b[a] = C->rc_coef[1 + a] ? C->rc_coef[1 + a] + off : nullptr;
+  cf.c = C->rc_coef[4] ? C->rc_coef[4] + off : nullptr;
+  hps_options o{};
+  o.version = 1;
+  o.want_root_map = root_map ? 1 : 0;
+  o.iti_leaf = C->opts.iti_leaf;
+  o.fp64_gemm = C->opts.fp64_gemm;
+  return hps_build(&t, C->p, C->q, &cf, f ? (const void*)(f + off) : nullptr, &o, st, out);
+}
+
+template <typename T>
+hps_status recompute_build(hps_handle* C, const hps_coeffs* cf, const void* f_in, int d, cudaStream_t st) {
+  const int dim = C->dim;
+  const int64_t n = C->nl * C->npts;
+  C->recompute = true;
+  C->sub_depth = d;
+  // device copies of the inputs: the caller may release theirs after the build
+  const double* src[5] = {cf->a, cf->b[0], cf->b[1], cf->b[2], cf->c};
+  for (int i = 0; i < 5; ++i) {
+    if (!src[i] || (i >= 1 && i <= 3 && i - 1 >= dim)) continue;
+    double* dcp = (double*)dalloc(C, (size_t)n * sizeof(double));
+    if (!dcp) return HPS_ERR_OOM;
+    HPS_CUDA(cudaMemcpyAsync(dcp, src[i], (size_t)n * sizeof(double), cudaMemcpyDefault, st));
+    C->rc_coef[i] = dcp;
+  }
+  if (f_in) {
+    C->rc_f = dalloc(C, (size_t)n * sizeof(T));
+    if (!C->rc_f) return HPS_ERR_OOM;
+    HPS_CUDA(cudaMemcpyAsync(C->rc_f, f_in, (size_t)n * sizeof(T), cudaMemcpyDefault, st));
+  }
+  // the handle above the subtree roots
+  hps_handle* Tp = new (std::nothrow) hps_handle();
+  if (!Tp) return HPS_ERR_OOM;
+  C->top = Tp;
+  Tp->dim = dim; Tp->kind = C->kind; Tp->p = C->p; Tp->q = C->q; Tp->iti = C->iti;
+  Tp->L = C->L - d;
+  Tp->nl = (int64_t)1 << (dim * Tp->L);
+  Tp->npts = C->npts;
+  Tp->nroot = C->nroot;
+  for (int a = 0; a < 3; ++a) { Tp->lo[a] = C->lo[a]; Tp->hi[a] = C->hi[a]; }
+  Tp->hlen = C->hlen;
+  Tp->eta = C->eta;
+  Tp->opts = C->opts;
+  Tp->num_sms = C->num_sms;
+  Tp->device = C->device;
+  Tp->last = st;
+  Tp->ext_depth = d;
+  if (cudaEventCreateWithFlags(&Tp->done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return HPS_ERR_CUDA;
+  }
+  const int side = 1 << d;
+  const int nbs = dim == 2 ? 4 * C->q * side : 6 * C->q * C->q * side * side;
+  Tp->leafTH = dalloc(Tp, (size_t)Tp->nl * nbs * (nbs + 1) * sizeof(T));
+  if (!Tp->leafTH) return HPS_ERR_OOM;
+  // each subtree: leaf stage and merges to its root, keep the root's [T | h]
+  for (int64_t s = 0; s < Tp->nl; ++s) {
+    hps_handle* Hs = nullptr;
+    HPS_TRY(build_subtree<T>(C, s, (const T*)C->rc_f, true, st, &Hs));
+    const LevelDev& R = Hs->lev[d - 1];
+    const bool ok = R.n_ext == nbs && R.nmerge == 1 && R.TP;
+    cudaError_t e = ok ? cudaMemcpyAsync((T*)Tp->leafTH + s * (int64_t)nbs * (nbs + 1), R.TP,
+                                         (size_t)nbs * (nbs + 1) * sizeof(T), cudaMemcpyDeviceToDevice, st)
+                       : cudaSuccess;
+    handle_end(Hs, st);
+    hps_free(Hs);
+    if (!ok) return HPS_ERR_INVALID;
+    HPS_CUDA(e);
+  }
+  // the merges above the roots
+  Tp->tcw.st = st;
+  Tp->tcw.err_slot = &Tp->dev_err;
+  Tp->tcw.enabled = C->opts.fp64_gemm == 0;
+  hps_status s;
+  {
+    hps::TcScope tc_scope(&Tp->tcw);
+    s = build_impl<T>(Tp, cf, nullptr, st);
+  }
+  if (Tp->tcw.p) {
+    cudaStreamSynchronize(st);
+    hps::tc_release(&Tp->tcw);
+  }
+  handle_end(Tp, st);
+  if (s == HPS_ERR_SINGULAR) C->err_node = -1;
+  return s;
+}
+
+template <typename T>
+hps_status recompute_solve(hps_handle* C, int nrhs, const void* g_in, const void* f_in, void* u_out,
+                           cudaStream_t st) {
+  hps_handle* Tp = C->top;
+  const int d = C->sub_depth;
+  const int64_t lps = (int64_t)1 << (C->dim * d);
+  const int64_t nsub = Tp->nl, npts = C->npts, nl = C->nl;
+  const int nbs = Tp->nb;
+  const size_t es = sizeof(T);
+  // stage host buffers in the composite handle's own workspace
+  const size_t gbytes = (size_t)C->nroot * nrhs * es, ubytes = (size_t)nl * npts * nrhs * es;
+  if (C->ws_nrhs < nrhs) {
+    for (void* pp : C->ws_allocs) dev_free(pp, st);
+    C->ws_allocs.clear();
+    C->ws_g = dalloc(C, gbytes, &C->ws_allocs);
+    C->ws_f = dalloc(C, ubytes, &C->ws_allocs);
+    C->ws_u = dalloc(C, ubytes, &C->ws_allocs);
+    C->rc_u = dalloc(C, (size_t)lps * npts * nrhs * es, &C->ws_allocs);
+    if (!C->ws_g || !C->ws_f || !C->ws_u || !C->rc_u) return HPS_ERR_OOM;
+    C->ws_nrhs = nrhs;
+  }
+  const T* g = (const T*)g_in;
+  if (!is_device_ptr(g_in)) {
+    HPS_CUDA(cudaMemcpyAsync(C->ws_g, g_in, gbytes, cudaMemcpyHostToDevice, st));
+    g = (const T*)C->ws_g;
+  }
+  const T* f = (const T*)f_in;
+  if (f_in && !is_device_ptr(f_in)) {
+    HPS_CUDA(cudaMemcpyAsync(C->ws_f, f_in, ubytes, cudaMemcpyHostToDevice, st));
+    f = (const T*)C->ws_f;
+  }
+  const bool host_u = !is_device_ptr(u_out);
+  T* u = host_u ? (T*)C->ws_u : (T*)u_out;
+  handle_begin(Tp, st);
+  HPS_TRY(ensure_ws<T>(Tp, nrhs));
+  // new sources: each subtree rebuilt with the column's source gives its root's h
+  if (f) {
+    for (int64_t s = 0; s < nsub; ++s)
+      for (int c = 0; c < nrhs; ++c) {
+        hps_handle* Hs = nullptr;
+        HPS_TRY(build_subtree<T>(C, s, f + (int64_t)c * nl * npts, true, st, &Hs));
+        const LevelDev& R = Hs->lev[d - 1];
+        cudaError_t e = cudaMemcpyAsync((T*)Tp->ws_hleaf + (s * nrhs + c) * (int64_t)nbs,
+                                        (const T*)R.TP + (int64_t)nbs * nbs, (size_t)nbs * es,
+                                        cudaMemcpyDeviceToDevice, st);
+        handle_end(Hs, st);
+        hps_free(Hs);
+        HPS_CUDA(e);
+      }
+  }
+  // upward pass above the roots (new sources), downward pass to the roots
+  Tp->ext_newf = f != nullptr;
+  hps_status rs = solve_impl<T>(Tp, nrhs, g, nullptr, Tp->ws_gleaf, st);
+  Tp->ext_newf = false;
+  handle_end(Tp, st);
+  HPS_TRY(rs);
+  // each subtree again: its downward pass and leaf output
+  for (int64_t s = 0; s < nsub; ++s) {
+    const T* gs = (const T*)Tp->ws_gleaf + s * (int64_t)nbs * nrhs;  // [nrhs][nbs]
+    if (!f) {
+      hps_handle* Hs = nullptr;
+      HPS_TRY(build_subtree<T>(C, s, (const T*)C->rc_f, false, st, &Hs));
+      hps_status ss = hps_solve_batched(Hs, nrhs, gs, nullptr, C->rc_u, st);
+      cudaError_t e = cudaSuccess;
+      if (ss == HPS_OK)
+        e = cudaMemcpy2DAsync(u + s * lps * npts, (size_t)nl * npts * es, C->rc_u, (size_t)lps * npts * es,
+                              (size_t)lps * npts * es, nrhs, cudaMemcpyDeviceToDevice, st);
+      handle_end(Hs, st);
+      hps_free(Hs);
+      HPS_TRY(ss);
+      HPS_CUDA(e);
+    } else {
+      for (int c = 0; c < nrhs; ++c) {
+        hps_handle* Hs = nullptr;
+        HPS_TRY(build_subtree<T>(C, s, f + (int64_t)c * nl * npts, false, st, &Hs));
+        hps_status ss = hps_solve(Hs, gs + (int64_t)c * nbs, nullptr, u + (int64_t)c * nl * npts + s * lps * npts, st);
+        hps_free(Hs);
+        HPS_TRY(ss);
+      }
+    }
+  }
+  if (host_u) {
+    HPS_CUDA(cudaMemcpyAsync(u_out, u, ubytes, cudaMemcpyDeviceToHost, st));
+    HPS_CUDA(cudaStreamSynchronize(st));
+  }
+  return HPS_OK;
+}
+
+}  // namespace
+
 thread_local int64_t g_last_err_node = -1;
 
 void drop_graphs(hps_handle* h) {
@@ -722,6 +999,7 @@ void drop_graphs(hps_handle* h) {
 void free_handle(hps_handle* h) {
   if (!h) return;
   if (h->done && h->done_recorded) cudaEventSynchronize(h->done);
+  if (h->top) free_handle(h->top);
   drop_graphs(h);
   for (void* p : h->ws_allocs) dev_free_idle(p);
   for (void* p : h->allocs) dev_free_idle(p);
@@ -958,9 +1236,27 @@ hps_status hps_build(const hps_tree* tree, int p, int q, const hps_coeffs* coeff
   h->tcw.st = st;
   h->tcw.err_slot = &h->dev_err;
   h->tcw.enabled = h->opts.fp64_gemm == 0;
+  // subtree recomputation when the planned footprint exceeds the budget
+  int rc_depth = 0;
+  if (!h->adaptive && h->opts.recompute_budget_mb > 0 && h->L >= 2) {
+    const int64_t budget = (int64_t)h->opts.recompute_budget_mb << 20;
+    if (uniform_plan(h->dim, h->L, p, q, h->iti, 0, true) > budget) {
+      const int64_t n = h->nl * h->npts;
+      const int64_t copies = (int64_t)(h->dim + 2) * n * 8 + (f ? n * (h->iti ? 16 : 8) : 0);
+      for (int d = h->L - 1; d >= 1 && !rc_depth; --d)
+        if (recompute_peak(h->dim, h->L, p, q, h->iti, d, copies) <= budget) rc_depth = d;
+      if (!rc_depth) {
+        handle_end(h, st);
+        free_handle(h);
+        return HPS_ERR_OOM;
+      }
+    }
+  }
   try {
     hps::TcScope tc_scope(&h->tcw);
     if (h->adaptive) s = adaptive_build(h, tree, coeffs, f, st);
+    else if (rc_depth)
+      s = h->iti ? recompute_build<cplx>(h, coeffs, f, rc_depth, st) : recompute_build<double>(h, coeffs, f, rc_depth, st);
     else s = h->iti ? build_impl<cplx>(h, coeffs, f, st) : build_impl<double>(h, coeffs, f, st);
   } catch (...) {
     s = HPS_ERR_INVALID;
@@ -996,7 +1292,9 @@ hps_status hps_solve_batched(hps_handle* h, int nrhs, const void* g, const void*
   handle_begin(h, st);
   hps_status s;
   try {
-    if (h->adaptive) s = adaptive_solve(h, nrhs, g, f, u, st);
+    if (h->recompute)
+      s = h->iti ? recompute_solve<cplx>(h, nrhs, g, f, u, st) : recompute_solve<double>(h, nrhs, g, f, u, st);
+    else if (h->adaptive) s = adaptive_solve(h, nrhs, g, f, u, st);
     else if (h->opts.graph_solve && !h->opts.profile && st && is_device_ptr(g) && is_device_ptr(u) &&
              (!f || is_device_ptr(f)))
       s = graph_solve(h, nrhs, g, f, u, st);
@@ -1020,7 +1318,8 @@ hps_status hps_solve_multi(int n, hps_handle* const* hs, const int* nrhs, const 
   std::vector<int> real_idx, cplx_idx;
   for (int i = 0; i < n; ++i) {
     hps_handle* h = hs[i];
-    if (!h || h->adaptive || nrhs[i] < 1 || !g[i] || !u[i] || h->device != dev) return HPS_ERR_INVALID;
+    if (!h || h->adaptive || h->recompute || nrhs[i] < 1 || !g[i] || !u[i] || h->device != dev)
+      return HPS_ERR_INVALID;
     for (int j = 0; j < i; ++j)
       if (hs[j] == h) return HPS_ERR_INVALID;
     if (!is_device_ptr(g[i]) || !is_device_ptr(u[i])) return HPS_ERR_INVALID;
@@ -1045,7 +1344,7 @@ hps_status hps_solve(hps_handle* h, const void* g, const void* f, void* u, struc
 
 hps_status hps_solve_adjoint(hps_handle* h, int nrhs, const void* ubar, void* gbar, void* fbar,
                              struct CUstream_st* stream) {
-  if (!h || !ubar || nrhs < 1 || h->adaptive) return HPS_ERR_INVALID;
+  if (!h || !ubar || nrhs < 1 || h->adaptive || h->recompute) return HPS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   handle_begin(h, st);
   hps_status s;
@@ -1141,7 +1440,7 @@ hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double 
 
 hps_status hps_coeff_gradient(hps_handle* h, int nrhs, const void* u, const void* fbar, double* ga, double* gb,
                               double* gc, struct CUstream_st* stream) {
-  if (!h || !u || !fbar || nrhs < 1 || h->adaptive) return HPS_ERR_INVALID;
+  if (!h || !u || !fbar || nrhs < 1 || h->adaptive || h->recompute) return HPS_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   handle_begin(h, st);
   const hps_status s = coeff_gradient(h, nrhs, u, fbar, ga, gb, gc, st);
@@ -1157,7 +1456,7 @@ hps_status hps_last_error_detail(hps_handle* h, int64_t* node) {
   return HPS_OK;
 }
 
-int64_t hps_device_bytes(const hps_handle* h) { return h ? h->bytes : 0; }
+int64_t hps_device_bytes(const hps_handle* h) { return h ? h->bytes + (h->top ? h->top->bytes : 0) : 0; }
 
 hps_status hps_plan_bytes(const hps_tree* tree, int p, int q, int kind, int64_t* bytes) {
   if (!bytes) return HPS_ERR_INVALID;
@@ -1301,7 +1600,8 @@ hps_status solve_noalloc_impl(hps_handle* h, int dev, const T* g, T* u, cudaStre
 }  // namespace
 
 extern "C" hps_status hps_solve_noalloc(hps_handle* h, const void* g, void* u, struct CUstream_st* stream) {
-  if (!h || !g || !u || h->adaptive || (h->L > 0 && h->lev[h->L - 1].lazy)) return HPS_ERR_INVALID;
+  if (!h || !g || !u || h->adaptive || h->recompute || (h->L > 0 && h->lev[h->L - 1].lazy))
+    return HPS_ERR_INVALID;
   // the handle, g and u must all live on the current device: a kernel given
   // pointers of another device would fault
   int dev = -1;
