@@ -63,17 +63,15 @@ def tensor_peak():
 WORKLOADS = {
     "helmholtz2d": {"workload": "helmholtz2d_iti_c128_depth6_p16", "equation": "Lap u + k^2 (1 - n(x)) u = f",
                     "dim": 2, "kind": "iti", "n_leaves": 4096, "depth": 6, "p": 16, "q": 14, "k": 20.0,
-                    "eta": 20.0, "seed_problem": 1, "cpu_depth": 3},
+                    "eta": 20.0, "seed_problem": 1},
     "poisson2d": {"workload": "poisson2d_dtn_f64_depth2_p8", "equation": "Lap u = f, Dirichlet",
-                  "dim": 2, "kind": "dtn", "n_leaves": 16, "depth": 2, "p": 8, "q": 6, "seed_problem": 0,
-                  "cpu_depth": 2},
+                  "dim": 2, "kind": "dtn", "n_leaves": 16, "depth": 2, "p": 8, "q": 6, "seed_problem": 0},
     "elliptic3d": {"workload": "elliptic3d_dtn_f64_depth3_p8", "equation": "div(a grad u) + c u = f",
-                   "dim": 3, "kind": "dtn", "n_leaves": 512, "depth": 3, "p": 8, "q": 6, "seed_problem": 2,
-                   "cpu_depth": 2},
+                   "dim": 3, "kind": "dtn", "n_leaves": 512, "depth": 3, "p": 8, "q": 6, "seed_problem": 2},
     "adaptive3d": {"workload": "adaptive3d_dtn_f64_p8_eps1e-4_depths2-5",
                    "equation": "div(a grad u) + c u = f, sharp source", "dim": 3, "kind": "dtn",
                    "depth": -1, "p": 8, "q": 6, "seed_problem": 3, "eps": 1e-4, "min_depth": 2,
-                   "max_depth": 5, "cpu_depth": None},
+                   "max_depth": 5},
 }
 # Serving workload: seeded operators (kind, depth, p drawn as listed) resident
 # in a request server; a Poisson stream of requests, 80 % solves with a new
@@ -104,6 +102,12 @@ def parse():
                     help="write the per-launch trace of the profiled step (JSON) to this path")
     ap.add_argument("--depth", type=int, default=None,
                     help="uniform tree depth override (smaller cases for profiler captures)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg of the default line")
+    ap.add_argument("--oracle-threads", type=int, default=8,
+                    help="BLAS threads of the oracle timings (OpenBLAS on many small matrices is slower "
+                         "with one thread per core)")
+    ap.add_argument("--oracle-sample", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-reps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--gemm", default="tc", choices=["tc", "fp64"],
                     help="tc: large build products on the tensor cores as exact digit-slice products "
                          "(default); fp64: every product on the FP64 pipe (hps_options.fp64_gemm)")
@@ -126,7 +130,6 @@ def parse():
         spec["n_leaves"] = (4 if spec["dim"] == 2 else 8) ** args.depth
         spec["workload"] = spec["workload"].replace(f"depth{WORKLOADS[args.workload]['depth']}",
                                                     f"depth{args.depth}")
-        spec["cpu_depth"] = min(spec["cpu_depth"], args.depth)
     spec["root"] = args.root
     spec["gemm"] = args.gemm
     if args.gemm == "fp64":
@@ -374,16 +377,6 @@ def run_ours(args, rank, world):
                    "exec_flops": sb[k]["exec_flops"] + ss[k]["exec_flops"],
                    "ms": sb[k]["ms"] + ss[k]["ms"]} for k in sb}
     flops_step = sum(v["flops"] for v in classes.values())
-    # algorithmic flops of the CPU-baseline sample (same problem, smaller depth)
-    sample_ratio = 1.0
-    if spec["cpu_depth"] is not None and spec["cpu_depth"] != spec["depth"]:
-        inp_s = host_inputs(P, spec, seed_offset=rank, depth=spec["cpu_depth"])
-        hs_ = _build(P, spec, inp_s, inp_s["coef"], inp_s["f"])
-        fl_s = sum(v["flops"] for v in P.hps_kernel_stats(hs_).values())
-        P.hps_solve(hs_, inp_s["g"], np.zeros((inp_s["nl"], inp_s["ppl"]), inp_s["f"].dtype), f=inp_s["f2"])
-        fl_s += sum(v["flops"] for v in P.hps_kernel_stats(hs_).values())
-        P.hps_free(hs_)
-        sample_ratio = flops_step / fl_s
     dom = max(classes, key=lambda k: classes[k]["ms"])
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     peak_tf = FP64_FLOP_PER_CLK_SM * 152 * sm_mhz * 1e6 / 1e12
@@ -436,7 +429,7 @@ def run_ours(args, rank, world):
     return {"value": value, "total_ms": total_ms, "per": per, "clocks": clocks, "roofline": roofline,
             "fp64_peak": peak_tf,
             "classes": classes, "flops_step": flops_step, "launches": launches[0] // max(args.steps, 1),
-            "e2e": e2e, "sample_ratio": sample_ratio, "n_leaves": nl, "phases": phases}
+            "e2e": e2e, "n_leaves": nl, "phases": phases}
 
 
 # ------------------------------------------------------------- CPU oracle --
@@ -472,75 +465,84 @@ def oracle_sample_step(spec, depth=None):
     return time.perf_counter() - t0
 
 
-def flop_ratio(spec):
-    """Algorithmic flops of the workload over those of its CPU sample, used
-    by the reference arm (which runs no GPU code).  Helmholtz: a closed-form
-    count of the leaf stage (LU of B, solves, T = QH Y) and of the ItI merges
-    (W, its LU, the W^{-1} and D21 solves, B X), within a few percent of the
-    library's own counts.  Other workloads: their samples are the full
-    problem, or for the uniform 3D problem the leaf-count ratio."""
-    if not spec["workload"].startswith("helmholtz"):
-        if spec["cpu_depth"] is None or spec["cpu_depth"] == spec["depth"]:
-            return 1.0
-        b = 4 if spec["dim"] == 2 else 8
-        return float(b ** (spec["depth"] - spec["cpu_depth"]))
-
-    def flops(depth):
-        p, q = spec["p"], spec["q"]
-        npts, nb = p * p, 4 * q
-        nl = 4 ** depth
-        leaf = nl * 8 * (npts ** 3 / 3 + npts ** 2 * (nb + 1) + nb * npts * (nb + 1))
-        merge = 0.0
-        n = q
-        for m in range(depth):
-            nm = 4 ** (depth - m - 1)
-            hn, ne = 4 * n, 8 * n
-            per = (hn ** 3 + hn * hn * (ne + 1) + hn ** 3 / 3 + hn * hn * (ne + 1)
-                   + hn * hn * (ne + 1) + (0 if m == depth - 1 else 4 * (2 * n) * (2 * n) * (ne + 1)))
-            merge += nm * 8 * per
-            n *= 2
-        return leaf + merge
-    return flops(spec["depth"]) / flops(spec["cpu_depth"])
+def oracle_times(args, depth, threads, reps=1):
+    """Wall times (s) of `reps` oracle build + new-source solves at `depth`,
+    run in a child process whose BLAS uses `threads` threads (the thread
+    count must be set before NumPy loads)."""
+    env = dict(os.environ)
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = str(threads)
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", args.workload, "--oracle-sample",
+           str(-1 if depth is None else depth), "--oracle-reps", str(reps)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])["seconds"]
 
 
-def cpu_baseline(spec, ratio, reps=1):
-    ts = [oracle_sample_step(spec, spec["cpu_depth"]) for _ in range(reps)]
-    t = min(ts)
-    if spec["depth"] < 0:
-        what = "the full adaptive problem (same refined tree)"
-    elif spec["cpu_depth"] == spec["depth"]:
-        what = f"the full problem (depth {spec['depth']})"
-    else:
-        what = (f"the same problem at depth {spec['cpu_depth']}, scaled to depth {spec['depth']} by the "
-                f"algorithmic flop ratio {ratio:.1f} (library counts)")
-    return {"value": round(1.0 / (t * ratio), 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"oracle (NumPy/SciPy LAPACK) build + new-source solve of {what}: {t:.2f} s",
-            "blas_threads_env": os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
-            or "default (all cores)"}
+def run_oracle_sample(args):
+    spec = args.spec
+    depth = None if args.oracle_sample < 0 else args.oracle_sample
+    ts = [oracle_sample_step(spec, depth) for _ in range(args.oracle_reps)]
+    print(json.dumps({"seconds": ts}), flush=True)
+    return 0
+
+
+def sample_depth(spec):
+    """Depth of the per-step oracle sample of the reference arm: one below
+    the workload's (a step of a few seconds), the full problem when that is
+    already small or adaptive."""
+    if spec["depth"] < 0 or spec["depth"] <= 3:
+        return None
+    return spec["depth"] - 1
+
+
+def cpu_baseline(args, spec):
+    """The oracle on the host: the full problem once with --oracle-threads
+    BLAS threads (the line's value, no scaling), and one single-threaded run
+    of the one-level-smaller problem."""
+    th = max(1, min(args.oracle_threads, os.cpu_count() or 1))
+    t_full = min(oracle_times(args, None, th))
+    out = {"value": round(1.0 / t_full, 6), "unit": UNIT, "cores": th, "kind": "oracle",
+           "sample": (f"oracle (NumPy/SciPy LAPACK) build + new-source solve of the full problem "
+                      f"({'depth ' + str(spec['depth']) if spec['depth'] >= 0 else 'the same refined tree'}): "
+                      f"{t_full:.2f} s with {th} BLAS threads (OPENBLAS_NUM_THREADS={th}; host has "
+                      f"{os.cpu_count()} cores)")}
+    sd = sample_depth(spec)
+    if sd is not None:
+        t1 = min(oracle_times(args, sd, 1))
+        out["single_thread"] = {"depth": sd, "seconds": round(t1, 3), "solves_per_s": round(1.0 / t1, 6),
+                                "blas_threads": 1}
+    return out
 
 
 def run_reference(args, rank):
+    """The oracle as the reference arm: each step one oracle build +
+    new-source solve of the one-level-smaller problem (a few seconds), scaled
+    to the full problem by the ratio of one full-size run to the mean of
+    those samples, all with --oracle-threads BLAS threads."""
     if rank != 0:
         return None
     spec = args.spec
-    for _ in range(args.warmup):
-        oracle_sample_step(spec, spec["cpu_depth"])
-    ratio = flop_ratio(spec)
-    ts = [oracle_sample_step(spec, spec["cpu_depth"]) for _ in range(args.steps)]
+    th = max(1, min(args.oracle_threads, os.cpu_count() or 1))
+    sd = sample_depth(spec)
+    ts = oracle_times(args, sd, th, reps=args.warmup + args.steps)[args.warmup:]
+    ratio, t_full = 1.0, None
+    if sd is not None:
+        t_full = min(oracle_times(args, None, th))
+        ratio = t_full / statistics.mean(ts)
     scaled = [t * ratio for t in ts]
     value = args.steps / sum(scaled)
-    cfg = {k: v for k, v in spec.items() if k not in ("cpu_depth",)}
+    cfg = dict(spec)
     cfg.update(COMMON)
+    what = (f"each step: oracle build + new-source solve at depth {sd} (mean {statistics.mean(ts):.2f} s), "
+            f"scaled by {ratio:.2f} = one full-depth run ({t_full:.2f} s) over that mean" if sd is not None
+            else f"each step: oracle build + new-source solve of the full problem (mean {statistics.mean(ts):.2f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * sum(scaled) / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128" if spec["kind"] == "iti" else "f64",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": (f"each step: oracle build + new-source solve at depth "
-                                        f"{spec['cpu_depth'] if spec['cpu_depth'] is not None else 'adaptive'}"
-                                        f" (mean {statistics.mean(ts):.2f} s), scaled by the flop ratio "
-                                        f"{ratio:.1f}")},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": th, "kind": "oracle",
+                             "sample": what + f"; {th} BLAS threads of {os.cpu_count()} host cores"},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return line
 
@@ -584,15 +586,14 @@ def serve_inputs(P, op, field_seed, rng):
     return d
 
 
-def run_serve(args, rank, world):
-    """Served solves/s and p50 / p99 latency of the request server against the
-    plain path (one request at a time, hps_build / hps_solve directly) on the
-    same seeded request stream and arrival times."""
-    import threading  # noqa: F401  (the server's threads are native)
+def serve_measure(spec):
+    """Served requests/s and p50 / p99 latency of the request server against
+    the plain path (one request at a time, hps_build / hps_solve directly) on
+    the same seeded request stream and arrival times, at each load of
+    spec["rates"] (a multiple of the plain path's measured capacity)."""
     import torch
     import paper_2503_17535_gb300 as P
 
-    spec = args.spec
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     ops, op_seed, op_bytes = serve_operators(P, spec)
     rng = np.random.default_rng(op_seed + 1)
@@ -686,7 +687,8 @@ def run_serve(args, rank, world):
         S.close()
         lat = [i["t_done_ms"] - i["t_submit_ms"] for i in infos]
         span = (max(i["t_done_ms"] for i in infos) - min(i["t_submit_ms"] for i in infos)) / 1e3
-        return {"lat_ms": lat, "span_s": span, "max_batch": st["max_batch_seen"], "batches": st["batches"]}
+        return {"lat_ms": lat, "span_s": span, "max_batch": st["max_batch_seen"], "batches": st["batches"],
+                "multi_batches": st["multi_batches"], "max_group": st["max_group_seen"]}
 
     def pct_of(v, q):
         return round(float(np.percentile(np.asarray(v), q)), 3)
@@ -703,11 +705,21 @@ def run_serve(args, rank, world):
         rates.append({"load": rho, "offered_per_s": round(lam, 3),
                       "served": {"solves_per_s": round(R / sv["span_s"], 3), "p50_ms": pct_of(sv["lat_ms"], 50),
                                  "p99_ms": pct_of(sv["lat_ms"], 99), "max_batch": sv["max_batch"],
-                                 "batches": sv["batches"]},
+                                 "batches": sv["batches"], "multi_operator_batches": sv["multi_batches"],
+                                 "max_operators_in_a_batch": sv["max_group"]},
                       "plain": {"solves_per_s": round(R / pl["span_s"], 3), "p50_ms": pct_of(pl["lat_ms"], 50),
                                 "p99_ms": pct_of(pl["lat_ms"], 99)}})
-    top = rates[-1]
     n_build = sum(1 for r in req if r[0] == "build")
+    return {"rates": rates, "ops": ops, "op_seed": op_seed, "op_bytes": op_bytes, "cap": cap,
+            "n_build": n_build, "R": R}
+
+
+def run_serve(args, rank, world):
+    spec = args.spec
+    m = serve_measure(spec)
+    rates, ops, op_seed, op_bytes, cap, n_build, R = (m["rates"], m["ops"], m["op_seed"], m["op_bytes"],
+                                                      m["cap"], m["n_build"], m["R"])
+    top = rates[-1]
     cfg = {k: v for k, v in spec.items() if k not in ("op_budget_gb",)}
     cfg.update({"operators": ops, "operator_seed": op_seed, "operator_bytes": int(op_bytes),
                 "requests_build": n_build, "requests_solve": R - n_build, "root": "lazy",
@@ -721,6 +733,20 @@ def run_serve(args, rank, world):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def serving_leg(args):
+    """A short run of the serving workload for the default line: its seeded
+    operators and request mix at 0.9 x the plain path's capacity."""
+    spec = dict(SERVE)
+    spec["requests"] = 40
+    spec["rates"] = [0.9]
+    m = serve_measure(spec)
+    r = m["rates"][0]
+    return {"workload": spec["workload"], "operators": m["ops"], "requests": m["R"],
+            "requests_build": m["n_build"], "load": r["load"], "offered_per_s": r["offered_per_s"],
+            "plain_capacity_per_s": round(m["cap"], 3), "served": r["served"], "plain": r["plain"],
+            "unit": "requests/s", "latency": "host clock, submit to result on the host"}
 
 
 # ------------------------------------------------------------ differentiation --
@@ -848,6 +874,8 @@ def main():
     if args.workload == "gemm":
         return run_gemm(args, rank, world)
     spec = args.spec
+    if args.oracle_sample is not None:
+        return run_oracle_sample(args)
     if args.impl == "reference":
         line = run_reference(args, rank)
         if line is not None:
@@ -861,7 +889,7 @@ def main():
         per = r["per"]
         p50, p99 = pct(per, 50), pct(per, 99)
         step_tf = r["flops_step"] / (statistics.median(per) / 1e3) / 1e12
-        cfg = {k: v for k, v in spec.items() if k not in ("cpu_depth",)}
+        cfg = dict(spec)
         cfg.update(COMMON)
         cfg["n_leaves"] = r["n_leaves"]
         cfg["parallelism"] = f"replicas x{world}"
@@ -879,8 +907,10 @@ def main():
                                        "gflops": round(v["flops"] / 1e9, 3),
                                        "exec_gflops": round(v["exec_flops"] / 1e9, 3)}
                                    for k, v in r["classes"].items()}}
+        if world == 1 and not args.no_serve and spec["workload"].startswith("helmholtz"):
+            line["serving"] = serving_leg(args)
         if world == 1 and not args.no_cpu:
-            line["cpu_baseline"] = cpu_baseline(spec, r["sample_ratio"])
+            line["cpu_baseline"] = cpu_baseline(args, spec)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
