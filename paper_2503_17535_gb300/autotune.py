@@ -35,6 +35,7 @@ CANDIDATES = {
     "lu_base_panels_many": [2, 4, 8],
     "tc_min_work_real": [25, 50, 100, 200, 400],
     "tc_min_work_cplx": [6, 12, 25, 50, 100],
+    "tc_min_k": [16, 33, 48, 64, 96],
 }
 MACROS = {
     "lu_base_panels_few": "HPS_TUNED_LU_BASE_PANELS_FEW",
@@ -43,6 +44,7 @@ MACROS = {
     "lu_cluster_panel": "HPS_TUNED_LU_CLUSTER_PANEL",
     "tc_min_work_real": "HPS_TUNED_TC_MIN_WORK_REAL",
     "tc_min_work_cplx": "HPS_TUNED_TC_MIN_WORK_CPLX",
+    "tc_min_k": "HPS_TUNED_TC_MIN_K",
 }
 
 

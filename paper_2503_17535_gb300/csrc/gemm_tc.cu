@@ -136,6 +136,7 @@ struct SplitSet {
   int R[MAXOPS], TR[MAXOPS], RT[MAXOPS];
   uint8_t* out[MAXOPS];
   int* ex[MAXOPS];    // biased exponent of each row's largest |entry| (0: zero row)
+  int items[MAXOPS];  // batch items to cut: 1 for an operand shared by every item
 };
 
 // One launch for all operands: CTA = 32 rows x 8 warps; warp w takes the
@@ -147,7 +148,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_split(SplitSet<T> ss, int K, int KT, int b0, int nb) {
   const int op = blockIdx.z / nb, bl = blockIdx.z % nb, b = b0 + bl;
   const int R = ss.R[op], TR = ss.TR[op], Rpad = ss.RT[op] * TR;
-  if (blockIdx.x * 32 >= Rpad) return;                 // uniform over the CTA
+  if (blockIdx.x * 32 >= Rpad || bl >= ss.items[op]) return;  // uniform over the CTA
   const Src<T>& s = ss.s[op];
   const int lr = threadIdx.x & 31, kw = threadIdx.x >> 5;
   const int r = blockIdx.x * 32 + lr;
@@ -271,6 +272,7 @@ struct GemmP {
   IMap crow;
   int cpart;           // complex C: component written (0 re, 1 im)
   int b0;              // first batch item of this launch
+  int a_bl, b_bl;      // 1, or 0 for an operand whose digits serve every item
   unsigned* err;
 };
 
@@ -310,8 +312,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
   if (warp == EPI_WARPS) {
     // producer: one bulk copy per operand per k step
     if (lane == 0) {
-      const uint8_t* a_src = g.As + ((int64_t)bl * g.MT + mt) * g.KT * (int64_t)ASTG;
-      const uint8_t* b_src = g.Bs + ((int64_t)bl * g.NT + nt) * g.KT * (int64_t)BSTG;
+      const uint8_t* a_src = g.As + ((int64_t)(bl * g.a_bl) * g.MT + mt) * g.KT * (int64_t)ASTG;
+      const uint8_t* b_src = g.Bs + ((int64_t)(bl * g.b_bl) * g.NT + nt) * g.KT * (int64_t)BSTG;
       for (int it = 0; it < g.KT; ++it) {
         const int s = it % NST;
         if (it >= NST && !mbar_wait(su32(&empty[s]), ((it / NST) & 1) ^ 1, abrt)) {
@@ -391,7 +393,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
     const int64_t ci = i < g.M ? (int64_t)g.crow.at(b, i) : 0;
     double* s_c = reinterpret_cast<double*>(smem + NST * STAGE);
     if (threadIdx.x < TN)
-      s_eb[threadIdx.x] = nt * TN + threadIdx.x < g.N ? row_exp(g.eb[(int64_t)bl * g.NT * TN + nt * TN + threadIdx.x]) : 0;
+      s_eb[threadIdx.x] = nt * TN + threadIdx.x < g.N ? row_exp(g.eb[(int64_t)(bl * g.b_bl) * g.NT * TN + nt * TN + threadIdx.x]) : 0;
     if (!BETA0 && i < g.M) {
 #pragma unroll 4
       for (int j = c0; j < c0 + ECOLS; ++j) {
@@ -455,7 +457,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
     asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");   // s_eb from other epilogue warps
     const bool amode1 = g.amode == 1, beta1 = g.beta == 1.0;
     if (ok && i < g.M) {
-      const int er = row_exp(g.ea[(int64_t)bl * g.MT * TM + i]);
+      const int er = row_exp(g.ea[(int64_t)(bl * g.a_bl) * g.MT * TM + i]);
 #pragma unroll
       for (int jj = 0; jj < ECOLS; ++jj) {
         const int j = c0 + jj;
@@ -544,6 +546,9 @@ bool tc_applicable(const GemmArgs<T>& g) {
   if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta || g.K > (1 << 20)) return false;
   if (w->force) return true;
   if (g.M < 32 || g.N < 16 || g.K < 16) return false;
+  // short inner dimensions: ten accumulators per output are read back for
+  // little work, so small items stay on the FP64 pipe
+  if (g.K < lu_tune(TUNE_TC_MIN_K) && (g.M < 512 || g.N < 512)) return false;
   if ((double)g.M * g.N * g.K * g.batch < 1.0e5 * lu_tune(TUNE_TC_MIN_WORK_REAL)) return false;
   return true;
 }
@@ -555,6 +560,7 @@ bool tc_applicable<cplx>(const GemmArgs<cplx>& g) {
   if (g.alpha.im != 0.0 || g.beta.im != 0.0) return false;
   if (w->force) return true;
   if (g.M < 32 || g.N < 16 || g.K < 16) return false;
+  if (g.K < lu_tune(TUNE_TC_MIN_K) && (g.M < 512 || g.N < 512)) return false;
   if ((double)g.M * g.N * g.K * g.batch < 1.0e5 * lu_tune(TUNE_TC_MIN_WORK_CPLX)) return false;
   return true;
 }
@@ -620,15 +626,30 @@ void launch_mma(const tc::GemmP<T>& p, int nb, int K, cudaStream_t st, Prof* pf)
 
 }  // namespace
 
+// An operand is the same matrix for every batch item when its items share
+// one base and its index maps do not depend on the item (the leaf stage's
+// Q and QH, for instance): its digits are then cut once and serve all items.
+template <typename T>
+bool shared_operand(const BOp<T>& X, const IMap& r, const IMap& k) {
+  return !X.ptrs && X.stride == 0 && (X.div == 1 || X.sub == 0) && (!r.idx || r.period == 1) &&
+         (!k.idx || k.period == 1);
+}
+
 template <typename T>
 cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   using namespace tc;
   constexpr int NP = std::is_same<T, cplx>::value ? 2 : 1;
   TcWorkspace* w = tc_workspace();
   const Sizes z = sizes(g.M, g.N, g.K);
-  const size_t per_item = NP * (z.a_item + z.b_item + z.ea_item + z.eb_item);
-  const int nb_max = (int)std::max<size_t>(1, std::min<size_t>(std::min(g.batch, 65535 / (2 * NP)), WS_CAP / per_item));
-  cudaError_t e = ensure_ws(w, per_item * nb_max, st);
+  const bool shA = g.batch > 1 && shared_operand(g.A, g.arow, g.acol);
+  const bool shB = g.batch > 1 && shared_operand(g.B, g.brow, IMap());
+  const size_t a_sz = z.a_item + z.ea_item, b_sz = z.b_item + z.eb_item;
+  const size_t fixed = NP * ((shA ? a_sz : 0) + (shB ? b_sz : 0));
+  const size_t per_item = std::max<size_t>(NP * ((shA ? 0 : a_sz) + (shB ? 0 : b_sz)), 1);
+  const size_t room = WS_CAP > fixed ? WS_CAP - fixed : 0;
+  const int nb_max = (int)std::max<size_t>(1, std::min<size_t>(std::min(g.batch, 65535 / (2 * NP)), room / per_item));
+  const size_t na = shA ? 1 : (size_t)nb_max, nbb = shB ? 1 : (size_t)nb_max;
+  cudaError_t e = ensure_ws(w, NP * (a_sz * na + b_sz * nbb), st);
   if (e != cudaSuccess) return e;
   uint8_t* base = static_cast<uint8_t*>(w->p);
   uint8_t* As[2];
@@ -638,12 +659,12 @@ cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   {
     uint8_t* q = base;
     for (int pt = 0; pt < NP; ++pt) {
-      As[pt] = q; q += z.a_item * nb_max;
-      Bs[pt] = q; q += z.b_item * nb_max;
+      As[pt] = q; q += z.a_item * na;
+      Bs[pt] = q; q += z.b_item * nbb;
     }
     for (int pt = 0; pt < NP; ++pt) {
-      ea[pt] = reinterpret_cast<int*>(q); q += z.ea_item * nb_max;
-      eb[pt] = reinterpret_cast<int*>(q); q += z.eb_item * nb_max;
+      ea[pt] = reinterpret_cast<int*>(q); q += z.ea_item * na;
+      eb[pt] = reinterpret_cast<int*>(q); q += z.eb_item * nbb;
     }
   }
   const int lsb = 62 - ceil_log2(std::max(g.K, 1));
@@ -658,16 +679,22 @@ cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
       Src<T> sa;
       sa.X = g.A; sa.rmap = g.arow; sa.kmap = g.acol; sa.rs = 1; sa.ks = g.A.ld; sa.part = pt;
       ss.s[nops] = sa; ss.R[nops] = g.M; ss.TR[nops] = TM; ss.RT[nops] = z.MT; ss.out[nops] = As[pt];
-      ss.ex[nops] = ea[pt]; ++nops;
+      ss.ex[nops] = ea[pt];
+      ss.items[nops] = (shA && b0 > 0) ? 0 : (shA ? 1 : nb);  // a shared operand is cut once per call
+      ++nops;
       Src<T> sb;
       sb.X = g.B; sb.kmap = g.brow; sb.rs = g.B.ld; sb.ks = 1; sb.part = pt;
       ss.s[nops] = sb; ss.R[nops] = g.N; ss.TR[nops] = TN; ss.RT[nops] = z.NT; ss.out[nops] = Bs[pt];
-      ss.ex[nops] = eb[pt]; ++nops;
+      ss.ex[nops] = eb[pt];
+      ss.items[nops] = (shB && b0 > 0) ? 0 : (shB ? 1 : nb);
+      ++nops;
     }
     launch_split<T>(ss, nops, g.K, z.KT, b0, nb, st, pf);
     GemmP<T> p;
     p.MT = z.MT; p.NT = z.NT; p.KT = z.KT; p.M = g.M; p.N = g.N; p.lsb = lsb;
     p.C = g.C; p.crow = g.crow; p.b0 = b0; p.err = *w->err_slot;
+    p.a_bl = shA ? 0 : 1;
+    p.b_bl = shB ? 0 : 1;
     // real: C = alpha A B + beta C; complex (real alpha, beta):
     //   C.re = alpha (Ar Br - Ai Bi) + beta C.re,  C.im = alpha (Ar Bi + Ai Br) + beta C.im
     const int npr = NP == 2 ? 4 : 1;

@@ -1009,7 +1009,8 @@ __global__ void k_ipiv_to_perm(const int* ipiv, int* perm, int n, int batch) {
 int& lu_tune(int param) {
   static int v[TUNE_COUNT] = {HPS_TUNED_LU_BASE_PANELS_FEW, HPS_TUNED_LU_BASE_PANELS_MANY,
                               HPS_TUNED_LU_FEW_MIN_N,       HPS_TUNED_LU_CLUSTER_PANEL,
-                              HPS_TUNED_TC_MIN_WORK_REAL,   HPS_TUNED_TC_MIN_WORK_CPLX};
+                              HPS_TUNED_TC_MIN_WORK_REAL,   HPS_TUNED_TC_MIN_WORK_CPLX,
+                              HPS_TUNED_TC_MIN_K};
   return v[param];
 }
 

@@ -101,11 +101,6 @@ struct GemmArgs {
 template <typename T>
 cudaError_t gemm(const GemmArgs<T>& g, cudaStream_t st, Prof* pf);
 
-// Tensor-core FP64 products (gemm_tc.cu): workspace for the operands' bf16
-// digit slices.  gemm() routes a product to the tensor cores when the calling
-// thread has an enabled workspace installed (TcScope) and the shape is large
-// enough; otherwise it runs on the FP64 pipe.  Kernel timeouts set
-// DEV_ERR_TIMEOUT in *err_slot.
 // Bounded-wait checks (hps_debug_wait_timeout): one CTA runs one of the
 // library's bounded waits on a word nothing else writes (linalg.cu: the group
 // barrier, which 0, and the triangular solves' flag wait, which 1, on the
@@ -114,6 +109,11 @@ cudaError_t debug_wait(int which, int satisfied, unsigned* words, unsigned long 
                        cudaStream_t st);
 cudaError_t debug_mbar_wait(int satisfied, long limit, unsigned* err, cudaStream_t st);
 
+// Tensor-core FP64 products (gemm_tc.cu): workspace for the operands' bf16
+// digit slices.  gemm() routes a product to the tensor cores when the calling
+// thread has an enabled workspace installed (TcScope) and the shape is large
+// enough; otherwise it runs on the FP64 pipe.  Kernel timeouts set
+// DEV_ERR_TIMEOUT in *err_slot.
 struct TcWorkspace {
   void* p = nullptr;
   size_t bytes = 0;
@@ -137,12 +137,6 @@ bool tc_applicable(const GemmArgs<T>& g);
 template <typename T>
 cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf);
 
-// LU with partial pivoting of `batch` n x n matrices (in place), LAPACK
-// semantics: ipiv[j] = row swapped with row j (0-based), perm = the row
-// permutation P with P A = L U (perm[i] = original row of row i).
-// G > 1 spreads each matrix over G co-resident CTAs (cooperative launch).
-// ipiv/perm are int arrays of `batch * n` (item stride n).  info[b] = first
-// zero-pivot column + 1 (0 if none).  dev_err receives DEV_ERR_* bits.
 // Shape choices of the batched LU, process-wide (hps_tune_set / hps_tune_get
 // expose them; the defaults are the values the autotuner measured best on
 // GB300, csrc/tuned.h).
@@ -153,7 +147,8 @@ enum LuTuneParam {
   TUNE_LU_CLUSTER_PANEL = 3,     // 1: tall panels in a thread-block cluster, 0: cooperative groups
   TUNE_TC_MIN_WORK_REAL = 4,     // real products go to the tensor cores from M N K batch >= this x 1e5
   TUNE_TC_MIN_WORK_CPLX = 5,     // complex products: the same threshold
-  TUNE_COUNT = 6
+  TUNE_TC_MIN_K = 6,             // products with K below this stay on the FP64 pipe unless M, N >= 512
+  TUNE_COUNT = 7
 };
 int& lu_tune(int param);
 
@@ -169,6 +164,12 @@ int lu_group_size(int n, int batch, int num_sms);
 template <typename T>
 size_t lu_pub_bytes(int n, int batch, int G);
 
+// LU with partial pivoting of `batch` n x n matrices (in place), LAPACK
+// semantics: ipiv[j] = row swapped with row j (0-based), perm = the row
+// permutation P with P A = L U (perm[i] = original row of row i).
+// G > 1 spreads each matrix over G co-resident CTAs (cooperative launch).
+// ipiv/perm are int arrays of `batch * n` (item stride n).  info[b] = first
+// zero-pivot column + 1 (0 if none).  dev_err receives DEV_ERR_* bits.
 template <typename T>
 cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, unsigned* dev_err,
                   int G, const LuWork& w, cudaStream_t st, Prof* pf);

@@ -171,3 +171,32 @@ def test_invalid_arguments(P):
         P.hps_gemm(A, A, A, mode=7)
     with pytest.raises(ValueError):
         P.hps_gemm(A, torch.zeros((1, 3, 5), dtype=torch.float64, device="cuda"), A)
+
+
+@pytest.mark.parametrize("shared", ["A", "B"])
+@pytest.mark.parametrize("cplx", [False, True], ids=["real", "complex"])
+def test_operand_shared_by_every_item(P, shared, cplx):
+    """An operand given with item stride 0 (the same matrix for every item,
+    as the leaf stage's Q and QH products are) is cut into digits once per
+    call and serves every item; the products stay within the bound."""
+    from paper_2503_17535_gb300 import _capi
+    rng = np.random.default_rng(31 if shared == "A" else 37)
+    batch, m, n, k = 7, 130, 57, 300
+    z = (lambda s: rng.standard_normal(s) + 1j * rng.standard_normal(s)) if cplx else rng.standard_normal
+    A = z((1 if shared == "A" else batch, m, k))
+    B = z((1 if shared == "B" else batch, k, n))
+    Ad, Bd = _colmajor(A), _colmajor(B)
+    Cd = _colmajor(np.zeros((batch, m, n), A.dtype))
+    st = _capi.lib().hps_gemm(_capi.HPS_C128 if cplx else _capi.HPS_F64, 0, m, n, k, batch, 1.0, Ad.data_ptr(), m,
+                              0 if shared == "A" else m * k, Bd.data_ptr(), k, 0 if shared == "B" else k * n, 0.0,
+                              Cd.data_ptr(), m, m * n, None)
+    torch.cuda.synchronize()
+    assert st == 0
+    C = _back(Cd)
+    Af, Bf = np.broadcast_to(A, (batch, m, k)), np.broadcast_to(B, (batch, k, n))
+    if not cplx:
+        _check(Af, Bf, np.zeros((batch, m, n)), C, 1.0, 0.0, rng)
+    else:
+        ref = np.matmul(Af, Bf)
+        scale = np.abs(Af).max() * np.abs(Bf).max() * k
+        assert np.abs(C - ref).max() <= 1e-14 * scale
