@@ -97,6 +97,20 @@ struct AGroup {
   } cb[8];
 };
 
+// The solve passes of one level of an adaptive tree as grouped launches:
+// device task tables (built with the solve workspace) and their sizes.
+struct ASolveLevel {
+  std::vector<int> merges;            // indices into am
+  ZeroTask<double>* zr = nullptr;     // up: zero r of every merge
+  ProjTask<double>* pr = nullptr;     // up: each child's h projected
+  ChildTask<double>* gh = nullptr;    // up: projected h into r and hp
+  GintTask<double>* gi = nullptr;     // down: gint of the non-lazy merges
+  ChildTask<double>* dc = nullptr;    // down: each child's projected data
+  ProjTask<double>* un = nullptr;     // down: unprojected onto the child
+  int nzr = 0, npr = 0, ngh = 0, ngi = 0, ndc = 0, nun = 0;
+  int64_t tzr = 0, tpr = 0, tgh = 0, tgi = 0, tdc = 0, tun = 0;
+};
+
 struct AMergeDev {
   int node = -1, n_ext = 0, n_int = 0;
   AChildDev ch[8];
@@ -112,6 +126,7 @@ struct AMergeDev {
 }  // namespace hps
 
 using hps::ATree;
+using hps::ASolveLevel;
 using hps::ItiElim;
 using hps::cplx;
 using hps::DtnLeafRef;
@@ -198,6 +213,7 @@ struct hps_handle {
   ATree at;
   std::vector<hps::AMergeDev> am;
   std::vector<hps::AGroup> ag;   // batched groups, deepest level first
+  std::vector<hps::ASolveLevel> alev;  // solve passes per level, deepest first
   std::vector<int> node_merge;   // tree node -> index in am, or -1
   double *dC2F = nullptr, *dF2C = nullptr, *dsleaf = nullptr;
   void* aproj_tmp = nullptr;     // projection temporaries (build)

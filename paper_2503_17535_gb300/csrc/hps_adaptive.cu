@@ -243,11 +243,27 @@ hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs*
   h->ag.clear();
   for (size_t mi = 0; mi < at.plans.size(); ++mi) h->node_merge[at.plans[mi].node] = (int)mi;
   std::vector<T*> Rof(at.plans.size(), nullptr);
+  // per level, every (merge, child) projection, fill and gather runs as one
+  // grouped launch per step (task tables uploaded per level)
+  std::vector<std::vector<ProjTask<T>>> keep_pc, keep_pr;
+  std::vector<std::vector<ZeroTask<T>>> keep_z;
+  std::vector<std::vector<GatherTask<T>>> keep_g;
   for (size_t i0 = 0; i0 < at.plans.size();) {
     const int lev = at.nodes[at.plans[i0].node].level;
     size_t i1 = i0;
     while (i1 < at.plans.size() && at.nodes[at.plans[i1].node].level == lev) ++i1;
     size_t roff = 0;
+    keep_pc.emplace_back();
+    keep_pr.emplace_back();
+    keep_z.emplace_back();
+    keep_g.emplace_back();
+    std::vector<ProjTask<T>>& tpc = keep_pc.back();
+    std::vector<ProjTask<T>>& tpr = keep_pr.back();
+    std::vector<ZeroTask<T>>& tz = keep_z.back();
+    std::vector<GatherTask<T>>& tg = keep_g.back();
+    int64_t tot_pc = 0, tot_pr = 0, tot_z = 0, tot_g = 0;
+    size_t tmp_elems = 0;                      // level temporary: projected columns of every child
+    std::vector<size_t> tmp_off;
     for (size_t mi = i0; mi < i1; ++mi) {
       const MergePlanA& pl = at.plans[mi];
       AMergeDev& M = h->am[mi];
@@ -290,21 +306,61 @@ hps_status adaptive_build(hps_handle* h, const hps_tree* tree, const hps_coeffs*
           return HPS_ERR_OOM;
         int n = 0, ld = 0;
         const T* Tc = child_T(h, nd.child[c], &n, &ld);
-        T* tmpT = (T*)h->aproj_tmp;
-        HPS_CUDA(proj_cols<T>(Tc, ld, n, CD.pj, h->dC2F, tmpT, n, st, pf));
-        HPS_CUDA(proj_rows<T>(tmpT, n, cp.np + 1, CD.pj, h->dF2C, (T*)CD.Tp, cp.np, st, pf));
+        ProjTask<T> pc{};
+        pc.src = Tc; pc.ld_src = ld; pc.nrc = n; pc.pj = CD.pj; pc.out = nullptr; pc.ld_out = n;
+        pc.elem0 = tot_pc;
+        tot_pc += (int64_t)n * (cp.np + 1);
+        tmp_off.push_back(tmp_elems);
+        tmp_elems += (size_t)n * (cp.np + 1);
+        tpc.push_back(pc);
+        ProjTask<T> pr{};
+        pr.src = nullptr; pr.ld_src = n; pr.nrc = cp.np + 1; pr.pj = CD.pj; pr.out = (T*)CD.Tp; pr.ld_out = cp.np;
+        pr.elem0 = tot_pr;
+        tot_pr += (int64_t)cp.np * (cp.np + 1);
+        tpr.push_back(pr);
       }
       T* R = (T*)h->scratch + roff;
       Rof[mi] = R;
       roff += (size_t)nI * (ne + 1);
-      HPS_CUDA(fill<T>(bop<T>((T*)M.D, 0, nI), nI, nI, 1, 0.0, 0.0, st, pf));
-      HPS_CUDA(fill<T>(bop<T>(R, 0, nI), nI, ne + 1, 1, 0.0, 0.0, st, pf));
-      HPS_CUDA(fill<T>(bop<T>((T*)M.TP, 0, ne), ne, ne + 1, 1, 0.0, 0.0, st, pf));
+      const std::pair<T*, int64_t> zs[3] = {{(T*)M.D, (int64_t)nI * nI}, {R, (int64_t)nI * (ne + 1)},
+                                            {(T*)M.TP, (int64_t)ne * (ne + 1)}};
+      for (const auto& z : zs) {
+        tz.push_back(ZeroTask<T>{z.first, z.second, tot_z});
+        tot_z += z.second;
+      }
       for (int c = 0; c < 8; ++c) {
         const AChildDev& CD = M.ch[c];
-        HPS_CUDA(merge_gather<T>((const T*)CD.Tp, 0, 1, 1, CD.pj.np, ne, nI, CD.ext, CD.var, CD.var, false,
-                                 (T*)M.D, R, (T*)M.TP, st, pf));
+        GatherTask<T> gt{};
+        gt.Tc = (const T*)CD.Tp; gt.nbc = CD.pj.np; gt.n_ext = ne; gt.n_int = nI;
+        gt.ext = CD.ext; gt.var = CD.var; gt.D = (T*)M.D; gt.R = R; gt.TP = (T*)M.TP;
+        gt.elem0 = tot_g;
+        tot_g += (int64_t)CD.pj.np * (CD.pj.np + 1);
+        tg.push_back(gt);
       }
+    }
+    {
+      // the level's temporary and task tables, then four launches
+      T* tmpL = (T*)dalloc(h, std::max<size_t>(tmp_elems, 1) * sizeof(T), &tmpbufs);
+      if (!tmpL) return HPS_ERR_OOM;
+      for (size_t t = 0; t < tpc.size(); ++t) {
+        tpc[t].out = tmpL + tmp_off[t];
+        tpr[t].src = tmpL + tmp_off[t];
+      }
+      auto up_tasks = [&](const auto& v) -> void* {
+        const size_t bytes = v.size() * sizeof(v[0]);
+        void* d = dalloc(h, std::max<size_t>(bytes, 16), &tmpbufs);
+        if (d && bytes && cudaMemcpyAsync(d, v.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return nullptr;
+        return d;
+      };
+      auto* dpc = (const ProjTask<T>*)up_tasks(tpc);
+      auto* dpr = (const ProjTask<T>*)up_tasks(tpr);
+      auto* dz = (const ZeroTask<T>*)up_tasks(tz);
+      auto* dg = (const GatherTask<T>*)up_tasks(tg);
+      if (!dpc || !dpr || !dz || !dg) return HPS_ERR_OOM;
+      HPS_CUDA(proj_cols_group<T>(dpc, (int)tpc.size(), tot_pc, h->dC2F, st, pf));
+      HPS_CUDA(proj_rows_group<T>(dpr, (int)tpr.size(), tot_pr, h->dF2C, st, pf));
+      HPS_CUDA(zero_group<T>(dz, (int)tz.size(), tot_z, st, pf));
+      HPS_CUDA(merge_gather_group<T>(dg, (int)tg.size(), tot_g, st, pf));
     }
     // groups of equal sizes within the level, in first-appearance order
     std::vector<std::pair<std::pair<int, int>, std::vector<int>>> groups;
@@ -482,6 +538,92 @@ static hps_status adaptive_ws(hps_handle* h, int nrhs) {
         cudaMemcpy(G.dhp, vh.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess)
       return HPS_ERR_CUDA;
   }
+  // task tables of the grouped solve passes, level by level (deepest first)
+  {
+    const ATree& at = h->at;
+    h->alev.clear();
+    for (size_t mi = 0; mi < h->am.size(); ++mi) {
+      const int lev = at.nodes[h->am[mi].node].level;
+      if (h->alev.empty() || at.nodes[h->am[(size_t)h->alev.back().merges[0]].node].level != lev)
+        h->alev.emplace_back();
+      h->alev.back().merges.push_back((int)mi);
+    }
+    size_t vtot = 0;
+    for (const AMergeDev& M : h->am)
+      for (int c = 0; c < 8; ++c) vtot += (size_t)M.ch[c].pj.np * nrhs;
+    T* vall = (T*)A(std::max<size_t>(vtot, 1) * es);
+    if (!vall) return HPS_ERR_OOM;
+    size_t voff = 0;
+    for (ASolveLevel& Lv : h->alev) {
+      std::vector<ZeroTask<T>> zr;
+      std::vector<ProjTask<T>> pr, un;
+      std::vector<ChildTask<T>> gh, dc;
+      std::vector<GintTask<T>> gi;
+      for (int mi : Lv.merges) {
+        AMergeDev& M = h->am[(size_t)mi];
+        const ANode& nd = at.nodes[M.node];
+        zr.push_back(ZeroTask<T>{(T*)M.r, (int64_t)M.n_int * nrhs, Lv.tzr});
+        Lv.tzr += (int64_t)M.n_int * nrhs;
+        if (!M.lazy) {
+          GintTask<T> t{};
+          t.X = (const T*)M.X; t.xp = (const T*)M.x; t.gpar = (const T*)M.g; t.gint = (T*)M.gint;
+          t.n_ext = M.n_ext; t.n_int = M.n_int; t.nrhs = nrhs; t.tile0 = Lv.tgi;
+          Lv.tgi += (int64_t)((M.n_int + 31) / 32) * nrhs;
+          gi.push_back(t);
+        }
+        for (int c = 0; c < 8; ++c) {
+          const AChildDev& CD = M.ch[c];
+          const int np = CD.pj.np;
+          T* v = vall + voff;
+          voff += (size_t)np * nrhs;
+          const ANode& K = at.nodes[nd.child[c]];
+          T *hc, *gc;
+          int ld;
+          if (K.leaf >= 0) {
+            hc = (T*)h->ws_hleaf + (int64_t)K.leaf * h->nb * nrhs;
+            gc = (T*)h->ws_gleaf + (int64_t)K.leaf * h->nb * nrhs;
+            ld = h->nb;
+          } else {
+            AMergeDev& C2 = h->am[(size_t)h->node_merge[nd.child[c]]];
+            hc = (T*)C2.hp;
+            gc = (T*)C2.g;
+            ld = C2.n_ext;
+          }
+          ProjTask<T> p{};
+          p.src = hc; p.ld_src = ld; p.nrc = nrhs; p.pj = CD.pj; p.out = v; p.ld_out = np; p.elem0 = Lv.tpr;
+          Lv.tpr += (int64_t)np * nrhs;
+          pr.push_back(p);
+          ChildTask<T> g2{};
+          g2.gint = v; g2.r = (T*)M.r; g2.hp = (T*)M.hp; g2.nbc = np; g2.n_ext = M.n_ext; g2.n_int = M.n_int;
+          g2.nrhs = nrhs; g2.ext = CD.ext; g2.var = CD.var; g2.elem0 = Lv.tgh;
+          Lv.tgh += (int64_t)np * nrhs;
+          gh.push_back(g2);
+          ChildTask<T> d{};
+          d.gpar = (const T*)M.g; d.gint = (T*)M.gint; d.out = v; d.nbc = np; d.n_ext = M.n_ext;
+          d.n_int = M.n_int; d.nrhs = nrhs; d.ext = CD.ext; d.var = CD.var; d.elem0 = Lv.tdc;
+          Lv.tdc += (int64_t)np * nrhs;
+          dc.push_back(d);
+          ProjTask<T> q{};
+          q.src = v; q.ld_src = np; q.nrc = nrhs; q.pj = CD.pj; q.out = gc; q.ld_out = ld; q.elem0 = Lv.tun;
+          Lv.tun += (int64_t)CD.pj.n * nrhs;
+          un.push_back(q);
+        }
+      }
+      auto up = [&](const auto& vec, auto** dst, int* cnt) -> bool {
+        const size_t bytes = std::max<size_t>(vec.size() * sizeof(vec[0]), 16);
+        void* d = A(bytes);
+        if (!d) return false;
+        if (!vec.empty() && cudaMemcpy(d, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice) != cudaSuccess)
+          return false;
+        *dst = (std::remove_reference_t<decltype(**dst)>*)d;
+        *cnt = (int)vec.size();
+        return true;
+      };
+      if (!up(zr, &Lv.zr, &Lv.nzr) || !up(pr, &Lv.pr, &Lv.npr) || !up(gh, &Lv.gh, &Lv.ngh) ||
+          !up(gi, &Lv.gi, &Lv.ngi) || !up(dc, &Lv.dc, &Lv.ndc) || !up(un, &Lv.un, &Lv.nun))
+        return HPS_ERR_OOM;
+    }
+  }
   h->ws_bytes = h->bytes - before;
   h->ws_nrhs = nrhs;
   return HPS_OK;
@@ -532,27 +674,15 @@ hps_status adaptive_solve(hps_handle* h, int nrhs, const void* g_in, const void*
     HPS_CUDA(scale_blocks<T>((T*)h->ws_hleaf, (int64_t)nb * nrhs, h->dsleaf, nl, st, pf));
     // level by level: gathers of every merge of the level, one batched
     // D^{-1} per group of equal sizes, then the B x products
+    size_t lv = 0;
     for (size_t g0 = 0; g0 < h->ag.size();) {
       size_t g1 = g0;
       while (g1 < h->ag.size() && h->ag[g1].level == h->ag[g0].level) ++g1;
-      for (size_t gi = g0; gi < g1; ++gi)
-        for (int mi : h->ag[gi].members) {
-          AMergeDev& M = h->am[(size_t)mi];
-          const ANode& nd = at.nodes[M.node];
-          const int ne = M.n_ext, nI = M.n_int;
-          HPS_CUDA(fill<T>(bop<T>((T*)M.r, 0, nI), nI, nrhs, 1, 0.0, 0.0, st, pf));
-          for (int c = 0; c < 8; ++c) {
-            const AChildDev& CD = M.ch[c];
-            const ANode& K = at.nodes[nd.child[c]];
-            const T* hc;
-            int ldh;
-            if (K.leaf >= 0) { hc = (const T*)h->ws_hleaf + (int64_t)K.leaf * nb * nrhs; ldh = nb; }
-            else { const AMergeDev& C2 = h->am[h->node_merge[nd.child[c]]]; hc = (const T*)C2.hp; ldh = C2.n_ext; }
-            HPS_CUDA(proj_rows<T>(hc, ldh, nrhs, CD.pj, h->dF2C, vt, CD.pj.np, st, pf));
-            HPS_CUDA(merge_gather_h<T>(vt, 1, 1, CD.pj.np, ne, nI, nrhs, CD.ext, CD.var, CD.var, false, (T*)M.r,
-                                       (T*)M.hp, st, pf));
-          }
-        }
+      // every merge of the level: zero r, project each child's h, gather it
+      const ASolveLevel& L = h->alev[lv++];
+      HPS_CUDA(zero_group<T>(L.zr, L.nzr, L.tzr, st, pf));
+      HPS_CUDA(proj_rows_group<T>(L.pr, L.npr, L.tpr, h->dF2C, st, pf));
+      HPS_CUDA(gather_h_group<T>(L.gh, L.ngh, L.tgh, st, pf));
       for (size_t gi = g0; gi < g1; ++gi) {
         const AGroup& G = h->ag[gi];
         const int nbat = (int)G.members.size();
@@ -568,12 +698,18 @@ hps_status adaptive_solve(hps_handle* h, int nrhs, const void* g_in, const void*
       g0 = g1;
     }
   }
-  // downward pass, root first
-  for (size_t k2 = h->am.size(); k2-- > 0;) {
-    AMergeDev& M = h->am[k2];
-    const ANode& nd = at.nodes[M.node];
-    const T* gpar = (M.node == 0) ? g : (const T*)M.g;
-    if (M.lazy) {
+  // downward pass, root level first: the root's data is copied into its own
+  // workspace so that every level's task tables refer to fixed buffers
+  if (!h->am.empty()) {
+    AMergeDev& R0 = h->am[(size_t)h->node_merge[0]];
+    HPS_CUDA(cudaMemcpyAsync(R0.g, g, (size_t)R0.n_ext * nrhs * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  }
+  for (size_t li = h->alev.size(); li-- > 0;) {
+    const ASolveLevel& L = h->alev[li];
+    for (int mi : L.merges) {
+      AMergeDev& M = h->am[(size_t)mi];
+      if (!M.lazy) continue;
+      const T* gpar = (const T*)M.g;
       // X holds [C | h_int]: t = -(C g + h), then g_int = D^{-1} t
       HPS_CUDA(down_gint<T>((const T*)M.X, newf ? (const T*)M.r : nullptr, gpar, 1, M.n_ext, M.n_int, nrhs,
                             (T*)M.x, st, pf));
@@ -583,21 +719,11 @@ hps_status adaptive_solve(hps_handle* h, int nrhs, const void* g_in, const void*
         HPS_CUDA(getrs_flags<T>((const T*)M.D, M.n_int, M.n_int, (T*)M.gint, M.n_int, nrhs, h->trsv, st, pf));
       else
         HPS_CUDA(getrs_inplace<T>(bop<T>((T*)M.D, 0, M.n_int), M.n_int, GI, nrhs, 1, st, pf));
-    } else {
-      HPS_CUDA(down_gint<T>((const T*)M.X, newf ? (const T*)M.x : nullptr, gpar, 1, M.n_ext, M.n_int, nrhs,
-                            (T*)M.gint, st, pf));
     }
-    for (int c = 0; c < 8; ++c) {
-      const AChildDev& CD = M.ch[c];
-      HPS_CUDA(down_children<T>(gpar, (const T*)M.gint, 1, 1, CD.pj.np, M.n_ext, M.n_int, nrhs, CD.ext, CD.var,
-                                vt, st, pf));
-      const ANode& K = at.nodes[nd.child[c]];
-      T* gc;
-      int ldg;
-      if (K.leaf >= 0) { gc = (T*)h->ws_gleaf + (int64_t)K.leaf * nb * nrhs; ldg = nb; }
-      else { AMergeDev& C2 = h->am[h->node_merge[nd.child[c]]]; gc = (T*)C2.g; ldg = C2.n_ext; }
-      HPS_CUDA(unproject<T>(vt, CD.pj.np, CD.pj, h->dC2F, gc, ldg, nrhs, st, pf));
-    }
+    // the level's other merges, their children's data and its unprojection
+    HPS_CUDA(gint_group<T>(L.gi, L.ngi, L.tgi, newf ? 1 : 0, st, pf));
+    HPS_CUDA(down_children_group<T>(L.dc, L.ndc, L.tdc, st, pf));
+    HPS_CUDA(unproject_group<T>(L.un, L.nun, L.tun, h->dC2F, st, pf));
   }
   const T* gleaf = h->am.empty() ? g : (const T*)h->ws_gleaf;
   HPS_CUDA(leaf_output<T>(h->lc, nl, nrhs, (const T*)h->leafX, newf ? (const T*)h->ws_xf : nullptr, gleaf, u, false,
