@@ -734,17 +734,18 @@ __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int n
 // whole panel.  Rows never move during the panel: a chosen pivot row is only
 // marked done, and the interchanges are recorded in LAPACK's form (ipiv) by
 // a replay of the swap sequence on the panel's top positions; at the end
-// every row is written to its final position.  Per column: each CTA
-// publishes its best candidate (|.|, current position, row, and the row's
-// panel values) in its own shared memory, one cluster barrier, every CTA
-// reads all CS candidates through distributed shared memory in one round,
-// picks the same pivot (largest magnitude, and on ties the lowest current
-// position -- the row order after the interchanges so far, which is the
-// choice of the cooperative kernel and of LAPACK), and updates its own rows.  Candidates are
-// double-buffered by column parity, so one barrier per column suffices: a CTA
-// cannot overwrite a buffer before every CTA has passed the next barrier,
-// which each reaches only after reading the buffer.  The barrier is the
-// hardware cluster barrier; there is no polling.
+// every row is written to its final position.  Per column: every warp
+// reduces its rows' candidates with shuffles and publishes its best (|.|,
+// current position, row, and the row's panel values) in its CTA's shared
+// memory; one cluster barrier; warp 0 of every CTA reads all 8 CS candidates
+// through distributed shared memory, picks the same pivot (largest
+// magnitude, and on ties the lowest current position -- the row order after
+// the interchanges so far, which is LAPACK's choice), copies its row and
+// forms the reciprocal; one block barrier; every thread updates its rows.
+// Candidates are double-buffered by column parity, so one cluster barrier
+// per column suffices: a warp cannot overwrite a buffer before every CTA has
+// passed the next barrier, which each reaches only after reading the buffer.
+// The barriers are the hardware ones; there is no polling.
 template <typename T>
 __global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k0, int nb, int* ipiv,
                                                           int* info) {
@@ -759,20 +760,15 @@ __global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k
   const int rc = max(0, min(ch, n - r0));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ps = reinterpret_cast<T*>(smem_raw);       // ch x nb, column-major
-  T* pubv = Ps + (size_t)ch * nb;               // 2 x nb: this CTA's candidate row
-  T* cand = pubv + 2 * nb;                      // CS x nb: every CTA's candidate row
-  int* chosen = reinterpret_cast<int*>(cand + (size_t)CS * nb);  // ch: pivot step of a row, or -1
-  __shared__ long long pub_m[2];
-  __shared__ int pub_r[2], pub_p[2];  // candidate's current position and row
-  __shared__ long long cm[16];
-  __shared__ int cr[16], cp[16];
-  __shared__ double red_m[8];
-  __shared__ int red_r[8], red_p[8];
-  __shared__ int s_win, s_lr;
-  __shared__ int phys_at[64], pos_top[64];      // swap replay on the top positions
+  T* pubv = Ps + (size_t)ch * nb;               // [2 slots][8 warps][nb]: candidate rows
+  T* Wv = pubv + 16 * nb;                       // the pivot row
+  int* chosen = reinterpret_cast<int*>(Wv + nb);  // ch: pivot step of a row, or -1
+  __shared__ long long pub_m[16];               // [slot][warp] candidate magnitude (bits)
+  __shared__ int pub_q[16], pub_p[16];          // its current position and row
+  __shared__ int phys_at[32], pos_top[32];      // swap replay on the top positions
   __shared__ double s_inv_raw[2];
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
+  const int lane = tid & 31, wid = tid >> 5;
   T* Ab = A.item(b);
   const int lda = A.ld;
 
@@ -789,8 +785,8 @@ __global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k
     if (piv_better(m, r0 + r, best, bpos)) { best = m; bpos = r0 + r; prow = r0 + r; }
   }
   for (int jj = 0; jj < nb; ++jj) {
-    const int j = k0 + jj, slot = jj & 1;
-    // this CTA's candidate
+    const int slot = jj & 1;
+    // this warp's candidate, published for the whole cluster
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const double m2 = __shfl_down_sync(0xffffffffu, best, o);
@@ -798,59 +794,58 @@ __global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k
       const int p2 = __shfl_down_sync(0xffffffffu, prow, o);
       if (piv_better(m2, q2, best, bpos)) { best = m2; bpos = q2; prow = p2; }
     }
-    if (lane == 0) { red_m[wid] = best; red_r[wid] = bpos; red_p[wid] = prow; }
-    __syncthreads();
-    if (tid == 0) {
-      double pm = red_m[0];
-      int pq = red_r[0], pr = red_p[0];
-      for (int w = 1; w < nw; ++w)
-        if (piv_better(red_m[w], red_r[w], pm, pq)) { pm = red_m[w]; pq = red_r[w]; pr = red_p[w]; }
-      pub_m[slot] = __double_as_longlong(pm);
-      pub_r[slot] = pq;
-      pub_p[slot] = pr;
-      s_lr = pm >= 0.0 ? pr - r0 : -1;
+    best = __shfl_sync(0xffffffffu, best, 0);
+    bpos = __shfl_sync(0xffffffffu, bpos, 0);
+    prow = __shfl_sync(0xffffffffu, prow, 0);
+    if (lane == 0) {
+      pub_m[slot * 8 + wid] = __double_as_longlong(best);
+      pub_q[slot * 8 + wid] = bpos;
+      pub_p[slot * 8 + wid] = prow;
     }
-    __syncthreads();
-    for (int c = tid; c < nb; c += nth) pubv[slot * nb + c] = s_lr >= 0 ? Ps[s_lr + (size_t)c * ch] : T(0.0);
+    if (lane < nb)
+      pubv[(slot * 8 + wid) * nb + lane] = best >= 0.0 ? Ps[(prow - r0) + (size_t)lane * ch] : T(0.0);
     cl.sync();
-    // every CTA's candidate, in one round of distributed shared memory reads
-    for (int e = tid; e < CS * nb; e += nth) {
-      const int q = e / nb, c = e - q * nb;
-      cand[e] = cl.map_shared_rank(pubv, q)[slot * nb + c];
-    }
-    if (tid < CS) {
-      cm[tid] = cl.map_shared_rank(pub_m, tid)[slot];
-      cr[tid] = cl.map_shared_rank(pub_r, tid)[slot];
-      cp[tid] = cl.map_shared_rank(pub_p, tid)[slot];
+    if (wid == 0) {
+      // every warp's candidate of the cluster, one round of remote reads
+      double cm = -1.0;
+      int cq = 0x7fffffff, cp = -1, cw = 0;
+      for (int e = lane; e < 8 * CS; e += 32) {
+        const int q = e >> 3, w = e & 7;
+        const double m = __longlong_as_double(cl.map_shared_rank(pub_m, q)[slot * 8 + w]);
+        const int qq = cl.map_shared_rank(pub_q, q)[slot * 8 + w];
+        if (piv_better(m, qq, cm, cq)) { cm = m; cq = qq; cp = cl.map_shared_rank(pub_p, q)[slot * 8 + w]; cw = e; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double m2 = __shfl_down_sync(0xffffffffu, cm, o);
+        const int q2 = __shfl_down_sync(0xffffffffu, cq, o);
+        const int p2 = __shfl_down_sync(0xffffffffu, cp, o);
+        const int w2 = __shfl_down_sync(0xffffffffu, cw, o);
+        if (piv_better(m2, q2, cm, cq)) { cm = m2; cq = q2; cp = p2; cw = w2; }
+      }
+      cm = __shfl_sync(0xffffffffu, cm, 0);
+      cq = __shfl_sync(0xffffffffu, cq, 0);
+      cp = __shfl_sync(0xffffffffu, cp, 0);
+      cw = __shfl_sync(0xffffffffu, cw, 0);
+      if (lane < nb) Wv[lane] = cl.map_shared_rank(pubv, cw >> 3)[(slot * 8 + (cw & 7)) * nb + lane];
+      __syncwarp();
+      if (lane == 0) {
+        *reinterpret_cast<T*>(s_inv_raw) = (cm == 0.0) ? T(0.0) : recip(Wv[jj]);
+        if (cp >= r0 && cp < r0 + rc) chosen[cp - r0] = jj;
+        // LAPACK interchange: swap position j with the winner's current position
+        const int j = k0 + jj;
+        const int rj = phys_at[jj];
+        pos_top[rj - k0] = cq;
+        if (cq - k0 < nb) phys_at[cq - k0] = rj;
+        phys_at[jj] = cp;
+        if (cp - k0 < nb) pos_top[cp - k0] = j;
+        if (g == 0) {
+          ipiv[(int64_t)b * n + j] = cq;
+          if (cm == 0.0 && info[b] == 0) info[b] = j + 1;
+        }
+      }
     }
     __syncthreads();
-    if (tid == 0) {
-      double pm = __longlong_as_double(cm[0]);
-      int pq = cr[0], wq = 0;
-      for (int q = 1; q < CS; ++q) {
-        const double m = __longlong_as_double(cm[q]);
-        if (piv_better(m, cr[q], pm, pq)) { pm = m; pq = cr[q]; wq = q; }
-      }
-      const int p = cp[wq];
-      s_win = wq;
-      const T pv = cand[wq * nb + jj];
-      *reinterpret_cast<T*>(s_inv_raw) = (pm == 0.0) ? T(0.0) : recip(pv);
-      if (g == wq) chosen[p - r0] = jj;
-      // LAPACK interchange: swap position j with the winner's current position
-      const bool ptop = p - k0 < nb;
-      const int qpos = pq;
-      const int rj = phys_at[jj];
-      pos_top[rj - k0] = qpos;
-      if (qpos - k0 < nb) phys_at[qpos - k0] = rj;
-      phys_at[jj] = p;
-      if (ptop) pos_top[p - k0] = j;
-      if (g == 0) {
-        ipiv[(int64_t)b * n + j] = qpos;
-        if (pm == 0.0 && info[b] == 0) info[b] = j + 1;
-      }
-    }
-    __syncthreads();
-    const T* Wv = cand + (size_t)s_win * nb;
     const T inv = *reinterpret_cast<const T*>(s_inv_raw);
     best = -1.0;
     bpos = 0x7fffffff;
@@ -891,7 +886,7 @@ __global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k
 template <typename T>
 size_t panel_cluster_smem(int rows, int nb, int cs) {
   const int ch = (rows + cs - 1) / cs;
-  return ((size_t)ch * nb + 2 * nb + (size_t)cs * nb) * sizeof(T) + (size_t)ch * sizeof(int) + 16;
+  return ((size_t)ch * nb + 17 * (size_t)nb) * sizeof(T) + (size_t)ch * sizeof(int) + 16;
 }
 
 template <typename T>
@@ -938,7 +933,7 @@ int panel_cluster_max() {
 template <typename T>
 int panel_cluster_size(int rows, int nb) {
   const int mx = panel_cluster_max<T>();
-  if (mx < 2 || nb > 64) return 0;
+  if (mx < 2 || nb > 32) return 0;
   int smem_max = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
