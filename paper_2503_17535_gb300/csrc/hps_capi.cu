@@ -308,7 +308,9 @@ hps_status build_impl(hps_handle* h, const hps_coeffs* cf, const void* f_in, cud
       // flags and a host-mapped error word for the flag-ordered solves
       const int nf = (ni + 31) / 32;
       h->trsv.flags = (unsigned*)dalloc(h, (size_t)nf * sizeof(unsigned));
-      if (!h->trsv.flags) return HPS_ERR_OOM;
+      h->trsv.dinv = dalloc(h, (size_t)2 * nf * 1024 * sizeof(T));
+      h->trsv.dinv_ready = false;
+      if (!h->trsv.flags || !h->trsv.dinv) return HPS_ERR_OOM;
       HPS_CUDA(cudaMemsetAsync(h->trsv.flags, 0, (size_t)nf * sizeof(unsigned), st));
       h->trsv.nflags = nf;
       HPS_CUDA(cudaHostAlloc((void**)&h->trsv_err_host, sizeof(int), cudaHostAllocMapped));

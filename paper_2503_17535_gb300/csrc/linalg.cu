@@ -1481,99 +1481,91 @@ cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaS
 // blocked getrs issues two launches per 32 rows, each far too small to fill
 // the GPU; here one launch per triangle walks the 32-row blocks in dependency
 // order (forward: first to last; backward: last to first).  CTA c takes the
-// logical blocks c, c + G, c + 2G, ... in increasing order; for each it
-// subtracts the contributions of all earlier blocks as their solutions are
-// published (warp w handles earlier blocks w, w + 8, ...), solves its own
-// 32 x 32 diagonal block with warp shuffles, writes the result and raises
-// the block's flag.  The launch is cooperative, so every CTA is resident, and
-// the earliest unfinished block depends only on finished ones: the walk
-// always makes progress.  Waits are bounded: on timeout the flag error word
-// is set and the block proceeds (wrong values, but the launch ends).
+// logical blocks c, c + G, c + 2G, ... in increasing order.  For each, all
+// eight warps subtract the contributions of the earlier blocks as their
+// solutions are published, warp w taking columns 4w .. 4w + 3 of every
+// earlier block (each warp loads its matrix entries before it waits, and the
+// FP64 work of one 32 x 32 block is spread over the whole SM); the block's
+// solution is then the product of the precomputed inverse of its 32 x 32
+// diagonal block (k_diag_block_inv) with the reduced right-hand side, split
+// the same way.  The launch is cooperative, so every CTA is resident, and the
+// earliest unfinished block depends only on finished ones: the walk always
+// makes progress.  Waits are bounded: on timeout the flag error word is set
+// and the block proceeds (wrong values, but the launch ends).
 template <typename T, int NR, bool UPPER>
 __global__ void __launch_bounds__(256) k_trsv_flags(const T* __restrict__ LU, int ld, int n, T* X, int ldx,
-                                                   int nrhs, unsigned* flags, unsigned epoch,
-                                                   volatile int* err) {
-  // warp 0: the block's right-hand side and diagonal solve; warps 1..7: the
-  // contributions of earlier blocks.  Every warp loads its 32 matrix entries
-  // per row before it waits for the solution they multiply, so the critical
-  // path per block is a flag, 32 values of x and 32 FMAs, not 32 loads.
-  __shared__ T part[7][NR][32];
+                                                   int nrhs, const T* __restrict__ dinv, unsigned* flags,
+                                                   unsigned epoch, volatile int* err) {
+  __shared__ T part[8][NR][32];
+  __shared__ T y[NR][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nblk = (n + 31) / 32;
   for (int t = blockIdx.x; t < nblk; t += gridDim.x) {
     const int j = UPPER ? nblk - 1 - t : t;
     const int r = j * 32 + lane;
     const bool rv = r < n;
-    if (w > 0) {
-      T acc[NR];
+    T acc[NR];
 #pragma unroll
-      for (int c = 0; c < NR; ++c) acc[c] = T(0.0);
-      for (int tp = w - 1; tp < t; tp += 7) {
-        const int i = UPPER ? nblk - 1 - tp : tp;
-        const int qn = min(32, n - i * 32);
-        const T* col = LU + (int64_t)(i * 32) * ld + r;
-        T a[32];
+    for (int c = 0; c < NR; ++c) acc[c] = T(0.0);
+    for (int tp = 0; tp < t; ++tp) {
+      const int i = UPPER ? nblk - 1 - tp : tp;
+      const int qn = min(32, n - i * 32);
+      T a[4];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) a[q] = (rv && q < qn) ? col[(int64_t)q * ld] : T(0.0);
-        if (lane == 0) {
-          if (!wait_flag(flags + i, epoch, 1ull << 24)) *err = 1;
-          __threadfence();
-        }
-        __syncwarp();
-        const int ri = i * 32 + lane;
-        T xi[NR];
+      for (int k = 0; k < 4; ++k) {
+        const int q = 4 * w + k;
+        a[k] = (rv && q < qn) ? LU[(int64_t)r + (int64_t)(i * 32 + q) * ld] : T(0.0);
+      }
+      if (lane == 0) {
+        if (!wait_flag(flags + i, epoch, 1ull << 24)) *err = 1;
+        __threadfence();
+      }
+      __syncwarp();
+      T xi[NR];
 #pragma unroll
-        for (int c = 0; c < NR; ++c) xi[c] = (ri < n && c < nrhs) ? ld_cg(X + ri + (int64_t)c * ldx) : T(0.0);
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-#pragma unroll
-          for (int c = 0; c < NR; ++c) acc[c] = fmsc(acc[c], a[q], shfl_val(xi[c], q));
+      for (int c = 0; c < NR; ++c) {
+        const int q = 4 * w + lane;
+        xi[c] = (lane < 4 && q < qn && c < nrhs) ? ld_cg(X + (int64_t)(i * 32 + q) + (int64_t)c * ldx) : T(0.0);
       }
 #pragma unroll
-      for (int c = 0; c < NR; ++c) part[w - 1][c][lane] = acc[c];
-    }
-    T dg[32], x[NR];
-    const int pb = min(32, n - j * 32);
-    if (w == 0) {
-      const T* dcol = LU + (int64_t)(j * 32) * ld + r;
+      for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int q = 0; q < 32; ++q) dg[q] = (rv && q < pb) ? dcol[(int64_t)q * ld] : T(0.0);
-#pragma unroll
-      for (int c = 0; c < NR; ++c) x[c] = (rv && c < nrhs) ? X[r + (int64_t)c * ldx] : T(0.0);
+        for (int c = 0; c < NR; ++c) acc[c] = fmsc(acc[c], a[k], shfl_val(xi[c], k));
     }
+#pragma unroll
+    for (int c = 0; c < NR; ++c) part[w][c][lane] = acc[c];
     __syncthreads();
     if (w == 0) {
 #pragma unroll
-      for (int c = 0; c < NR; ++c)
-        for (int k = 0; k < 7; ++k) x[c] = x[c] + part[k][c][lane];
-      if (!UPPER) {
-#pragma unroll
-        for (int cc = 0; cc < 31; ++cc) {
-#pragma unroll
-          for (int c = 0; c < NR; ++c) {
-            const T xc = shfl_val(x[c], cc);
-            if (lane > cc && lane < pb) x[c] = fmsc(x[c], dg[cc], xc);
-          }
-        }
-      } else {
-        T d = T(1.0);
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (q == lane) d = dg[q];
-        const T dinv = (!rv || is_zero(d)) ? T(0.0) : recip(d);
-#pragma unroll
-        for (int cc = 31; cc >= 0; --cc) {
-#pragma unroll
-          for (int c = 0; c < NR; ++c) {
-            if (lane == cc) x[c] = x[c] * dinv;
-            const T xc = shfl_val(x[c], cc);
-            if (lane < cc) x[c] = fmsc(x[c], dg[cc], xc);
-          }
-        }
+      for (int c = 0; c < NR; ++c) {
+        T sum = (rv && c < nrhs) ? X[r + (int64_t)c * ldx] : T(0.0);
+        for (int k = 0; k < 8; ++k) sum = sum + part[k][c][lane];
+        y[c][lane] = sum;
       }
+    }
+    __syncthreads();
+    // x_j = inv(diagonal block j) y, the inverse column-major 32 x 32
+    const T* Dj = dinv + (int64_t)j * 1024;
+    T acc2[NR];
 #pragma unroll
-      for (int c = 0; c < NR; ++c)
-        if (rv && c < nrhs) X[r + (int64_t)c * ldx] = x[c];
+    for (int c = 0; c < NR; ++c) acc2[c] = T(0.0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = 4 * w + k;
+      const T dq = Dj[lane + 32 * q];
+#pragma unroll
+      for (int c = 0; c < NR; ++c) acc2[c] = fmac(acc2[c], dq, y[c][q]);
+    }
+#pragma unroll
+    for (int c = 0; c < NR; ++c) part[w][c][lane] = acc2[c];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        T xs = T(0.0);
+        for (int k = 0; k < 8; ++k) xs = xs + part[k][c][lane];
+        if (rv && c < nrhs) X[r + (int64_t)c * ldx] = xs;
+      }
       __threadfence();
       __syncwarp();
       if (lane == 0) atomicExch(flags + j, epoch);
@@ -1582,9 +1574,45 @@ __global__ void __launch_bounds__(256) k_trsv_flags(const T* __restrict__ LU, in
   }
 }
 
+// Inverses of the 32 x 32 diagonal blocks of an LU factor (column-major,
+// 32 x 32 each): tri 0 the unit lower L_jj, tri 1 the upper U_jj; a partial
+// last block is completed with the identity, a zero pivot gives a zero row
+// of the inverse (a singular factor was reported by the factorisation).
+// One CTA per (block, triangle), thread c computes column c by substitution.
+template <typename T>
+__global__ void __launch_bounds__(32) k_diag_block_inv(const T* __restrict__ LU, int ld, int n, T* out) {
+  const int j = blockIdx.x, tri = blockIdx.y, c = threadIdx.x, nblk = gridDim.x;
+  const int pb = min(32, n - j * 32);
+  const T* Dj = LU + (int64_t)(j * 32) + (int64_t)(j * 32) * ld;
+  T x[32];
+  if (tri == 0) {
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr) {
+      T v = rr == c ? T(1.0) : T(0.0);
+      if (rr < pb)
+        for (int k = 0; k < rr; ++k) v = fmsc(v, Dj[rr + (int64_t)k * ld], x[k]);
+      x[rr] = v;
+    }
+  } else {
+#pragma unroll
+    for (int rr = 31; rr >= 0; --rr) {
+      T v = rr == c ? T(1.0) : T(0.0);
+      if (rr < pb) {
+        for (int k = rr + 1; k < pb; ++k) v = fmsc(v, Dj[rr + (int64_t)k * ld], x[k]);
+        const T d = Dj[rr + (int64_t)rr * ld];
+        v = is_zero(d) ? T(0.0) : v * recip(d);
+      }
+      x[rr] = v;
+    }
+  }
+  T* o = out + ((int64_t)tri * nblk + j) * 1024;
+#pragma unroll
+  for (int rr = 0; rr < 32; ++rr) o[rr + 32 * c] = x[rr];
+}
+
 template <typename T>
 bool trsv_flags_applicable(int n, int nrhs, int batch, const TrsvWork& w) {
-  return batch == 1 && nrhs >= 1 && nrhs <= 8 && n >= 128 && w.flags && w.dev_err &&
+  return batch == 1 && nrhs >= 1 && nrhs <= 8 && n >= 128 && w.flags && w.dev_err && w.dinv &&
          (n + 31) / 32 <= w.nflags;
 }
 
@@ -1610,7 +1638,8 @@ cudaError_t launch_trsv_flags(const T* LU, int n, int ld, T* X, int ldx, int nrh
   const unsigned ep = ++w.epoch;
   unsigned* fl = w.flags;
   int* errp = const_cast<int*>(w.dev_err);
-  void* args[] = {(void*)&LU, &ld, &n, &X, &ldx, &nrhs, &fl, (void*)&ep, &errp};
+  const T* dv = static_cast<const T*>(w.dinv) + (UPPER ? (int64_t)nblk * 1024 : 0);
+  void* args[] = {(void*)&LU, &ld, &n, &X, &ldx, &nrhs, (void*)&dv, &fl, (void*)&ep, &errp};
   return cudaLaunchCooperativeKernel((void*)k_trsv_flags<T, NR, UPPER>, dim3(G), dim3(256), args, 0, st);
 }
 
@@ -1628,6 +1657,15 @@ cudaError_t getrs_flags(const T* LU, int n, int ld, T* X, int ldx, int nrhs, Trs
                         Prof* pf) {
   constexpr double F = fma_flops<T>();
   cudaError_t e;
+  if (!w.dinv_ready) {
+    // the diagonal blocks' inverses, once per factor (its storage was sized
+    // with the flags)
+    if (pf) pf->begin(st);
+    k_diag_block_inv<T><<<dim3((n + 31) / 32, 2), 32, 0, st>>>(LU, ld, n, static_cast<T*>(w.dinv));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (pf) pf->end(K_OTHER, 0.0, st);
+    w.dinv_ready = true;
+  }
   if (pf) {
     pf->begin(st);
     pf->note(n, nrhs, 32, 1);

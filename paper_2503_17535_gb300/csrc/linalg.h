@@ -195,6 +195,8 @@ cudaError_t getrs_inplace(BOp<T> LU, int n, BOp<T> X, int nrhs, int batch, cudaS
 struct TrsvWork {
   unsigned* flags = nullptr;
   int nflags = 0;
+  void* dinv = nullptr;        // 2 x nflags inverses of the 32 x 32 diagonal blocks (T)
+  bool dinv_ready = false;     // formed on the first solve with the factor
   unsigned epoch = 0;
   volatile int* host_err = nullptr;  // host-mapped
   volatile int* dev_err = nullptr;   // its device alias
