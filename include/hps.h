@@ -341,13 +341,16 @@ hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double 
  *       = 0), else on the FP64 pipe;
  *   HPS_TUNE_TC_MIN_WORK_CPLX    (5): the same threshold for complex products;
  *   HPS_TUNE_TC_MIN_K            (6): products with an inner dimension below
- *       this stay on the FP64 pipe unless both M and N are at least 512.
+ *       this stay on the FP64 pipe unless both M and N are at least 512;
+ *   HPS_TUNE_TC_CHUNK_MB         (7): MiB of digit slices a batched tensor-core
+ *       product cuts per launch group (the batch is cut into groups of items
+ *       that fit; small groups are still in L2 when the products read them).
  * Every choice gives the same pivots and results up to rounding.  Not to be
  * changed while a build runs.  HPS_ERR_INVALID for an unknown parameter or a
  * value outside 0 .. 2^20. */
 enum { HPS_TUNE_LU_BASE_PANELS_FEW = 0, HPS_TUNE_LU_BASE_PANELS_MANY = 1, HPS_TUNE_LU_FEW_MIN_N = 2,
        HPS_TUNE_LU_CLUSTER_PANEL = 3, HPS_TUNE_TC_MIN_WORK_REAL = 4, HPS_TUNE_TC_MIN_WORK_CPLX = 5,
-       HPS_TUNE_TC_MIN_K = 6 };
+       HPS_TUNE_TC_MIN_K = 6, HPS_TUNE_TC_CHUNK_MB = 7 };
 hps_status hps_tune_set(int param, int value);
 hps_status hps_tune_get(int param, int* value);
 

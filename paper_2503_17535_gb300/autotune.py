@@ -36,6 +36,7 @@ CANDIDATES = {
     "tc_min_work_real": [25, 50, 100, 200, 400],
     "tc_min_work_cplx": [6, 12, 25, 50, 100],
     "tc_min_k": [16, 33, 48, 64, 96],
+    "tc_chunk_mb": [16, 32, 64, 128, 1024],
 }
 MACROS = {
     "lu_base_panels_few": "HPS_TUNED_LU_BASE_PANELS_FEW",
@@ -45,6 +46,7 @@ MACROS = {
     "tc_min_work_real": "HPS_TUNED_TC_MIN_WORK_REAL",
     "tc_min_work_cplx": "HPS_TUNED_TC_MIN_WORK_CPLX",
     "tc_min_k": "HPS_TUNED_TC_MIN_K",
+    "tc_chunk_mb": "HPS_TUNED_TC_CHUNK_MB",
 }
 
 

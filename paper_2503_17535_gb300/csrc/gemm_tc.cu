@@ -646,7 +646,10 @@ cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   const size_t a_sz = z.a_item + z.ea_item, b_sz = z.b_item + z.eb_item;
   const size_t fixed = NP * ((shA ? a_sz : 0) + (shB ? b_sz : 0));
   const size_t per_item = std::max<size_t>(NP * ((shA ? 0 : a_sz) + (shB ? 0 : b_sz)), 1);
-  const size_t room = WS_CAP > fixed ? WS_CAP - fixed : 0;
+  // batch items per launch group: their digit slices stay within the cap
+  // (small enough and they are still in L2 when the products read them)
+  const size_t cap = std::min<size_t>(WS_CAP, (size_t)std::max(lu_tune(TUNE_TC_CHUNK_MB), 1) << 20);
+  const size_t room = cap > fixed ? cap - fixed : 0;
   const int nb_max = (int)std::max<size_t>(1, std::min<size_t>(std::min(g.batch, 65535 / (2 * NP)), room / per_item));
   const size_t na = shA ? 1 : (size_t)nb_max, nbb = shB ? 1 : (size_t)nb_max;
   cudaError_t e = ensure_ws(w, NP * (a_sz * na + b_sz * nbb), st);

@@ -1005,7 +1005,7 @@ int& lu_tune(int param) {
   static int v[TUNE_COUNT] = {HPS_TUNED_LU_BASE_PANELS_FEW, HPS_TUNED_LU_BASE_PANELS_MANY,
                               HPS_TUNED_LU_FEW_MIN_N,       HPS_TUNED_LU_CLUSTER_PANEL,
                               HPS_TUNED_TC_MIN_WORK_REAL,   HPS_TUNED_TC_MIN_WORK_CPLX,
-                              HPS_TUNED_TC_MIN_K};
+                              HPS_TUNED_TC_MIN_K,           HPS_TUNED_TC_CHUNK_MB};
   return v[param];
 }
 

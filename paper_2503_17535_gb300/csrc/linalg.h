@@ -148,7 +148,8 @@ enum LuTuneParam {
   TUNE_TC_MIN_WORK_REAL = 4,     // real products go to the tensor cores from M N K batch >= this x 1e5
   TUNE_TC_MIN_WORK_CPLX = 5,     // complex products: the same threshold
   TUNE_TC_MIN_K = 6,             // products with K below this stay on the FP64 pipe unless M, N >= 512
-  TUNE_COUNT = 7
+  TUNE_TC_CHUNK_MB = 7,          // digit slices of one launch group of a batched product, MiB
+  TUNE_COUNT = 8
 };
 int& lu_tune(int param);
 
