@@ -326,6 +326,27 @@ hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double 
                     int64_t strideA, const void* B, int ldb, int64_t strideB, double beta, void* C, int ldc,
                     int64_t strideC, struct CUstream_st* stream);
 
+/* Batched LU factorisation with partial pivoting, in place (no counterpart in
+ * the paper beyond the merge factor of D in Sec. 3.3 and the leaf
+ * eliminations of Sec. 2.2-2.3, which the paper leaves to its library; this
+ * is the factorisation hps_build runs there, exposed so that callers and
+ * tests can run it alone).  `batch` column-major n x n matrices, item b at
+ * A + b*strideA with leading dimension lda (elements); dtype HPS_F64 or
+ * HPS_C128 (interleaved complex).  On return each item holds L (unit lower,
+ * below the diagonal) and U (upper), and ipiv[b*n + j] (0-based) is the row
+ * interchanged with row j at step j -- LAPACK's getrf convention, with the
+ * same pivot choice: the largest magnitude (|re| + |im| for complex), and on
+ * ties the lowest position in the row order reached so far.  info[b] = 0, or
+ * the first column + 1 whose pivot is exactly zero.  mode 0: trailing
+ * updates on the tensor cores where hps_build would put them; mode 1: FP64
+ * pipe only.  Device pointers only (A, ipiv of batch*n ints, info of batch
+ * ints); enqueued on `stream` and synchronised before return.
+ * HPS_ERR_INVALID for bad sizes, dtype or mode; HPS_ERR_OOM when the
+ * transient workspace cannot be allocated; HPS_ERR_TIMEOUT when a bounded
+ * wait inside a kernel gave up (A is then undefined). */
+hps_status hps_getrf(int dtype, int mode, int n, int batch, void* A, int lda, int64_t strideA, int* ipiv,
+                     int* info, struct CUstream_st* stream);
+
 /* Shape choices of the batched LU and of the product routing (no
  * counterpart in the paper, which factors and multiplies with its library).  Process-wide, read at each factorisation;
  * the defaults come from the autotuner's table (timed builds on GB300).
@@ -344,13 +365,17 @@ hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double 
  *       this stay on the FP64 pipe unless both M and N are at least 512;
  *   HPS_TUNE_TC_CHUNK_MB         (7): MiB of digit slices a batched tensor-core
  *       product cuts per launch group (the batch is cut into groups of items
- *       that fit; small groups are still in L2 when the products read them).
+ *       that fit; small groups are still in L2 when the products read them);
+ *   HPS_TUNE_TC_PERSIST_MIN_K    (8): tensor-core products with an inner
+ *       dimension of at least this run one CTA per SM that walks its tiles
+ *       (copies and products of the next tile overlap the epilogue of the
+ *       last), shorter ones one CTA per tile.
  * Every choice gives the same pivots and results up to rounding.  Not to be
  * changed while a build runs.  HPS_ERR_INVALID for an unknown parameter or a
  * value outside 0 .. 2^20. */
 enum { HPS_TUNE_LU_BASE_PANELS_FEW = 0, HPS_TUNE_LU_BASE_PANELS_MANY = 1, HPS_TUNE_LU_FEW_MIN_N = 2,
        HPS_TUNE_LU_CLUSTER_PANEL = 3, HPS_TUNE_TC_MIN_WORK_REAL = 4, HPS_TUNE_TC_MIN_WORK_CPLX = 5,
-       HPS_TUNE_TC_MIN_K = 6, HPS_TUNE_TC_CHUNK_MB = 7 };
+       HPS_TUNE_TC_MIN_K = 6, HPS_TUNE_TC_CHUNK_MB = 7, HPS_TUNE_TC_PERSIST_MIN_K = 8 };
 hps_status hps_tune_set(int param, int value);
 hps_status hps_tune_get(int param, int* value);
 

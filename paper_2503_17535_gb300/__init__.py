@@ -533,6 +533,33 @@ def hps_gemm(A, B, C, alpha: float = 1.0, beta: float = 0.0, mode: int = 0, stre
     return C
 
 
+def hps_getrf(A, ipiv=None, info=None, mode: int = 0, stream=None):
+    """LU with partial pivoting, in place, of a batch of column-major n x n
+    matrices held as a contiguous device tensor of shape (batch, n, n) (each
+    item's columns contiguous), float64 or complex128: LAPACK's getrf
+    convention (unit L below the diagonal, U on and above it, 0-based
+    interchanges).  Returns (A, ipiv, info) with ipiv (batch, n) and info
+    (batch,) int32 device tensors.  mode 0: trailing updates on the tensor
+    cores as in hps_build; mode 1: FP64 pipe only.  Synchronises the stream."""
+    import torch
+    if not _is_torch(A) or A.dim() != 3 or A.shape[1] != A.shape[2]:
+        raise ValueError("hps_getrf: A must be a (batch, n, n) device tensor")
+    batch, n, _ = A.shape
+    cp = A.is_complex()
+    if ipiv is None:
+        ipiv = torch.empty((batch, n), dtype=torch.int32, device=A.device)
+    if info is None:
+        info = torch.empty((batch,), dtype=torch.int32, device=A.device)
+    for t, nm, cnt in ((ipiv, "ipiv", batch * n), (info, "info", batch)):
+        if not _is_torch(t) or t.dtype != torch.int32 or not t.is_contiguous() or t.numel() != cnt:
+            raise ValueError(f"hps_getrf: {nm} must be a contiguous int32 device tensor of {cnt} elements")
+    keep: list = []
+    ap = _ptr(A, cp, A.numel(), "A", keep)
+    _check(_capi.lib().hps_getrf(HPS_C128 if cp else HPS_F64, int(mode), n, batch, ap, max(n, 1), n * n,
+                                 ipiv.data_ptr(), info.data_ptr(), _stream(stream)), "hps_getrf")
+    return A, ipiv, info
+
+
 def hps_debug_fail_alloc(n: int) -> None:
     """Fault injection for tests: the n-th handle allocation from now on fails
     as out-of-memory (host side); n <= 0 disarms."""
@@ -555,7 +582,7 @@ def hps_debug_wait_timeout(which: int, satisfied: bool, limit_polls: int, stream
 
 TUNE_PARAMS = {"lu_base_panels_few": 0, "lu_base_panels_many": 1, "lu_few_min_n": 2, "lu_cluster_panel": 3,
                "tc_min_work_real": 4, "tc_min_work_cplx": 5, "tc_min_k": 6,
-               "tc_chunk_mb": 7}
+               "tc_chunk_mb": 7, "tc_persist_min_k": 8}
 
 
 def hps_tune_set(name: str, value: int) -> None:

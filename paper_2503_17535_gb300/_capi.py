@@ -22,7 +22,7 @@ EXPORTED = [
     "hps_nodes", "hps_sizes", "hps_build", "hps_solve", "hps_solve_batched", "hps_solve_multi", "hps_free",
     "hps_error_string", "hps_last_error_detail", "hps_device_bytes", "hps_last_launch_count",
     "hps_kernel_stats", "hps_set_profiling", "hps_solve_noalloc", "hps_refine", "hps_trace_count",
-    "hps_trace_get", "hps_plan_bytes", "hps_solve_adjoint", "hps_coeff_gradient", "hps_gemm",
+    "hps_trace_get", "hps_plan_bytes", "hps_solve_adjoint", "hps_coeff_gradient", "hps_gemm", "hps_getrf",
     "hps_debug_fail_alloc", "hps_debug_alloc_count", "hps_debug_wait_timeout",
     "hps_tune_set", "hps_tune_get",
     # request server (include/hps_serve.h)
@@ -133,6 +133,8 @@ def lib() -> ctypes.CDLL:
     L.hps_gemm.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, c_double, c_void_p, c_int, c_int64,
                            c_void_p, c_int, c_int64, c_double, c_void_p, c_int, c_int64, c_void_p]
     L.hps_gemm.restype = c_int
+    L.hps_getrf.argtypes = [c_int, c_int, c_int, c_int, c_void_p, c_int, c_int64, c_void_p, c_void_p, c_void_p]
+    L.hps_getrf.restype = c_int
     L.hps_debug_fail_alloc.argtypes = [c_int64]
     L.hps_debug_fail_alloc.restype = None
     L.hps_debug_alloc_count.argtypes = []

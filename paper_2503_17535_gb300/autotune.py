@@ -11,7 +11,7 @@ writes the setting with the smallest summed median build time to tuned.h.
 Every setting gives the same factorisation up to rounding (same pivots), so
 only time is compared.
 
-    python -m paper_2503_17535_gb300.autotune [--out PATH] [--reps 3]
+    python -m paper_2503_17535_gb300.autotune [--out PATH] [--reps 3] [--params a,b]
 
 Needs a GPU; rebuild the library afterwards to make the values the defaults.
 """
@@ -37,6 +37,7 @@ CANDIDATES = {
     "tc_min_work_cplx": [6, 12, 25, 50, 100],
     "tc_min_k": [16, 33, 48, 64, 96],
     "tc_chunk_mb": [16, 32, 64, 128, 1024],
+    "tc_persist_min_k": [0, 48, 64, 128, 1 << 20],
 }
 MACROS = {
     "lu_base_panels_few": "HPS_TUNED_LU_BASE_PANELS_FEW",
@@ -47,6 +48,7 @@ MACROS = {
     "tc_min_work_cplx": "HPS_TUNED_TC_MIN_WORK_CPLX",
     "tc_min_k": "HPS_TUNED_TC_MIN_K",
     "tc_chunk_mb": "HPS_TUNED_TC_CHUNK_MB",
+    "tc_persist_min_k": "HPS_TUNED_TC_PERSIST_MIN_K",
 }
 
 
@@ -126,7 +128,13 @@ def main():
     ap.add_argument("--log", default=None, help="write every measurement (JSON) to this path")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--passes", type=int, default=2)
+    ap.add_argument("--params", default=None,
+                    help="comma-separated parameters to tune (default: all); the others keep their values")
     args = ap.parse_args()
+    tuned = list(CANDIDATES) if not args.params else args.params.split(",")
+    for k in tuned:
+        if k not in CANDIDATES:
+            raise SystemExit(f"unknown parameter {k}; known: {', '.join(CANDIDATES)}")
     import torch
     import paper_2503_17535_gb300 as P
     if not torch.cuda.is_available():
@@ -140,8 +148,8 @@ def main():
     best_total = sum(cur.values())
     print("start", best, round(best_total, 1), flush=True)
     for _ in range(args.passes):
-        for k, values in CANDIDATES.items():
-            for v in values:
+        for k in tuned:
+            for v in CANDIDATES[k]:
                 if v == best[k]:
                     continue
                 trial = dict(best)

@@ -45,11 +45,25 @@ __host__ __device__ inline double mag1(double a) { return fabs(a); }
 __host__ __device__ inline double mag1(cplx a) { return fabs(a.re) + fabs(a.im); }
 __host__ __device__ inline double recip(double a) { return 1.0 / a; }
 __host__ __device__ inline cplx recip(cplx a) {
-  // 1/(x+iy) = (x - iy)/(x^2+y^2), with scaling by the larger component
-  double s = fmax(fabs(a.re), fabs(a.im));
-  double xr = a.re / s, xi = a.im / s;
-  double d = s * (xr * xr + xi * xi);
-  return cplx(xr / d, -xi / d);
+  // 1/(x+iy) = (x - iy)/(x^2+y^2).  On the device x and y are first scaled by
+  // the power of two 2^-e that brings max(|x|, |y|) into [1, 2) (exact), so
+  // that the squared magnitude can neither overflow nor underflow and one
+  // division suffices (the FP64 pipe is the scarce unit here); extreme
+  // exponents, and the host, scale by the larger component instead.
+#ifdef __CUDA_ARCH__
+  const double s = fmax(fabs(a.re), fabs(a.im));
+  const int eb = (int)((__double_as_longlong(s) >> 52) & 0x7ff);   // biased exponent of s
+  if (eb >= 64 && eb <= 1982) {
+    const double sc = __longlong_as_double((long long)(2046 - eb) << 52);   // 2^(1023 - eb)
+    const double xr = a.re * sc, xi = a.im * sc;
+    const double r = sc / fma(xr, xr, xi * xi);
+    return cplx(xr * r, -xi * r);
+  }
+#endif
+  double s2 = fmax(fabs(a.re), fabs(a.im));
+  double xr2 = a.re / s2, xi2 = a.im / s2;
+  double d = s2 * (xr2 * xr2 + xi2 * xi2);
+  return cplx(xr2 / d, -xi2 / d);
 }
 __host__ __device__ inline bool is_zero(double a) { return a == 0.0; }
 __host__ __device__ inline bool is_zero(cplx a) { return a.re == 0.0 && a.im == 0.0; }

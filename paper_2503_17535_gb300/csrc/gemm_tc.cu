@@ -63,7 +63,8 @@ constexpr int BSTG = DIG * BBLK;
 constexpr int STAGE = ASTG + BSTG;
 constexpr int QGRP = 5;             // B digits stacked into one MMA (N = 5 * 48 = 240 <= 256)
 constexpr int NST = 3;
-constexpr int CSTG = TN * TM * 8;     // the C tile staged for the epilogue (column-major)
+constexpr int TMP = TM + 1;          // C staging row stride (odd: transposed reads spread over banks)
+constexpr int CSTG = TN * TMP * 8;    // the C tile staged for the epilogue (column-major)
 constexpr int SMEM = NST * STAGE + CSTG;
 constexpr int TMEM_COLS = 512;
 constexpr int EPI_WARPS = 8;        // two per TMEM lane quarter, each half of the tile's columns
@@ -273,19 +274,26 @@ struct GemmP {
   int cpart;           // complex C: component written (0 re, 1 im)
   int b0;              // first batch item of this launch
   int a_bl, b_bl;      // 1, or 0 for an operand whose digits serve every item
+  int nitems;          // batch items of this launch (tiles: MT NT nitems)
   unsigned* err;
 };
 
-template <typename T, bool BETA0>
+template <typename T, bool BETA0, bool TRANS>
 __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
+  // Persistent: CTA c takes the tiles c, c + gridDim.x, ... of the launch
+  // (tile t = item t / (MT NT), then row tile, then column tile), so that the
+  // next tile's copies and products overlap this tile's epilogue and the
+  // TMEM allocation and barrier set-up happen once per CTA.  The stage ring,
+  // the accumulator hand-over (acc_full / acc_empty) and their phases run on
+  // across tiles.
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[NST], empty[NST], acc_full, acc_empty;
   __shared__ int s_eb[TN];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bl = blockIdx.y;
-  const int mt = blockIdx.x % g.MT, nt = blockIdx.x / g.MT;
+  const int tiles_item = g.MT * g.NT;
+  const int ntiles = tiles_item * g.nitems;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)),
                  "r"(TMEM_COLS));
@@ -310,69 +318,84 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
   const uint32_t sbase = su32(smem);
 
   if (warp == EPI_WARPS) {
-    // producer: one bulk copy per operand per k step
+    // producer: one bulk copy per operand per k step, the ring running on
+    // across tiles
     if (lane == 0) {
-      const uint8_t* a_src = g.As + ((int64_t)(bl * g.a_bl) * g.MT + mt) * g.KT * (int64_t)ASTG;
-      const uint8_t* b_src = g.Bs + ((int64_t)(bl * g.b_bl) * g.NT + nt) * g.KT * (int64_t)BSTG;
-      for (int it = 0; it < g.KT; ++it) {
-        const int s = it % NST;
-        if (it >= NST && !mbar_wait(su32(&empty[s]), ((it / NST) & 1) ^ 1, abrt)) {
-          *abrt = 1;
-          atomicOr(g.err, DEV_ERR_TIMEOUT);
-          break;
+      long it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int bl = t / tiles_item, rem = t % tiles_item;
+        const int mt = rem % g.MT, nt = rem / g.MT;
+        const uint8_t* a_src = g.As + ((int64_t)(bl * g.a_bl) * g.MT + mt) * g.KT * (int64_t)ASTG;
+        const uint8_t* b_src = g.Bs + ((int64_t)(bl * g.b_bl) * g.NT + nt) * g.KT * (int64_t)BSTG;
+        for (int k = 0; k < g.KT; ++k, ++it) {
+          const int s = (int)(it % NST);
+          if (it >= NST && !mbar_wait(su32(&empty[s]), (int)((it / NST) & 1) ^ 1, abrt)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = su32(&full[s]), dst = sbase + s * STAGE;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE) : "memory");
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       ::"r"(dst), "l"(a_src + (int64_t)k * ASTG), "r"(ASTG), "r"(fb) : "memory");
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       ::"r"(dst + ASTG), "l"(b_src + (int64_t)k * BSTG), "r"(BSTG), "r"(fb) : "memory");
         }
-        const uint32_t fb = su32(&full[s]), dst = sbase + s * STAGE;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(STAGE) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(dst), "l"(a_src + (int64_t)it * ASTG), "r"(ASTG), "r"(fb) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(dst + ASTG), "l"(b_src + (int64_t)it * BSTG), "r"(BSTG), "r"(fb) : "memory");
+      }
+      if (!ok) {
+        *abrt = 1;
+        atomicOr(g.err, DEV_ERR_TIMEOUT);
       }
     }
   } else if (warp == EPI_WARPS + 1) {
-    // MMA issue: 53 digit-pair products per k step into the 10 diagonal accumulators
+    // MMA issue: 55 digit-pair products per k step into the 10 diagonal accumulators
     if (lane == 0) {
       // B's digit blocks lie one after another with the same row-group stride,
       // so digits q0 .. q0+n-1 form one operand of n * 48 rows, and A_p times
       // it lands in the accumulators of diagonals p+q0 .. p+q0+n-1, which are
       // adjacent in TMEM: one MMA (N <= 240) per (p, group of <= 5 digits).
       const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TM >> 4) << 24);
-      int it = 0;
+      long it = 0, cc = 0;   // k steps and accumulator chunks issued so far
       bool ok = true;
-      for (int c = 0; c < nchunk && ok; ++c) {
-        if (c > 0 && !mbar_wait(su32(&acc_empty), (c - 1) & 1, abrt)) { ok = false; break; }
-        fence_after();
-        const int kbeg = it, kend = min(g.KT, (c + 1) * KCT);
-        for (; it < kend; ++it) {
-          const int s = it % NST;
-          if (!mbar_wait(su32(&full[s]), (it / NST) & 1, abrt)) { ok = false; break; }
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int kk = 0;
+        for (int c = 0; c < nchunk && ok; ++c, ++cc) {
+          // the epilogue has read the previous chunk's accumulators
+          if (cc > 0 && !mbar_wait(su32(&acc_empty), (int)((cc - 1) & 1), abrt)) { ok = false; break; }
           fence_after();
-          const uint32_t a0 = sbase + s * STAGE, b0 = a0 + ASTG;
+          const int kend = min(g.KT, (c + 1) * KCT);
+          const int kbeg = kk;
+          for (; kk < kend; ++kk, ++it) {
+            const int s = (int)(it % NST);
+            if (!mbar_wait(su32(&full[s]), (int)((it / NST) & 1), abrt)) { ok = false; break; }
+            fence_after();
+            const uint32_t a0 = sbase + s * STAGE, b0 = a0 + ASTG;
 #pragma unroll
-          for (int p = 0; p < DIG; ++p) {
-            const uint64_t ad = sdesc(a0 + p * ABLK, 128, 256);
-            const int nq_all = (DSUM - 1 - p) < DIG ? (DSUM - 1 - p) : DIG;   // q = 0 .. nq_all-1
+            for (int p = 0; p < DIG; ++p) {
+              const uint64_t ad = sdesc(a0 + p * ABLK, 128, 256);
+              const int nq_all = (DSUM - 1 - p) < DIG ? (DSUM - 1 - p) : DIG;   // q = 0 .. nq_all-1
 #pragma unroll
-            for (int q0 = 0; q0 < nq_all; q0 += QGRP) {
-              const int nq = (nq_all - q0) < QGRP ? (nq_all - q0) : QGRP;
-              // the first k step of a chunk overwrites: p = 0 covers every diagonal once
-              const uint32_t acc = (it != kbeg || p != 0) ? 1u : 0u;
-              const uint64_t bd = sdesc(b0 + q0 * BBLK, 128, 256);
-              const uint32_t idesc = idesc0 | ((uint32_t)((nq * TN) >> 3) << 17);
-              asm volatile(
-                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)((p + q0) * TN)),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              for (int q0 = 0; q0 < nq_all; q0 += QGRP) {
+                const int nq = (nq_all - q0) < QGRP ? (nq_all - q0) : QGRP;
+                // the first k step of a chunk overwrites: p = 0 covers every diagonal once
+                const uint32_t acc = (kk != kbeg || p != 0) ? 1u : 0u;
+                const uint64_t bd = sdesc(b0 + q0 * BBLK, 128, 256);
+                const uint32_t idesc = idesc0 | ((uint32_t)((nq * TN) >> 3) << 17);
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)((p + q0) * TN)),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              }
             }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(&empty[s]))
+                         : "memory");
           }
+          if (!ok) break;
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           su32(&empty[s]))
+                           su32(&acc_full))
                        : "memory");
         }
-        if (!ok) break;
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         su32(&acc_full))
-                     : "memory");
       }
       if (!ok) {
         *abrt = 1;
@@ -383,31 +406,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
     // epilogue: warp w reads TMEM lane quarter w % 4 (its rows) and column
     // half w / 4; thread = row, 24 fixed-point sums.  While the MMAs run, the
     // C tile (beta != 0) and the columns' exponents are staged in shared
-    // memory with asynchronous copies.
+    // memory with asynchronous copies.  A transposed tile (rows of C^T are
+    // C's columns) is staged and stored by all epilogue threads with the tile
+    // column fastest, so that its global accesses stay coalesced, and each
+    // thread's results pass through shared memory.  Every epilogue thread
+    // runs the same tiles and the same named barriers; after a wait gives up
+    // it skips the remaining waits and stores but still takes the barriers.
     const int quarter = warp & 3, c0 = (warp >> 2) * ECOLS;
     const int row = quarter * 32 + lane;
-    const int i = mt * TM + row;
-    const int b = g.b0 + bl;
-    double* Cb = reinterpret_cast<double*>(g.C.item(b));
-    constexpr int W = (int)(sizeof(T) / sizeof(double));
-    const int64_t ci = i < g.M ? (int64_t)g.crow.at(b, i) : 0;
     double* s_c = reinterpret_cast<double*>(smem + NST * STAGE);
-    if (threadIdx.x < TN)
-      s_eb[threadIdx.x] = nt * TN + threadIdx.x < g.N ? row_exp(g.eb[(int64_t)(bl * g.b_bl) * g.NT * TN + nt * TN + threadIdx.x]) : 0;
-    if (!BETA0 && i < g.M) {
-#pragma unroll 4
-      for (int j = c0; j < c0 + ECOLS; ++j) {
-        const int col = nt * TN + j;
-        if (col >= g.N) break;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(s_c + j * TM + row)),
-                     "l"(Cb + (ci + (int64_t)col * g.C.ld) * W + g.cpart)
-                     : "memory");
-      }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    long long R[ECOLS];
-#pragma unroll
-    for (int j = 0; j < ECOLS; ++j) R[j] = 0;
+    constexpr int SLD = TRANS ? TMP : TM;   // staging stride
+    constexpr int W = (int)(sizeof(T) / sizeof(double));
+    const int etid = threadIdx.x;   // 0 .. 32 * EPI_WARPS - 1
     // diagonal d = di + 2 has weight 2^{-6d}; R counts units of 2^{-lsb}.
     // Adjacent diagonals pair up exactly in 32 bits (y = x_d * 64 + x_{d+1},
     // |y| < 2^29), the pairs of d = 2..7 form H (units 2^{-42}) and those of
@@ -415,66 +425,126 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
     // rounded once.  lsb is at least 42 (K <= 2^20).
     const int shH = g.lsb - 42, shL = 66 - g.lsb;
     const long long halfL = 1ll << (shL - 1);
+    const bool amode1 = g.amode == 1, beta1 = g.beta == 1.0;
     bool ok = true;
-    for (int c = 0; c < nchunk; ++c) {
-      if (!mbar_wait(su32(&acc_full), c & 1, abrt)) { ok = false; break; }
-      fence_after();
+    long cc = 0;   // accumulator chunks consumed so far
+    bool first = true;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int bl = t / tiles_item, rem = t % tiles_item;
+      const int mt = rem % g.MT, nt = rem / g.MT;
+      const int i = mt * TM + row;
+      const int b = g.b0 + bl;
+      double* Cb = reinterpret_cast<double*>(g.C.item(b));
+      const int64_t ci = (!TRANS && i < g.M) ? (int64_t)g.crow.at(b, i) : 0;
+      // the previous tile's conversion has finished with s_eb and s_c
+      if (!first) asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");
+      first = false;
+      if (threadIdx.x < TN)
+        s_eb[threadIdx.x] = nt * TN + threadIdx.x < g.N ? row_exp(g.eb[(int64_t)(bl * g.b_bl) * g.NT * TN + nt * TN + threadIdx.x]) : 0;
+      // the old C values of a normal tile go straight to registers (issued
+      // now, they arrive while the products finish); a transposed tile's are
+      // staged in shared memory, tile column fastest
+      double cold[ECOLS];
+      if constexpr (!TRANS) {
+        if (!BETA0 && ok && i < g.M) {
 #pragma unroll
-      for (int cg = 0; cg < ECOLS / 4; ++cg) {
-        uint32_t v[NDIAG][4];
-#pragma unroll
-        for (int di = 0; di < NDIAG; ++di) {
-          const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(di * TN + c0 + cg * 4);
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                       : "=r"(v[di][0]), "=r"(v[di][1]), "=r"(v[di][2]), "=r"(v[di][3])
-                       : "r"(ta));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          // an fp32 holding an integer below 2^22, plus 1.5 * 2^23, has the
-          // integer in its low mantissa bits: x = bits - 0x4B400000
-          int y[NDIAG / 2];
-#pragma unroll
-          for (int k = 0; k < NDIAG / 2; ++k) {
-            const uint32_t a = __float_as_uint(__uint_as_float(v[2 * k][j]) + 12582912.0f);
-            const uint32_t c2 = __float_as_uint(__uint_as_float(v[2 * k + 1][j]) + 12582912.0f);
-            y[k] = (int)(a * 64u + c2 - 65u * 0x4B400000u);
+          for (int jj = 0; jj < ECOLS; ++jj) {
+            const int col = nt * TN + c0 + jj;
+            cold[jj] = col < g.N ? Cb[(ci + (int64_t)col * g.C.ld) * W + g.cpart] : 0.0;
           }
-          const long long H = ((long long)y[0] << 24) + ((long long)y[1] << 12) + (long long)y[2];
-          const long long L = ((long long)y[3] << 12) + (long long)y[4];
-          R[cg * 4 + j] += (H << shH) + ((L + halfL) >> shL);
         }
       }
-      fence_before();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&acc_empty)) : "memory");
+      if (!BETA0 && ok) {
+        if constexpr (TRANS) {
+          for (int e2 = etid; e2 < TM * TN; e2 += 32 * EPI_WARPS) {
+            const int j = e2 % TN, r = e2 / TN;
+            const int crw = nt * TN + j, ccol = mt * TM + r;
+            if (crw < g.N && ccol < g.M)
+              asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(s_c + j * TMP + r)),
+                           "l"(Cb + ((int64_t)g.crow.at(b, crw) + (int64_t)ccol * g.C.ld) * W + g.cpart)
+                           : "memory");
+          }
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      long long R[ECOLS];
+#pragma unroll
+      for (int j = 0; j < ECOLS; ++j) R[j] = 0;
+      for (int c = 0; c < nchunk; ++c, ++cc) {
+        if (!ok) continue;
+        if (!mbar_wait(su32(&acc_full), (int)(cc & 1), abrt)) { ok = false; continue; }
+        fence_after();
+#pragma unroll
+        for (int cg = 0; cg < ECOLS / 4; ++cg) {
+          uint32_t v[NDIAG][4];
+#pragma unroll
+          for (int di = 0; di < NDIAG; ++di) {
+            const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(di * TN + c0 + cg * 4);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(v[di][0]), "=r"(v[di][1]), "=r"(v[di][2]), "=r"(v[di][3])
+                         : "r"(ta));
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            // an fp32 holding an integer below 2^22, plus 1.5 * 2^23, has the
+            // integer in its low mantissa bits: x = bits - 0x4B400000
+            int y[NDIAG / 2];
+#pragma unroll
+            for (int k = 0; k < NDIAG / 2; ++k) {
+              const uint32_t a = __float_as_uint(__uint_as_float(v[2 * k][j]) + 12582912.0f);
+              const uint32_t c2 = __float_as_uint(__uint_as_float(v[2 * k + 1][j]) + 12582912.0f);
+              y[k] = (int)(a * 64u + c2 - 65u * 0x4B400000u);
+            }
+            const long long H = ((long long)y[0] << 24) + ((long long)y[1] << 12) + (long long)y[2];
+            const long long L = ((long long)y[3] << 12) + (long long)y[4];
+            R[cg * 4 + j] += (H << shH) + ((L + halfL) >> shL);
+          }
+        }
+        fence_before();
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&acc_empty)) : "memory");
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");   // s_eb and s_c from other epilogue threads
+      if (ok && i < g.M) {
+        const int er = row_exp(g.ea[(int64_t)(bl * g.a_bl) * g.MT * TM + i]);
+#pragma unroll
+        for (int jj = 0; jj < ECOLS; ++jj) {
+          const int j = c0 + jj;
+          const int col = nt * TN + j;
+          if (col >= g.N) break;
+          double val = fixed_to_double(R[jj], er + s_eb[j] - g.lsb);
+          double* sp = s_c + j * SLD + row;
+          double c_old = 0.0;
+          if constexpr (!BETA0) c_old = TRANS ? *sp : cold[jj];
+          double out;
+          if (amode1) {                // alpha = +-1: a sign flip
+            val = __longlong_as_double(__double_as_longlong(val) ^ g.asign);
+            if (BETA0) out = val;
+            else if (beta1) out = c_old + val;
+            else out = fma(g.beta, c_old, val);
+          } else {
+            if (BETA0) out = g.alpha * val;
+            else out = fma(g.alpha, val, g.beta * c_old);
+          }
+          if constexpr (!TRANS) Cb[(ci + (int64_t)col * g.C.ld) * W + g.cpart] = out;
+          else *sp = out;
+        }
+      }
+      if constexpr (TRANS) {
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");
+        if (ok)
+          for (int e2 = etid; e2 < TM * TN; e2 += 32 * EPI_WARPS) {
+            const int j = e2 % TN, r = e2 / TN;
+            const int crw = nt * TN + j, ccol = mt * TM + r;
+            if (crw < g.N && ccol < g.M)
+              Cb[((int64_t)g.crow.at(b, crw) + (int64_t)ccol * g.C.ld) * W + g.cpart] = s_c[j * TMP + r];
+          }
+      }
     }
     if (!ok) {
       *abrt = 1;
       atomicOr(g.err, DEV_ERR_TIMEOUT);
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    asm volatile("bar.sync 1, %0;" ::"r"(32 * EPI_WARPS) : "memory");   // s_eb from other epilogue warps
-    const bool amode1 = g.amode == 1, beta1 = g.beta == 1.0;
-    if (ok && i < g.M) {
-      const int er = row_exp(g.ea[(int64_t)(bl * g.a_bl) * g.MT * TM + i]);
-#pragma unroll
-      for (int jj = 0; jj < ECOLS; ++jj) {
-        const int j = c0 + jj;
-        const int col = nt * TN + j;
-        if (col >= g.N) break;
-        double val = fixed_to_double(R[jj], er + s_eb[j] - g.lsb);
-        double* cp = Cb + (ci + (int64_t)col * g.C.ld) * W + g.cpart;
-        if (amode1) {                // alpha = +-1: a sign flip
-          val = __longlong_as_double(__double_as_longlong(val) ^ g.asign);
-          if (BETA0) *cp = val;
-          else if (beta1) *cp = s_c[j * TM + row] + val;
-          else *cp = fma(g.beta, s_c[j * TM + row], val);
-        } else {
-          if (BETA0) *cp = g.alpha * val;
-          else *cp = fma(g.alpha, val, g.beta * s_c[j * TM + row]);
-        }
-      }
     }
   }
   fence_before();
@@ -499,11 +569,11 @@ int ceil_log2(int64_t x) {
   return c;
 }
 
-template <typename T, bool BETA0>
+template <typename T, bool BETA0, bool TRANS>
 void set_smem_attr() {
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_gemm_tc<T, BETA0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    cudaFuncSetAttribute(k_gemm_tc<T, BETA0, TRANS>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   });
 }
 
@@ -540,12 +610,28 @@ void tc_release(TcWorkspace* w) {
   if (w) { w->p = nullptr; w->bytes = 0; }
 }
 
+// Fraction of the 128 x 48 output tiles that holds the product, in the
+// better of the two orientations.
+static double tile_fill(int M, int N) {
+  using namespace tc;
+  const double mn = (double)M * N;
+  const double normal = (double)((M + TM - 1) / TM) * TM * ((N + TN - 1) / TN) * TN;
+  const double trans = (double)((N + TM - 1) / TM) * TM * ((M + TN - 1) / TN) * TN;
+  return mn / std::min(normal, trans);
+}
+
 template <typename T>
 bool tc_applicable(const GemmArgs<T>& g) {
   const TcWorkspace* w = tc_workspace();
   if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta || g.K > (1 << 20)) return false;
   if (w->force) return true;
-  if (g.M < 32 || g.N < 16 || g.K < 16) return false;
+  // one side of at least 32 and the other of at least 16: the short side
+  // goes to the 48-wide tile dimension (transposed tiling when M is short)
+  if (std::min(g.M, g.N) < 16 || std::max(g.M, g.N) < 32 || g.K < 16) return false;
+  // a side below 32 fills at best two thirds of the 48-wide tile side: such
+  // products go to the tensor cores only while the tiles stay over ~28 % full
+  // (measured: 28 x 113 gains there, 28 x 57 loses)
+  if (std::min(g.M, g.N) < 32 && tile_fill(g.M, g.N) < 0.28) return false;
   // short inner dimensions: ten accumulators per output are read back for
   // little work, so small items stay on the FP64 pipe
   if (g.K < lu_tune(TUNE_TC_MIN_K) && (g.M < 512 || g.N < 512)) return false;
@@ -559,7 +645,8 @@ bool tc_applicable<cplx>(const GemmArgs<cplx>& g) {
   if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta || g.K > (1 << 20)) return false;
   if (g.alpha.im != 0.0 || g.beta.im != 0.0) return false;
   if (w->force) return true;
-  if (g.M < 32 || g.N < 16 || g.K < 16) return false;
+  if (std::min(g.M, g.N) < 16 || std::max(g.M, g.N) < 32 || g.K < 16) return false;
+  if (std::min(g.M, g.N) < 32 && tile_fill(g.M, g.N) < 0.28) return false;
   if (g.K < lu_tune(TUNE_TC_MIN_K) && (g.M < 512 || g.N < 512)) return false;
   if ((double)g.M * g.N * g.K * g.batch < 1.0e5 * lu_tune(TUNE_TC_MIN_WORK_CPLX)) return false;
   return true;
@@ -605,19 +692,26 @@ void launch_split(const tc::SplitSet<T>& ss, int nops, int K, int KT, int b0, in
 }
 
 template <typename T>
-void launch_mma(const tc::GemmP<T>& p, int nb, int K, cudaStream_t st, Prof* pf) {
+void launch_mma(const tc::GemmP<T>& p, bool trans, int nb, int M, int N, int K, cudaStream_t st, Prof* pf) {
   if (pf) {
     pf->begin(st);
-    pf->note(p.M, p.N, K, nb);
+    pf->note(M, N, K, nb);
   }
-  dim3 grid(p.MT * p.NT, nb);
-  if (p.beta == 0.0) {
-    tc::set_smem_attr<T, true>();
-    tc::k_gemm_tc<T, true><<<grid, tc::THREADS, tc::SMEM, st>>>(p);
-  } else {
-    tc::set_smem_attr<T, false>();
-    tc::k_gemm_tc<T, false><<<grid, tc::THREADS, tc::SMEM, st>>>(p);
-  }
+  // persistent (from the tuned inner dimension on): at most one CTA per SM,
+  // which the shared-memory ring and the TMEM accumulators allow anyway; else
+  // one CTA per tile
+  const int64_t ntiles = (int64_t)p.MT * p.NT * nb;
+  const bool persist = K >= lu_tune(TUNE_TC_PERSIST_MIN_K);
+  dim3 grid((unsigned)(persist ? std::min<int64_t>(ntiles, device_sms()) : ntiles));
+  auto go = [&](auto beta0, auto trans) {
+    constexpr bool B0 = decltype(beta0)::value, TR = decltype(trans)::value;
+    tc::set_smem_attr<T, B0, TR>();
+    tc::k_gemm_tc<T, B0, TR><<<grid, tc::THREADS, tc::SMEM, st>>>(p);
+  };
+  using t_ = std::true_type;
+  using f_ = std::false_type;
+  if (p.beta == 0.0) { if (trans) go(t_(), t_()); else go(t_(), f_()); }
+  else { if (trans) go(f_(), t_()); else go(f_(), f_()); }
   // executed: bf16 tensor-core flops of the digit products over the padded tiles
   const double npairs = tc::npairs();
   const double exec = 2.0 * npairs * (double)p.MT * tc::TM * (double)p.NT * tc::TN * (double)p.KT * tc::TK * nb;
@@ -635,27 +729,48 @@ bool shared_operand(const BOp<T>& X, const IMap& r, const IMap& k) {
          (!k.idx || k.period == 1);
 }
 
+// Orientation of the output tiles: C = A B in 128 x 48 tiles of C, or
+// C^T = B^T A^T in 128 x 48 tiles of C^T (48-row tiles of C), the latter
+// when it takes a quarter fewer waves of tiles over the SMs -- a product with few rows (the
+// 32-row updates of the recursive LU and triangular solves, M = 32..64)
+// wastes most of a 128-row tile but fits a 48-column one; a grid that fits
+// in one wave either way stays in the normal form.
+static bool tc_transposed(int M, int N, int batch) {
+  using namespace tc;
+  const int64_t sms = device_sms();
+  const int64_t normal = (int64_t)((M + TM - 1) / TM) * ((N + TN - 1) / TN) * batch;
+  const int64_t trans = (int64_t)((N + TM - 1) / TM) * ((M + TN - 1) / TN) * batch;
+  // one CTA per SM: the time goes with the number of waves of tiles; the
+  // transposed epilogue (staged through shared memory) costs more per tile,
+  // so it has to save at least a quarter of the waves
+  return 4 * ((trans + sms - 1) / sms) <= 3 * ((normal + sms - 1) / sms);
+}
+
 template <typename T>
 cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   using namespace tc;
   constexpr int NP = std::is_same<T, cplx>::value ? 2 : 1;
   TcWorkspace* w = tc_workspace();
-  const Sizes z = sizes(g.M, g.N, g.K);
+  const bool tr = tc_transposed(g.M, g.N, g.batch);
+  // rows of the A slot (the 128-row tiles) and of the B slot (48-row tiles)
+  const int Ma = tr ? g.N : g.M, Nb = tr ? g.M : g.N;
+  const Sizes z = sizes(Ma, Nb, g.K);
   const bool shA = g.batch > 1 && shared_operand(g.A, g.arow, g.acol);
   const bool shB = g.batch > 1 && shared_operand(g.B, g.brow, IMap());
+  const bool shSa = tr ? shB : shA, shSb = tr ? shA : shB;   // per slot
   const size_t a_sz = z.a_item + z.ea_item, b_sz = z.b_item + z.eb_item;
-  const size_t fixed = NP * ((shA ? a_sz : 0) + (shB ? b_sz : 0));
-  const size_t per_item = std::max<size_t>(NP * ((shA ? 0 : a_sz) + (shB ? 0 : b_sz)), 1);
+  const size_t fixed = NP * ((shSa ? a_sz : 0) + (shSb ? b_sz : 0));
+  const size_t per_item = std::max<size_t>(NP * ((shSa ? 0 : a_sz) + (shSb ? 0 : b_sz)), 1);
   // batch items per launch group: their digit slices stay within the cap
   // (small enough and they are still in L2 when the products read them)
   const size_t cap = std::min<size_t>(WS_CAP, (size_t)std::max(lu_tune(TUNE_TC_CHUNK_MB), 1) << 20);
   const size_t room = cap > fixed ? cap - fixed : 0;
   const int nb_max = (int)std::max<size_t>(1, std::min<size_t>(std::min(g.batch, 65535 / (2 * NP)), room / per_item));
-  const size_t na = shA ? 1 : (size_t)nb_max, nbb = shB ? 1 : (size_t)nb_max;
+  const size_t na = shSa ? 1 : (size_t)nb_max, nbb = shSb ? 1 : (size_t)nb_max;
   cudaError_t e = ensure_ws(w, NP * (a_sz * na + b_sz * nbb), st);
   if (e != cudaSuccess) return e;
   uint8_t* base = static_cast<uint8_t*>(w->p);
-  uint8_t* As[2];
+  uint8_t* As[2];   // digits of the A slot, per real part
   uint8_t* Bs[2];
   int* ea[2];
   int* eb[2];
@@ -679,38 +794,42 @@ cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
     SplitSet<T> ss;
     int nops = 0;
     for (int pt = 0; pt < NP; ++pt) {
+      // A (M x K) and B^T (N x K) as row sources
       Src<T> sa;
       sa.X = g.A; sa.rmap = g.arow; sa.kmap = g.acol; sa.rs = 1; sa.ks = g.A.ld; sa.part = pt;
-      ss.s[nops] = sa; ss.R[nops] = g.M; ss.TR[nops] = TM; ss.RT[nops] = z.MT; ss.out[nops] = As[pt];
-      ss.ex[nops] = ea[pt];
-      ss.items[nops] = (shA && b0 > 0) ? 0 : (shA ? 1 : nb);  // a shared operand is cut once per call
-      ++nops;
       Src<T> sb;
       sb.X = g.B; sb.kmap = g.brow; sb.rs = g.B.ld; sb.ks = 1; sb.part = pt;
-      ss.s[nops] = sb; ss.R[nops] = g.N; ss.TR[nops] = TN; ss.RT[nops] = z.NT; ss.out[nops] = Bs[pt];
+      ss.s[nops] = tr ? sb : sa; ss.R[nops] = Ma; ss.TR[nops] = TM; ss.RT[nops] = z.MT; ss.out[nops] = As[pt];
+      ss.ex[nops] = ea[pt];
+      ss.items[nops] = (shSa && b0 > 0) ? 0 : (shSa ? 1 : nb);  // a shared operand is cut once per call
+      ++nops;
+      ss.s[nops] = tr ? sa : sb; ss.R[nops] = Nb; ss.TR[nops] = TN; ss.RT[nops] = z.NT; ss.out[nops] = Bs[pt];
       ss.ex[nops] = eb[pt];
-      ss.items[nops] = (shB && b0 > 0) ? 0 : (shB ? 1 : nb);
+      ss.items[nops] = (shSb && b0 > 0) ? 0 : (shSb ? 1 : nb);
       ++nops;
     }
     launch_split<T>(ss, nops, g.K, z.KT, b0, nb, st, pf);
     GemmP<T> p;
-    p.MT = z.MT; p.NT = z.NT; p.KT = z.KT; p.M = g.M; p.N = g.N; p.lsb = lsb;
+    p.MT = z.MT; p.NT = z.NT; p.KT = z.KT; p.M = Ma; p.N = Nb; p.lsb = lsb;
     p.C = g.C; p.crow = g.crow; p.b0 = b0; p.err = *w->err_slot;
-    p.a_bl = shA ? 0 : 1;
-    p.b_bl = shB ? 0 : 1;
+    p.a_bl = shSa ? 0 : 1;
+    p.b_bl = shSb ? 0 : 1;
+    p.nitems = nb;
     // real: C = alpha A B + beta C; complex (real alpha, beta):
     //   C.re = alpha (Ar Br - Ai Bi) + beta C.re,  C.im = alpha (Ar Bi + Ai Br) + beta C.im
+    // (transposed, the A slot holds B's parts and the B slot A's)
     const int npr = NP == 2 ? 4 : 1;
     for (int k = 0; k < npr; ++k) {
       static const int pa[4] = {0, 1, 0, 1}, pb[4] = {0, 1, 1, 0}, pc[4] = {0, 0, 1, 1};
-      p.As = As[pa[k]]; p.ea = ea[pa[k]];
-      p.Bs = Bs[pb[k]]; p.eb = eb[pb[k]];
+      const int sa_part = tr ? pb[k] : pa[k], sb_part = tr ? pa[k] : pb[k];
+      p.As = As[sa_part]; p.ea = ea[sa_part];
+      p.Bs = Bs[sb_part]; p.eb = eb[sb_part];
       p.cpart = pc[k];
       p.alpha = (k == 1) ? -alpha : alpha;
       p.beta = (k == 1 || k == 3) ? 1.0 : beta;
       p.amode = (p.alpha == 1.0 || p.alpha == -1.0) ? 1 : 0;
       p.asign = p.alpha == -1.0 ? (long long)(1ull << 63) : 0ll;
-      launch_mma<T>(p, nb, g.K, st, pf);
+      launch_mma<T>(p, tr, nb, g.M, g.N, g.K, st, pf);
     }
   }
   return cudaGetLastError();

@@ -1440,6 +1440,55 @@ hps_status hps_gemm(int dtype, int mode, int m, int n, int k, int batch, double 
   return (herr & hps::DEV_ERR_TIMEOUT) ? HPS_ERR_TIMEOUT : HPS_OK;
 }
 
+hps_status hps_getrf(int dtype, int mode, int n, int batch, void* A, int lda, int64_t strideA, int* ipiv,
+                     int* info, struct CUstream_st* stream) {
+  if ((dtype != HPS_F64 && dtype != HPS_C128) || (mode != 0 && mode != 1)) return HPS_ERR_INVALID;
+  if (n < 0 || batch < 0 || !A || !ipiv || !info || lda < std::max(n, 1)) return HPS_ERR_INVALID;
+  if (batch > 1 && strideA < (int64_t)lda * n) return HPS_ERR_INVALID;
+  if (n == 0 || batch == 0) return HPS_OK;
+  if (batch > (1 << 30) / std::max(n, 1)) return HPS_ERR_INVALID;
+  if (!is_device_ptr(A) || !is_device_ptr(ipiv) || !is_device_ptr(info)) return HPS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  HPS_CUDA(cudaGetDevice(&dev));
+  HPS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool cp = dtype == HPS_C128;
+  const int G = cp ? hps::lu_group_size<hps::cplx>(n, batch, sms) : hps::lu_group_size<double>(n, batch, sms);
+  hps::LuWork luw;
+  luw.pub_bytes = cp ? hps::lu_pub_bytes<hps::cplx>(n, batch, G) : hps::lu_pub_bytes<double>(n, batch, G);
+  unsigned* derr = nullptr;
+  int* perm = nullptr;
+  cudaError_t e = cudaMalloc(&derr, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMalloc(&perm, sizeof(int) * (size_t)batch * n);
+  if (e == cudaSuccess) e = cudaMalloc(&luw.bars, sizeof(unsigned) * 2 * (size_t)batch);
+  if (e == cudaSuccess && luw.pub_bytes) e = cudaMalloc(&luw.pub, luw.pub_bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(luw.bars, 0, sizeof(unsigned) * 2 * (size_t)batch, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(info, 0, sizeof(int) * (size_t)batch, st);
+  hps::TcWorkspace w;
+  w.err_slot = &derr;
+  w.enabled = mode == 0;
+  if (e == cudaSuccess) {
+    hps::TcScope scope(&w);
+    if (cp) e = hps::getrf<hps::cplx>(hps::bop<hps::cplx>((hps::cplx*)A, strideA, lda), n, batch, ipiv, perm, info, derr, G, luw, st,
+                                 nullptr);
+    else e = hps::getrf<double>(hps::bop<double>((double*)A, strideA, lda), n, batch, ipiv, perm, info, derr, G, luw,
+                                st, nullptr);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  unsigned herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  hps::tc_release(&w);
+  if (e != cudaSuccess) cudaStreamSynchronize(st);
+  cudaFree(luw.pub);
+  cudaFree(luw.bars);
+  cudaFree(perm);
+  cudaFree(derr);
+  if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return HPS_ERR_OOM; }
+  if (e != cudaSuccess) { cudaGetLastError(); return HPS_ERR_CUDA; }
+  return (herr & hps::DEV_ERR_TIMEOUT) ? HPS_ERR_TIMEOUT : HPS_OK;
+}
+
 hps_status hps_coeff_gradient(hps_handle* h, int nrhs, const void* u, const void* fbar, double* ga, double* gb,
                               double* gc, struct CUstream_st* stream) {
   if (!h || !u || !fbar || nrhs < 1 || h->adaptive || h->recompute) return HPS_ERR_INVALID;

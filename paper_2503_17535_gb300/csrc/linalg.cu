@@ -544,6 +544,25 @@ cudaError_t fill(BOp<T> C, int M, int N, int batch, T value, T diag, cudaStream_
   return cudaGetLastError();
 }
 
+// Streaming multiprocessors of the current device (queried once per process).
+int device_sms() {
+  static const int sms = [] {
+    int dev = 0, s = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 1;
+    }
+    return s > 0 ? s : 1;
+  }();
+  return sms;
+}
+
+// whole-warp shuffle of a real or complex value
+__device__ inline double shfl_val(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ inline cplx shfl_val(cplx v, int src) {
+  return cplx(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+}
+
 // ------------------------------------------------------------ panel LU ----
 
 // Factor the panel A[k0:n, k0:k0+nb) of each matrix with partial pivoting.
@@ -558,6 +577,24 @@ cudaError_t fill(BOp<T> C, int M, int N, int batch, T value, T diag, cudaStream_
 __device__ __forceinline__ bool piv_better(double m, int r, double best_m, int best_r) {
   const long long a = __double_as_longlong(m), b = __double_as_longlong(best_m);
   return a > b || (a == b && r < best_r);
+}
+
+// The panel rows [r0, r0 + rc) x columns [k0, k0 + nb) into shared memory
+// (column-major, ch rows) with asynchronous copies: every load is in flight
+// at once (plain loads would wait one by one, since the compiler cannot tell
+// the global source from the shared destination).  Ends with the copies done
+// for this thread; the caller's barrier publishes them.
+template <typename T>
+__device__ __forceinline__ void load_panel(T* Ps, const T* Ab, int lda, int r0, int k0, int rc, int ch, int nb,
+                                           int tid, int nth) {
+  for (int c = 0; c < nb; ++c)
+    for (int r = tid; r < rc; r += nth)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(
+                       Ps + r + (size_t)c * ch)),
+                   "l"(Ab + (int64_t)(r0 + r) + (int64_t)(k0 + c) * lda), "n"((int)sizeof(T))
+                   : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 template <typename T, bool COOP>
@@ -592,8 +629,7 @@ __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int n
   while (CT < 16 && CT * 2 <= nb && (nth / (CT * 2)) >= rc && nth / (CT * 2) >= 32) CT *= 2;
   const int RT = nth / CT, rt = tid % RT, ct = tid / RT;
 
-  for (int c = 0; c < nb; ++c)
-    for (int r = tid; r < rc; r += nth) Ps[r + (size_t)c * ch] = Ab[(int64_t)(r0 + r) + (int64_t)(k0 + c) * lda];
+  load_panel(Ps, Ab, lda, r0, k0, rc, ch, nb, tid, nth);
   __syncthreads();
   T* pv = COOP ? pubv + (size_t)b * 2 * (G + 1) * nb : nullptr;
   double* pm = COOP ? pubm + (size_t)b * 2 * G : nullptr;
@@ -733,19 +769,21 @@ __global__ void __launch_bounds__(256) k_lu_panel(BOp<T> A, int n, int k0, int n
 // of the matrix's cluster, each held in that CTA's shared memory for the
 // whole panel.  Rows never move during the panel: a chosen pivot row is only
 // marked done, and the interchanges are recorded in LAPACK's form (ipiv) by
-// a replay of the swap sequence on the panel's top positions; at the end
-// every row is written to its final position.  Per column: every warp
-// reduces its rows' candidates with shuffles and publishes its best (|.|,
-// current position, row, and the row's panel values) in its CTA's shared
-// memory; one cluster barrier; warp 0 of every CTA reads all 8 CS candidates
-// through distributed shared memory, picks the same pivot (largest
-// magnitude, and on ties the lowest current position -- the row order after
-// the interchanges so far, which is LAPACK's choice), copies its row and
-// forms the reciprocal; one block barrier; every thread updates its rows.
-// Candidates are double-buffered by column parity, so one cluster barrier
-// per column suffices: a warp cannot overwrite a buffer before every CTA has
-// passed the next barrier, which each reaches only after reading the buffer.
-// The barriers are the hardware ones; there is no polling.
+// a replay of the swap sequence on the panel's top positions (every warp
+// keeps its own copy in registers, lane t for position k0 + t); at the end
+// every row is written to its final position.
+//
+// Per column, one block barrier and one cluster barrier, and no remote load:
+// every warp reduces its rows' candidates with shuffles; warp 0 reduces the
+// eight warp candidates to the CTA's candidate (largest magnitude, and on ties
+// the lowest current position -- the row order after the interchanges so far,
+// which is LAPACK's choice), forms the reciprocal of its pivot-column entry
+// and pushes the candidate -- magnitude, position, row, reciprocal and the
+// row's panel values -- into the shared memory of every CTA of the cluster.
+// After the cluster barrier every warp picks the same pivot from its own
+// shared memory and updates its rows.  Candidates are double-buffered by
+// column parity: a CTA pushes into a slot again only two columns later, after
+// a barrier that every CTA reaches only once it has finished with the slot.
 template <typename T>
 __global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k0, int nb, int* ipiv,
                                                           int* info) {
@@ -759,24 +797,27 @@ __global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k
   const int r0 = k0 + g * ch;
   const int rc = max(0, min(ch, n - r0));
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Ps = reinterpret_cast<T*>(smem_raw);       // ch x nb, column-major
-  T* pubv = Ps + (size_t)ch * nb;               // [2 slots][8 warps][nb]: candidate rows
-  T* Wv = pubv + 16 * nb;                       // the pivot row
-  int* chosen = reinterpret_cast<int*>(Wv + nb);  // ch: pivot step of a row, or -1
-  __shared__ long long pub_m[16];               // [slot][warp] candidate magnitude (bits)
-  __shared__ int pub_q[16], pub_p[16];          // its current position and row
-  __shared__ int phys_at[32], pos_top[32];      // swap replay on the top positions
-  __shared__ double s_inv_raw[2];
+  T* Ps = reinterpret_cast<T*>(smem_raw);              // ch x nb, column-major
+  T* cv = Ps + (size_t)ch * nb;                        // [2 slots][CS][nb]: every CTA's candidate row
+  int* chosen = reinterpret_cast<int*>(cv + (size_t)2 * CS * nb);  // ch: pivot step of a row, or -1
+  __shared__ long long wm[8];                          // warp candidates of this CTA
+  __shared__ int wq[8], wp[8];
+  __shared__ long long cm[2 * 16];                     // [slot][CTA] pushed candidates
+  __shared__ int cq[2 * 16], cr[2 * 16];
+  __shared__ double cinv_raw[2 * 16 * 2];              // their reciprocals (T)
+  T* cinv = reinterpret_cast<T*>(cinv_raw);
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5;
+  const int kmax = (ch + nth - 1) / nth;               // row slots per thread, uniform over the CTA
   T* Ab = A.item(b);
   const int lda = A.ld;
 
-  for (int c = 0; c < nb; ++c)
-    for (int r = tid; r < rc; r += nth) Ps[r + (size_t)c * ch] = Ab[(int64_t)(r0 + r) + (int64_t)(k0 + c) * lda];
+  load_panel(Ps, Ab, lda, r0, k0, rc, ch, nb, tid, nth);
   for (int r = tid; r < ch; r += nth) chosen[r] = -1;
-  if (tid < nb) { phys_at[tid] = k0 + tid; pos_top[tid] = k0 + tid; }
-  __syncthreads();
+  int phys = k0 + lane;   // row now at position k0 + lane
+  int pos = k0 + lane;    // current position of row k0 + lane
+  // every CTA of the cluster has started before any writes into its shared memory
+  cl.sync();
   // (magnitude, current position) orders candidates; prow is the row itself
   double best = -1.0;
   int bpos = 0x7fffffff, prow = -1;
@@ -786,7 +827,6 @@ __global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k
   }
   for (int jj = 0; jj < nb; ++jj) {
     const int slot = jj & 1;
-    // this warp's candidate, published for the whole cluster
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const double m2 = __shfl_down_sync(0xffffffffu, best, o);
@@ -794,66 +834,84 @@ __global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k
       const int p2 = __shfl_down_sync(0xffffffffu, prow, o);
       if (piv_better(m2, q2, best, bpos)) { best = m2; bpos = q2; prow = p2; }
     }
-    best = __shfl_sync(0xffffffffu, best, 0);
-    bpos = __shfl_sync(0xffffffffu, bpos, 0);
-    prow = __shfl_sync(0xffffffffu, prow, 0);
-    if (lane == 0) {
-      pub_m[slot * 8 + wid] = __double_as_longlong(best);
-      pub_q[slot * 8 + wid] = bpos;
-      pub_p[slot * 8 + wid] = prow;
-    }
-    if (lane < nb)
-      pubv[(slot * 8 + wid) * nb + lane] = best >= 0.0 ? Ps[(prow - r0) + (size_t)lane * ch] : T(0.0);
-    cl.sync();
-    if (wid == 0) {
-      // every warp's candidate of the cluster, one round of remote reads
-      double cm = -1.0;
-      int cq = 0x7fffffff, cp = -1, cw = 0;
-      for (int e = lane; e < 8 * CS; e += 32) {
-        const int q = e >> 3, w = e & 7;
-        const double m = __longlong_as_double(cl.map_shared_rank(pub_m, q)[slot * 8 + w]);
-        const int qq = cl.map_shared_rank(pub_q, q)[slot * 8 + w];
-        if (piv_better(m, qq, cm, cq)) { cm = m; cq = qq; cp = cl.map_shared_rank(pub_p, q)[slot * 8 + w]; cw = e; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double m2 = __shfl_down_sync(0xffffffffu, cm, o);
-        const int q2 = __shfl_down_sync(0xffffffffu, cq, o);
-        const int p2 = __shfl_down_sync(0xffffffffu, cp, o);
-        const int w2 = __shfl_down_sync(0xffffffffu, cw, o);
-        if (piv_better(m2, q2, cm, cq)) { cm = m2; cq = q2; cp = p2; cw = w2; }
-      }
-      cm = __shfl_sync(0xffffffffu, cm, 0);
-      cq = __shfl_sync(0xffffffffu, cq, 0);
-      cp = __shfl_sync(0xffffffffu, cp, 0);
-      cw = __shfl_sync(0xffffffffu, cw, 0);
-      if (lane < nb) Wv[lane] = cl.map_shared_rank(pubv, cw >> 3)[(slot * 8 + (cw & 7)) * nb + lane];
-      __syncwarp();
-      if (lane == 0) {
-        *reinterpret_cast<T*>(s_inv_raw) = (cm == 0.0) ? T(0.0) : recip(Wv[jj]);
-        if (cp >= r0 && cp < r0 + rc) chosen[cp - r0] = jj;
-        // LAPACK interchange: swap position j with the winner's current position
-        const int j = k0 + jj;
-        const int rj = phys_at[jj];
-        pos_top[rj - k0] = cq;
-        if (cq - k0 < nb) phys_at[cq - k0] = rj;
-        phys_at[jj] = cp;
-        if (cp - k0 < nb) pos_top[cp - k0] = j;
-        if (g == 0) {
-          ipiv[(int64_t)b * n + j] = cq;
-          if (cm == 0.0 && info[b] == 0) info[b] = j + 1;
-        }
-      }
-    }
+    if (lane == 0) { wm[wid] = __double_as_longlong(best); wq[wid] = bpos; wp[wid] = prow; }
     __syncthreads();
-    const T inv = *reinterpret_cast<const T*>(s_inv_raw);
+    if (wid == 0) {
+      double m = -1.0;
+      int q = 0x7fffffff, p = -1;
+      if (lane < 8) { m = __longlong_as_double(wm[lane]); q = wq[lane]; p = wp[lane]; }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        const double m2 = __shfl_down_sync(0xffffffffu, m, o);
+        const int q2 = __shfl_down_sync(0xffffffffu, q, o);
+        const int p2 = __shfl_down_sync(0xffffffffu, p, o);
+        if (piv_better(m2, q2, m, q)) { m = m2; q = q2; p = p2; }
+      }
+      m = __shfl_sync(0xffffffffu, m, 0);
+      q = __shfl_sync(0xffffffffu, q, 0);
+      p = __shfl_sync(0xffffffffu, p, 0);
+      const bool has = m >= 0.0;
+      const T v = (has && lane < nb) ? Ps[(p - r0) + (size_t)lane * ch] : T(0.0);
+      T inv = T(0.0);
+      if (lane == jj && has && m != 0.0) inv = recip(v);
+      inv = shfl_val(inv, jj);
+      for (int d = 0; d < CS; ++d)
+        if (lane < nb) cl.map_shared_rank(cv, d)[((size_t)slot * CS + g) * nb + lane] = v;
+      if (lane < CS) {
+        const int e2 = slot * 16 + g;
+        cl.map_shared_rank(cm, lane)[e2] = __double_as_longlong(m);
+        cl.map_shared_rank(cq, lane)[e2] = q;
+        cl.map_shared_rank(cr, lane)[e2] = p;
+        cl.map_shared_rank(cinv, lane)[e2] = inv;
+      }
+    }
+    cl.sync();
+    // the pivot, chosen by every warp from its own CTA's shared memory
+    double pm = -1.0;
+    int pq = 0x7fffffff, pp = -1, pw = 0;
+    if (lane < CS) {
+      pm = __longlong_as_double(cm[slot * 16 + lane]);
+      pq = cq[slot * 16 + lane];
+      pp = cr[slot * 16 + lane];
+      pw = lane;
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      const double m2 = __shfl_down_sync(0xffffffffu, pm, o);
+      const int q2 = __shfl_down_sync(0xffffffffu, pq, o);
+      const int p2 = __shfl_down_sync(0xffffffffu, pp, o);
+      const int w2 = __shfl_down_sync(0xffffffffu, pw, o);
+      if (piv_better(m2, q2, pm, pq)) { pm = m2; pq = q2; pp = p2; pw = w2; }
+    }
+    pm = __shfl_sync(0xffffffffu, pm, 0);
+    pq = __shfl_sync(0xffffffffu, pq, 0);
+    pp = __shfl_sync(0xffffffffu, pp, 0);
+    pw = __shfl_sync(0xffffffffu, pw, 0);
+    const T* Wv = cv + ((size_t)slot * CS + pw) * nb;
+    const T inv = cinv[slot * 16 + pw];
+    const int j = k0 + jj;
+    if (pp >= r0 && pp < r0 + rc && (pp - r0) % nth == tid) chosen[pp - r0] = jj;
+    // LAPACK interchange: position j <-> the winner's current position pq
+    {
+      const int rj = __shfl_sync(0xffffffffu, phys, jj);
+      if (lane == rj - k0) pos = pq;
+      if (pq - k0 < nb && lane == pq - k0) phys = rj;
+      if (lane == jj) phys = pp;
+      if (pp - k0 < nb && lane == pp - k0) pos = j;
+    }
+    if (g == 0 && tid == 0) {
+      ipiv[(int64_t)b * n + j] = pq;
+      if (pm == 0.0 && info[b] == 0) info[b] = j + 1;
+    }
     best = -1.0;
     bpos = 0x7fffffff;
     prow = -1;
-    for (int r = tid; r < rc; r += nth) {
-      if (chosen[r] >= 0) continue;
+    for (int k = 0; k < kmax; ++k) {
+      const int r = tid + k * nth;
       const int pr = r0 + r;
-      const int pos = pr - k0 < nb ? pos_top[pr - k0] : pr;  // after this column's interchange
+      const int ptop = __shfl_sync(0xffffffffu, pos, (pr - k0) & 31);
+      if (r >= rc || chosen[r] >= 0) continue;
+      const int cpos = pr - k0 < nb ? ptop : pr;  // after this column's interchange
       const T l = Ps[r + (size_t)jj * ch] * inv;
       Ps[r + (size_t)jj * ch] = l;
       for (int c = jj + 1; c < nb; ++c) {
@@ -861,32 +919,36 @@ __global__ void __launch_bounds__(256) k_lu_panel_cluster(BOp<T> A, int n, int k
         Ps[r + (size_t)c * ch] = v;
         if (c == jj + 1) {
           const double m = mag1(v);
-          if (piv_better(m, pos, best, bpos)) { best = m; bpos = pos; prow = pr; }
+          if (piv_better(m, cpos, best, bpos)) { best = m; bpos = cpos; prow = pr; }
         }
       }
     }
   }
-  __syncthreads();
   // rows to their final positions
-  for (int r = tid; r < rc; r += nth) {
+  for (int k = 0; k < kmax; ++k) {
+    const int r = tid + k * nth;
     const int pr = r0 + r;
+    const int ptop = __shfl_sync(0xffffffffu, pos, (pr - k0) & 31);
+    if (r >= rc) continue;
     int dst = pr;
     if (chosen[r] >= 0) dst = k0 + chosen[r];
-    else if (pr - k0 < nb) dst = pos_top[pr - k0];
+    else if (pr - k0 < nb) dst = ptop;
     for (int c = 0; c < nb; ++c) Ab[(int64_t)dst + (int64_t)(k0 + c) * lda] = Ps[r + (size_t)c * ch];
   }
-  // no CTA leaves while another may still read its candidates
   cl.sync();
 }
 
-// Cluster shape for a panel of `rows` rows: the smallest power of two of
-// CTAs with at most 256 rows each (one row per thread), at least 2, at most
-// the largest cluster the device runs with the kernel's shared memory; 0 when
-// the panel does not fit (the cooperative kernel is used then).
+// Cluster shape for a panel of `rows` rows of `batch` matrices: a power of
+// two of CTAs, at least 2, growing while a CTA would hold more than 128 rows
+// and the clusters of all matrices still fit on the SMs at once (the panel's
+// FP64 update is spread over more SMs), then until the chunk fits in shared
+// memory; at most the largest cluster the device runs with the kernel's
+// shared memory; 0 when the panel does not fit (the cooperative kernel is
+// used then).
 template <typename T>
 size_t panel_cluster_smem(int rows, int nb, int cs) {
   const int ch = (rows + cs - 1) / cs;
-  return ((size_t)ch * nb + 17 * (size_t)nb) * sizeof(T) + (size_t)ch * sizeof(int) + 16;
+  return ((size_t)ch * nb + 2 * (size_t)cs * nb) * sizeof(T) + (size_t)ch * sizeof(int) + 16;
 }
 
 template <typename T>
@@ -931,7 +993,7 @@ int panel_cluster_max() {
 }
 
 template <typename T>
-int panel_cluster_size(int rows, int nb) {
+int panel_cluster_size(int rows, int nb, int batch) {
   const int mx = panel_cluster_max<T>();
   if (mx < 2 || nb > 32) return 0;
   int smem_max = 0, dev = 0;
@@ -941,48 +1003,113 @@ int panel_cluster_size(int rows, int nb) {
     return 0;
   }
   int cs = 2;
-  while (cs < mx && (rows + cs - 1) / cs > 256) cs *= 2;
+  while (cs < mx && (rows + cs - 1) / cs > 128 && (int64_t)batch * cs * 2 <= device_sms()) cs *= 2;
   while (cs <= mx && panel_cluster_smem<T>(rows, nb, cs) + 8192 > (size_t)smem_max) cs *= 2;
   return cs <= mx ? cs : 0;
 }
 
 // Apply the panel's interchanges to every column outside the panel and
 // solve U12 = L11^{-1} A12 for the columns in [k0 + nb, trsm_end).
-template <typename T>
+//
+// The nb interchanges are first composed into one permutation of at most
+// 2 nb rows: warp 0 replays them with lane t holding the row now at
+// position k0 + t, and for a step whose partner lies below the panel's top,
+// lane jj recording that outside position and the row it received (a later
+// step with the same partner takes the record over).  Every thread then reads
+// all moved entries of its column at once and writes them back permuted --
+// one round trip per column instead of one per interchange -- and solves its
+// top block in registers.
+template <typename T, int NB, bool REG>
 __global__ void __launch_bounds__(128) k_laswp_trsm(BOp<T> A, int n, int k0, int nb, const int* ipiv,
                                                     int trsm_end) {
   extern __shared__ unsigned char smem_raw[];
   T* L11 = reinterpret_cast<T*>(smem_raw);  // nb x nb, column-major
-  __shared__ int piv[64];
+  __shared__ int src_top[32], dst_out[32], src_out[32];
   const int b = blockIdx.y;
   T* Ab = A.item(b);
   const int lda = A.ld;
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    int r = e % nb, c = e / nb;
-    L11[e] = Ab[(int64_t)(k0 + r) + (int64_t)(k0 + c) * lda];
+  const bool any_trsm = trsm_end > k0 + nb;
+  if (any_trsm)
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+      const int r = e % nb, c = e / nb;
+      L11[e] = Ab[(int64_t)(k0 + r) + (int64_t)(k0 + c) * lda];
+    }
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const int* ip = ipiv + (int64_t)b * n + k0;
+    const int pl = lane < nb ? ip[lane] : 0;   // all interchanges in one load
+    int content = k0 + lane;   // row whose entries sit at position k0 + lane
+    int opos = -1, ocont = -1; // outside position last swapped at this lane's step, and its row
+    for (int jj = 0; jj < nb; ++jj) {
+      const int p = __shfl_sync(0xffffffffu, pl, jj);
+      const int cj = __shfl_sync(0xffffffffu, content, jj);
+      if (p < k0 + nb) {
+        const int cp = __shfl_sync(0xffffffffu, content, p - k0);
+        if (lane == jj) content = cp;
+        if (lane == p - k0) content = cj;
+      } else {
+        const unsigned m = __ballot_sync(0xffffffffu, opos == p);
+        const int owner = m ? 31 - __clz((int)m) : 0;
+        const int held = __shfl_sync(0xffffffffu, ocont, owner);
+        const int cur = m ? held : p;   // never swapped before: still row p
+        if (m && lane == owner) opos = -1;
+        if (lane == jj) { content = cur; opos = p; ocont = cj; }
+      }
+    }
+    src_top[lane] = lane < nb ? content : 0;
+    dst_out[lane] = lane < nb ? opos : -1;
+    src_out[lane] = ocont;
   }
-  for (int e = threadIdx.x; e < nb; e += blockDim.x) piv[e] = ipiv[(int64_t)b * n + k0 + e];
   __syncthreads();
   const int ncols_out = n - nb;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncols_out; t += gridDim.x * blockDim.x) {
     const int c = (t < k0) ? t : t + nb;
     T* col = Ab + (int64_t)c * lda;
-    for (int jj = 0; jj < nb; ++jj) {
-      int p = piv[jj];
-      int j = k0 + jj;
-      if (p != j) { T tmp = col[j]; col[j] = col[p]; col[p] = tmp; }
-    }
-    if (c >= k0 + nb && c < trsm_end) {
-      T x[64];
-#pragma unroll 8
-      for (int jj = 0; jj < nb; ++jj) x[jj] = col[k0 + jj];
-      for (int jj = 1; jj < nb; ++jj) {
-        T s = x[jj];
-        for (int ii = 0; ii < jj; ++ii) s = fmsc(s, L11[jj + ii * nb], x[ii]);
-        x[jj] = s;
+    T x[NB], xo[NB];
+    if constexpr (REG) {
+      // few CTAs (one or a few matrices): the whole column in registers,
+      // every load in flight at once, the solve unrolled
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q < nb) x[q] = col[src_top[q]];
+        if (q < nb && dst_out[q] >= 0) xo[q] = col[src_out[q]];
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < nb && dst_out[q] >= 0) col[dst_out[q]] = xo[q];
+      if (c >= k0 + nb && c < trsm_end) {
+#pragma unroll
+        for (int jj = 1; jj < NB; ++jj) {
+          if (jj < nb) {
+            T s = x[jj];
+#pragma unroll
+            for (int ii = 0; ii < jj; ++ii) s = fmsc(s, L11[jj + ii * nb], x[ii]);
+            x[jj] = s;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < nb) col[k0 + q] = x[q];
+    } else {
+      // many matrices: runtime-indexed arrays (local memory, L1-resident) keep
+      // the registers, and so the occupancy that hides the FP64 solve's
+      // latency, where the unrolled form would take ~250 registers a thread
+      for (int q = 0; q < nb; ++q) {
+        x[q] = col[src_top[q]];
+        if (dst_out[q] >= 0) xo[q] = col[src_out[q]];
+      }
+      for (int q = 0; q < nb; ++q)
+        if (dst_out[q] >= 0) col[dst_out[q]] = xo[q];
+      if (c >= k0 + nb && c < trsm_end) {
+        for (int jj = 1; jj < nb; ++jj) {
+          T s = x[jj];
+          for (int ii = 0; ii < jj; ++ii) s = fmsc(s, L11[jj + ii * nb], x[ii]);
+          x[jj] = s;
+        }
       }
 #pragma unroll 8
-      for (int jj = 0; jj < nb; ++jj) col[k0 + jj] = x[jj];
+      for (int q = 0; q < nb; ++q) col[k0 + q] = x[q];
     }
   }
 }
@@ -1005,7 +1132,8 @@ int& lu_tune(int param) {
   static int v[TUNE_COUNT] = {HPS_TUNED_LU_BASE_PANELS_FEW, HPS_TUNED_LU_BASE_PANELS_MANY,
                               HPS_TUNED_LU_FEW_MIN_N,       HPS_TUNED_LU_CLUSTER_PANEL,
                               HPS_TUNED_TC_MIN_WORK_REAL,   HPS_TUNED_TC_MIN_WORK_CPLX,
-                              HPS_TUNED_TC_MIN_K,           HPS_TUNED_TC_CHUNK_MB};
+                              HPS_TUNED_TC_MIN_K,           HPS_TUNED_TC_CHUNK_MB,
+                              HPS_TUNED_TC_PERSIST_MIN_K};
   return v[param];
 }
 
@@ -1079,7 +1207,7 @@ static cudaError_t lu_leaf(BOp<T> A, int n, int k0, int nb, int trsm_end, int ba
     pfl += below * (nb - jj - 1) + below;
   }
   pfl *= F * batch;
-  const int CS = (Gk > 1 && lu_tune(TUNE_LU_CLUSTER_PANEL)) ? panel_cluster_size<T>(rows, nb) : 0;
+  const int CS = (Gk > 1 && lu_tune(TUNE_LU_CLUSTER_PANEL)) ? panel_cluster_size<T>(rows, nb, batch) : 0;
   if (pf) {
     pf->begin(st);
     pf->note(rows, nb, CS > 1 ? CS : Gk, batch);  // k: CTAs per matrix
@@ -1120,13 +1248,17 @@ static cudaError_t lu_leaf(BOp<T> A, int n, int k0, int nb, int trsm_end, int ba
   if (pf) pf->end(K_LU_PANEL, pfl, st);
   if (n > nb) {
     const int ncols = n - nb;
-    int bx = std::min((ncols + 127) / 128, 1024);
+    // few matrices: 32-thread CTAs, so that the columns spread over the SMs
+    const bool few = ((ncols + 127) / 128) * batch < 2 * device_sms();
+    const int tpb = few ? 32 : 128;
+    int bx = std::min((ncols + tpb - 1) / tpb, 1024);
     size_t sm2 = (size_t)nb * nb * sizeof(T);
     if (pf) {
       pf->begin(st);
       pf->note(nb, ncols, nb, batch);
     }
-    k_laswp_trsm<T><<<dim3(bx, batch), 128, sm2, st>>>(A, n, k0, nb, ipiv, trsm_end);
+    if (few) k_laswp_trsm<T, LuNB<T>::NB, true><<<dim3(bx, batch), tpb, sm2, st>>>(A, n, k0, nb, ipiv, trsm_end);
+    else k_laswp_trsm<T, LuNB<T>::NB, false><<<dim3(bx, batch), tpb, sm2, st>>>(A, n, k0, nb, ipiv, trsm_end);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (pf) pf->end(K_LASWP_TRSM, F * 0.5 * nb * (nb - 1) * (double)std::max(0, trsm_end - k0 - nb) * batch, st);
   }
@@ -1244,10 +1376,6 @@ cudaError_t permute_rows(BOp<T> src, BOp<T> dst, const int* perm, int n, int nrh
 // per right-hand side column, lane r owning row r (pb <= 32): each step
 // broadcasts the solved entry with a shuffle and the lanes below (above)
 // update their row, so a single column is solved in pb dependent steps.
-__device__ inline double shfl_val(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-__device__ inline cplx shfl_val(cplx v, int src) {
-  return cplx(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
-}
 
 template <typename T, bool UPPER>
 __global__ void __launch_bounds__(128) k_trsm_diag(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch) {
@@ -1394,8 +1522,14 @@ cudaError_t trsm_diag(BOp<T> LU, BOp<T> X, int p0, int pb, int nrhs, int batch, 
   const size_t sm = ((size_t)pb * pb + pb) * sizeof(T);
   const int by = std::min(batch, 65535);
   if (pb == 32 && nrhs >= 16 && batch <= 65535) {
-    constexpr int CT = sizeof(T) == 8 ? 128 : 32;   // static shared memory stays below 48 KB
-    k_trsm32<T, UPPER, CT><<<dim3((nrhs + CT - 1) / CT, batch), CT, 0, st>>>(LU, X, p0, nrhs, batch);
+    // 128 columns per CTA (real data) unless that leaves most SMs idle; the
+    // complex tile keeps 32 so that static shared memory stays below 48 KB
+    bool wide = false;
+    if constexpr (sizeof(T) == 8) {
+      wide = ((nrhs + 127) / 128) * batch >= 2 * device_sms();
+      if (wide) k_trsm32<T, UPPER, 128><<<dim3((nrhs + 127) / 128, batch), 128, 0, st>>>(LU, X, p0, nrhs, batch);
+    }
+    if (!wide) k_trsm32<T, UPPER, 32><<<dim3((nrhs + 31) / 32, batch), 32, 0, st>>>(LU, X, p0, nrhs, batch);
   } else if (nrhs >= 16) {
     const int bx = std::min((nrhs + 127) / 128, 1024);
     k_trsm_diag_cols<T, UPPER><<<dim3(bx, by), 128, sm, st>>>(LU, X, p0, pb, nrhs, batch);

@@ -149,9 +149,13 @@ enum LuTuneParam {
   TUNE_TC_MIN_WORK_CPLX = 5,     // complex products: the same threshold
   TUNE_TC_MIN_K = 6,             // products with K below this stay on the FP64 pipe unless M, N >= 512
   TUNE_TC_CHUNK_MB = 7,          // digit slices of one launch group of a batched product, MiB
-  TUNE_COUNT = 8
+  TUNE_TC_PERSIST_MIN_K = 8,     // tensor-core products with K at least this walk their tiles persistently
+  TUNE_COUNT = 9
 };
 int& lu_tune(int param);
+
+// Streaming multiprocessors of the current device (queried once per process).
+int device_sms();
 
 struct LuWork {
   unsigned* bars = nullptr;   // 2 * batch barrier words (zeroed)

@@ -94,6 +94,11 @@ def _check(A, B, C0, C, alpha, beta, rng, nsample=24):
         assert float(d) <= lim, (b, i, j, float(d), lim)
 
 
+# A product whose transposed tiling (C^T = B^T A^T in 128 x 48 tiles of C^T)
+# takes fewer waves of CTAs over the SMs runs transposed: the few-row shapes
+# of the recursive LU and triangular solves with many items (32 x 114 x 400,
+# 48 x 225 x 200, 40 x 1000 x 20 items); everything that fits one wave stays
+# in the normal form.
 SHAPES = [
     (1, 1, 1, 1),
     (130, 50, 17, 3),      # ragged M, N and K tiles
@@ -101,8 +106,10 @@ SHAPES = [
     (200, 97, 449, 2),     # ragged K tail
     (300, 130, 700, 1),    # three accumulation chunks
     (64, 33, 32, 5),
+    (32, 114, 32, 400),    # transposed: one 128 x 48 tile of C^T per item
+    (48, 225, 56, 200),    # transposed, two 128-row tiles of C^T per item
+    (40, 1000, 300, 20),   # transposed, eight 128-row tiles of C^T, two chunks
 ]
-
 
 @pytest.mark.parametrize("m,n,k,batch", SHAPES, ids=[f"{s[0]}x{s[1]}x{s[2]}b{s[3]}" for s in SHAPES])
 @pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-1.0, 1.0), (0.5, -2.0)], ids=["set", "sub", "general"])
@@ -132,11 +139,13 @@ def test_wide_dynamic_range_and_zero_rows(P):
     _check(A, B, C0, C, 1.0, 0.0, rng)
 
 
-def test_complex_product(P):
+@pytest.mark.parametrize("m,n,k,batch", [(130, 60, 470, 2), (200, 60, 300, 2), (32, 114, 32, 400)],
+                         ids=["ragged", "normal", "transposed"])
+def test_complex_product(P, m, n, k, batch):
     """Complex products run as four real digit-slice products, one pair per
-    component of C: Re = Ar Br - Ai Bi, Im = Ar Bi + Ai Br."""
-    rng = np.random.default_rng(3)
-    batch, m, n, k = 2, 130, 60, 470
+    component of C: Re = Ar Br - Ai Bi, Im = Ar Bi + Ai Br (in the transposed
+    tiling the A slot holds B's parts and the B slot A's)."""
+    rng = np.random.default_rng(3 + m)
     z = lambda s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
     A, B, C0 = z((batch, m, k)), z((batch, k, n)), z((batch, m, n))
     Ar, Ai, Br, Bi = A.real, A.imag, B.real, B.imag
@@ -173,15 +182,16 @@ def test_invalid_arguments(P):
         P.hps_gemm(A, torch.zeros((1, 3, 5), dtype=torch.float64, device="cuda"), A)
 
 
+@pytest.mark.parametrize("m,batch", [(32, 160), (300, 7)], ids=["transposed", "normal"])
 @pytest.mark.parametrize("shared", ["A", "B"])
 @pytest.mark.parametrize("cplx", [False, True], ids=["real", "complex"])
-def test_operand_shared_by_every_item(P, shared, cplx):
+def test_operand_shared_by_every_item(P, shared, cplx, m, batch):
     """An operand given with item stride 0 (the same matrix for every item,
     as the leaf stage's Q and QH products are) is cut into digits once per
     call and serves every item; the products stay within the bound."""
     from paper_2503_17535_gb300 import _capi
     rng = np.random.default_rng(31 if shared == "A" else 37)
-    batch, m, n, k = 7, 130, 57, 300
+    n, k = 114, 300
     z = (lambda s: rng.standard_normal(s) + 1j * rng.standard_normal(s)) if cplx else rng.standard_normal
     A = z((1 if shared == "A" else batch, m, k))
     B = z((1 if shared == "B" else batch, k, n))
