@@ -315,8 +315,10 @@ void hps_free(hps_handle* h);
  * digit-slice product that hps_build uses (operands cut into ten 6-bit bf16
  * digits per row of A / column of B, the 55 digit products whose digit
  * indices sum to at most 11 accumulated exactly in fp32, recombined in
- * 64-bit integers; a transient device workspace of up
- * to about 1 GB); mode 1: the FP64-pipe kernels.  Device pointers only; C must
+ * 64-bit integers; for complex data the real and imaginary parts of a row /
+ * column share one scale and each component of C is one accumulation of two
+ * real products; a transient device workspace of up to about 1 GB); mode 1:
+ * the FP64-pipe kernels.  Device pointers only; C must
  * not overlap A or B.  Enqueued on `stream` and synchronised before return.
  * HPS_ERR_INVALID for bad sizes, dtype or mode; HPS_ERR_OOM when device
  * memory cannot be allocated (mode 0 runs the product on the FP64 pipe when

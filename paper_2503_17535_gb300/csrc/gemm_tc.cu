@@ -36,8 +36,13 @@
 // columns, and eight epilogue warps (two per TMEM lane quarter, one per half
 // of the columns) read them back while the C tile waits in shared memory.
 //
-// Complex products are four real products (re*re, im*im, re*im, im*re),
-// each written into its component of C.
+// Complex products are two launches, one per component of C, each
+// accumulating two real products in the same TMEM accumulators
+// (Re = Ar Br - Ai Bi with the second product negated by the MMA's negate-B
+// bit, Im = Ar Bi + Ai Br): the real and imaginary parts of a row of A (a
+// column of B) are scaled by one power of two, above the largest |re| or |im|
+// of the row, so that their digit products carry the same weights; the
+// error bound above then holds with 2K terms and those joint row scales.
 #include "devmem.h"
 #include "linalg.h"
 
@@ -121,30 +126,95 @@ struct Src {
   BOp<T> X;
   IMap rmap, kmap;
   int64_t rs = 1, ks = 1;
-  int part = 0;
 };
 
 // exponent e of a row (max |x| < 2^e) from its biased maximum exponent
 __device__ __forceinline__ int row_exp(int evm) { return evm ? evm - 1022 : 0; }
 
-// The operands of one product call (A and B, and for complex data their
-// real and imaginary parts): rows x K each, cut into digit blocks with
-// row tiles of TR rows.
+// The operands of one product call (A and B) as rows x K, cut into digit
+// blocks with row tiles of TR rows.  A complex operand yields the digits of
+// its real part in out and of its imaginary part in out2, both scaled by one
+// power of two per row (above the row's largest |re| or |im|), so that the
+// products of both parts can share accumulators.
 constexpr int MAXOPS = 4;
 template <typename T>
 struct SplitSet {
   Src<T> s[MAXOPS];
   int R[MAXOPS], TR[MAXOPS], RT[MAXOPS];
   uint8_t* out[MAXOPS];
+  uint8_t* out2[MAXOPS];  // imaginary part's digits (complex operands)
   int* ex[MAXOPS];    // biased exponent of each row's largest |entry| (0: zero row)
   int items[MAXOPS];  // batch items to cut: 1 for an operand shared by every item
 };
 
+__device__ __forceinline__ unsigned long long mag_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long mag_bits(const cplx& v) {
+  return max(mag_bits(v.re), mag_bits(v.im));
+}
+
+// Balanced base-64 digits of v 2^{FRAC - e} rounded to an integer, as bf16
+// values, for the 8 consecutive k of one 16-byte row segment of a block:
+// blk points at digit 0's segment; digit p lies BLK bytes further.
+__device__ __forceinline__ void put_digits(const double (&v)[8], int e, uint8_t* blk, int BLK) {
+  int dg[8][DIG];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v[c]);
+    const int ev = (int)((u >> 52) & 0x7FF);
+    // |v| 2^{FRAC - e} rounded to an integer (<= 2^FRAC), then signed
+    const long long m = (long long)((u & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+    const int sh = ev - (1075 - FRAC) - e;
+    long long x = 0;
+    if (ev != 0) {
+      if (sh >= 0) x = m << sh;
+      else if (sh > -62) x = ((m >> (-sh - 1)) + 1) >> 1;
+    }
+    if (u >> 63) x = -x;
+    // balanced base-64 digits, least significant first, in 32-bit halves:
+    // x = hi 2^30 + lo with 0 <= lo < 2^30.  A digit is d = (t & 63) - 32
+    // with t = v + 32, and the rest is (v - d) / 64 = t >> 6.  Five digits
+    // of lo leave a carry of 0 or 1 into hi; four of hi leave the leading
+    // digit (|.| <= 64).
+    int lo = (int)(x & 0x3FFFFFFFll), hi = (int)(x >> 30);
+#pragma unroll
+    for (int p = DIG - 1; p >= DIG - 5; --p) {
+      const int t = lo + 32;
+      dg[c][p] = (t & 63) - 32;
+      lo = t >> BITS;
+    }
+    hi += lo;
+#pragma unroll
+    for (int p = DIG - 6; p > 0; --p) {
+      const int t = hi + 32;
+      dg[c][p] = (t & 63) - 32;
+      hi = t >> BITS;
+    }
+    dg[c][0] = hi;
+  }
+#pragma unroll
+  for (int p = 0; p < DIG; ++p) {
+    uint32_t w[4];
+#pragma unroll
+    for (int c = 0; c < 8; c += 2) {
+      // d (|d| <= 64) as an exact float: 1.5 * 2^23 + d has d in its low
+      // mantissa bits; subtracting 1.5 * 2^23 leaves d, whose upper 16
+      // bits are its bf16 encoding (d has at most 7 significant bits)
+      const float f0 = __int_as_float(0x4B400000 + dg[c][p]) - 12582912.0f;
+      const float f1 = __int_as_float(0x4B400000 + dg[c + 1][p]) - 12582912.0f;
+      w[c >> 1] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+    }
+    *reinterpret_cast<uint4*>(blk + (int64_t)p * BLK) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
 // One launch for all operands: CTA = 32 rows x 8 warps; warp w takes the
 // 8-deep k groups w, w+8, ...  Pass 1 finds each row's largest magnitude
-// (compared as bit patterns, which order like the values), pass 2 writes
-// the balanced base-64 digits of the row scaled by 2^{FRAC - e}, rounded to
-// an integer.
+// (compared as bit patterns, which order like the values; over both parts
+// of a complex row), pass 2 writes the balanced base-64 digits of the row
+// scaled by 2^{FRAC - e}, rounded to an integer (both parts of a complex
+// row from one read).
 template <typename T>
 __global__ void __launch_bounds__(256) k_split(SplitSet<T> ss, int K, int KT, int b0, int nb) {
   const int op = blockIdx.z / nb, bl = blockIdx.z % nb, b = b0 + bl;
@@ -164,8 +234,7 @@ __global__ void __launch_bounds__(256) k_split(SplitSet<T> ss, int K, int KT, in
       for (int c = 0; c < 8; ++c) {
         const int k = gi * 8 + c;
         if (k >= K) break;
-        const double v = part_of(X[roff + (int64_t)s.kmap.at(b, k) * s.ks], s.part);
-        mx = max(mx, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
+        mx = max(mx, mag_bits(X[roff + (int64_t)s.kmap.at(b, k) * s.ks]));
       }
   smax[kw][lr] = mx;
   __syncthreads();
@@ -178,62 +247,24 @@ __global__ void __launch_bounds__(256) k_split(SplitSet<T> ss, int K, int KT, in
   const int e = row_exp(evm);
   const int BLK = TR * TK * 2;
   const int tile = r / TR, rr = r % TR;
-  uint8_t* base = ss.out[op] + ((int64_t)bl * ss.RT[op] + tile) * KT * (int64_t)(DIG * BLK) + (rr >> 3) * 256 +
-                  (rr & 7) * 16;
+  const int64_t rowoff = ((int64_t)bl * ss.RT[op] + tile) * KT * (int64_t)(DIG * BLK) + (rr >> 3) * 256 + (rr & 7) * 16;
   for (int gi = kw; gi < ngrp; gi += 8) {
     const int k0 = gi * 8;
-    int dg[8][DIG];
+    T xv[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int k = k0 + c;
-      double v = 0.0;
-      if (live && !zero && k < K) v = part_of(X[roff + (int64_t)s.kmap.at(b, k) * s.ks], s.part);
-      const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-      const int ev = (int)((u >> 52) & 0x7FF);
-      // |v| 2^{FRAC - e} rounded to an integer (<= 2^FRAC), then signed
-      const long long m = (long long)((u & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-      const int sh = ev - (1075 - FRAC) - e;
-      long long x = 0;
-      if (ev != 0) {
-        if (sh >= 0) x = m << sh;
-        else if (sh > -62) x = ((m >> (-sh - 1)) + 1) >> 1;
-      }
-      if (u >> 63) x = -x;
-      // balanced base-64 digits, least significant first, in 32-bit halves:
-      // x = hi 2^30 + lo with 0 <= lo < 2^30.  A digit is d = (t & 63) - 32
-      // with t = v + 32, and the rest is (v - d) / 64 = t >> 6.  Five digits
-      // of lo leave a carry of 0 or 1 into hi; four of hi leave the leading
-      // digit (|.| <= 64).
-      int lo = (int)(x & 0x3FFFFFFFll), hi = (int)(x >> 30);
-#pragma unroll
-      for (int p = DIG - 1; p >= DIG - 5; --p) {
-        const int t = lo + 32;
-        dg[c][p] = (t & 63) - 32;
-        lo = t >> BITS;
-      }
-      hi += lo;
-#pragma unroll
-      for (int p = DIG - 6; p > 0; --p) {
-        const int t = hi + 32;
-        dg[c][p] = (t & 63) - 32;
-        hi = t >> BITS;
-      }
-      dg[c][0] = hi;
+      xv[c] = (live && !zero && k < K) ? X[roff + (int64_t)s.kmap.at(b, k) * s.ks] : T(0.0);
     }
-    uint8_t* blk = base + (int64_t)(k0 >> 4) * (DIG * BLK) + ((k0 >> 3) & 1) * 128;
+    const int64_t boff = rowoff + (int64_t)(k0 >> 4) * (DIG * BLK) + ((k0 >> 3) & 1) * 128;
+    double v[8];
 #pragma unroll
-    for (int p = 0; p < DIG; ++p) {
-      uint32_t w[4];
+    for (int c = 0; c < 8; ++c) v[c] = part_of(xv[c], 0);
+    put_digits(v, e, ss.out[op] + boff, BLK);
+    if constexpr (std::is_same<T, cplx>::value) {
 #pragma unroll
-      for (int c = 0; c < 8; c += 2) {
-        // d (|d| <= 64) as an exact float: 1.5 * 2^23 + d has d in its low
-        // mantissa bits; subtracting 1.5 * 2^23 leaves d, whose upper 16
-        // bits are its bf16 encoding (d has at most 7 significant bits)
-        const float f0 = __int_as_float(0x4B400000 + dg[c][p]) - 12582912.0f;
-        const float f1 = __int_as_float(0x4B400000 + dg[c + 1][p]) - 12582912.0f;
-        w[c >> 1] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
-      }
-      *reinterpret_cast<uint4*>(blk + (int64_t)p * BLK) = make_uint4(w[0], w[1], w[2], w[3]);
+      for (int c = 0; c < 8; ++c) v[c] = part_of(xv[c], 1);
+      put_digits(v, e, ss.out2[op] + boff, BLK);
     }
   }
 }
@@ -262,6 +293,12 @@ template <typename T>
 struct GemmP {
   const uint8_t* As;
   const uint8_t* Bs;
+  // two products into the same accumulators (the two terms of one component
+  // of a complex product): after the KT k steps of As Bs, KT more of
+  // As2 Bs2, negated when neg2 (the operands of both share their row scales)
+  const uint8_t* As2;
+  const uint8_t* Bs2;
+  int pair, neg2;
   const int* ea;
   const int* eb;
   int MT, NT, KT, M, N;
@@ -314,7 +351,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
   fence_after();
   const uint32_t tmem = tslot;
   volatile int* abrt = &abort_flag;
-  const int nchunk = (g.KT + KCT - 1) / KCT;
+  const int KTV = g.pair ? 2 * g.KT : g.KT;   // k steps of a tile (both products of a pair)
+  const int nchunk = (KTV + KCT - 1) / KCT;
   const uint32_t sbase = su32(smem);
 
   if (warp == EPI_WARPS) {
@@ -326,9 +364,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int bl = t / tiles_item, rem = t % tiles_item;
         const int mt = rem % g.MT, nt = rem / g.MT;
-        const uint8_t* a_src = g.As + ((int64_t)(bl * g.a_bl) * g.MT + mt) * g.KT * (int64_t)ASTG;
-        const uint8_t* b_src = g.Bs + ((int64_t)(bl * g.b_bl) * g.NT + nt) * g.KT * (int64_t)BSTG;
-        for (int k = 0; k < g.KT; ++k, ++it) {
+        const int64_t a_off = ((int64_t)(bl * g.a_bl) * g.MT + mt) * g.KT * (int64_t)ASTG;
+        const int64_t b_off = ((int64_t)(bl * g.b_bl) * g.NT + nt) * g.KT * (int64_t)BSTG;
+        for (int vk = 0; vk < KTV; ++vk, ++it) {
+          const bool second = vk >= g.KT;
+          const int k = second ? vk - g.KT : vk;
+          const uint8_t* a_src = (second ? g.As2 : g.As) + a_off;
+          const uint8_t* b_src = (second ? g.Bs2 : g.Bs) + b_off;
           const int s = (int)(it % NST);
           if (it >= NST && !mbar_wait(su32(&empty[s]), (int)((it / NST) & 1) ^ 1, abrt)) {
             ok = false;
@@ -363,13 +405,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
           // the epilogue has read the previous chunk's accumulators
           if (cc > 0 && !mbar_wait(su32(&acc_empty), (int)((cc - 1) & 1), abrt)) { ok = false; break; }
           fence_after();
-          const int kend = min(g.KT, (c + 1) * KCT);
+          const int kend = min(KTV, (c + 1) * KCT);
           const int kbeg = kk;
           for (; kk < kend; ++kk, ++it) {
             const int s = (int)(it % NST);
             if (!mbar_wait(su32(&full[s]), (int)((it / NST) & 1), abrt)) { ok = false; break; }
             fence_after();
             const uint32_t a0 = sbase + s * STAGE, b0 = a0 + ASTG;
+            // the second product of a pair enters negated: negate-B bit of the
+            // instruction descriptor
+            const uint32_t ineg = (g.neg2 && kk >= g.KT) ? (1u << 14) : 0u;
 #pragma unroll
             for (int p = 0; p < DIG; ++p) {
               const uint64_t ad = sdesc(a0 + p * ABLK, 128, 256);
@@ -380,7 +425,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(GemmP<T> g) {
                 // the first k step of a chunk overwrites: p = 0 covers every diagonal once
                 const uint32_t acc = (kk != kbeg || p != 0) ? 1u : 0u;
                 const uint64_t bd = sdesc(b0 + q0 * BBLK, 128, 256);
-                const uint32_t idesc = idesc0 | ((uint32_t)((nq * TN) >> 3) << 17);
+                const uint32_t idesc = idesc0 | ineg | ((uint32_t)((nq * TN) >> 3) << 17);
                 asm volatile(
                     "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)((p + q0) * TN)),
@@ -712,10 +757,12 @@ void launch_mma(const tc::GemmP<T>& p, bool trans, int nb, int M, int N, int K, 
   using f_ = std::false_type;
   if (p.beta == 0.0) { if (trans) go(t_(), t_()); else go(t_(), f_()); }
   else { if (trans) go(f_(), t_()); else go(f_(), f_()); }
-  // executed: bf16 tensor-core flops of the digit products over the padded tiles
+  // executed: bf16 tensor-core flops of the digit products over the padded
+  // tiles; algorithmic: 2 M N K per real product (a pair holds two)
   const double npairs = tc::npairs();
-  const double exec = 2.0 * npairs * (double)p.MT * tc::TM * (double)p.NT * tc::TN * (double)p.KT * tc::TK * nb;
-  if (pf) pf->end(K_GEMM_TC, 2.0 * p.M * (double)p.N * K * nb, st, exec);
+  const double nprod = p.pair ? 2.0 : 1.0;
+  const double exec = 2.0 * npairs * nprod * (double)p.MT * tc::TM * (double)p.NT * tc::TN * (double)p.KT * tc::TK * nb;
+  if (pf) pf->end(K_GEMM_TC, 2.0 * nprod * M * (double)N * K * nb, st, exec);
 }
 
 }  // namespace
@@ -758,77 +805,90 @@ cudaError_t gemm_tc(const GemmArgs<T>& g, cudaStream_t st, Prof* pf) {
   const bool shA = g.batch > 1 && shared_operand(g.A, g.arow, g.acol);
   const bool shB = g.batch > 1 && shared_operand(g.B, g.brow, IMap());
   const bool shSa = tr ? shB : shA, shSb = tr ? shA : shB;   // per slot
-  const size_t a_sz = z.a_item + z.ea_item, b_sz = z.b_item + z.eb_item;
-  const size_t fixed = NP * ((shSa ? a_sz : 0) + (shSb ? b_sz : 0));
-  const size_t per_item = std::max<size_t>(NP * ((shSa ? 0 : a_sz) + (shSb ? 0 : b_sz)), 1);
+  // per item and slot: NP digit arrays and one exponent array (the parts of
+  // a complex row share their scale)
+  const size_t a_sz = NP * z.a_item + z.ea_item, b_sz = NP * z.b_item + z.eb_item;
+  const size_t fixed = (shSa ? a_sz : 0) + (shSb ? b_sz : 0);
+  const size_t per_item = std::max<size_t>((shSa ? 0 : a_sz) + (shSb ? 0 : b_sz), 1);
   // batch items per launch group: their digit slices stay within the cap
   // (small enough and they are still in L2 when the products read them)
   const size_t cap = std::min<size_t>(WS_CAP, (size_t)std::max(lu_tune(TUNE_TC_CHUNK_MB), 1) << 20);
   const size_t room = cap > fixed ? cap - fixed : 0;
-  const int nb_max = (int)std::max<size_t>(1, std::min<size_t>(std::min(g.batch, 65535 / (2 * NP)), room / per_item));
+  const int nb_max = (int)std::max<size_t>(1, std::min<size_t>(std::min(g.batch, 65535 / 2), room / per_item));
   const size_t na = shSa ? 1 : (size_t)nb_max, nbb = shSb ? 1 : (size_t)nb_max;
-  cudaError_t e = ensure_ws(w, NP * (a_sz * na + b_sz * nbb), st);
+  cudaError_t e = ensure_ws(w, a_sz * na + b_sz * nbb, st);
   if (e != cudaSuccess) return e;
   uint8_t* base = static_cast<uint8_t*>(w->p);
-  uint8_t* As[2];   // digits of the A slot, per real part
-  uint8_t* Bs[2];
-  int* ea[2];
-  int* eb[2];
+  uint8_t* As[2] = {nullptr, nullptr};   // digits of the A slot, per real part
+  uint8_t* Bs[2] = {nullptr, nullptr};
+  int* ea;
+  int* eb;
   {
     uint8_t* q = base;
     for (int pt = 0; pt < NP; ++pt) {
       As[pt] = q; q += z.a_item * na;
       Bs[pt] = q; q += z.b_item * nbb;
     }
-    for (int pt = 0; pt < NP; ++pt) {
-      ea[pt] = reinterpret_cast<int*>(q); q += z.ea_item * na;
-      eb[pt] = reinterpret_cast<int*>(q); q += z.eb_item * nbb;
-    }
+    ea = reinterpret_cast<int*>(q); q += z.ea_item * na;
+    eb = reinterpret_cast<int*>(q); q += z.eb_item * nbb;
   }
-  const int lsb = 62 - ceil_log2(std::max(g.K, 1));
+  // fixed-point fraction bits: a complex component sums 2K products
+  const int lsb = 62 - ceil_log2(std::max(NP * g.K, 1));
   double alpha, beta;
   if constexpr (NP == 2) { alpha = g.alpha.re; beta = g.beta.re; }
   else { alpha = g.alpha; beta = g.beta; }
   for (int b0 = 0; b0 < g.batch; b0 += nb_max) {
     const int nb = std::min(nb_max, g.batch - b0);
     SplitSet<T> ss;
-    int nops = 0;
-    for (int pt = 0; pt < NP; ++pt) {
-      // A (M x K) and B^T (N x K) as row sources
-      Src<T> sa;
-      sa.X = g.A; sa.rmap = g.arow; sa.kmap = g.acol; sa.rs = 1; sa.ks = g.A.ld; sa.part = pt;
-      Src<T> sb;
-      sb.X = g.B; sb.kmap = g.brow; sb.rs = g.B.ld; sb.ks = 1; sb.part = pt;
-      ss.s[nops] = tr ? sb : sa; ss.R[nops] = Ma; ss.TR[nops] = TM; ss.RT[nops] = z.MT; ss.out[nops] = As[pt];
-      ss.ex[nops] = ea[pt];
-      ss.items[nops] = (shSa && b0 > 0) ? 0 : (shSa ? 1 : nb);  // a shared operand is cut once per call
-      ++nops;
-      ss.s[nops] = tr ? sa : sb; ss.R[nops] = Nb; ss.TR[nops] = TN; ss.RT[nops] = z.NT; ss.out[nops] = Bs[pt];
-      ss.ex[nops] = eb[pt];
-      ss.items[nops] = (shSb && b0 > 0) ? 0 : (shSb ? 1 : nb);
-      ++nops;
-    }
-    launch_split<T>(ss, nops, g.K, z.KT, b0, nb, st, pf);
+    // A (M x K) and B^T (N x K) as row sources
+    Src<T> sa;
+    sa.X = g.A; sa.rmap = g.arow; sa.kmap = g.acol; sa.rs = 1; sa.ks = g.A.ld;
+    Src<T> sb;
+    sb.X = g.B; sb.kmap = g.brow; sb.rs = g.B.ld; sb.ks = 1;
+    ss.s[0] = tr ? sb : sa; ss.R[0] = Ma; ss.TR[0] = TM; ss.RT[0] = z.MT;
+    ss.out[0] = As[0]; ss.out2[0] = As[1]; ss.ex[0] = ea;
+    ss.items[0] = (shSa && b0 > 0) ? 0 : (shSa ? 1 : nb);  // a shared operand is cut once per call
+    ss.s[1] = tr ? sa : sb; ss.R[1] = Nb; ss.TR[1] = TN; ss.RT[1] = z.NT;
+    ss.out[1] = Bs[0]; ss.out2[1] = Bs[1]; ss.ex[1] = eb;
+    ss.items[1] = (shSb && b0 > 0) ? 0 : (shSb ? 1 : nb);
+    launch_split<T>(ss, 2, g.K, z.KT, b0, nb, st, pf);
     GemmP<T> p;
     p.MT = z.MT; p.NT = z.NT; p.KT = z.KT; p.M = Ma; p.N = Nb; p.lsb = lsb;
     p.C = g.C; p.crow = g.crow; p.b0 = b0; p.err = *w->err_slot;
     p.a_bl = shSa ? 0 : 1;
     p.b_bl = shSb ? 0 : 1;
     p.nitems = nb;
-    // real: C = alpha A B + beta C; complex (real alpha, beta):
-    //   C.re = alpha (Ar Br - Ai Bi) + beta C.re,  C.im = alpha (Ar Bi + Ai Br) + beta C.im
-    // (transposed, the A slot holds B's parts and the B slot A's)
-    const int npr = NP == 2 ? 4 : 1;
-    for (int k = 0; k < npr; ++k) {
-      static const int pa[4] = {0, 1, 0, 1}, pb[4] = {0, 1, 1, 0}, pc[4] = {0, 0, 1, 1};
-      const int sa_part = tr ? pb[k] : pa[k], sb_part = tr ? pa[k] : pb[k];
-      p.As = As[sa_part]; p.ea = ea[sa_part];
-      p.Bs = Bs[sb_part]; p.eb = eb[sb_part];
-      p.cpart = pc[k];
-      p.alpha = (k == 1) ? -alpha : alpha;
-      p.beta = (k == 1 || k == 3) ? 1.0 : beta;
-      p.amode = (p.alpha == 1.0 || p.alpha == -1.0) ? 1 : 0;
-      p.asign = p.alpha == -1.0 ? (long long)(1ull << 63) : 0ll;
+    p.ea = ea; p.eb = eb;
+    p.alpha = alpha;
+    p.beta = beta;
+    p.amode = (alpha == 1.0 || alpha == -1.0) ? 1 : 0;
+    p.asign = alpha == -1.0 ? (long long)(1ull << 63) : 0ll;
+    if constexpr (NP == 1) {
+      p.As = As[0]; p.Bs = Bs[0];
+      p.As2 = nullptr; p.Bs2 = nullptr; p.pair = 0; p.neg2 = 0;
+      p.cpart = 0;
+      launch_mma<T>(p, tr, nb, g.M, g.N, g.K, st, pf);
+    } else {
+      // complex (real alpha, beta), each component one launch of two
+      // products into the same accumulators:
+      //   C.re = alpha (Ar Br - Ai Bi) + beta C.re,  C.im = alpha (Ar Bi + Ai Br) + beta C.im
+      // (transposed, the A slot holds B's parts and the B slot A's)
+      uint8_t* const* Ap = tr ? Bs : As;   // digits of A's parts
+      uint8_t* const* Bp = tr ? As : Bs;   // digits of B's parts
+      auto slots = [&](int a_part, int b_part, const uint8_t*& sa_d, const uint8_t*& sb_d) {
+        sa_d = tr ? Bp[b_part] : Ap[a_part];
+        sb_d = tr ? Ap[a_part] : Bp[b_part];
+      };
+      p.pair = 1;
+      slots(0, 0, p.As, p.Bs);
+      slots(1, 1, p.As2, p.Bs2);
+      p.neg2 = 1;
+      p.cpart = 0;
+      launch_mma<T>(p, tr, nb, g.M, g.N, g.K, st, pf);
+      slots(0, 1, p.As, p.Bs);
+      slots(1, 0, p.As2, p.Bs2);
+      p.neg2 = 0;
+      p.cpart = 1;
       launch_mma<T>(p, tr, nb, g.M, g.N, g.K, st, pf);
     }
   }

@@ -96,6 +96,16 @@ bool grow_dev(DevBuf& b, size_t bytes, cudaStream_t st) {
     b.p = nullptr;
     return false;
   }
+  // A stream-ordered allocation is mapped when its stream reaches it; until
+  // then a pointer query (the solve entry points' device-pointer check) may
+  // not recognise it.  The stream is idle here (it is the free stream a
+  // dispatch picked), so waiting for it costs next to nothing.
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    hps::dev_free(b.p, st);
+    b.p = nullptr;
+    return false;
+  }
   b.cap = bytes;
   return true;
 }

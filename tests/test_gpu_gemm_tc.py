@@ -142,9 +142,12 @@ def test_wide_dynamic_range_and_zero_rows(P):
 @pytest.mark.parametrize("m,n,k,batch", [(130, 60, 470, 2), (200, 60, 300, 2), (32, 114, 32, 400)],
                          ids=["ragged", "normal", "transposed"])
 def test_complex_product(P, m, n, k, batch):
-    """Complex products run as four real digit-slice products, one pair per
-    component of C: Re = Ar Br - Ai Bi, Im = Ar Bi + Ai Br (in the transposed
-    tiling the A slot holds B's parts and the B slot A's)."""
+    """Complex products run as one launch per component of C, two real
+    digit-slice products into shared accumulators: Re = Ar Br - Ai Bi, Im =
+    Ar Bi + Ai Br (in the transposed tiling the A slot holds B's parts and the
+    B slot A's).  The parts of a row of A (column of B) share one scale, so
+    each component is the real product [Ar Ai] [Br; -Bi] (resp. [Bi; Br]) of
+    inner dimension 2K, and the bound is that product's."""
     rng = np.random.default_rng(3 + m)
     z = lambda s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
     A, B, C0 = z((batch, m, k)), z((batch, k, n)), z((batch, m, n))
@@ -154,8 +157,9 @@ def test_complex_product(P, m, n, k, batch):
         C = _run(P, A, B, C0, alpha, beta, 0)
         ref = alpha * np.matmul(A, B) + beta * C0
         slack = (2 * k + 8) * 2.0 ** -53 * 2 * (mag + np.abs(C0)) + 2.0 ** -51 * np.abs(ref)
-        tol_re = _bound(Ar, Br, k) + _bound(Ai, Bi, k) + slack
-        tol_im = _bound(Ar, Bi, k) + _bound(Ai, Br, k) + slack
+        Acat = np.concatenate([Ar, Ai], axis=2)
+        tol_re = _bound(Acat, np.concatenate([Br, -Bi], axis=1), 2 * k) + slack
+        tol_im = _bound(Acat, np.concatenate([Bi, Br], axis=1), 2 * k) + slack
         assert np.all(np.abs(C.real - ref.real) <= tol_re)
         assert np.all(np.abs(C.imag - ref.imag) <= tol_im)
 
