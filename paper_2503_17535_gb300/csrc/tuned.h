@@ -2,7 +2,7 @@
 // GB300 (hps_tune_set in include/hps.h).  Written by
 // paper_2503_17535_gb300/autotune.py from timed builds of the benchmark
 // workloads (summed median build time, ms, at the chosen values:
-// {"helmholtz2d_iti_p16_depth6": 194.63, "elliptic3d_dtn_p8_depth3": 151.56, "adaptive3d_dtn_p8": 123.39}); rerun it to regenerate.
+// {"helmholtz2d_iti_p16_depth6": 174.7, "elliptic3d_dtn_p8_depth3": 151.36, "adaptive3d_dtn_p8": 123.62}); rerun it to regenerate.
 #pragma once
 
 #define HPS_TUNED_LU_CLUSTER_PANEL 1
@@ -10,7 +10,7 @@
 #define HPS_TUNED_LU_FEW_MIN_N 4096
 #define HPS_TUNED_LU_BASE_PANELS_MANY 8
 #define HPS_TUNED_TC_MIN_WORK_REAL 50
-#define HPS_TUNED_TC_MIN_WORK_CPLX 100
+#define HPS_TUNED_TC_MIN_WORK_CPLX 50
 #define HPS_TUNED_TC_MIN_K 16
 #define HPS_TUNED_TC_CHUNK_MB 1024
 #define HPS_TUNED_TC_PERSIST_MIN_K 0
