@@ -89,9 +89,9 @@ TC_DIGIT_PRODUCTS = 55
 # under profiles/); None where no capture of the current kernels exists
 NCU_TRAFFIC = {
     ("helmholtz2d_iti_c128_depth6_p16", "gemm_tc"): {
-        "bytes_per_launch": 112531000,
-        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the 1236 k_gemm_tc launches of one "
-                  "build (139.1 GB), profiles/k_gemm_tc_traffic_helmholtz2d_depth6.md"},
+        "bytes_per_launch": 182930000,
+        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the 581 k_gemm_tc launches of one "
+                  "build (106.3 GB), profiles/k_gemm_tc_traffic_helmholtz2d_depth6.md"},
 }
 
 COMMON = {"seed_solve_source": 11, "root_map": False, "step": "hps_build + hps_solve(new f) + hps_free",
