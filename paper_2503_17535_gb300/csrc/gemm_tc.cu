@@ -665,6 +665,9 @@ static double tile_fill(int M, int N) {
   return mn / std::min(normal, trans);
 }
 
+// At most 8 rows against many columns and a long inner dimension.
+static bool few_rows_long_k(int M, int N, int K) { return M <= 8 && N >= 32 && K >= 32; }
+
 template <typename T>
 bool tc_applicable(const GemmArgs<T>& g) {
   const TcWorkspace* w = tc_workspace();
@@ -672,11 +675,15 @@ bool tc_applicable(const GemmArgs<T>& g) {
   if (w->force) return true;
   // one side of at least 32 and the other of at least 16: the short side
   // goes to the 48-wide tile dimension (transposed tiling when M is short)
-  if (std::min(g.M, g.N) < 16 || std::max(g.M, g.N) < 32 || g.K < 16) return false;
+  if (std::min(g.M, g.N) < 1 || std::max(g.M, g.N) < 32 || g.K < 16) return false;
+  if (std::min(g.M, g.N) < 16 && !few_rows_long_k(g.M, g.N, g.K)) return false;
   // a side below 32 fills at best two thirds of the 48-wide tile side: such
   // products go to the tensor cores only while the tiles stay over ~28 % full
-  // (measured: 28 x 113 gains there, 28 x 57 loses)
-  if (std::min(g.M, g.N) < 32 && tile_fill(g.M, g.N) < 0.28) return false;
+  // (measured: 28 x 113 gains there, 28 x 57 loses) -- except products of
+  // at most 8 rows, N >= 32 and K >= 32, which the FP64-pipe kernels run at
+  // under half their rate (4 x 114 x 64: 0.14 TFLOP/s); few columns stay on
+  // the FP64 pipe's skinny kernels
+  if (std::min(g.M, g.N) < 32 && tile_fill(g.M, g.N) < 0.28 && !few_rows_long_k(g.M, g.N, g.K)) return false;
   // short inner dimensions: ten accumulators per output are read back for
   // little work, so small items stay on the FP64 pipe
   if (g.K < lu_tune(TUNE_TC_MIN_K) && (g.M < 512 || g.N < 512)) return false;
@@ -690,8 +697,9 @@ bool tc_applicable<cplx>(const GemmArgs<cplx>& g) {
   if (!w || !w->enabled || !w->err_slot || !*w->err_slot || g.ta || g.K > (1 << 20)) return false;
   if (g.alpha.im != 0.0 || g.beta.im != 0.0) return false;
   if (w->force) return true;
-  if (std::min(g.M, g.N) < 16 || std::max(g.M, g.N) < 32 || g.K < 16) return false;
-  if (std::min(g.M, g.N) < 32 && tile_fill(g.M, g.N) < 0.28) return false;
+  if (std::min(g.M, g.N) < 1 || std::max(g.M, g.N) < 32 || g.K < 16) return false;
+  if (std::min(g.M, g.N) < 16 && !few_rows_long_k(g.M, g.N, g.K)) return false;
+  if (std::min(g.M, g.N) < 32 && tile_fill(g.M, g.N) < 0.28 && !few_rows_long_k(g.M, g.N, g.K)) return false;
   if (g.K < lu_tune(TUNE_TC_MIN_K) && (g.M < 512 || g.N < 512)) return false;
   if ((double)g.M * g.N * g.K * g.batch < 1.0e5 * lu_tune(TUNE_TC_MIN_WORK_CPLX)) return false;
   return true;
