@@ -371,13 +371,16 @@ hps_status hps_getrf(int dtype, int mode, int n, int batch, void* A, int lda, in
  *   HPS_TUNE_TC_PERSIST_MIN_K    (8): tensor-core products with an inner
  *       dimension of at least this run one CTA per SM that walks its tiles
  *       (copies and products of the next tile overlap the epilogue of the
- *       last), shorter ones one CTA per tile.
+ *       last), shorter ones one CTA per tile;
+ *   HPS_TUNE_LU_PANEL_NB_FEW     (9): panel width (8 .. 32 columns; complex
+ *       panels at most 16) of the LU of batches of fewer than 8 matrices.
  * Every choice gives the same pivots and results up to rounding.  Not to be
  * changed while a build runs.  HPS_ERR_INVALID for an unknown parameter or a
  * value outside 0 .. 2^20. */
 enum { HPS_TUNE_LU_BASE_PANELS_FEW = 0, HPS_TUNE_LU_BASE_PANELS_MANY = 1, HPS_TUNE_LU_FEW_MIN_N = 2,
        HPS_TUNE_LU_CLUSTER_PANEL = 3, HPS_TUNE_TC_MIN_WORK_REAL = 4, HPS_TUNE_TC_MIN_WORK_CPLX = 5,
-       HPS_TUNE_TC_MIN_K = 6, HPS_TUNE_TC_CHUNK_MB = 7, HPS_TUNE_TC_PERSIST_MIN_K = 8 };
+       HPS_TUNE_TC_MIN_K = 6, HPS_TUNE_TC_CHUNK_MB = 7, HPS_TUNE_TC_PERSIST_MIN_K = 8,
+       HPS_TUNE_LU_PANEL_NB_FEW = 9 };
 hps_status hps_tune_set(int param, int value);
 hps_status hps_tune_get(int param, int* value);
 

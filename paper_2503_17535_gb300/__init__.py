@@ -582,7 +582,7 @@ def hps_debug_wait_timeout(which: int, satisfied: bool, limit_polls: int, stream
 
 TUNE_PARAMS = {"lu_base_panels_few": 0, "lu_base_panels_many": 1, "lu_few_min_n": 2, "lu_cluster_panel": 3,
                "tc_min_work_real": 4, "tc_min_work_cplx": 5, "tc_min_k": 6,
-               "tc_chunk_mb": 7, "tc_persist_min_k": 8}
+               "tc_chunk_mb": 7, "tc_persist_min_k": 8, "lu_panel_nb_few": 9}
 
 
 def hps_tune_set(name: str, value: int) -> None:

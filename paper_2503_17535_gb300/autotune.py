@@ -38,6 +38,7 @@ CANDIDATES = {
     "tc_min_k": [16, 33, 48, 64, 96],
     "tc_chunk_mb": [16, 32, 64, 128, 1024],
     "tc_persist_min_k": [0, 48, 64, 128, 1 << 20],
+    "lu_panel_nb_few": [16, 32],
 }
 MACROS = {
     "lu_base_panels_few": "HPS_TUNED_LU_BASE_PANELS_FEW",
@@ -49,6 +50,7 @@ MACROS = {
     "tc_min_k": "HPS_TUNED_TC_MIN_K",
     "tc_chunk_mb": "HPS_TUNED_TC_CHUNK_MB",
     "tc_persist_min_k": "HPS_TUNED_TC_PERSIST_MIN_K",
+    "lu_panel_nb_few": "HPS_TUNED_LU_PANEL_NB_FEW",
 }
 
 

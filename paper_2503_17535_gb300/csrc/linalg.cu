@@ -1133,7 +1133,7 @@ int& lu_tune(int param) {
                               HPS_TUNED_LU_FEW_MIN_N,       HPS_TUNED_LU_CLUSTER_PANEL,
                               HPS_TUNED_TC_MIN_WORK_REAL,   HPS_TUNED_TC_MIN_WORK_CPLX,
                               HPS_TUNED_TC_MIN_K,           HPS_TUNED_TC_CHUNK_MB,
-                              HPS_TUNED_TC_PERSIST_MIN_K};
+                              HPS_TUNED_TC_PERSIST_MIN_K,   HPS_TUNED_LU_PANEL_NB_FEW};
   return v[param];
 }
 
@@ -1279,9 +1279,8 @@ static cudaError_t rtrsm_lower(BOp<T> LU, BOp<T> X, int p0, int n1, int nrhs, in
 // order; the bulk of the trailing updates becomes a few large-K products
 // (on the tensor cores) instead of n / nb products of inner dimension nb.
 template <typename T>
-static cudaError_t rgetrf(BOp<T> A, int n, int c0, int c1, int base_w, int batch, int* ipiv, int* info,
+static cudaError_t rgetrf(BOp<T> A, int n, int c0, int c1, int base_w, int nb0, int batch, int* ipiv, int* info,
                           unsigned* dev_err, int G, const LuWork& w, cudaStream_t st, Prof* pf) {
-  const int nb0 = LuNB<T>::NB;
   const int wdt = c1 - c0;
   cudaError_t e;
   if (wdt <= base_w) {
@@ -1302,7 +1301,7 @@ static cudaError_t rgetrf(BOp<T> A, int n, int c0, int c1, int base_w, int batch
     return cudaSuccess;
   }
   const int cm = c0 + ((wdt / 2 + nb0 - 1) / nb0) * nb0;
-  if ((e = rgetrf<T>(A, n, c0, cm, base_w, batch, ipiv, info, dev_err, G, w, st, pf)) != cudaSuccess) return e;
+  if ((e = rgetrf<T>(A, n, c0, cm, base_w, nb0, batch, ipiv, info, dev_err, G, w, st, pf)) != cudaSuccess) return e;
   // U12: rows [c0, cm), columns [cm, c1)
   BOp<T> L11 = shifted(A, (int64_t)c0 + (int64_t)c0 * A.ld);
   BOp<T> A12 = shifted(A, (int64_t)c0 + (int64_t)cm * A.ld);
@@ -1316,7 +1315,7 @@ static cudaError_t rgetrf(BOp<T> A, int n, int c0, int c1, int base_w, int batch
     g.alpha = T(-1.0); g.beta = T(1.0);
     if ((e = gemm(g, st, pf)) != cudaSuccess) return e;
   }
-  return rgetrf<T>(A, n, cm, c1, base_w, batch, ipiv, info, dev_err, G, w, st, pf);
+  return rgetrf<T>(A, n, cm, c1, base_w, nb0, batch, ipiv, info, dev_err, G, w, st, pf);
 }
 
 template <typename T>
@@ -1330,12 +1329,17 @@ cudaError_t getrf(BOp<T> A, int n, int batch, int* ipiv, int* perm, int* info, u
   // so that the trailing updates are a few large-K products.
   const int nbp = LuNB<T>::NB;
   int base_w = lu_tune(TUNE_LU_BASE_PANELS_MANY) * nbp;
+  // panel width: the kernels' maximum, or narrower for few matrices (the
+  // panel's FP64 update, ~n^2 nb / 2 multiply-adds on the few SMs of a
+  // cluster, against twice the panels and trailing updates of half the K)
+  int pnb = nbp;
   if (batch < 8) {
     const int bp = lu_tune(TUNE_LU_BASE_PANELS_FEW);
     base_w = (bp <= 0 || n < lu_tune(TUNE_LU_FEW_MIN_N)) ? n : bp * nbp;
+    pnb = std::max(8, std::min(nbp, lu_tune(TUNE_LU_PANEL_NB_FEW) / 8 * 8));
   }
   if (base_w < nbp) base_w = nbp;
-  if ((e = rgetrf<T>(A, n, 0, n, base_w, batch, ipiv, info, dev_err, G, w, st, pf)) != cudaSuccess) return e;
+  if ((e = rgetrf<T>(A, n, 0, n, base_w, pnb, batch, ipiv, info, dev_err, G, w, st, pf)) != cudaSuccess) return e;
   if (pf) pf->begin(st);
   k_ipiv_to_perm<<<(batch + 127) / 128, 128, 0, st>>>(ipiv, perm, n, batch);
   if (pf) pf->end(K_OTHER, 0.0, st);

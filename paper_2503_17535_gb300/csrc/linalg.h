@@ -150,7 +150,8 @@ enum LuTuneParam {
   TUNE_TC_MIN_K = 6,             // products with K below this stay on the FP64 pipe unless M, N >= 512
   TUNE_TC_CHUNK_MB = 7,          // digit slices of one launch group of a batched product, MiB
   TUNE_TC_PERSIST_MIN_K = 8,     // tensor-core products with K at least this walk their tiles persistently
-  TUNE_COUNT = 9
+  TUNE_LU_PANEL_NB_FEW = 9,      // panel width of the LU of batches of fewer than 8 matrices (8 .. 32)
+  TUNE_COUNT = 10
 };
 int& lu_tune(int param);
 

@@ -112,6 +112,15 @@ def test_root_sized_lu_matches_lapack(P, n, cplx):
     check(P, A, 0, n_floor=1)
 
 
+def test_narrow_panels_for_few_matrices_match_lapack(tune):
+    """The tuned panel width of few-matrix batches (16 instead of 32 for real
+    data): the same interchanges and factors."""
+    P = tune
+    P.hps_tune_set("lu_panel_nb_few", 16)
+    A = random_batch(3456, 1, False, seed=17)
+    check(P, A, 0, n_floor=1)
+
+
 def test_cooperative_panel_matches_lapack(tune):
     """The same results with the thread-block-cluster panel switched off."""
     P = tune
