@@ -28,13 +28,15 @@
 // tensor core's canonical no-swizzle layout (8-row x 16-byte core matrices;
 // a 16-deep k step of a 128-row A tile is one 4 KB block per digit, of a
 // 48-column B tile one 1.5 KB block), so that one k step of all digits is one
-// contiguous bulk copy (cp.async.bulk) per operand.  The GEMM kernel runs one
-// 128 x 48 output tile per CTA: a producer warp streams the digit blocks
-// through a 3-stage shared-memory ring, one thread issues the products as
-// 15 MMAs per k step (digits of B stacked along N, up to 5 per MMA, land in
-// adjacent diagonal accumulators), ten TMEM accumulators take 480 of the 512
-// columns, and eight epilogue warps (two per TMEM lane quarter, one per half
-// of the columns) read them back while the C tile waits in shared memory.
+// contiguous bulk copy (cp.async.bulk) per operand.  The GEMM kernel computes
+// 128 x 48 output tiles, one CTA per SM walking the launch's tiles: a
+// producer warp streams the digit blocks through a 3-stage shared-memory
+// ring, one thread issues the products as 15 MMAs per k step (digits of B
+// stacked along N, up to 5 per MMA, land in adjacent diagonal accumulators),
+// ten TMEM accumulators take 480 of the 512 columns, and eight epilogue
+// warps (two per TMEM lane quarter, one per half of the columns) read them
+// back while the next tile's copies and products proceed.  A product with
+// few rows may run transposed (C^T = B^T A^T, C's rows on the 48-wide side).
 //
 // Complex products are two launches, one per component of C, each
 // accumulating two real products in the same TMEM accumulators

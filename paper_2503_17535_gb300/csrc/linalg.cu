@@ -1,12 +1,16 @@
 // Batched FP64 / complex128 dense kernels: gathered GEMM, panel LU with
-// partial pivoting (one CTA or a cooperative group of CTAs per matrix), row
-// interchanges + triangular update, and blocked triangular solves.
+// partial pivoting (one CTA per matrix, a thread-block cluster per matrix,
+// or a cooperative group of CTAs per matrix), row interchanges + triangular
+// update, recursive LU and triangular solves, and flag-ordered solves of a
+// single large factor.
 //
 // GB300 has about 1 TFLOP/s of FP64 (2 DFMA per clock per SM), so every
 // kernel here is bound by the FP64 pipe long before HBM or shared memory:
 // the designs aim at keeping all 152 SMs issuing FMAs (enough CTAs per level,
-// cooperative groups for single large matrices) and at spending no FP64
-// instruction that is not part of the algorithm.
+// clusters or cooperative groups for single large matrices), at spending no
+// FP64 instruction that is not part of the algorithm, and at keeping FP64
+// latency chains (a reciprocal, a serial load) off the per-column critical
+// path of the panels.
 #include "linalg.h"
 
 #include <cooperative_groups.h>
